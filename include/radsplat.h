@@ -1,0 +1,294 @@
+/*
+ * radsplat.h -- C ABI of the GB300 (sm_103a) tile-based Gaussian-splatting hot path
+ * of RadSplat (arXiv 2403.13806).
+ *
+ * The library renders a set of 3D Gaussians (Sec. 3.2 "Gaussian Splatting") into one
+ * or many views, scores every Gaussian by its largest ray contribution alpha*T
+ * (Eq. importance-score, Sec. 3.3), turns those scores into pruning / visibility
+ * masks (Sec. 3.3 "Pruning", Eq. importance-score-vis), picks the nearest camera
+ * cluster for a test view (Sec. 3.4 "Visibility List-Based Rendering"), and
+ * differentiates the rendered images for optimisation (Sec. 3.2 "Radiance
+ * Field-based Supervision").
+ *
+ * Conventions shared by every entry point
+ *   - Ownership: the caller owns every buffer.  Device pointers point to device
+ *     memory (e.g. PyTorch tensors); host pointers are marked HOST.  No entry point
+ *     allocates device memory; temporary storage is the caller's workspace, sized by
+ *     rs_workspace_size().  Inputs are const and never written.  Outputs are written
+ *     and not read, except the accumulators named below (importance, gradients),
+ *     which the caller zeroes once and which calls then accumulate into.
+ *   - Streams: every call enqueues work on `stream` and returns without waiting for
+ *     the device (no host synchronisation), so a whole pipeline can be captured in a
+ *     CUDA graph.  `stream` is a cudaStream_t passed as void*; NULL is the legacy
+ *     default stream.
+ *   - Errors: the return value reports argument, workspace and launch errors at call
+ *     time.  Conditions only the device can see (instance capacity overflow, a
+ *     bounded wait that gave up, culled non-finite inputs) are written to the
+ *     caller's rs_device_status block, which the caller reads after synchronising.
+ *     Kernels never trap: on overflow they clamp their writes and record the status.
+ *   - Layouts: parameters are FP32 structure-of-arrays; images are planar
+ *     [3][H][W] FP32 per view; world-to-camera matrices are row-major 3x4 with
+ *     OpenCV axes (x right, y down, z forward); pixel (u, v) samples image point (u, v).
+ *   - Alignment: every float4-typed array (documented as [n][4]) must be 16-byte
+ *     aligned, every [n][2] float array 8-byte aligned; PyTorch allocations satisfy this.
+ */
+#ifndef RADSPLAT_H
+#define RADSPLAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RS_ABI_VERSION 1
+
+typedef enum rs_status {
+  RS_OK = 0,
+  RS_ERR_INVALID_ARG = 1,  /* a pointer, size or option is out of range */
+  RS_ERR_WORKSPACE = 2,    /* ws_bytes below rs_workspace_size() */
+  RS_ERR_UNSUPPORTED = 3,  /* e.g. sh_degree > 3, tile shape not in the supported set */
+  RS_ERR_CUDA = 4,         /* a CUDA launch or runtime call failed */
+  RS_ERR_CAPACITY = 5,     /* device-reported: more (tile, Gaussian) instances than capacity */
+  RS_ERR_TIMEOUT = 6       /* device-reported: a bounded wait gave up */
+} rs_status;
+
+/* Device-side status block (device memory, caller-owned, zeroed by the caller before
+ * the first call of a sequence).  Fields only ever grow; `code` keeps the first error. */
+typedef struct rs_device_status {
+  int32_t code;          /* RS_OK, RS_ERR_CAPACITY or RS_ERR_TIMEOUT */
+  int32_t nonfinite;     /* projected items culled for non-finite parameters */
+  int64_t required;      /* largest instance count any rs_bin_sort needed */
+  int64_t n_instances;   /* instances the last rs_bin_sort produced (<= capacity) */
+  int64_t reserved;
+} rs_device_status;
+
+/* Gaussian parameters, Sec. 3.2: position p, scale s (stored as log s), rotation q
+ * (w, x, y, z; normalised inside the library), opacity o (stored as the logit of o),
+ * SH coefficients k of degree sh_degree <= 3.  All device, FP32, SoA:
+ *   means[3][n], log_scales[3][n], quats[4][n], opacity_logit[n],
+ *   sh[(sh_degree+1)^2 * 3][n]  with row = coefficient * 3 + channel. */
+typedef struct rs_gaussians {
+  const float* means;
+  const float* log_scales;
+  const float* quats;
+  const float* opacity_logit;
+  const float* sh;
+  int64_t n;
+  int32_t sh_degree;
+  int32_t reserved;
+} rs_gaussians;
+
+/* Pinhole camera (HOST struct): world-to-camera [R|t] (row-major 3x4) and intrinsics. */
+typedef struct rs_camera {
+  float viewmat[12];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+} rs_camera;
+
+/* Per-view descriptor as the kernels read it (128 bytes).  rs_views_prepare() fills
+ * an array of these on the host; the caller copies it to device memory and passes
+ * that copy in rs_view_batch.views. */
+typedef struct rs_view {
+  float viewmat[12];     /* world -> camera */
+  float fx, fy, cx, cy;
+  float campos[3];       /* camera centre -R^T t in world space */
+  float lim_x, lim_y;    /* 1.3 * (W/2)/fx, 1.3 * (H/2)/fy: clamp of x/z, y/z inside J */
+  int32_t width, height;
+  int32_t tiles_x, tiles_y;
+  int32_t tile_base;     /* first global tile id of the view */
+  int64_t pixel_base;    /* first pixel of the view in the T_final / last buffers */
+  int64_t item_base;     /* first projected item of the view */
+  int64_t n_items;       /* projected items of the view */
+} rs_view;
+
+/* A batch of views rendered together.  Items are (view, Gaussian) pairs: view v owns
+ * items [item_base, item_base + n_items).  If subset_idx is NULL, item i of view v is
+ * Gaussian (i - item_base) and n_items equals the number of Gaussians; otherwise it is
+ * Gaussian subset_idx[i] (a visibility list, Sec. 3.4; ascending within each view). */
+typedef struct rs_view_batch {
+  const rs_view* views;        /* DEVICE [n_views] */
+  const uint32_t* subset_idx;  /* DEVICE [n_items] or NULL */
+  int32_t n_views;
+  int32_t n_tiles;             /* total tiles over all views */
+  int64_t n_items;             /* total items */
+  int64_t n_pixels;            /* total pixels (sum of W*H) */
+  int32_t tile_w, tile_h;      /* tile shape: 16x16, 32x8 or 8x8 */
+} rs_view_batch;
+
+/* Rasterizer options.  rs_config_default() gives the readings the library uses for
+ * what the paper leaves to the 3DGS renderer it cites (Sec. 3.2, Sec. 3.4). */
+typedef struct rs_config {
+  float eps2d;           /* dilation added to the diagonal of Sigma' (px^2), default 0.3 */
+  float near_plane;      /* cull if the FP32 camera depth <= near_plane, default 0.2 */
+  float bg[3];           /* background colour composited with T_final, default 0 */
+  int32_t batch;         /* Gaussians staged in shared memory per step of the blend (0: auto) */
+  int32_t reserved[2];
+} rs_config;
+
+/* Projected items (all device, [n_items] rows):
+ *   xy[n][2]       image-space mean
+ *   conic_o[n][4]  (a, b, c, o): inverse of Sigma' = [[a, b], [b, c]] and the opacity
+ *   rgb_d[n][4]    (r, g, b, depth): SH colour and the FP32 front-to-back order key
+ *   rect[n][4]     uint16 tiles (x0, y0, x1, y1), half-open, covering every pixel whose
+ *                  alpha can reach 1/255; all zero for a culled item
+ *   n_tiles[n]     (x1-x0)*(y1-y0), 0 for a culled item */
+typedef struct rs_projected {
+  float* xy;
+  float* conic_o;
+  float* rgb_d;
+  uint16_t* rect;
+  uint32_t* n_tiles;
+} rs_projected;
+
+/* Tile lists.  After rs_bin_sort, vals[ranges[2t] .. ranges[2t+1]) are the items that
+ * touch global tile t, front to back (by the FP32 depth key, ties to the lower item).
+ * keys (optional, may be NULL) receive the 64-bit sort keys (tile << 32 | depth bits)
+ * in the same order.  The instance count is written to the device status block. */
+typedef struct rs_bins {
+  uint64_t* keys;        /* DEVICE [capacity] or NULL */
+  uint32_t* vals;        /* DEVICE [capacity] */
+  uint32_t* ranges;      /* DEVICE [n_tiles][2] */
+  int64_t capacity;      /* rows of keys/vals, < 2^32 */
+} rs_bins;
+
+/* Gradient accumulators (device, FP32, same layouts as rs_gaussians; accumulated). */
+typedef struct rs_gaussian_grads {
+  float* means;
+  float* log_scales;
+  float* quats;
+  float* opacity_logit;
+  float* sh;
+} rs_gaussian_grads;
+
+typedef enum rs_filter_mode {
+  RS_PRUNE_BELOW = 0,    /* mask = h < t: points the pruning step removes (Sec. 3.3) */
+  RS_KEEP_ABOVE = 1      /* mask = h > t: points active for a cluster (Eq. importance-score-vis) */
+} rs_filter_mode;
+
+typedef enum rs_stage {
+  RS_STAGE_PROJECT = 0,
+  RS_STAGE_BIN_SORT = 1,
+  RS_STAGE_RENDER = 2,
+  RS_STAGE_BACKWARD = 3,
+  RS_STAGE_FILTER = 4
+} rs_stage;
+
+/* ---- host helpers (no device work) ---------------------------------------------- */
+
+/* Library ABI version (RS_ABI_VERSION). */
+int32_t rs_abi_version(void);
+
+/* Human-readable name of a status code (static string). */
+const char* rs_status_str(rs_status s);
+
+/* Default options: eps2d 0.3, near 0.2, bg 0, batch 0 (auto). */
+rs_config rs_config_default(void);
+
+/* Fill n_views descriptors (HOST out_views[n_views]) from HOST cameras and per-view item
+ * counts (HOST n_items[n_views]), and the sizes of `batch` (views and subset_idx are left
+ * for the caller to set).  Tile shape must be 16x16, 32x8 or 8x8.
+ * Errors: RS_ERR_INVALID_ARG (null pointer, empty or oversized view, total tiles >= 2^31),
+ * RS_ERR_UNSUPPORTED (tile shape). */
+rs_status rs_views_prepare(const rs_camera* cams, int32_t n_views, const int64_t* n_items,
+                           int32_t tile_w, int32_t tile_h, rs_view* out_views,
+                           rs_view_batch* batch);
+
+/* Workspace bytes a stage needs for this batch (capacity = instance rows of rs_bins). */
+size_t rs_workspace_size(rs_stage stage, const rs_view_batch* batch, int64_t capacity);
+
+/* Sizes of the ABI structs, for bindings that mirror them: writes up to n entries in the
+ * order rs_gaussians, rs_camera, rs_view, rs_view_batch, rs_config, rs_projected, rs_bins,
+ * rs_gaussian_grads, rs_device_status; returns how many it wrote. */
+int32_t rs_struct_sizes(int64_t* out, int32_t n);
+
+/* ---- hot path ---------------------------------------------------------------------- */
+
+/* rs_project -- Sec. 3.2 "Gaussian Splatting": for every item (view v, Gaussian i),
+ * Sigma = R S S^T R^T, Sigma' = J M Sigma M^T J^T + eps2d*I (M the view rotation, J the
+ * Jacobian of the perspective projection at the camera-space mean, x/z and y/z clamped
+ * to lim_x/lim_y inside J), the conic (Sigma')^-1, the image mean, o = sigmoid(logit),
+ * the colour max(0, 0.5 + sum k_lm Y_lm(d)) from degree-sh_degree SH along
+ * d = normalise(p - campos), the FP32 order key
+ *   depth = fmaf(M20, px, fmaf(M21, py, fmaf(M22, pz, t2))),
+ * and the tile rectangle of the bounding box of {alpha >= 1/255}.  Items whose depth
+ * <= near_plane, whose parameters are not finite (counted in status->nonfinite), whose
+ * quaternion is zero, whose opacity is below 1/255 or whose support misses the image
+ * get n_tiles = 0.
+ * ws: unused (pass NULL, 0).  Errors: RS_ERR_INVALID_ARG, RS_ERR_UNSUPPORTED
+ * (sh_degree), RS_ERR_CUDA. */
+rs_status rs_project(const rs_gaussians* g, const rs_view_batch* batch, const rs_config* cfg,
+                     const rs_projected* out, rs_device_status* status, void* stream);
+
+/* rs_bin_sort -- tile binning with duplicated 64-bit (tile | depth) keys and a device
+ * radix sort (the front-to-back order Eq. render-gs needs, per tile).  Every item is
+ * duplicated once per tile of its rect; the instances are sorted by
+ * key = (global tile id) << 32 | float bits of depth, stably with respect to item order
+ * (an LSD radix sort whose low 32 bits, constant per item, are sorted over the items
+ * before duplication).  Writes vals, ranges, and keys if non-NULL.
+ * If the instance count K exceeds bins->capacity, status->code = RS_ERR_CAPACITY,
+ * status->required = K, and only the first capacity instances are written (the lists
+ * are then incomplete; re-run with capacity >= required).
+ * ws: rs_workspace_size(RS_STAGE_BIN_SORT, batch, capacity) bytes of device memory.
+ * Errors: RS_ERR_INVALID_ARG, RS_ERR_WORKSPACE, RS_ERR_CUDA. */
+rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* batch,
+                      const rs_bins* bins, void* ws, size_t ws_bytes,
+                      rs_device_status* status, void* stream);
+
+/* rs_render -- Eq. (render-gs): per pixel, walk its tile's list front to back with
+ * alpha = min(0.99, o exp(power)), power = -(a dx^2 + c dy^2)/2 - b dx dy; skip entries
+ * with power > 0 or alpha < 1/255; stop before the first entry whose T(1-alpha) < 1e-4;
+ * C = sum c_j alpha_j T_j + T_final * bg.
+ * Outputs (device; any may be NULL to skip it): image [3 * n_pixels] planar per view
+ * (view v's channel c starts at 3*pixel_base + c*H*W), T_final [n_pixels],
+ * last [n_pixels] (1 + position in the tile list of the last composited entry, 0 if none).
+ * importance (may be NULL): uint32 [n_gaussians] holding the float bits of
+ * h_i = max alpha_i T_i over composited entries (Eq. importance-score), max-accumulated
+ * across calls; zero it before the first view.  n_gaussians is the length of importance
+ * (the Gaussian ids are item - item_base, or subset_idx[item]).
+ * Errors: RS_ERR_INVALID_ARG, RS_ERR_CUDA. */
+rs_status rs_render(const rs_projected* proj, const rs_bins* bins, const rs_view_batch* batch,
+                    const rs_config* cfg, float* image, float* T_final, int32_t* last,
+                    uint32_t* importance, int64_t n_gaussians, void* stream);
+
+/* rs_importance -- Eq. (importance-score) over every view of the batch: rs_render with
+ * no image outputs; importance (required) as in rs_render. */
+rs_status rs_importance(const rs_projected* proj, const rs_bins* bins,
+                        const rs_view_batch* batch, const rs_config* cfg,
+                        uint32_t* importance, int64_t n_gaussians, void* stream);
+
+/* rs_filter -- Sec. 3.3 pruning mask m_i = 1(h_i < t) (RS_PRUNE_BELOW) or the
+ * visibility indicator 1(h_i > t) of Eq. (importance-score-vis) (RS_KEEP_ABOVE) for
+ * h (device float [n]); mask (device uint8 [n], may be NULL), idx (device uint32 [n],
+ * may be NULL: the indices with mask 1 in ascending order), count (device uint32 [1]).
+ * ws: rs_workspace_size(RS_STAGE_FILTER, ...) with batch->n_items = n.
+ * Errors: RS_ERR_INVALID_ARG, RS_ERR_WORKSPACE, RS_ERR_CUDA. */
+rs_status rs_filter(const float* h, int64_t n, float t, rs_filter_mode mode, uint8_t* mask,
+                    uint32_t* idx, uint32_t* count, void* ws, size_t ws_bytes, void* stream);
+
+/* rs_filter_nearest -- Sec. 3.4: for each of n_cams camera centres (device float [n][3]),
+ * the nearest of k cluster centres (device float [k][3]) by the FP32 squared distance
+ * ((x0-c0)^2 + (x1-c1)^2) + (x2-c2)^2, ties to the lower index; out device int32 [n].
+ * Errors: RS_ERR_INVALID_ARG, RS_ERR_CUDA. */
+rs_status rs_filter_nearest(const float* centres, int32_t k, const float* cam_centres,
+                            int32_t n_cams, int32_t* out, void* stream);
+
+/* rs_render_backward -- derivative of Eq. (render-gs) for the training loss of Sec. 3.2:
+ * given dL/dimage (device, layout of rs_render's image) and the forward's T_final and
+ * last, walks each pixel's list back to front from `last` (T_j recovered as
+ * T_{j+1}/(1-alpha_j)), then chains through the projection to the parameters.
+ * Gradients are ADDED into `grads` (zero them first); items of all views of the same
+ * Gaussian are summed.  ws: rs_workspace_size(RS_STAGE_BACKWARD, batch, 0) bytes.
+ * Errors: RS_ERR_INVALID_ARG, RS_ERR_WORKSPACE, RS_ERR_UNSUPPORTED, RS_ERR_CUDA. */
+rs_status rs_render_backward(const rs_gaussians* g, const rs_view_batch* batch,
+                             const rs_config* cfg, const rs_projected* proj,
+                             const rs_bins* bins, const float* T_final, const int32_t* last,
+                             const float* dL_dimage, const rs_gaussian_grads* grads,
+                             void* ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RADSPLAT_H */

@@ -1,0 +1,355 @@
+"""PyTorch-facing binding of the C ABI (include/radsplat.h).
+
+Tensors provide device memory and the current CUDA stream; every computation runs in
+the library's kernels.  Unsigned device arrays (uint32 item ids, uint16 rects, uint32
+importance bits) are held in int32 / int16 tensors with the same bits.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+__all__ = ["Gaussians", "ViewBatch", "Projected", "Bins", "DeviceStatus", "Workspace", "config", "project",
+           "bin_sort", "render", "importance", "filter", "nearest", "render_backward", "Rasterizer",
+           "RadSplatFunction", "split_images", "importance_as_float"]
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def config(eps2d: float = 0.3, near_plane: float = 0.2, bg=(0.0, 0.0, 0.0)) -> N.RsConfig:
+    c = N.lib().rs_config_default()
+    c.eps2d = eps2d
+    c.near_plane = near_plane
+    for i in range(3):
+        c.bg[i] = float(bg[i])
+    return c
+
+
+class Gaussians:
+    """FP32 structure-of-arrays parameters on the device (Sec. 3.2)."""
+
+    def __init__(self, means, log_scales, quats, opacity_logit, sh, sh_degree: int):
+        self.means, self.log_scales, self.quats = means, log_scales, quats
+        self.opacity_logit, self.sh, self.sh_degree = opacity_logit, sh, int(sh_degree)
+        for t in self.tensors():
+            if t.dtype != torch.float32 or not t.is_contiguous():
+                raise ValueError("Gaussian parameters must be contiguous float32 tensors")
+
+    @classmethod
+    def from_scene(cls, scene, device="cuda"):
+        return cls(*(torch.as_tensor(np.ascontiguousarray(a, np.float32), device=device) for a in scene.arrays()),
+                   scene.sh_degree)
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[1])
+
+    def tensors(self):
+        return (self.means, self.log_scales, self.quats, self.opacity_logit, self.sh)
+
+    def struct(self) -> N.RsGaussians:
+        return N.RsGaussians(self.means.data_ptr(), self.log_scales.data_ptr(), self.quats.data_ptr(),
+                             self.opacity_logit.data_ptr(), self.sh.data_ptr(), self.n, self.sh_degree, 0)
+
+
+def _camera_struct(cam) -> N.RsCamera:
+    c = N.RsCamera()
+    vm = np.asarray(cam["viewmat"], dtype=np.float32).reshape(12)
+    for i in range(12):
+        c.viewmat[i] = float(vm[i])
+    c.fx, c.fy, c.cx, c.cy = (float(cam[k]) for k in ("fx", "fy", "cx", "cy"))
+    c.width, c.height = int(cam["width"]), int(cam["height"])
+    return c
+
+
+class ViewBatch:
+    """Views rendered together (rs_view_batch): descriptors on the device, optional
+    per-view ascending visibility lists (Sec. 3.4)."""
+
+    def __init__(self, cams: Sequence[dict], n_gaussians: int, subsets: Optional[Sequence] = None,
+                 tile=(16, 16), device="cuda"):
+        V = len(cams)
+        if subsets is not None and len(subsets) != V:
+            raise ValueError("one subset per view")
+        n_items = np.array([len(s) for s in subsets] if subsets is not None else [n_gaussians] * V, dtype=np.int64)
+        cam_arr = (N.RsCamera * V)(*[_camera_struct(c) for c in cams])
+        host = (N.RsView * V)()
+        b = N.RsViewBatch()
+        N.call("rs_views_prepare", cam_arr, V, n_items.ctypes.data_as(ctypes.c_void_p), int(tile[0]), int(tile[1]),
+               host, N.ref(b))
+        raw = np.frombuffer(bytes(host), dtype=np.uint8).copy()
+        self.views_dev = torch.as_tensor(raw, device=device)
+        self.views_host = host
+        if subsets is not None:
+            sub = np.concatenate([np.asarray(s, dtype=np.uint32) for s in subsets]).view(np.int32)
+            self.subset = torch.as_tensor(sub, device=device)
+        else:
+            self.subset = None
+        b.views = self.views_dev.data_ptr()
+        b.subset_idx = self.subset.data_ptr() if self.subset is not None else None
+        self.batch = b
+        self.cams = list(cams)
+        self.n_gaussians = int(n_gaussians)
+        self.tile = (int(tile[0]), int(tile[1]))
+
+    @property
+    def n_views(self):
+        return self.batch.n_views
+
+    @property
+    def n_items(self):
+        return self.batch.n_items
+
+    @property
+    def n_tiles(self):
+        return self.batch.n_tiles
+
+    @property
+    def n_pixels(self):
+        return self.batch.n_pixels
+
+
+@dataclass
+class Projected:
+    xy: torch.Tensor        # [M, 2] f32
+    conic_o: torch.Tensor   # [M, 4] f32
+    rgb_d: torch.Tensor     # [M, 4] f32
+    rect: torch.Tensor      # [M, 4] int16 (uint16 bits)
+    n_tiles: torch.Tensor   # [M] int32 (uint32 bits)
+
+    @classmethod
+    def empty(cls, m: int, device="cuda"):
+        m = max(int(m), 1)
+        return cls(torch.empty((m, 2), dtype=torch.float32, device=device),
+                   torch.empty((m, 4), dtype=torch.float32, device=device),
+                   torch.empty((m, 4), dtype=torch.float32, device=device),
+                   torch.empty((m, 4), dtype=torch.int16, device=device),
+                   torch.empty((m,), dtype=torch.int32, device=device))
+
+    def struct(self) -> N.RsProjected:
+        return N.RsProjected(self.xy.data_ptr(), self.conic_o.data_ptr(), self.rgb_d.data_ptr(),
+                             self.rect.data_ptr(), self.n_tiles.data_ptr())
+
+
+@dataclass
+class Bins:
+    vals: torch.Tensor                  # [capacity] int32 (uint32 item ids)
+    ranges: torch.Tensor                # [n_tiles, 2] int32
+    keys: Optional[torch.Tensor]        # [capacity] int64 (uint64 bits) or None
+    capacity: int
+
+    @classmethod
+    def empty(cls, capacity: int, n_tiles: int, keys: bool = False, device="cuda"):
+        capacity = max(int(capacity), 1)
+        return cls(torch.empty(capacity, dtype=torch.int32, device=device),
+                   torch.empty((max(n_tiles, 1), 2), dtype=torch.int32, device=device),
+                   torch.empty(capacity, dtype=torch.int64, device=device) if keys else None, capacity)
+
+    def struct(self) -> N.RsBins:
+        return N.RsBins(self.keys.data_ptr() if self.keys is not None else None, self.vals.data_ptr(),
+                        self.ranges.data_ptr(), self.capacity)
+
+
+class DeviceStatus:
+    """rs_device_status in device memory (32 bytes)."""
+
+    def __init__(self, device="cuda"):
+        self.t = torch.zeros(4, dtype=torch.int64, device=device)
+
+    def ptr(self):
+        return ctypes.c_void_p(self.t.data_ptr())
+
+    def zero_(self):
+        self.t.zero_()
+
+    def read(self) -> dict:
+        a = self.t.cpu().numpy()
+        code_nonfinite = a[0:1].view(np.int32)
+        return {"code": int(code_nonfinite[0]), "nonfinite": int(code_nonfinite[1]), "required": int(a[1]),
+                "n_instances": int(a[2])}
+
+
+class Workspace:
+    """A byte buffer that grows on request (never shrinks)."""
+
+    def __init__(self, device="cuda"):
+        self.device = device
+        self.t = None
+
+    def get(self, nbytes: int) -> torch.Tensor:
+        nbytes = max(int(nbytes), 256)
+        if self.t is None or self.t.numel() < nbytes:
+            self.t = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        return self.t
+
+
+def project(g: Gaussians, vb: ViewBatch, cfg: Optional[N.RsConfig] = None, status: Optional[DeviceStatus] = None,
+            out: Optional[Projected] = None, stream=None) -> Projected:
+    cfg = cfg or config()
+    out = out or Projected.empty(vb.n_items, g.means.device)
+    N.call("rs_project", N.ref(g.struct()), N.ref(vb.batch), N.ref(cfg), N.ref(out.struct()),
+           status.ptr() if status else None, _stream(stream))
+    return out
+
+
+def bin_sort(proj: Projected, vb: ViewBatch, bins: Bins, ws: Workspace, status: DeviceStatus, stream=None) -> Bins:
+    nbytes = N.lib().rs_workspace_size(N.RS_STAGE_BIN_SORT, N.ref(vb.batch), bins.capacity)
+    w = ws.get(nbytes)
+    N.call("rs_bin_sort", N.ref(proj.struct()), N.ref(vb.batch), N.ref(bins.struct()), _ptr(w), w.numel(),
+           status.ptr(), _stream(stream))
+    return bins
+
+
+def render(proj: Projected, bins: Bins, vb: ViewBatch, cfg: Optional[N.RsConfig] = None, image=True,
+           T_final=True, last=True, importance: Optional[torch.Tensor] = None, stream=None):
+    """Returns (image [3*n_pixels] planar per view, T_final [n_pixels], last [n_pixels])."""
+    cfg = cfg or config()
+    dev = proj.xy.device
+    img = torch.empty(3 * vb.n_pixels, dtype=torch.float32, device=dev) if image is True else image
+    T = torch.empty(vb.n_pixels, dtype=torch.float32, device=dev) if T_final is True else T_final
+    L = torch.empty(vb.n_pixels, dtype=torch.int32, device=dev) if last is True else last
+    img = img if img is not False else None
+    T = T if T is not False else None
+    L = L if L is not False else None
+    n_g = importance.numel() if importance is not None else 0
+    N.call("rs_render", N.ref(proj.struct()), N.ref(bins.struct()), N.ref(vb.batch), N.ref(cfg), _ptr(img),
+           _ptr(T), _ptr(L), _ptr(importance), n_g, _stream(stream))
+    return img, T, L
+
+
+def importance(proj: Projected, bins: Bins, vb: ViewBatch, h: torch.Tensor, cfg=None, stream=None) -> torch.Tensor:
+    """Max-accumulates Eq. (importance-score) over the batch's views into h (int32 bits of float32)."""
+    cfg = cfg or config()
+    N.call("rs_importance", N.ref(proj.struct()), N.ref(bins.struct()), N.ref(vb.batch), N.ref(cfg), _ptr(h),
+           h.numel(), _stream(stream))
+    return h
+
+
+def importance_as_float(h: torch.Tensor) -> torch.Tensor:
+    return h.view(torch.float32)
+
+
+def filter(h: torch.Tensor, t: float, mode: int, ws: Optional[Workspace] = None, mask=True, idx=True, stream=None):
+    """Sec. 3.3 / Eq. (importance-score-vis): (mask uint8 [n], idx int32 [n], count int32 [1])."""
+    n = h.numel()
+    dev = h.device
+    ws = ws or Workspace(dev)
+    vb = N.RsViewBatch()
+    vb.n_items = n
+    nbytes = N.lib().rs_workspace_size(N.RS_STAGE_FILTER, N.ref(vb), 0)
+    w = ws.get(nbytes)
+    m = torch.empty(max(n, 1), dtype=torch.uint8, device=dev) if mask is True else (mask or None)
+    ix = torch.empty(max(n, 1), dtype=torch.int32, device=dev) if idx is True else (idx or None)
+    cnt = torch.empty(1, dtype=torch.int32, device=dev)
+    hf = h.view(torch.float32) if h.dtype == torch.int32 else h
+    N.call("rs_filter", _ptr(hf), n, float(t), int(mode), _ptr(m), _ptr(ix), _ptr(cnt), _ptr(w), w.numel(),
+           _stream(stream))
+    return m, ix, cnt
+
+
+def nearest(centres: torch.Tensor, cam_centres: torch.Tensor, stream=None) -> torch.Tensor:
+    """Sec. 3.4: index of the nearest cluster centre for each camera centre."""
+    out = torch.empty(cam_centres.shape[0], dtype=torch.int32, device=cam_centres.device)
+    N.call("rs_filter_nearest", _ptr(centres), centres.shape[0], _ptr(cam_centres), cam_centres.shape[0], _ptr(out),
+           _stream(stream))
+    return out
+
+
+def render_backward(g: Gaussians, vb: ViewBatch, proj: Projected, bins: Bins, T_final, last, dL_dimage,
+                    grads: Sequence[torch.Tensor], ws: Workspace, cfg=None, stream=None):
+    """Adds d(L)/d(params) into grads (means, log_scales, quats, opacity_logit, sh)."""
+    cfg = cfg or config()
+    gs = N.RsGaussianGrads(*(t.data_ptr() for t in grads))
+    nbytes = N.lib().rs_workspace_size(N.RS_STAGE_BACKWARD, N.ref(vb.batch), 0)
+    w = ws.get(nbytes)
+    N.call("rs_render_backward", N.ref(g.struct()), N.ref(vb.batch), N.ref(cfg), N.ref(proj.struct()),
+           N.ref(bins.struct()), _ptr(T_final), _ptr(last), _ptr(dL_dimage), N.ref(gs), _ptr(w), w.numel(),
+           _stream(stream))
+
+
+def split_images(flat: torch.Tensor, vb: ViewBatch) -> List[torch.Tensor]:
+    out = []
+    for v in range(vb.n_views):
+        hv = vb.views_host[v]
+        base = 3 * hv.pixel_base
+        out.append(flat[base: base + 3 * hv.width * hv.height].view(3, hv.height, hv.width))
+    return out
+
+
+class Rasterizer:
+    """Owns workspaces and the instance capacity for repeated renders of view batches.
+
+    The capacity grows on demand: rs_bin_sort reports the instance count it needed, and a
+    render whose count exceeded the capacity is redone with a larger one (one host
+    synchronisation per call on this path; fixed-capacity graph replay avoids it)."""
+
+    def __init__(self, cfg: Optional[N.RsConfig] = None, device="cuda", capacity: int = 0, keys: bool = False):
+        self.cfg = cfg or config()
+        self.device = device
+        self.capacity = int(capacity)
+        self.keys = keys
+        self.ws_sort = Workspace(device)
+        self.ws_bwd = Workspace(device)
+        self.status = DeviceStatus(device)
+        self._bins = None
+
+    def bins_for(self, vb: ViewBatch) -> Bins:
+        if self._bins is None or self._bins.capacity < self.capacity or self._bins.ranges.shape[0] < vb.n_tiles \
+                or (self.keys and self._bins.keys is None):
+            self._bins = Bins.empty(self.capacity, vb.n_tiles, keys=self.keys, device=self.device)
+        b = self._bins
+        return Bins(b.vals, b.ranges[:max(vb.n_tiles, 1)], b.keys, b.capacity)
+
+    def forward(self, g: Gaussians, vb: ViewBatch, importance: Optional[torch.Tensor] = None, image=True):
+        if self.capacity <= 0:
+            self.capacity = max(4 * vb.n_items, 1 << 16)
+        self.status.zero_()
+        proj = project(g, vb, self.cfg, self.status)
+        while True:
+            bins = self.bins_for(vb)
+            bin_sort(proj, vb, bins, self.ws_sort, self.status)
+            st = self.status.read()
+            if st["required"] <= bins.capacity:
+                break
+            self.capacity = int(st["required"] * 1.25) + 1024
+            self.status.zero_()
+        img, T, L = render(proj, bins, vb, self.cfg, image=image, importance=importance)
+        return {"image": img, "T_final": T, "last": L, "proj": proj, "bins": bins, "n_instances": st["n_instances"]}
+
+
+class RadSplatFunction(torch.autograd.Function):
+    """Differentiable render of a view batch: params -> flat planar images [3*n_pixels]."""
+
+    @staticmethod
+    def forward(ctx, means, log_scales, quats, opacity_logit, sh, vb: ViewBatch, rast: Rasterizer, sh_degree: int):
+        g = Gaussians(means.detach(), log_scales.detach(), quats.detach(), opacity_logit.detach(), sh.detach(),
+                      sh_degree)
+        out = rast.forward(g, vb)
+        ctx.g, ctx.vb, ctx.rast = g, vb, rast
+        ctx.proj, ctx.bins = out["proj"], out["bins"]
+        ctx.save_for_backward(out["T_final"], out["last"])
+        return out["image"]
+
+    @staticmethod
+    def backward(ctx, dL_dimage):
+        T_final, last = ctx.saved_tensors
+        g = ctx.g
+        grads = [torch.zeros_like(t) for t in g.tensors()]
+        render_backward(g, ctx.vb, ctx.proj, ctx.bins, T_final, last, dL_dimage.contiguous(), grads,
+                        ctx.rast.ws_bwd, ctx.rast.cfg)
+        return (*grads, None, None, None)

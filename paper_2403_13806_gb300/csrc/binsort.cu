@@ -1,0 +1,283 @@
+// rs_bin_sort: duplicated (tile | depth) keys and a device radix sort.
+//
+// The 64-bit key of an instance is (global tile id) << 32 | float bits of the item's depth.
+// An LSD radix sort processes the least significant digits first; the low 32 bits depend
+// on the item only, so their passes are run over the N items before duplication (four
+// 8-bit passes), and the expansion then emits every item's tiles in that depth order.  The
+// remaining passes sort the K instances stably on the tile id alone, over only the
+// ceil(log2(tiles)) significant bits.  The result -- permutation and keys -- is exactly
+// that of a stable sort of the 64-bit keys emitted in item order.
+//
+// Pipeline (one stream, no host synchronisation; K lives in device memory):
+//   k_depth_keys -> 4 depth passes -> k_count_blocks -> k_count_top (K, capacity check)
+//   -> k_emit (warp-cooperative expansion, coalesced stores) -> tile passes
+//   -> memset(ranges) -> k_ranges -> [k_keys]
+#include "radix.cuh"
+#include "radsplat.h"
+#include "rs_common.cuh"
+
+namespace rs {
+
+constexpr int kEmitThreads = 256;
+
+struct BinWs {
+  uint32_t* dkeys[2];
+  uint32_t* dvals[2];
+  unsigned long long* bsum;   // per emission block: instances, then exclusive prefix
+  uint32_t* tkeys[2];
+  uint32_t* tvals;
+  uint32_t* hist;
+  uint32_t* counters;         // [0] = instances written (min(K, capacity))
+  int grid_depth, grid_tile;
+  size_t bytes;
+};
+
+static BinWs bin_ws_layout(void* base, int64_t n_items, int64_t capacity) {
+  BinWs w{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* p = base ? static_cast<char*>(base) + off : nullptr;
+    off += align_up(bytes, 256);
+    return p;
+  };
+  const size_t ni = (size_t)(n_items > 0 ? n_items : 1);
+  const size_t cap = (size_t)(capacity > 0 ? capacity : 1);
+  const int64_t nblk = (n_items + kEmitThreads - 1) / kEmitThreads;
+  w.grid_depth = radix::grid_for(n_items, 2 * kNumSMs);
+  w.grid_tile = radix::grid_for(capacity, 2 * kNumSMs);
+  const int hist_grid = w.grid_depth > w.grid_tile ? w.grid_depth : w.grid_tile;
+  for (int i = 0; i < 2; ++i) w.dkeys[i] = reinterpret_cast<uint32_t*>(take(ni * 4));
+  for (int i = 0; i < 2; ++i) w.dvals[i] = reinterpret_cast<uint32_t*>(take(ni * 4));
+  w.bsum = reinterpret_cast<unsigned long long*>(take((size_t)(nblk > 0 ? nblk : 1) * 8));
+  for (int i = 0; i < 2; ++i) w.tkeys[i] = reinterpret_cast<uint32_t*>(take(cap * 4));
+  w.tvals = reinterpret_cast<uint32_t*>(take(cap * 4));
+  w.hist = reinterpret_cast<uint32_t*>(take(radix::hist_bytes(hist_grid)));
+  w.counters = reinterpret_cast<uint32_t*>(take(64));
+  w.bytes = off;
+  return w;
+}
+
+__global__ void k_depth_keys(const float4* __restrict__ rgb_d, int64_t n, uint32_t* __restrict__ keys,
+                             uint32_t* __restrict__ vals) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  keys[i] = __float_as_uint(rgb_d[i].w);
+  vals[i] = (uint32_t)i;
+}
+
+// Instances per block of kEmitThreads depth-sorted items.
+__global__ void __launch_bounds__(kEmitThreads) k_count_blocks(const uint32_t* __restrict__ order, int64_t n,
+                                                               const uint32_t* __restrict__ n_tiles,
+                                                               unsigned long long* __restrict__ bsum) {
+  __shared__ unsigned long long s[kEmitThreads / 32];
+  const int64_t i = (int64_t)blockIdx.x * kEmitThreads + threadIdx.x;
+  unsigned long long c = i < n ? (unsigned long long)n_tiles[order[i]] : 0ull;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long t = 0;
+    for (int w = 0; w < kEmitThreads / 32; ++w) t += s[w];
+    bsum[blockIdx.x] = t;
+  }
+}
+
+// Exclusive prefix over the block counts (one block), the instance total K, and the
+// capacity check.
+__global__ void __launch_bounds__(1024) k_count_top(unsigned long long* __restrict__ bsum, int64_t nblk,
+                                                    int64_t capacity, uint32_t* __restrict__ counters,
+                                                    rs_device_status* st) {
+  __shared__ unsigned long long s_w[32];
+  __shared__ unsigned long long s_carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_carry = 0ull;
+  __syncthreads();
+  for (int64_t b0 = 0; b0 < nblk; b0 += 1024) {
+    const int64_t b = b0 + threadIdx.x;
+    const unsigned long long v = b < nblk ? bsum[b] : 0ull;
+    unsigned long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      unsigned long long w = s_w[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      s_w[lane] = w;
+    }
+    __syncthreads();
+    const unsigned long long carry = s_carry;
+    const unsigned long long excl = carry + (warp ? s_w[warp - 1] : 0ull) + x - v;
+    if (b < nblk) bsum[b] = excl;
+    __syncthreads();
+    if (threadIdx.x == 1023) s_carry = carry + s_w[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const unsigned long long K = s_carry;
+    const unsigned long long written = K < (unsigned long long)capacity ? K : (unsigned long long)capacity;
+    counters[0] = (uint32_t)written;
+    if (st) {
+      atomicMax(reinterpret_cast<unsigned long long*>(&st->required), K);
+      st->n_instances = (int64_t)written;
+      if (K > (unsigned long long)capacity) atomicCAS(&st->code, 0, (int)RS_ERR_CAPACITY);
+    }
+  }
+}
+
+// Expansion: each warp takes 32 consecutive depth-sorted items and writes their
+// instances contiguously (tile ids row-major inside each rect); lanes locate the item of
+// their instance by a binary search over the warp's inclusive prefix.
+__global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restrict__ order, int64_t n,
+                                                       const uint32_t* __restrict__ n_tiles,
+                                                       const ushort4* __restrict__ rect,
+                                                       const rs_view* __restrict__ views, int n_views,
+                                                       const unsigned long long* __restrict__ bpre,
+                                                       int64_t capacity, uint32_t* __restrict__ tkeys,
+                                                       uint32_t* __restrict__ tvals) {
+  __shared__ uint32_t s_wtot[kEmitThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * kEmitThreads + threadIdx.x;
+  uint32_t item = 0, cnt = 0;
+  ushort4 rc = make_ushort4(0, 0, 0, 0);
+  int tile_base = 0, tiles_x = 0;
+  if (i < n) {
+    item = order[i];
+    cnt = n_tiles[item];
+    if (cnt) {
+      rc = rect[item];
+      const int v = find_view_by_item(views, n_views, (int64_t)item);
+      tile_base = views[v].tile_base;
+      tiles_x = views[v].tiles_x;
+    }
+  }
+  uint32_t incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
+  if (lane == 0) s_wtot[warp] = wtot;
+  __syncthreads();
+  unsigned long long wbase = bpre[blockIdx.x];
+  for (int w = 0; w < warp; ++w) wbase += s_wtot[w];
+  const uint32_t excl = incl - cnt;
+  const int rw = (int)rc.z - (int)rc.x;
+  for (uint32_t e0 = 0; e0 < wtot; e0 += 32) {
+    const uint32_t e = e0 + lane;
+    int lo = 0;
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) {
+      const uint32_t v = __shfl_sync(0xffffffffu, incl, lo + s - 1);
+      if (v <= e) lo += s;
+    }
+    const int owner = lo < 31 ? lo : 31;
+    const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, owner);
+    const int o_rw = __shfl_sync(0xffffffffu, rw, owner);
+    const int o_x0 = __shfl_sync(0xffffffffu, (int)rc.x, owner);
+    const int o_y0 = __shfl_sync(0xffffffffu, (int)rc.y, owner);
+    const int o_tb = __shfl_sync(0xffffffffu, tile_base, owner);
+    const int o_tx = __shfl_sync(0xffffffffu, tiles_x, owner);
+    const uint32_t o_item = __shfl_sync(0xffffffffu, item, owner);
+    if (e < wtot) {
+      const uint32_t r = e - o_excl;
+      const uint32_t ty = r / (uint32_t)o_rw;
+      const uint32_t tx = r - ty * (uint32_t)o_rw;
+      const unsigned long long pos = wbase + e;
+      if (pos < (unsigned long long)capacity) {
+        tkeys[pos] = (uint32_t)o_tb + (uint32_t)(o_y0 + (int)ty) * (uint32_t)o_tx + (uint32_t)(o_x0 + (int)tx);
+        tvals[pos] = o_item;
+      }
+    }
+  }
+}
+
+__global__ void k_ranges(const uint32_t* __restrict__ tkeys, const uint32_t* __restrict__ counters,
+                         uint32_t n_tiles, uint32_t* __restrict__ ranges) {
+  const int64_t K = counters[0];
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t t = tkeys[k];
+    if (t >= n_tiles) continue;   // only a rect outside its view's tile grid could produce this
+    if (k == 0 || tkeys[k - 1] != t) ranges[2 * (int64_t)t] = (uint32_t)k;
+    if (k == K - 1 || tkeys[k + 1] != t) ranges[2 * (int64_t)t + 1] = (uint32_t)(k + 1);
+  }
+}
+
+__global__ void k_keys(const uint32_t* __restrict__ tkeys, const uint32_t* __restrict__ vals,
+                       const float4* __restrict__ rgb_d, const uint32_t* __restrict__ counters,
+                       unsigned long long* __restrict__ keys) {
+  const int64_t K = counters[0];
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x)
+    keys[k] = ((unsigned long long)tkeys[k] << 32) | (unsigned long long)__float_as_uint(rgb_d[vals[k]].w);
+}
+
+static int bits_for(int64_t n) {
+  int b = 1;
+  while (b < 32 && ((int64_t)1 << b) < n) ++b;
+  return b;
+}
+
+size_t bin_sort_ws_bytes(int64_t n_items, int64_t capacity) { return bin_ws_layout(nullptr, n_items, capacity).bytes; }
+
+}  // namespace rs
+
+using namespace rs;
+
+extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* batch, const rs_bins* bins,
+                                 void* ws, size_t ws_bytes, rs_device_status* status, void* stream) {
+  if (!proj || !batch || !bins) return RS_ERR_INVALID_ARG;
+  if (!bins->vals || !bins->ranges || bins->capacity <= 0 || bins->capacity >= ((int64_t)1 << 32))
+    return RS_ERR_INVALID_ARG;
+  if (batch->n_items < 0 || batch->n_items >= ((int64_t)1 << 32) || batch->n_tiles <= 0 || !batch->views)
+    return RS_ERR_INVALID_ARG;
+  if (!proj->rgb_d || !proj->rect || !proj->n_tiles) return RS_ERR_INVALID_ARG;
+  const BinWs w = bin_ws_layout(ws, batch->n_items, bins->capacity);
+  if (!ws || ws_bytes < w.bytes || !aligned<uint4>(ws, 256)) return RS_ERR_WORKSPACE;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t n = batch->n_items;
+  const int64_t cap = bins->capacity;
+  const float4* rgb_d = reinterpret_cast<const float4*>(proj->rgb_d);
+
+  if (cudaMemsetAsync(w.counters, 0, 64, s) != cudaSuccess) return RS_ERR_CUDA;
+  if (cudaMemsetAsync(bins->ranges, 0, (size_t)batch->n_tiles * 2 * sizeof(uint32_t), s) != cudaSuccess)
+    return RS_ERR_CUDA;
+  if (n == 0) {
+    k_count_top<<<1, 1024, 0, s>>>(w.bsum, 0, cap, w.counters, status);
+    return launch_status();
+  }
+  // 1) items by depth (four 8-bit passes; even count leaves the result in buffer 0)
+  k_depth_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rgb_d, n, w.dkeys[0], w.dvals[0]);
+  radix::sort_pairs(w.dkeys[0], w.dvals[0], w.dkeys[1], w.dvals[1], n, nullptr, n, 32, w.hist, w.grid_depth, s,
+                    false);
+  const uint32_t* order = w.dvals[0];
+  // 2) instance offsets in depth order and K
+  const int64_t nblk = (n + kEmitThreads - 1) / kEmitThreads;
+  k_count_blocks<<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n, proj->n_tiles, w.bsum);
+  k_count_top<<<1, 1024, 0, s>>>(w.bsum, nblk, cap, w.counters, status);
+  // 3) expansion; the tile passes then ping-pong so that the final values land in bins->vals
+  const int tbits = bits_for(batch->n_tiles);
+  const int passes = radix::sort_passes(tbits);
+  uint32_t* v_first = (passes % 2 == 0) ? bins->vals : w.tvals;
+  uint32_t* v_second = (passes % 2 == 0) ? w.tvals : bins->vals;
+  k_emit<<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n, proj->n_tiles, reinterpret_cast<const ushort4*>(proj->rect),
+                                                 batch->views, batch->n_views, w.bsum, cap, w.tkeys[0], v_first);
+  // 4) stable sort of the instances on the tile id
+  const int cur = radix::sort_pairs(w.tkeys[0], v_first, w.tkeys[1], v_second, 0, w.counters, cap, tbits, w.hist,
+                                    w.grid_tile, s, true);
+  const uint32_t* tk = w.tkeys[cur];
+  // 5) per-tile ranges and (optionally) the 64-bit keys
+  const int rgrid = 4 * kNumSMs;
+  k_ranges<<<rgrid, 256, 0, s>>>(tk, w.counters, (uint32_t)batch->n_tiles, bins->ranges);
+  if (bins->keys)
+    k_keys<<<rgrid, 256, 0, s>>>(tk, bins->vals, rgb_d, w.counters, reinterpret_cast<unsigned long long*>(bins->keys));
+  return launch_status();
+}
