@@ -287,6 +287,15 @@ rs_status rs_render_backward(const rs_gaussians* g, const rs_view_batch* batch,
                              const float* dL_dimage, const rs_gaussian_grads* grads,
                              void* ws, size_t ws_bytes, void* stream);
 
+/* rs_l1_loss -- the L1 photometric loss used for the synthetic training step (a stand-in
+ * for the radiance-field supervision of Sec. 3.2, whose teacher renders are not
+ * available): loss = mean |image - target| over n values, and
+ * dL_dimage = sign(image - target) / n (0 where they are equal).  image, target,
+ * dL_dimage: device float [n]; loss: device double [1], overwritten.
+ * Errors: RS_ERR_INVALID_ARG, RS_ERR_CUDA. */
+rs_status rs_l1_loss(const float* image, const float* target, int64_t n, float* dL_dimage,
+                     double* loss, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -168,24 +168,43 @@ def render_torch(scene, cam, eps2d=0.3, near=0.2, bg=(0.0, 0.0, 0.0), pixels=Non
     return img.numpy(), T.numpy()
 
 
-def gradients(scene, cam, dL_dimage, eps2d=0.3, near=0.2, bg=(0.0, 0.0, 0.0), chunk=4096):
+def gradients(scene, cam, dL_dimage, eps2d=0.3, near=0.2, bg=(0.0, 0.0, 0.0), chunk=4096, pixels=None):
     """d(sum dL_dimage * image)/d(params) in FP64 for one view.
 
-    dL_dimage: [3,H,W].  Returns a dict with the parameter gradients (same layouts
-    as the scene arrays) and the image-space gradients per Gaussian:
-    g_xy [N,2], g_conic [N,3] (w.r.t. (a, b, c) with power = -(a dx^2 + c dy^2)/2 - b dx dy),
-    g_opacity [N], g_rgb [N,3].  Culled Gaussians get zeros."""
-    _, order = _fixed_decisions(scene, cam, eps2d, near)
+    dL_dimage: [3,H,W], or [P,3] for the listed pixels [P,2] (u, v).  Returns a dict with
+    the parameter gradients (same layouts as the scene arrays) and the image-space
+    gradients per Gaussian: g_xy [N,2], g_conic [N,3] (w.r.t. (a, b, c) with
+    power = -(a dx^2 + c dy^2)/2 - b dx dy), g_opacity [N], g_rgb [N,3].  Culled
+    Gaussians get zeros.  With pixels given, each chunk of pixels composites only the
+    Gaussians whose support box contains one of its pixels (every other Gaussian has
+    alpha < 1/255 there and is skipped anyway), so the result is the same."""
+    proj, order = _fixed_decisions(scene, cam, eps2d, near)
     W, H = cam["width"], cam["height"]
     p = params_of(scene)
     xy, conic, o, rgb = project_torch(p, cam, eps2d)
     leaves = [t.detach().clone().requires_grad_(True) for t in (xy, conic, o, rgb)]
-    vv, uu = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
-    pixels = np.stack([uu.ravel(), vv.ravel()], axis=1)
-    g = torch.as_tensor(np.asarray(dL_dimage, dtype=np.float64).reshape(3, -1).T)   # [P,3]
+    if pixels is None:
+        vv, uu = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+        pixels = np.stack([uu.ravel(), vv.ravel()], axis=1)
+        g = torch.as_tensor(np.asarray(dL_dimage, dtype=np.float64).reshape(3, -1).T)   # [P,3]
+        prune = False
+    else:
+        pixels = np.asarray(pixels).reshape(-1, 2)
+        g = torch.as_tensor(np.asarray(dL_dimage, dtype=np.float64).reshape(-1, 3))
+        prune = True
     ordt = torch.as_tensor(order)
+    if prune:
+        oxy = proj["xy"][order]
+        ext = proj["ext"][order] * (1.0 + 1e-6) + 1e-6
     for s in range(0, pixels.shape[0], chunk):
-        img, _ = composite_torch(*leaves, ordt, pixels[s:s + chunk], bg)
+        pc = pixels[s:s + chunk]
+        sel = ordt
+        if prune:
+            hit = np.zeros(len(order), dtype=bool)
+            for u, v in pc:
+                hit |= (np.abs(oxy[:, 0] - u) <= ext[:, 0]) & (np.abs(oxy[:, 1] - v) <= ext[:, 1])
+            sel = ordt[torch.as_tensor(hit)]
+        img, _ = composite_torch(*leaves, sel, pc, bg)
         (img * g[s:s + chunk]).sum().backward()
     grads2d = [lf.grad if lf.grad is not None else torch.zeros_like(lf) for lf in leaves]
     torch.autograd.backward([xy, conic, o, rgb], grads2d)

@@ -265,9 +265,11 @@ static int entry_cmp(const void* a, const void* b) {
  * Per pixel: image[3], T_final, last_id (id of the last composited entry, -1 if
  * none), n_contrib, ambiguous (1 if, before compositing stops, a skip or stop
  * decision lies within a relative amb_rel of its threshold, or 0 < |power| <= 1e-9).
- * Per Gaussian (in/out, max-accumulated): h over unflagged pixels; h_amb over
- * flagged pixels, of alpha*T for every entry up to and including the stopping
- * one (entries skipped only by a near-threshold alpha included).
+ * Per Gaussian (in/out, max-accumulated): h, alpha*T of every composited entry that
+ * precedes the pixel's first near-threshold decision (an unflagged pixel has none);
+ * h_amb, alpha*T of every entry from that decision up to and including the stopping
+ * one (entries skipped only by a near-threshold alpha included), which a different
+ * rounding of the decision could change.
  * Returns 0, or -1 on allocation failure. */
 int or_render(int64_t n, const double* xy, const double* conic, const double* opacity,
               const double* rgb, const float* depth, const int32_t* valid, const double* ext,
@@ -322,7 +324,8 @@ int or_render(int64_t n, const double* xy, const double* conic, const double* op
     or_entry* ent = (or_entry*)malloc(sizeof(or_entry) * cap);
     int64_t* hid = (int64_t*)malloc(sizeof(int64_t) * cap);
     double* hval = (double*)malloc(sizeof(double) * cap);
-    if (!ent || !hid || !hval) fail = 1;
+    int64_t* hpos = (int64_t*)malloc(sizeof(int64_t) * cap);
+    if (!ent || !hid || !hval || !hpos) fail = 1;
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 16)
 #endif
@@ -355,7 +358,8 @@ int or_render(int64_t n, const double* xy, const double* conic, const double* op
           ent = (or_entry*)realloc(ent, sizeof(or_entry) * cap);
           hid = (int64_t*)realloc(hid, sizeof(int64_t) * cap);
           hval = (double*)realloc(hval, sizeof(double) * cap);
-          if (!ent || !hid || !hval) { fail = 1; break; }
+          hpos = (int64_t*)realloc(hpos, sizeof(int64_t) * cap);
+          if (!ent || !hid || !hval || !hpos) { fail = 1; break; }
         }
         ent[ne].depth = depth[j];
         ent[ne].id = j;
@@ -368,15 +372,15 @@ int or_render(int64_t n, const double* xy, const double* conic, const double* op
       qsort(ent, (size_t)ne, sizeof(or_entry), entry_cmp);
       double T = 1.0, C[3] = {0.0, 0.0, 0.0};
       int64_t last = -1, cnt = 0, stop = ne;
-      int amb = 0;
+      int64_t amb_at = -1;   /* sorted position of the first near-threshold decision */
       for (int64_t e = 0; e < ne; ++e) {
-        if (ent[e].power != 0.0 && fabs(ent[e].power) <= 1e-9) amb = 1;
-        if (fabs(ent[e].araw - OR_ALPHA_MIN) <= amb_rel * OR_ALPHA_MIN) amb = 1;
+        if (amb_at < 0 && ent[e].power != 0.0 && fabs(ent[e].power) <= 1e-9) amb_at = e;
+        if (amb_at < 0 && fabs(ent[e].araw - OR_ALPHA_MIN) <= amb_rel * OR_ALPHA_MIN) amb_at = e;
         if (ent[e].power > 0.0) continue;
         double a = ent[e].alpha;
         if (a < OR_ALPHA_MIN) continue;
         double Tn = T * (1.0 - a);
-        if (fabs(Tn - OR_T_MIN) <= amb_rel * OR_T_MIN) amb = 1;
+        if (amb_at < 0 && fabs(Tn - OR_T_MIN) <= amb_rel * OR_T_MIN) amb_at = e;
         if (Tn < OR_T_MIN) { stop = e; break; }
         const double* c = rgb + 3 * ent[e].id;
         C[0] += c[0] * a * T;
@@ -384,10 +388,12 @@ int or_render(int64_t n, const double* xy, const double* conic, const double* op
         C[2] += c[2] * a * T;
         hid[cnt] = ent[e].id;
         hval[cnt] = a * T;
+        hpos[cnt] = e;
         T = Tn;
         last = ent[e].id;
         ++cnt;
       }
+      const int amb = amb_at >= 0;
       for (int ch = 0; ch < 3; ++ch) image[3 * k + ch] = C[ch] + T * (bg ? bg[ch] : 0.0);
       T_final[k] = T;
       last_id[k] = (int32_t)last;
@@ -397,14 +403,15 @@ int or_render(int64_t n, const double* xy, const double* conic, const double* op
 #pragma omp critical(or_importance)
 #endif
       {
-        if (!amb) {
-          for (int64_t e = 0; e < cnt; ++e)
-            if (hval[e] > h[hid[e]]) h[hid[e]] = hval[e];
-        } else if (h_amb) {
+        /* entries composited before the first near-threshold decision are unaffected by
+           how that decision falls; the rest go to h_amb */
+        for (int64_t e = 0; e < cnt; ++e)
+          if ((!amb || hpos[e] < amb_at) && hval[e] > h[hid[e]]) h[hid[e]] = hval[e];
+        if (amb && h_amb) {
           double Tp = 1.0;
           for (int64_t e = 0; e < ne && e <= stop; ++e) {
             double val = ent[e].alpha * Tp;
-            if (val > h_amb[ent[e].id]) h_amb[ent[e].id] = val;
+            if (e >= amb_at && val > h_amb[ent[e].id]) h_amb[ent[e].id] = val;
             if (ent[e].power <= 0.0 && ent[e].alpha >= OR_ALPHA_MIN) Tp *= (1.0 - ent[e].alpha);
           }
         }
@@ -413,6 +420,7 @@ int or_render(int64_t n, const double* xy, const double* conic, const double* op
     free(ent);
     free(hid);
     free(hval);
+    free(hpos);
   }
   free(cell_start);
   free(cell_list);

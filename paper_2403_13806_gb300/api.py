@@ -353,3 +353,13 @@ class RadSplatFunction(torch.autograd.Function):
         render_backward(g, ctx.vb, ctx.proj, ctx.bins, T_final, last, dL_dimage.contiguous(), grads,
                         ctx.rast.ws_bwd, ctx.rast.cfg)
         return (*grads, None, None, None)
+
+
+def l1_loss(image: torch.Tensor, target: torch.Tensor, dL_dimage: Optional[torch.Tensor] = None,
+            loss: Optional[torch.Tensor] = None, stream=None):
+    """Mean |image - target| (float64 [1]) and its gradient (rs_l1_loss)."""
+    n = image.numel()
+    g = torch.empty_like(image) if dL_dimage is None else dL_dimage
+    l = torch.empty(1, dtype=torch.float64, device=image.device) if loss is None else loss
+    N.call("rs_l1_loss", _ptr(image), _ptr(target), n, _ptr(g), _ptr(l), _stream(stream))
+    return l, g

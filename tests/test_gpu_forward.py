@@ -127,18 +127,29 @@ def test_images_identical_across_tile_shapes():
     assert np.array_equal(imgs[0], imgs[1]) and np.array_equal(imgs[0], imgs[2])
 
 
+def check_importance(h_gpu, h, h_amb, min_strict=0.8):
+    """h: max alpha*T over entries no near-threshold decision precedes; h_amb: over the
+    others.  Flipping an alpha decision rescales later T by at most 1/(1 - 1/255), and a
+    stop flip adds or removes the stopping entry (included in h_amb), so
+    h - tol <= h_gpu <= max(h, FLIP h_amb) + tol; where FLIP h_amb <= h + tol the two
+    bounds meet and the check is |h_gpu - h| <= tol."""
+    flip = 1.0 + 1.0 / 254.0 + 1e-4
+    upper = np.maximum(h, flip * h_amb)
+    assert np.all(h_gpu >= h - IMG_TOL)
+    assert np.all(h_gpu <= upper + IMG_TOL)
+    strict = flip * h_amb <= h + IMG_TOL
+    assert np.abs(h_gpu[strict] - h[strict]).max() <= IMG_TOL
+    assert strict.mean() >= min_strict, strict.mean()
+    assert h_gpu.max() <= 0.99
+    return strict.mean()
+
+
 def test_importance_matches_oracle():
     scene, cams = synth.config1(n=20000, n_views=4, width=320, height=208)
     out = gpu_forward(scene, cams)
     h_gpu = out["h"].view(torch.float32).cpu().numpy().astype(np.float64)
     h, h_amb = oracle.importance(scene, cams)
-    clean = (h_amb == 0) | (h_amb < h - 1e-3)
-    assert np.abs(h_gpu[clean] - h[clean]).max() <= IMG_TOL
-    rest = ~clean
-    assert np.all(h_gpu[rest] <= np.maximum(h, h_amb * 1.01)[rest] + IMG_TOL)
-    assert np.all(h_gpu[rest] >= h[rest] - IMG_TOL)
-    assert h_gpu.max() <= 0.99
-    assert rest.sum() < 0.01 * scene.n
+    check_importance(h_gpu, h, h_amb)
 
 
 def test_multiview_batch_with_subsets():
@@ -157,8 +168,7 @@ def test_multiview_batch_with_subsets():
         hv, ha = oracle.importance(scene.subset(subsets[v].astype(np.int64)), [cams[v]])
         np.maximum.at(h, subsets[v].astype(np.int64), hv)
         np.maximum.at(h_amb, subsets[v].astype(np.int64), ha)
-    clean = (h_amb == 0) | (h_amb < h - 1e-3)
-    assert np.abs(h_gpu[clean] - h[clean]).max() <= IMG_TOL
+    check_importance(h_gpu, h, h_amb)
 
 
 def test_empty_and_degenerate_inputs():
