@@ -253,8 +253,8 @@ def filter(h: torch.Tensor, t: float, mode: int, ws: Optional[Workspace] = None,
     vb.n_items = n
     nbytes = N.lib().rs_workspace_size(N.RS_STAGE_FILTER, N.ref(vb), 0)
     w = ws.get(nbytes)
-    m = torch.empty(max(n, 1), dtype=torch.uint8, device=dev) if mask is True else (mask or None)
-    ix = torch.empty(max(n, 1), dtype=torch.int32, device=dev) if idx is True else (idx or None)
+    m = torch.empty(max(n, 1), dtype=torch.uint8, device=dev) if mask is True else (None if mask is False else mask)
+    ix = torch.empty(max(n, 1), dtype=torch.int32, device=dev) if idx is True else (None if idx is False else idx)
     cnt = torch.empty(1, dtype=torch.int32, device=dev)
     hf = h.view(torch.float32) if h.dtype == torch.int32 else h
     N.call("rs_filter", _ptr(hf), n, float(t), int(mode), _ptr(m), _ptr(ix), _ptr(cnt), _ptr(w), w.numel(),

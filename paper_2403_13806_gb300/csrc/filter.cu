@@ -161,7 +161,7 @@ using namespace rs;
 
 extern "C" rs_status rs_filter(const float* h, int64_t n, float t, rs_filter_mode mode, uint8_t* mask,
                                uint32_t* idx, uint32_t* count, void* ws, size_t ws_bytes, void* stream) {
-  if (!h || !count || n < 0 || n >= ((int64_t)1 << 32)) return RS_ERR_INVALID_ARG;
+  if ((!h && n > 0) || !count || n < 0 || n >= ((int64_t)1 << 32)) return RS_ERR_INVALID_ARG;
   if (mode != RS_PRUNE_BELOW && mode != RS_KEEP_ABOVE) return RS_ERR_INVALID_ARG;
   if (!ws || ws_bytes < filter_ws_bytes(n)) return RS_ERR_WORKSPACE;
   return filter_launch(h, n, t, (int)mode, mask, idx, count, static_cast<uint32_t*>(ws),
