@@ -43,15 +43,15 @@ static BinWs bin_ws_layout(void* base, int64_t n_items, int64_t capacity) {
   const size_t ni = (size_t)(n_items > 0 ? n_items : 1);
   const size_t cap = (size_t)(capacity > 0 ? capacity : 1);
   const int64_t nblk = (n_items + kEmitThreads - 1) / kEmitThreads;
-  w.grid_depth = radix::grid_for(n_items, 2 * kNumSMs);
-  w.grid_tile = radix::grid_for(capacity, 2 * kNumSMs);
+  w.grid_depth = radix::grid_for(n_items);
+  w.grid_tile = radix::grid_for(capacity);
   const int hist_grid = w.grid_depth > w.grid_tile ? w.grid_depth : w.grid_tile;
   for (int i = 0; i < 2; ++i) w.dkeys[i] = reinterpret_cast<uint32_t*>(take(ni * 4));
   for (int i = 0; i < 2; ++i) w.dvals[i] = reinterpret_cast<uint32_t*>(take(ni * 4));
   w.bsum = reinterpret_cast<unsigned long long*>(take((size_t)(nblk > 0 ? nblk : 1) * 8));
   for (int i = 0; i < 2; ++i) w.tkeys[i] = reinterpret_cast<uint32_t*>(take(cap * 4));
   w.tvals = reinterpret_cast<uint32_t*>(take(cap * 4));
-  w.hist = reinterpret_cast<uint32_t*>(take(radix::hist_bytes(hist_grid)));
+  w.hist = reinterpret_cast<uint32_t*>(take(radix::scratch_words(hist_grid) * 4));
   w.counters = reinterpret_cast<uint32_t*>(take(64));
   w.bytes = off;
   return w;
@@ -201,14 +201,35 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
   }
 }
 
+// Tile boundaries of the sorted tile ids: each thread owns 4 consecutive keys (one 16-byte
+// load) and compares across its neighbours.  A key outside [0, n_tiles) can only come from
+// a rect outside its view's tile grid and is ignored.
 __global__ void k_ranges(const uint32_t* __restrict__ tkeys, const uint32_t* __restrict__ counters,
                          uint32_t n_tiles, uint32_t* __restrict__ ranges) {
   const int64_t K = counters[0];
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t t = tkeys[k];
-    if (t >= n_tiles) continue;   // only a rect outside its view's tile grid could produce this
-    if (k == 0 || tkeys[k - 1] != t) ranges[2 * (int64_t)t] = (uint32_t)k;
-    if (k == K - 1 || tkeys[k + 1] != t) ranges[2 * (int64_t)t + 1] = (uint32_t)(k + 1);
+  const int64_t n4 = (K + 3) / 4;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k0 = 4 * q;
+    uint32_t t[4];
+    if (k0 + 3 < K) {
+      const uint4 v = *reinterpret_cast<const uint4*>(tkeys + k0);
+      t[0] = v.x; t[1] = v.y; t[2] = v.z; t[3] = v.w;
+    } else {
+      for (int j = 0; j < 4; ++j) t[j] = (k0 + j < K) ? tkeys[k0 + j] : 0xffffffffu;
+    }
+    uint32_t prev = k0 > 0 ? tkeys[k0 - 1] : 0xffffffffu;
+    const uint32_t next = (k0 + 4 < K) ? tkeys[k0 + 4] : 0xffffffffu;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t k = k0 + j;
+      if (k >= K) break;
+      const uint32_t nx = (j < 3) ? ((k + 1 < K) ? t[j + 1] : 0xffffffffu) : next;
+      if (t[j] < n_tiles) {
+        if (k == 0 || prev != t[j]) ranges[2 * (int64_t)t[j]] = (uint32_t)k;
+        if (k == K - 1 || nx != t[j]) ranges[2 * (int64_t)t[j] + 1] = (uint32_t)(k + 1);
+      }
+      prev = t[j];
+    }
   }
 }
 
@@ -256,8 +277,7 @@ extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* 
   }
   // 1) items by depth (four 8-bit passes; even count leaves the result in buffer 0)
   k_depth_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rgb_d, n, w.dkeys[0], w.dvals[0]);
-  radix::sort_pairs(w.dkeys[0], w.dvals[0], w.dkeys[1], w.dvals[1], n, nullptr, n, 32, w.hist, w.grid_depth, s,
-                    false);
+  radix::sort_pairs(w.dkeys[0], w.dvals[0], w.dkeys[1], w.dvals[1], n, nullptr, 32, w.hist, w.grid_depth, s, false);
   const uint32_t* order = w.dvals[0];
   // 2) instance offsets in depth order and K
   const int64_t nblk = (n + kEmitThreads - 1) / kEmitThreads;
@@ -271,7 +291,7 @@ extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* 
   k_emit<<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n, proj->n_tiles, reinterpret_cast<const ushort4*>(proj->rect),
                                                  batch->views, batch->n_views, w.bsum, cap, w.tkeys[0], v_first);
   // 4) stable sort of the instances on the tile id
-  const int cur = radix::sort_pairs(w.tkeys[0], v_first, w.tkeys[1], v_second, 0, w.counters, cap, tbits, w.hist,
+  const int cur = radix::sort_pairs(w.tkeys[0], v_first, w.tkeys[1], v_second, 0, w.counters, tbits, w.hist,
                                     w.grid_tile, s, true);
   const uint32_t* tk = w.tkeys[cur];
   // 5) per-tile ranges and (optionally) the 64-bit keys
