@@ -1,16 +1,19 @@
 // rs_render / rs_importance: per-tile front-to-back compositing, Eq. (render-gs), with the
 // importance max of Eq. (importance-score) fused in.
 //
-// One CTA per (view, tile), one thread per pixel.  The tile's sorted list is consumed in
-// batches of one record per thread, staged into shared memory in blend-ready form
-// (conic pre-scaled to the log2 domain), so that the inner loop per (pixel, Gaussian) pair
-// is FP32 arithmetic plus one ex2.  A CTA stops fetching batches once every pixel is done
-// (__syncthreads_count), and a warp leaves a batch early once all of its lanes are done.
+// One CTA per (view, tile); each thread owns two vertically adjacent pixels, so every
+// Gaussian record read from shared memory serves two pixel evaluations.  The tile's sorted
+// list is consumed in batches of two records per thread, staged into shared memory in
+// blend-ready form (conic pre-scaled to the log2 domain), so the inner loop per
+// (pixel, Gaussian) pair is FP32 arithmetic plus one ex2.  A CTA stops fetching batches
+// once every pixel is done (__syncthreads_count), and a warp leaves a batch early once all
+// of its pixels are done.
 // Importance: composited alpha*T values are max-reduced across the warp (redux.sync on the
 // float bits, which order like the values for non-negative floats), then across the CTA in
 // shared memory, then one global atomicMax per (tile, Gaussian).
 #include <math.h>
 
+#include "blend.cuh"
 #include "radsplat.h"
 #include "rs_common.cuh"
 
@@ -33,14 +36,44 @@ struct RenderArgs {
   int64_t n_gaussians;
 };
 
+struct PixelState {
+  float T, c0, c1, c2;
+  int last;
+  bool done;
+};
+
+// One (pixel, Gaussian) step of the blend rule; returns the composited weight alpha*T
+// (0 if the entry was skipped or compositing stopped here).
+__device__ __forceinline__ float blend_step(PixelState& s, const float4& g, const float4& g2, const float4& col,
+                                            float fu, float fv, int pos) {
+  if (s.done) return 0.f;
+  const float p2 = blend_power(g, g2, fu, fv);
+  if (!(p2 <= 0.f && p2 >= g2.y)) return 0.f;
+  const float alpha = fminf(kAlphaMax, __fmul_rn(g2.z, exp2f(p2)));
+  if (alpha < kAlphaMin) return 0.f;
+  const float Tn = s.T * (1.f - alpha);
+  if (Tn < kTMin) {
+    s.done = true;
+    return 0.f;
+  }
+  const float w = alpha * s.T;
+  s.c0 = fmaf(w, col.x, s.c0);
+  s.c1 = fmaf(w, col.y, s.c1);
+  s.c2 = fmaf(w, col.z, s.c2);
+  s.T = Tn;
+  s.last = pos + 1;
+  return w;
+}
+
 template <int TW, int TH, bool IMAGE, bool IMPORTANCE>
-__global__ void __launch_bounds__(TW* TH) k_render(RenderArgs a) {
-  constexpr int NT = TW * TH;
-  __shared__ float4 s_geo[NT];     // (x, y, A, B)   A,B,C: conic times -log2(e)/2, -log2(e), -log2(e)/2
-  __shared__ float4 s_geo2[NT];    // (C, cut, o, 0) cut: below it alpha < 1/255 for sure
-  __shared__ float4 s_col[NT];     // (r, g, b, 0)
-  __shared__ uint32_t s_h[IMPORTANCE ? NT : 1];
-  __shared__ uint32_t s_gid[IMPORTANCE ? NT : 1];
+__global__ void __launch_bounds__(TW* TH / 2) k_render(RenderArgs a) {
+  constexpr int NT = TW * TH / 2;   // threads; each owns pixels (x, 2r) and (x, 2r + 1)
+  constexpr int NB = 2 * NT;        // records per batch
+  __shared__ float4 s_geo[NB];
+  __shared__ float4 s_geo2[NB];
+  __shared__ float4 s_col[NB];
+  __shared__ uint32_t s_h[IMPORTANCE ? NB : 1];
+  __shared__ uint32_t s_gid[IMPORTANCE ? NB : 1];
 
   const int tile = blockIdx.x;
   const int v = find_view_by_tile(a.views, a.n_views, tile);
@@ -51,95 +84,82 @@ __global__ void __launch_bounds__(TW* TH) k_render(RenderArgs a) {
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int pu = txi * TW + (tid % TW);
-  const int pv = tyi * TH + (tid / TW);
-  const bool inside = pu < cam.width && pv < cam.height;
-  const float fu = (float)pu, fv = (float)pv;
+  const int pv0 = tyi * TH + 2 * (tid / TW);
+  const bool in0 = pu < cam.width && pv0 < cam.height;
+  const bool in1 = pu < cam.width && pv0 + 1 < cam.height;
+  const float fu = (float)pu, fv0 = (float)pv0, fv1 = (float)(pv0 + 1);
   const uint2 rg = a.ranges[tile];
   const uint32_t start = rg.x, end = rg.y;
 
-  float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f;
-  int last = 0;
-  bool done = !inside;
+  PixelState s0{1.f, 0.f, 0.f, 0.f, 0, !in0};
+  PixelState s1{1.f, 0.f, 0.f, 0.f, 0, !in1};
 
-  for (uint32_t b0 = start; b0 < end; b0 += NT) {
-    if (__syncthreads_count(!done) == 0) break;
-    const int nb = (int)min((uint32_t)NT, end - b0);
-    if (tid < nb) {
-      const uint32_t item = __ldg(a.vals + b0 + tid);
-      const float2 p = __ldg(a.xy + item);
-      const float4 co = __ldg(a.conic_o + item);
-      const float4 cd = __ldg(a.rgb_d + item);
-      const float A = -0.5f * kLog2e * co.x, B = -kLog2e * co.y, C = -0.5f * kLog2e * co.z;
-      // alpha = o 2^p2 < 1/255  <=>  p2 < log2(1/(255 o)); the cut sits a little below so
-      // that only surely-skipped pairs avoid the exact test
-      const float cut = log2f(kAlphaMin / co.w) - 1e-3f;
-      s_geo[tid] = make_float4(p.x, p.y, A, B);
-      s_geo2[tid] = make_float4(C, cut, co.w, 0.f);
-      s_col[tid] = make_float4(cd.x, cd.y, cd.z, 0.f);
-      if (IMPORTANCE) {
-        s_h[tid] = 0u;
-        s_gid[tid] = a.subset ? __ldg(a.subset + item) : (uint32_t)((int64_t)item - cam.item_base);
-      }
-    }
-    __syncthreads();
-    for (int j = 0; j < nb; ++j) {
-      float w = 0.f;
-      if (!done) {
-        const float4 g = s_geo[j];
-        const float4 g2 = s_geo2[j];
-        const float dx = g.x - fu, dy = g.y - fv;
-        const float p2 = dx * fmaf(g.z, dx, g.w * dy) + g2.x * dy * dy;
-        if (p2 <= 0.f && p2 >= g2.y) {
-          const float alpha = fminf(kAlphaMax, g2.z * exp2f(p2));
-          if (alpha >= kAlphaMin) {
-            const float Tn = T * (1.f - alpha);
-            if (Tn < kTMin) {
-              done = true;
-            } else {
-              w = alpha * T;
-              const float4 col = s_col[j];
-              c0 = fmaf(w, col.x, c0);
-              c1 = fmaf(w, col.y, c1);
-              c2 = fmaf(w, col.z, c2);
-              T = Tn;
-              last = (int)(b0 - start) + j + 1;
-            }
-          }
+  for (uint32_t b0 = start; b0 < end; b0 += NB) {
+    if (__syncthreads_count(!(s0.done && s1.done)) == 0) break;
+    const int nb = (int)min((uint32_t)NB, end - b0);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int slot = tid + k * NT;
+      if (slot < nb) {
+        const uint32_t item = __ldg(a.vals + b0 + slot);
+        stage_record(a.xy, a.conic_o, a.rgb_d, item, s_geo[slot], s_geo2[slot], s_col[slot]);
+        if (IMPORTANCE) {
+          s_h[slot] = 0u;
+          s_gid[slot] = a.subset ? __ldg(a.subset + item) : (uint32_t)((int64_t)item - cam.item_base);
         }
       }
-      if (IMPORTANCE) {
-        const uint32_t m = __reduce_max_sync(0xffffffffu, __float_as_uint(w));
-        if (lane == 0 && m) atomicMax(&s_h[j], m);
-      }
-      if (__all_sync(0xffffffffu, done)) break;
     }
     __syncthreads();
-    if (IMPORTANCE && tid < nb) {
-      const uint32_t m = s_h[tid];
-      if (m && (int64_t)s_gid[tid] < a.n_gaussians) atomicMax(a.importance + s_gid[tid], m);
+    const int base = (int)(b0 - start);
+    for (int j = 0; j < nb; ++j) {
+      const float4 g = s_geo[j];
+      const float4 g2 = s_geo2[j];
+      const float4 col = s_col[j];
+      const float w0 = blend_step(s0, g, g2, col, fu, fv0, base + j);
+      const float w1 = blend_step(s1, g, g2, col, fu, fv1, base + j);
+      if (IMPORTANCE) {
+        const uint32_t m = __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(w0, w1)));
+        if (lane == 0 && m) atomicMax(&s_h[j], m);
+      }
+      if (__all_sync(0xffffffffu, s0.done && s1.done)) break;
+    }
+    __syncthreads();
+    if (IMPORTANCE) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const int slot = tid + k * NT;
+        if (slot < nb) {
+          const uint32_t m = s_h[slot];
+          if (m && (int64_t)s_gid[slot] < a.n_gaussians) atomicMax(a.importance + s_gid[slot], m);
+        }
+      }
     }
   }
 
-  if (inside) {
-    const int64_t HW = (int64_t)cam.width * cam.height;
-    const int64_t pix = (int64_t)pv * cam.width + pu;
+  const int64_t HW = (int64_t)cam.width * cam.height;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const PixelState& s = k ? s1 : s0;
+    if (k ? !in1 : !in0) continue;
+    const int64_t pix = (int64_t)(pv0 + k) * cam.width + pu;
     if (IMAGE) {
       float* img = a.image + 3 * cam.pixel_base;
-      img[pix] = c0 + T * a.bg0;
-      img[HW + pix] = c1 + T * a.bg1;
-      img[2 * HW + pix] = c2 + T * a.bg2;
+      img[pix] = s.c0 + s.T * a.bg0;
+      img[HW + pix] = s.c1 + s.T * a.bg1;
+      img[2 * HW + pix] = s.c2 + s.T * a.bg2;
     }
-    if (a.T_final) a.T_final[cam.pixel_base + pix] = T;
-    if (a.last) a.last[cam.pixel_base + pix] = last;
+    if (a.T_final) a.T_final[cam.pixel_base + pix] = s.T;
+    if (a.last) a.last[cam.pixel_base + pix] = s.last;
   }
 }
 
 template <int TW, int TH>
 static void launch_render(const RenderArgs& a, int n_tiles, bool image, bool imp, cudaStream_t s) {
-  if (image && imp) k_render<TW, TH, true, true><<<n_tiles, TW * TH, 0, s>>>(a);
-  else if (image) k_render<TW, TH, true, false><<<n_tiles, TW * TH, 0, s>>>(a);
-  else if (imp) k_render<TW, TH, false, true><<<n_tiles, TW * TH, 0, s>>>(a);
-  else k_render<TW, TH, false, false><<<n_tiles, TW * TH, 0, s>>>(a);
+  constexpr int NT = TW * TH / 2;
+  if (image && imp) k_render<TW, TH, true, true><<<n_tiles, NT, 0, s>>>(a);
+  else if (image) k_render<TW, TH, true, false><<<n_tiles, NT, 0, s>>>(a);
+  else if (imp) k_render<TW, TH, false, true><<<n_tiles, NT, 0, s>>>(a);
+  else k_render<TW, TH, false, false><<<n_tiles, NT, 0, s>>>(a);
 }
 
 rs_status render_dispatch(const rs_projected* proj, const rs_bins* bins, const rs_view_batch* batch,

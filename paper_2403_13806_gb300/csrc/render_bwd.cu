@@ -1,16 +1,17 @@
 // rs_render_backward: derivative of Eq. (render-gs) (training loss of Sec. 3.2), in two
 // kernels.
 //
-// k_render_bwd -- one CTA per (view, tile), one thread per pixel, the tile list walked back
+// k_render_bwd -- one CTA per (view, tile), two pixels per thread, the tile list walked back
 //   to front from the largest `last` of the tile.  Each pixel recovers T_j = T_{j+1}/(1-a_j)
 //   from its T_final and accumulates, per composited entry j,
 //     dL/dc_j     = a_j T_j dL/dC
 //     dL/da_j     = T_j (c_j . dL/dC) - (S_j . dL/dC + T_final bg . dL/dC) / (1 - a_j)
 //   (S_j: colour composited behind j), and through a = o exp(power) (no gradient where the
 //   0.99 clamp is active) the image-space gradients of the mean, conic and opacity.  The
-//   nine per-pair values are summed across the warp (butterfly shuffles, only for entries
-//   some lane composited), across the CTA in shared memory, and added to per-item buffers
-//   with two float4 and one float atomic per (tile, entry).
+//   nine values of a thread's two pixels are summed in registers, across the warp by
+//   recursive halving (16 shuffles, only for entries some lane composited), across the
+//   CTA through per-warp shared-memory slots, and added to per-item buffers with two
+//   float4 and one float atomic per (tile, entry).
 // k_project_bwd -- one thread per Gaussian (all views of the Gaussian summed in registers)
 //   or, for visibility-list batches, one thread per item with atomic adds; chains the
 //   image-space gradients through the inverse 2x2 conic, Sigma' = (T R S)(T R S)^T + eps I,
@@ -19,6 +20,7 @@
 #include <math.h>
 
 #include "radsplat.h"
+#include "blend.cuh"
 #include "rs_common.cuh"
 #include "sh.cuh"
 
@@ -45,15 +47,81 @@ struct BwdBlendArgs {
   Grad2D g;
 };
 
+// Per-pixel state of the back-to-front walk.
+struct BwdPixel {
+  float T;      // transmittance after the current entry (T_final at the start)
+  float G0, G1, G2;
+  float bgG;    // T_final * (bg . dL/dC)
+  float SG;     // (colour composited behind the current entry) . dL/dC
+  int last;     // entries at positions >= last were not composited
+};
+
+// Adds the nine image-space gradient terms of entry e of one pixel into r (slots 0..8:
+// d/dx, d/dy, d/da, d/db, d/dc, d/do, d/dr, d/dg, d/db(lue)); returns whether the entry was
+// composited for this pixel.  The skip decisions replay the forward ones exactly.
+__device__ __forceinline__ bool bwd_step(BwdPixel& p, const float4& g, const float4& g2, const float4& col, float fu,
+                                         float fv, int e, float* r) {
+  if (e >= p.last) return false;
+  const float p2 = blend_power(g, g2, fu, fv);
+  if (!(p2 <= 0.f && p2 >= g2.y)) return false;
+  const float ex = exp2f(p2);
+  const float raw = __fmul_rn(g2.z, ex);
+  const float alpha = fminf(kAlphaMax, raw);
+  if (alpha < kAlphaMin) return false;
+  const float inv = __fdividef(1.f, 1.f - alpha);
+  const float Tj = p.T * inv;
+  const float w = alpha * Tj;
+  const float cG = col.x * p.G0 + col.y * p.G1 + col.z * p.G2;
+  const float dLda = Tj * cG - (p.SG + p.bgG) * inv;
+  r[6] += w * p.G0;
+  r[7] += w * p.G1;
+  r[8] += w * p.G2;
+  if (raw < kAlphaMax) {
+    const float dLdpow = dLda * alpha;          // d alpha / d power = alpha
+    r[5] += dLda * ex;                          // d alpha / d o = exp(power)
+    // power = p2 ln 2, p2 = A dx^2 + B dx dy + C dy^2 with dx = mean - pixel
+    const float dx = g.x - fu, dy = g.y - fv;
+    const float k = dLdpow * 0.6931471805599453f;
+    r[0] += k * (2.f * g.z * dx + g.w * dy);
+    r[1] += k * (g.w * dx + 2.f * g2.x * dy);
+    r[2] += -0.5f * dLdpow * dx * dx;
+    r[3] += -dLdpow * dx * dy;
+    r[4] += -0.5f * dLdpow * dy * dy;
+  }
+  p.SG = fmaf(w, cG, p.SG);
+  p.T = Tj;
+  return true;
+}
+
+// Sums v[0..15] over the warp by recursive halving: at each step a lane keeps half of its
+// values and trades the other half with its partner, so the 16 sums take 16 shuffles.
+// On return lanes 2c and 2c + 1 hold the warp total of component c.
+__device__ __forceinline__ float warp_transpose_sum16(float (&v)[16]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+    const bool hi = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const float send = hi ? v[i] : v[i + h];
+      const float keep = hi ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW* TH) k_render_bwd(BwdBlendArgs a) {
-  constexpr int NT = TW * TH;
+__global__ void __launch_bounds__(TW* TH / 2) k_render_bwd(BwdBlendArgs a) {
+  constexpr int NT = TW * TH / 2;   // threads; each owns pixels (x, 2r) and (x, 2r + 1)
   constexpr int NW = NT / 32;
-  __shared__ float4 s_geo[NT];
-  __shared__ float4 s_geo2[NT];
-  __shared__ float4 s_col[NT];
-  __shared__ uint32_t s_item[NT];
-  __shared__ float s_acc[9][NT];
+  constexpr int NB = NT;            // records per batch (one per thread: keeps shared memory < 48 KB)
+  constexpr int PS = NB + 1;        // padded stride: the nine components land in distinct banks
+  __shared__ float4 s_geo[NB];
+  __shared__ float4 s_geo2[NB];
+  __shared__ float4 s_col[NB];
+  __shared__ uint32_t s_item[NB];
+  __shared__ float s_part[NW][9 * PS];
   __shared__ int s_maxlast[NW];
 
   const int tile = blockIdx.x;
@@ -64,25 +132,31 @@ __global__ void __launch_bounds__(TW* TH) k_render_bwd(BwdBlendArgs a) {
   const int txi = local - tyi * cam.tiles_x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int pu = txi * TW + (tid % TW);
-  const int pv = tyi * TH + (tid / TW);
-  const bool inside = pu < cam.width && pv < cam.height;
-  const float fu = (float)pu, fv = (float)pv;
+  const int pv0 = tyi * TH + 2 * (tid / TW);
+  const float fu = (float)pu;
   const uint2 rg = a.ranges[tile];
   const uint32_t start = rg.x;
 
-  float T = 1.f, G0 = 0.f, G1 = 0.f, G2 = 0.f, bgG = 0.f;
-  int my_last = 0;
-  if (inside) {
-    const int64_t HW = (int64_t)cam.width * cam.height;
-    const int64_t pix = (int64_t)pv * cam.width + pu;
-    const float* gi = a.dL_dimage + 3 * cam.pixel_base;
-    G0 = gi[pix];
-    G1 = gi[HW + pix];
-    G2 = gi[2 * HW + pix];
-    T = a.T_final[cam.pixel_base + pix];
-    my_last = a.last[cam.pixel_base + pix];
-    bgG = T * (a.bg0 * G0 + a.bg1 * G1 + a.bg2 * G2);
+  BwdPixel px[2];
+  const int64_t HW = (int64_t)cam.width * cam.height;
+  const float* gi = a.dL_dimage + 3 * cam.pixel_base;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    BwdPixel& p = px[k];
+    p.T = 1.f;
+    p.G0 = p.G1 = p.G2 = p.bgG = p.SG = 0.f;
+    p.last = 0;
+    if (pu < cam.width && pv0 + k < cam.height) {
+      const int64_t pix = (int64_t)(pv0 + k) * cam.width + pu;
+      p.G0 = gi[pix];
+      p.G1 = gi[HW + pix];
+      p.G2 = gi[2 * HW + pix];
+      p.T = a.T_final[cam.pixel_base + pix];
+      p.last = a.last[cam.pixel_base + pix];
+      p.bgG = p.T * (a.bg0 * p.G0 + a.bg1 * p.G1 + a.bg2 * p.G2);
+    }
   }
+  const int my_last = max(px[0].last, px[1].last);
   int wl = my_last;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
@@ -92,94 +166,59 @@ __global__ void __launch_bounds__(TW* TH) k_render_bwd(BwdBlendArgs a) {
 #pragma unroll
   for (int w = 0; w < NW; ++w) max_last = max(max_last, s_maxlast[w]);
 
-  float SG = 0.f;   // (colour composited behind the current entry) . dL/dC
-  for (int hi = max_last; hi > 0; hi -= NT) {
-    const int lo = max(hi - NT, 0);
+  for (int hi = max_last; hi > 0; hi -= NB) {
+    const int lo = max(hi - NB, 0);
     const int nb = hi - lo;
     __syncthreads();
     if (tid < nb) {
       const uint32_t item = __ldg(a.vals + start + lo + tid);
-      const float2 p = __ldg(a.xy + item);
-      const float4 co = __ldg(a.conic_o + item);
-      const float4 cd = __ldg(a.rgb_d + item);
-      // identical staging arithmetic to the forward, so the skip decisions replay exactly
-      const float A = -0.5f * kLog2e * co.x, B = -kLog2e * co.y, C = -0.5f * kLog2e * co.z;
-      const float cut = log2f(kAlphaMin / co.w) - 1e-3f;
-      s_geo[tid] = make_float4(p.x, p.y, A, B);
-      s_geo2[tid] = make_float4(C, cut, co.w, 0.f);
-      s_col[tid] = make_float4(cd.x, cd.y, cd.z, 0.f);
+      stage_record(a.xy, a.conic_o, a.rgb_d, item, s_geo[tid], s_geo2[tid], s_col[tid]);
       s_item[tid] = item;
-#pragma unroll
-      for (int c = 0; c < 9; ++c) s_acc[c][tid] = 0.f;
     }
     __syncthreads();
+    float* part = s_part[warp];
     for (int j = nb - 1; j >= 0; --j) {
-      const int e = lo + j;     // 0-based position in the tile list
-      float r[9];
-#pragma unroll
-      for (int c = 0; c < 9; ++c) r[c] = 0.f;
-      bool act = false;
-      if (e < my_last) {
-        const float4 g = s_geo[j];
-        const float4 g2 = s_geo2[j];
-        const float dx = g.x - fu, dy = g.y - fv;
-        const float p2 = dx * fmaf(g.z, dx, g.w * dy) + g2.x * dy * dy;
-        if (p2 <= 0.f && p2 >= g2.y) {
-          const float ex = exp2f(p2);
-          const float raw = g2.z * ex;
-          const float alpha = fminf(kAlphaMax, raw);
-          if (alpha >= kAlphaMin) {
-            act = true;
-            const float one_m = 1.f - alpha;
-            const float Tj = T / one_m;
-            const float w = alpha * Tj;
-            const float4 col = s_col[j];
-            const float cG = col.x * G0 + col.y * G1 + col.z * G2;
-            const float dLda = Tj * cG - (SG + bgG) / one_m;
-            r[6] = w * G0;
-            r[7] = w * G1;
-            r[8] = w * G2;
-            if (raw < kAlphaMax) {
-              const float dLdpow = dLda * alpha;          // d alpha / d power = alpha
-              r[5] = dLda * ex;                           // d alpha / d o = exp(power)
-              // power = p2 ln 2 with p2 = A dx^2 + B dx dy + C dy^2, dx = mean - pixel
-              const float k = dLdpow * 0.6931471805599453f;
-              r[0] = k * (2.f * g.z * dx + g.w * dy);
-              r[1] = k * (g.w * dx + 2.f * g2.x * dy);
-              r[2] = -0.5f * dLdpow * dx * dx;
-              r[3] = -dLdpow * dx * dy;
-              r[4] = -0.5f * dLdpow * dy * dy;
-            }
-            SG = fmaf(w, cG, SG);
-            T = Tj;
-          }
-        }
+      const int e = lo + j;
+      if (!__any_sync(0xffffffffu, e < my_last)) {
+        if (lane < 9) part[lane * PS + j] = 0.f;
+        continue;
       }
+      const float4 g = s_geo[j];
+      const float4 g2 = s_geo2[j];
+      const float4 col = s_col[j];
+      float r[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) r[c] = 0.f;
+      bool act = bwd_step(px[0], g, g2, col, fu, (float)pv0, e, r);
+      act |= bwd_step(px[1], g, g2, col, fu, (float)(pv0 + 1), e, r);
       if (__any_sync(0xffffffffu, act)) {
-#pragma unroll
-        for (int c = 0; c < 9; ++c) {
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) r[c] += __shfl_xor_sync(0xffffffffu, r[c], o);
-        }
-        if (lane < 9) {
-          float val = r[0];
-#pragma unroll
-          for (int c = 1; c < 9; ++c) val = (lane == c) ? r[c] : val;
-          atomicAdd(&s_acc[lane][j], val);
-        }
+        const float tot = warp_transpose_sum16(r);
+        if ((lane & 1) == 0 && lane < 18) part[(lane >> 1) * PS + j] = tot;
+      } else if (lane < 9) {
+        part[lane * PS + j] = 0.f;
       }
     }
     __syncthreads();
-    if (tid < nb) {
-      const float4 va = make_float4(s_acc[0][tid], s_acc[1][tid], s_acc[2][tid], s_acc[3][tid]);
-      const float4 vb = make_float4(s_acc[4][tid], s_acc[5][tid], s_acc[6][tid], s_acc[7][tid]);
-      const float vc = s_acc[8][tid];
-      if (va.x != 0.f || va.y != 0.f || va.z != 0.f || va.w != 0.f || vb.x != 0.f || vb.y != 0.f || vb.z != 0.f ||
-          vb.w != 0.f || vc != 0.f) {
-        const uint32_t item = s_item[tid];
-        atomicAdd(a.g.ga + item, va);
-        atomicAdd(a.g.gb + item, vb);
-        atomicAdd(a.g.gc + item, vc);
+    {
+      const int slot = tid;
+      if (slot < nb) {
+        float c[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          float acc = 0.f;
+#pragma unroll
+          for (int w = 0; w < NW; ++w) acc += s_part[w][q * PS + slot];
+          c[q] = acc;
+        }
+        bool nz = false;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) nz |= (c[q] != 0.f);
+        if (nz) {
+          const uint32_t item = s_item[slot];
+          atomicAdd(a.g.ga + item, make_float4(c[0], c[1], c[2], c[3]));
+          atomicAdd(a.g.gb + item, make_float4(c[4], c[5], c[6], c[7]));
+          atomicAdd(a.g.gc + item, c[8]);
+        }
       }
     }
   }
@@ -481,7 +520,7 @@ size_t backward_ws_bytes(const rs_view_batch* batch) { return bwd_ws_layout(null
 
 template <int TW, int TH>
 static void launch_bwd_blend(const BwdBlendArgs& a, int n_tiles, cudaStream_t s) {
-  k_render_bwd<TW, TH><<<n_tiles, TW * TH, 0, s>>>(a);
+  k_render_bwd<TW, TH><<<n_tiles, TW * TH / 2, 0, s>>>(a);
 }
 
 }  // namespace rs
