@@ -9,9 +9,12 @@
 // that of a stable sort of the 64-bit keys emitted in item order.
 //
 // Pipeline (one stream, no host synchronisation; K lives in device memory):
-//   k_depth_keys -> 4 depth passes -> k_count_blocks -> k_count_top (K, capacity check)
-//   -> k_emit (warp-cooperative expansion, coalesced stores) -> tile passes
+//   k_depth_keys -> 4 depth passes (reduce-then-scan radix over the N items)
+//   -> k_count_blocks -> k_count_top (K, capacity check)
+//   -> k_emit (warp-cooperative expansion, coalesced stores)
+//   -> tile passes (one single-pass look-back radix launch per 8-bit digit over the K instances)
 //   -> memset(ranges) -> k_ranges -> [k_keys]
+#include "onesweep.cuh"
 #include "radix.cuh"
 #include "radsplat.h"
 #include "rs_common.cuh"
@@ -19,6 +22,7 @@
 namespace rs {
 
 constexpr int kEmitThreads = 256;
+constexpr int64_t kOnesweepMax = (int64_t)1 << 30;   // look-back words carry 30-bit counts
 
 struct BinWs {
   uint32_t* dkeys[2];
@@ -27,6 +31,7 @@ struct BinWs {
   uint32_t* tkeys[2];
   uint32_t* tvals;
   uint32_t* hist;
+  uint32_t* sweep;            // decoupled look-back scratch of the instance sort
   uint32_t* counters;         // [0] = instances written (min(K, capacity))
   int grid_depth, grid_tile;
   size_t bytes;
@@ -52,6 +57,7 @@ static BinWs bin_ws_layout(void* base, int64_t n_items, int64_t capacity) {
   for (int i = 0; i < 2; ++i) w.tkeys[i] = reinterpret_cast<uint32_t*>(take(cap * 4));
   w.tvals = reinterpret_cast<uint32_t*>(take(cap * 4));
   w.hist = reinterpret_cast<uint32_t*>(take(radix::scratch_words(hist_grid) * 4));
+  w.sweep = capacity < kOnesweepMax ? reinterpret_cast<uint32_t*>(take(onesweep::scratch_words(capacity) * 4)) : nullptr;
   w.counters = reinterpret_cast<uint32_t*>(take(64));
   w.bytes = off;
   return w;
@@ -291,8 +297,11 @@ extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* 
   k_emit<<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n, proj->n_tiles, reinterpret_cast<const ushort4*>(proj->rect),
                                                  batch->views, batch->n_views, w.bsum, cap, w.tkeys[0], v_first);
   // 4) stable sort of the instances on the tile id
-  const int cur = radix::sort_pairs(w.tkeys[0], v_first, w.tkeys[1], v_second, 0, w.counters, tbits, w.hist,
-                                    w.grid_tile, s, true);
+  const int cur = (cap < kOnesweepMax)
+                      ? onesweep::sort_pairs(w.tkeys[0], v_first, w.tkeys[1], v_second, w.counters, cap, tbits,
+                                             w.sweep, status, s, true)
+                      : radix::sort_pairs(w.tkeys[0], v_first, w.tkeys[1], v_second, 0, w.counters, tbits, w.hist,
+                                          w.grid_tile, s, true);
   const uint32_t* tk = w.tkeys[cur];
   // 5) per-tile ranges and (optionally) the 64-bit keys
   const int rgrid = 4 * kNumSMs;
