@@ -201,6 +201,14 @@ def run_ours(args):
     st.zero_()
     barrier()
     with ClockSampler(local) as clk:
+        # keep the GPU busy for ~1 s before the timed region so the clock sampler (100 ms
+        # period) sees the clocks under this load; then time exactly `steps` replays
+        t_end = time.perf_counter() + 1.0
+        while time.perf_counter() < t_end:
+            for _ in range(8):
+                graph.replay()
+            torch.cuda.synchronize()
+        barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -221,8 +229,9 @@ def run_ours(args):
     value = ms_per_step / views_total   # whole job: all ranks' views in the max-over-ranks step time
 
     # per-stage times of the same batched step (plain launches, events on this stream)
-    stage_ms = stage_times(api, N, g, vb, cfg, st, proj, bins, ws_sort, img, T, L, h, target, dL, loss, grads, ws_bwd,
-                           ws_f, mask, idx, reps=max(3, min(args.steps, 10)))
+    stage_ms, kernel_ms = stage_times(api, N, g, vb, cfg, st, proj, bins, ws_sort, img, T, L, h, target, dL, loss,
+                                      grads, ws_bwd, ws_f, mask, idx, reps=max(3, min(args.steps, 10)))
+    pairs = int(L.to(torch.int64).sum().item())   # entries walked by the backward (sum of last over pixels)
 
     # plain: the same views one at a time, no graph
     plain = None
@@ -235,8 +244,8 @@ def run_ours(args):
 
     # roofline of the dominant kernel
     hbm, peak_kind, pk = peaks()
-    roof = roofline(stage_ms, vb, scene.n, sres, hbm, peak_kind)
-    launches = launches_per_step(vb, cap) * args.steps
+    roof = roofline(kernel_ms, vb, sres, hbm, peak_kind, pairs)
+    launches = int(round(sum(v["launches_per_step"] for v in kernel_ms.values()))) * args.steps
 
     if rank == 0:
         cpu = cpu_baseline(args)
@@ -252,6 +261,8 @@ def run_ours(args):
             "fps_forward_single_view": round(fps, 1) if fps else None,
             "instances_per_view": int(sres["n_instances"] / V),
             "stage_ms_per_step": {k: round(v, 5) for k, v in stage_ms.items()},
+            "kernel_ms_per_step": {k: round(v["ms_per_step"], 5) for k, v in
+                                   sorted(kernel_ms.items(), key=lambda kv: -kv[1]["ms_per_step"])},
             "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
             "gpu_launches": launches,
         }
@@ -263,14 +274,19 @@ def run_ours(args):
 
 def stage_times(api, N, g, vb, cfg, st, proj, bins, ws_sort, img, T, L, h, target, dL, loss, grads, ws_bwd, ws_f,
                 mask, idx, reps):
+    """Per-stage times (CUDA events around each C-ABI call) and per-kernel times (the
+    library's own launch events, rs_profile_*) of the same step with plain launches."""
     import torch
     names = ["project", "bin_sort", "render_importance", "l1", "backward", "filter"]
     acc = {k: 0.0 for k in names}
+    kern = {}
     for r in range(reps + 1):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
         h.zero_()
         for t in grads:
             t.zero_()
+        if r == 1:
+            N.profile_enable(True)
         ev[0].record()
         api.project(g, vb, cfg, st, out=proj); ev[1].record()
         api.bin_sort(proj, vb, bins, ws_sort, st); ev[2].record()
@@ -283,7 +299,14 @@ def stage_times(api, N, g, vb, cfg, st, proj, bins, ws_sort, img, T, L, h, targe
             continue   # warm-up pass
         for i, k in enumerate(names):
             acc[k] += ev[i].elapsed_time(ev[i + 1]) / reps
-    return acc
+    for name, ms in N.profile_records():
+        c = kern.setdefault(name, [0, 0.0])
+        c[0] += 1
+        c[1] += ms
+    N.profile_enable(False)
+    kernels = {k: {"launches_per_step": v[0] / reps, "ms_per_step": v[1] / reps, "ms_per_launch": v[1] / v[0]}
+               for k, v in kern.items()}
+    return acc, kernels
 
 
 def plain_loop(api, N, torch, g, vb1, cfg, target, cams, reps, dev):
@@ -390,25 +413,38 @@ def e2e_run(api, N, torch, scene, vb, cfg, target, cap, reps, dev):
             "d2h_bytes_per_step": 8}
 
 
-def launches_per_step(vb, cap):
-    """Kernels of the library per batched step (memsets are not kernels)."""
-    tiles_bits = max(1, int(np.ceil(np.log2(max(vb.n_tiles, 2)))))
-    tile_passes = (tiles_bits + 7) // 8
-    sort = 1 + 4 * 2 + 2 + 1 + tile_passes * 2 + 1     # depth keys, depth passes, count, emit, tile passes, ranges
-    return 1 + sort + 1 + 1 + 2 + 3                      # project, sort, render, l1, backward(2), filter(3)
+# FP32 lane-operations per second of the GB300: 152 SMs x 128 FP32 lanes x 2070 MHz.
+ALU_PEAK_OPS = 152 * 128 * 2070e6
+# FP32 operations per (pixel, Gaussian) pair of the blend kernels, counted from their source:
+# forward 22 (offset 2, quadratic form 5, tests 3, exp2 and scale 2, clamp and test 2,
+# transmittance 3, weight 1, colour 3, bookkeeping 1); backward 46.
+OPS_PER_PAIR = {"k_render_importance": 22, "k_render": 22, "k_render_bwd": 46}
 
 
-def roofline(stage_ms, vb, n, sres, hbm, peak_kind):
-    """HBM roofline of the projection kernel (one launch per step): algorithmic bytes =
-    236 B of parameters read per Gaussian and view + 52 B of projected record written."""
-    items = vb.n_items
-    bytes_alg = items * (236 + 52)
-    t = stage_ms["project"] / 1000.0
-    achieved = bytes_alg / t / 1e9 if t > 0 else None
-    return {"kernel": "k_project<3>", "bound": "hbm", "achieved": round(achieved, 1) if achieved else None,
-            "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4) if achieved else None,
-            "traffic": None, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-            "bytes_per_launch": int(bytes_alg)}
+def roofline(kernel_ms, vb, sres, hbm, peak_kind, pairs):
+    """Roofline of the kernel with the largest share of the step (library launch events).
+
+    Algorithmic work per launch: the instance sort pass moves 2 x K x (key + value bytes);
+    the projection 288 B per item; the emission 6 or 8 B per instance; the blend kernels
+    FP32 operations per evaluated pair (pairs = sum over pixels of entries walked)."""
+    name, rec = max(kernel_ms.items(), key=lambda kv: kv[1]["ms_per_step"])
+    t = rec["ms_per_launch"] / 1000.0
+    K = sres["n_instances"]
+    kb = 2 if vb.n_tiles <= 65536 else 4
+    hbm_bytes = {"k_onesweep": 2 * K * (kb + 4), "k_project": vb.n_items * (236 + 52), "k_emit": K * (kb + 4),
+                 "k_ranges": K * kb, "k_project_bwd": vb.n_items * (236 + 36 + 236)}
+    if name in hbm_bytes:
+        a = hbm_bytes[name] / t / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": round(a, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(a / hbm, 4), "traffic": None, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "work_per_launch": int(hbm_bytes[name]), "ms_per_launch": round(rec["ms_per_launch"], 5)}
+    ops = pairs * OPS_PER_PAIR.get(name, 0)
+    a = ops / t / 1e12
+    peak = ALU_PEAK_OPS / 1e12
+    return {"kernel": name, "bound": "alu", "achieved": round(a, 2), "peak": round(peak, 2), "unit": "TOP/s (FP32 lane ops)",
+            "frac": round(a / peak, 4), "traffic": None,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz", "work_per_launch": int(ops),
+            "ms_per_launch": round(rec["ms_per_launch"], 5)}
 
 
 # ------------------------------------------------------------------ CPU oracle

@@ -296,6 +296,20 @@ rs_status rs_render_backward(const rs_gaussians* g, const rs_view_batch* batch,
 rs_status rs_l1_loss(const float* image, const float* target, int64_t n, float* dL_dimage,
                      double* loss, void* stream);
 
+/* ---- tracing ------------------------------------------------------------------------ */
+
+/* Per-launch timing of the library's kernels (no counterpart in the paper; used to measure
+ * each kernel against its roofline).  rs_profile_enable(1) clears the records and starts
+ * bracketing every kernel launch of the library with two CUDA events on the launch's
+ * stream (launches on a stream being captured into a CUDA graph are not recorded);
+ * rs_profile_enable(0) clears and stops.  rs_profile_count() is the number of records;
+ * rs_profile_read(i, &name, &ms) waits for record i and gives the kernel's name (static
+ * string) and device time in milliseconds.  Host-side state, guarded by a mutex.
+ * Errors: RS_ERR_INVALID_ARG (index or null pointer), RS_ERR_CUDA. */
+rs_status rs_profile_enable(int32_t on);
+int32_t rs_profile_count(void);
+rs_status rs_profile_read(int32_t i, const char** name, float* ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -83,6 +83,9 @@ SIGNATURES = {
     "rs_filter_nearest": (ctypes.c_int, [P, c_int32, P, c_int32, P, P]),
     "rs_render_backward": (ctypes.c_int, [P, P, P, P, P, P, P, P, P, P, c_size_t, P]),
     "rs_l1_loss": (ctypes.c_int, [P, P, c_int64, P, P, P]),
+    "rs_profile_enable": (ctypes.c_int, [c_int32]),
+    "rs_profile_count": (c_int32, []),
+    "rs_profile_read": (ctypes.c_int, [c_int32, P, P]),
 }
 
 _lib = None
@@ -129,3 +132,19 @@ def call(fn: str, *args):
 
 def ref(x):
     return ctypes.byref(x)
+
+
+def profile_enable(on: bool):
+    call("rs_profile_enable", 1 if on else 0)
+
+
+def profile_records():
+    """[(kernel name, device ms)] of the launches recorded since profile_enable(True)."""
+    L = lib()
+    out = []
+    for i in range(L.rs_profile_count()):
+        name = ctypes.c_char_p()
+        ms = ctypes.c_float()
+        call("rs_profile_read", i, ctypes.byref(name), ctypes.byref(ms))
+        out.append((name.value.decode(), ms.value))
+    return out

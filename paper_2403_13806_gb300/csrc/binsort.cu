@@ -12,26 +12,26 @@
 //   k_depth_keys -> 4 depth passes (reduce-then-scan radix over the N items)
 //   -> k_count_blocks -> k_count_top (K, capacity check)
 //   -> k_emit (warp-cooperative expansion, coalesced stores)
-//   -> tile passes (one single-pass look-back radix launch per 8-bit digit over the K instances)
+//   -> tile passes (per-tile histogram, per-digit scan, per-tile stable scatter, per 8-bit digit)
 //   -> memset(ranges) -> k_ranges -> [k_keys]
-#include "onesweep.cuh"
+#include "radix_tiles.cuh"
 #include "radix.cuh"
+#include "profile.cuh"
 #include "radsplat.h"
 #include "rs_common.cuh"
 
 namespace rs {
 
 constexpr int kEmitThreads = 256;
-constexpr int64_t kOnesweepMax = (int64_t)1 << 30;   // look-back words carry 30-bit counts
 
 struct BinWs {
   uint32_t* dkeys[2];
   uint32_t* dvals[2];
   unsigned long long* bsum;   // per emission block: instances, then exclusive prefix
-  uint32_t* tkeys[2];
+  char* tkeys[2];
   uint32_t* tvals;
   uint32_t* hist;
-  uint32_t* sweep;            // decoupled look-back scratch of the instance sort
+  uint32_t* sweep;            // per-tile digit counters of the instance sort
   uint32_t* counters;         // [0] = instances written (min(K, capacity))
   int grid_depth, grid_tile;
   size_t bytes;
@@ -54,10 +54,10 @@ static BinWs bin_ws_layout(void* base, int64_t n_items, int64_t capacity) {
   for (int i = 0; i < 2; ++i) w.dkeys[i] = reinterpret_cast<uint32_t*>(take(ni * 4));
   for (int i = 0; i < 2; ++i) w.dvals[i] = reinterpret_cast<uint32_t*>(take(ni * 4));
   w.bsum = reinterpret_cast<unsigned long long*>(take((size_t)(nblk > 0 ? nblk : 1) * 8));
-  for (int i = 0; i < 2; ++i) w.tkeys[i] = reinterpret_cast<uint32_t*>(take(cap * 4));
+  for (int i = 0; i < 2; ++i) w.tkeys[i] = take(cap * 4);   // uint16 or uint32 tile ids
   w.tvals = reinterpret_cast<uint32_t*>(take(cap * 4));
   w.hist = reinterpret_cast<uint32_t*>(take(radix::scratch_words(hist_grid) * 4));
-  w.sweep = capacity < kOnesweepMax ? reinterpret_cast<uint32_t*>(take(onesweep::scratch_words(capacity) * 4)) : nullptr;
+  w.sweep = reinterpret_cast<uint32_t*>(take(tiles::scratch_words(capacity) * 4));
   w.counters = reinterpret_cast<uint32_t*>(take(64));
   w.bytes = off;
   return w;
@@ -142,12 +142,13 @@ __global__ void __launch_bounds__(1024) k_count_top(unsigned long long* __restri
 // Expansion: each warp takes 32 consecutive depth-sorted items and writes their
 // instances contiguously (tile ids row-major inside each rect); lanes locate the item of
 // their instance by a binary search over the warp's inclusive prefix.
+template <typename KeyT>
 __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restrict__ order, int64_t n,
                                                        const uint32_t* __restrict__ n_tiles,
                                                        const ushort4* __restrict__ rect,
                                                        const rs_view* __restrict__ views, int n_views,
                                                        const unsigned long long* __restrict__ bpre,
-                                                       int64_t capacity, uint32_t* __restrict__ tkeys,
+                                                       int64_t capacity, KeyT* __restrict__ tkeys,
                                                        uint32_t* __restrict__ tvals) {
   __shared__ uint32_t s_wtot[kEmitThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
       const uint32_t tx = r - ty * (uint32_t)o_rw;
       const unsigned long long pos = wbase + e;
       if (pos < (unsigned long long)capacity) {
-        tkeys[pos] = (uint32_t)o_tb + (uint32_t)(o_y0 + (int)ty) * (uint32_t)o_tx + (uint32_t)(o_x0 + (int)tx);
+        tkeys[pos] = (KeyT)((uint32_t)o_tb + (uint32_t)(o_y0 + (int)ty) * (uint32_t)o_tx + (uint32_t)(o_x0 + (int)tx));
         tvals[pos] = o_item;
       }
     }
@@ -210,26 +211,30 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
 // Tile boundaries of the sorted tile ids: each thread owns 4 consecutive keys (one 16-byte
 // load) and compares across its neighbours.  A key outside [0, n_tiles) can only come from
 // a rect outside its view's tile grid and is ignored.
-__global__ void k_ranges(const uint32_t* __restrict__ tkeys, const uint32_t* __restrict__ counters,
+template <typename KeyT>
+__global__ void k_ranges(const KeyT* __restrict__ tkeys, const uint32_t* __restrict__ counters,
                          uint32_t n_tiles, uint32_t* __restrict__ ranges) {
+  constexpr int V = 16 / sizeof(KeyT);   // keys per 16-byte load
   const int64_t K = counters[0];
-  const int64_t n4 = (K + 3) / 4;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t k0 = 4 * q;
-    uint32_t t[4];
-    if (k0 + 3 < K) {
-      const uint4 v = *reinterpret_cast<const uint4*>(tkeys + k0);
-      t[0] = v.x; t[1] = v.y; t[2] = v.z; t[3] = v.w;
-    } else {
-      for (int j = 0; j < 4; ++j) t[j] = (k0 + j < K) ? tkeys[k0 + j] : 0xffffffffu;
-    }
-    uint32_t prev = k0 > 0 ? tkeys[k0 - 1] : 0xffffffffu;
-    const uint32_t next = (k0 + 4 < K) ? tkeys[k0 + 4] : 0xffffffffu;
+  const int64_t nq = (K + V - 1) / V;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k0 = V * q;
+    uint32_t t[V];
+    if (k0 + V - 1 < K) {
+      const uint4 w = *reinterpret_cast<const uint4*>(tkeys + k0);
+      const KeyT* kk = reinterpret_cast<const KeyT*>(&w);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < V; ++j) t[j] = kk[j];
+    } else {
+      for (int j = 0; j < V; ++j) t[j] = (k0 + j < K) ? (uint32_t)tkeys[k0 + j] : 0xffffffffu;
+    }
+    uint32_t prev = k0 > 0 ? (uint32_t)tkeys[k0 - 1] : 0xffffffffu;
+    const uint32_t next = (k0 + V < K) ? (uint32_t)tkeys[k0 + V] : 0xffffffffu;
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
       const int64_t k = k0 + j;
       if (k >= K) break;
-      const uint32_t nx = (j < 3) ? ((k + 1 < K) ? t[j + 1] : 0xffffffffu) : next;
+      const uint32_t nx = (j < V - 1) ? ((k + 1 < K) ? t[j + 1] : 0xffffffffu) : next;
       if (t[j] < n_tiles) {
         if (k == 0 || prev != t[j]) ranges[2 * (int64_t)t[j]] = (uint32_t)k;
         if (k == K - 1 || nx != t[j]) ranges[2 * (int64_t)t[j] + 1] = (uint32_t)(k + 1);
@@ -239,7 +244,8 @@ __global__ void k_ranges(const uint32_t* __restrict__ tkeys, const uint32_t* __r
   }
 }
 
-__global__ void k_keys(const uint32_t* __restrict__ tkeys, const uint32_t* __restrict__ vals,
+template <typename KeyT>
+__global__ void k_keys(const KeyT* __restrict__ tkeys, const uint32_t* __restrict__ vals,
                        const float4* __restrict__ rgb_d, const uint32_t* __restrict__ counters,
                        unsigned long long* __restrict__ keys) {
   const int64_t K = counters[0];
@@ -254,6 +260,30 @@ static int bits_for(int64_t n) {
 }
 
 size_t bin_sort_ws_bytes(int64_t n_items, int64_t capacity) { return bin_ws_layout(nullptr, n_items, capacity).bytes; }
+
+// Expansion, stable sort of the instances on the tile id, ranges and optional keys, with
+// tile ids held as KeyT (16-bit whenever every tile id fits).
+template <typename KeyT>
+static void sort_instances(const BinWs& w, const uint32_t* order, int64_t n, const rs_projected* proj,
+                           const rs_view_batch* batch, const rs_bins* bins, int64_t cap, int64_t nblk,
+                           uint32_t* v_first, uint32_t* v_second, rs_device_status* status, cudaStream_t s) {
+  KeyT* k0 = reinterpret_cast<KeyT*>(w.tkeys[0]);
+  KeyT* k1 = reinterpret_cast<KeyT*>(w.tkeys[1]);
+  { prof::Scope ps("k_emit", s);
+  k_emit<KeyT><<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n, proj->n_tiles,
+                                                       reinterpret_cast<const ushort4*>(proj->rect), batch->views,
+                                                       batch->n_views, w.bsum, cap, k0, v_first); }
+  const int tbits = bits_for(batch->n_tiles);
+  const int cur = tiles::sort_pairs<KeyT>(k0, v_first, k1, v_second, w.counters, cap, tbits, w.sweep, s, true);
+  const KeyT* tk = cur ? k1 : k0;
+  const int rgrid = 4 * kNumSMs;
+  { prof::Scope ps("k_ranges", s);
+  k_ranges<KeyT><<<rgrid, 256, 0, s>>>(tk, w.counters, (uint32_t)batch->n_tiles, bins->ranges); }
+  prof::Scope ps("k_keys", s);
+  if (bins->keys)
+    k_keys<KeyT><<<rgrid, 256, 0, s>>>(tk, bins->vals, reinterpret_cast<const float4*>(proj->rgb_d), w.counters,
+                                       reinterpret_cast<unsigned long long*>(bins->keys));
+}
 
 }  // namespace rs
 
@@ -282,31 +312,24 @@ extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* 
     return launch_status();
   }
   // 1) items by depth (four 8-bit passes; even count leaves the result in buffer 0)
-  k_depth_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rgb_d, n, w.dkeys[0], w.dvals[0]);
+  { prof::Scope ps("k_depth_keys", s);
+  k_depth_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rgb_d, n, w.dkeys[0], w.dvals[0]); }
   radix::sort_pairs(w.dkeys[0], w.dvals[0], w.dkeys[1], w.dvals[1], n, nullptr, 32, w.hist, w.grid_depth, s, false);
   const uint32_t* order = w.dvals[0];
   // 2) instance offsets in depth order and K
   const int64_t nblk = (n + kEmitThreads - 1) / kEmitThreads;
-  k_count_blocks<<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n, proj->n_tiles, w.bsum);
-  k_count_top<<<1, 1024, 0, s>>>(w.bsum, nblk, cap, w.counters, status);
+  { prof::Scope ps("k_count_blocks", s);
+  k_count_blocks<<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n, proj->n_tiles, w.bsum); }
+  { prof::Scope ps("k_count_top", s);
+  k_count_top<<<1, 1024, 0, s>>>(w.bsum, nblk, cap, w.counters, status); }
   // 3) expansion; the tile passes then ping-pong so that the final values land in bins->vals
   const int tbits = bits_for(batch->n_tiles);
   const int passes = radix::sort_passes(tbits);
   uint32_t* v_first = (passes % 2 == 0) ? bins->vals : w.tvals;
   uint32_t* v_second = (passes % 2 == 0) ? w.tvals : bins->vals;
-  k_emit<<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n, proj->n_tiles, reinterpret_cast<const ushort4*>(proj->rect),
-                                                 batch->views, batch->n_views, w.bsum, cap, w.tkeys[0], v_first);
-  // 4) stable sort of the instances on the tile id
-  const int cur = (cap < kOnesweepMax)
-                      ? onesweep::sort_pairs(w.tkeys[0], v_first, w.tkeys[1], v_second, w.counters, cap, tbits,
-                                             w.sweep, status, s, true)
-                      : radix::sort_pairs(w.tkeys[0], v_first, w.tkeys[1], v_second, 0, w.counters, tbits, w.hist,
-                                          w.grid_tile, s, true);
-  const uint32_t* tk = w.tkeys[cur];
-  // 5) per-tile ranges and (optionally) the 64-bit keys
-  const int rgrid = 4 * kNumSMs;
-  k_ranges<<<rgrid, 256, 0, s>>>(tk, w.counters, (uint32_t)batch->n_tiles, bins->ranges);
-  if (bins->keys)
-    k_keys<<<rgrid, 256, 0, s>>>(tk, bins->vals, rgb_d, w.counters, reinterpret_cast<unsigned long long*>(bins->keys));
+  if (batch->n_tiles <= 65536)
+    sort_instances<uint16_t>(w, order, n, proj, batch, bins, cap, nblk, v_first, v_second, status, s);
+  else
+    sort_instances<uint32_t>(w, order, n, proj, batch, bins, cap, nblk, v_first, v_second, status, s);
   return launch_status();
 }

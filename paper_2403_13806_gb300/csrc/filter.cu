@@ -6,6 +6,7 @@
 // byte mask), one exclusive scan of the block counts, and an order-preserving scatter of
 // the indices (block-local scan with warp ballots).  The block counts are the only
 // scratch memory (4 bytes per 4096 elements).
+#include "profile.cuh"
 #include "radsplat.h"
 #include "rs_common.cuh"
 
@@ -149,8 +150,11 @@ rs_status filter_launch(const float* h, int64_t n, float t, int mode, uint8_t* m
     if (cudaMemsetAsync(count, 0, sizeof(uint32_t), s) != cudaSuccess) return RS_ERR_CUDA;
     return RS_OK;
   }
-  k_filter_count<<<(unsigned)nblk, kFiltThreads, 0, s>>>(h, n, t, mode, mask, bcount);
-  k_filter_scan<<<1, 1024, 0, s>>>(bcount, nblk, count);
+  { prof::Scope ps("k_filter_count", s);
+  k_filter_count<<<(unsigned)nblk, kFiltThreads, 0, s>>>(h, n, t, mode, mask, bcount); }
+  { prof::Scope ps("k_filter_scan", s);
+  k_filter_scan<<<1, 1024, 0, s>>>(bcount, nblk, count); }
+  prof::Scope ps("k_filter_scatter", s);
   if (idx) k_filter_scatter<<<(unsigned)nblk, kFiltThreads, 0, s>>>(h, n, t, mode, bcount, idx);
   return launch_status();
 }
@@ -173,6 +177,7 @@ extern "C" rs_status rs_filter_nearest(const float* centres, int32_t k, const fl
   if (!centres || !cam_centres || !out || k <= 0 || n_cams < 0 || k > 4096) return RS_ERR_INVALID_ARG;
   if (n_cams == 0) return RS_OK;
   const int threads = 128;
+  prof::Scope ps("k_nearest", reinterpret_cast<cudaStream_t>(stream));
   k_nearest<<<(n_cams + threads - 1) / threads, threads, (size_t)k * 3 * sizeof(float),
               reinterpret_cast<cudaStream_t>(stream)>>>(centres, k, cam_centres, n_cams, out);
   return launch_status();

@@ -1,4 +1,5 @@
 // rs_l1_loss: mean absolute error and its gradient (one HBM-bound pass).
+#include "profile.cuh"
 #include "radsplat.h"
 #include "rs_common.cuh"
 
@@ -51,6 +52,7 @@ extern "C" rs_status rs_l1_loss(const float* image, const float* target, int64_t
   const bool vec = aligned<float4>(image, 16) && aligned<float4>(target, 16) && aligned<float4>(dL_dimage, 16);
   const int64_t n4 = vec ? n / 4 : 0;
   const int grid = 4 * kNumSMs;
+  prof::Scope ps("k_l1", s);
   k_l1<<<grid, 256, 0, s>>>(reinterpret_cast<const float4*>(image), reinterpret_cast<const float4*>(target), n4,
                             image, target, n, 1.0f / (float)n, reinterpret_cast<float4*>(dL_dimage), dL_dimage, loss);
   return launch_status();

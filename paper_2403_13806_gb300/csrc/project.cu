@@ -5,6 +5,7 @@
 // ushort4 and one uint32 per item.  The kernel is bound by HBM bandwidth.
 #include <math.h>
 
+#include "profile.cuh"
 #include "radsplat.h"
 #include "rs_common.cuh"
 #include "sh.cuh"
@@ -198,6 +199,7 @@ extern "C" rs_status rs_project(const rs_gaussians* g, const rs_view_batch* batc
   const int64_t blocks = (batch->n_items + threads - 1) / threads;
   if (blocks > 0x7fffffffLL) return RS_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  prof::Scope ps("k_project", s);
   switch (g->sh_degree) {
     case 0: k_project<0><<<(unsigned)blocks, threads, 0, s>>>(a); break;
     case 1: k_project<1><<<(unsigned)blocks, threads, 0, s>>>(a); break;

@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "profile.cuh"
+
 namespace rs {
 namespace radix {
 
@@ -257,9 +259,12 @@ inline int sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, in
     uint32_t* vi = cur ? v1 : v0;
     uint32_t* ko = cur ? k0 : k1;
     uint32_t* vo = cur ? v0 : v1;
-    k_upsweep<<<grid, kThreads, 0, s>>>(ki, n_host, n_dev, shift, rb, hist);
-    k_hist_scan<<<1 << rb, kThreads, 0, s>>>(hist, grid, rb, off, tot);
+    { ::rs::prof::Scope ps("k_upsweep", s);
+    k_upsweep<<<grid, kThreads, 0, s>>>(ki, n_host, n_dev, shift, rb, hist); }
+    { ::rs::prof::Scope ps("k_hist_scan", s);
+    k_hist_scan<<<1 << rb, kThreads, 0, s>>>(hist, grid, rb, off, tot); }
     const bool last = (p == passes - 1);
+    ::rs::prof::Scope ps("k_downsweep", s);
     k_downsweep<<<grid, kThreads, 0, s>>>(ki, vi, (last && !write_last_keys) ? nullptr : ko, vo, n_host, n_dev,
                                           shift, rb, off, tot);
     cur ^= 1;

@@ -1,0 +1,254 @@
+// Stable LSD radix sort of (key, uint32 value) pairs for large inputs such as the
+// duplicated tile instances: one CTA per tile of 2048 keys in every kernel, and no waits
+// between CTAs.  Keys are 16-bit when every key fits (fewer bytes per pass), else 32-bit.
+//
+// A pass over one digit (<= 8 bits) is three kernels:
+//   k_tile_hist  -- per tile: its digit histogram, stored digit-major cnt[d][tile];
+//   k_tile_scan  -- one CTA per digit: exclusive prefix of cnt[d][.] over the tiles (in
+//                   place) and the digit's total;
+//   k_tile_sort  -- per tile: digit bases (exclusive prefix of the totals) plus the tile's
+//                   prefixes give the global position of its first key of each digit; the
+//                   tile's keys are ranked stably (warp match and per-warp counters),
+//                   reordered by digit in shared memory, and each digit run is stored
+//                   contiguously.
+// The per-tile counters cost 2 x 1 KB per 2048 keys of extra traffic per pass and make
+// every tile independent, so the scatter runs at full occupancy.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "profile.cuh"
+#include "radix.cuh"
+
+namespace rs {
+namespace tiles {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 8;
+constexpr int kTile = kThreads * kItems;   // 2048
+constexpr int kR = 256;
+
+template <typename KeyT, int TILE = kTile>
+__global__ void __launch_bounds__(kThreads) k_tile_hist(const KeyT* __restrict__ keys, const uint32_t* __restrict__ n_dev,
+                                                        int shift, int rbits, int64_t n_tiles_max,
+                                                        uint32_t* __restrict__ cnt) {
+  __shared__ uint32_t s[kWarps][kR];
+  const int warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kWarps * kR; i += kThreads) (&s[0][0])[i] = 0u;
+  __syncthreads();
+  const int64_t n = *n_dev;
+  const int64_t tile = blockIdx.x;
+  const int64_t t0 = tile * TILE;
+  const uint32_t mask = (1u << rbits) - 1u;
+  if (t0 < n) {
+    const int tn = (int)min((int64_t)TILE, n - t0);
+    constexpr int kVec = 16 / sizeof(KeyT);
+    if (tn == TILE) {
+      const uint4* kv = reinterpret_cast<const uint4*>(keys + t0);
+      for (int i = threadIdx.x; i < TILE / kVec; i += kThreads) {
+        const uint4 w = __ldcs(kv + i);
+        const KeyT* k = reinterpret_cast<const KeyT*>(&w);
+#pragma unroll
+        for (int j = 0; j < kVec; ++j) atomicAdd(&s[warp][((uint32_t)k[j] >> shift) & mask], 1u);
+      }
+    } else {
+      for (int i = threadIdx.x; i < tn; i += kThreads)
+        atomicAdd(&s[warp][((uint32_t)keys[t0 + i] >> shift) & mask], 1u);
+    }
+  }
+  __syncthreads();
+  const int d = threadIdx.x;
+  uint32_t c = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) c += s[w][d];
+  cnt[(int64_t)d * n_tiles_max + tile] = c;   // zero for tiles past the count
+}
+
+// One CTA per digit d: exclusive prefix of cnt[d][0 .. n_tiles) in place; tot[d] = total.
+__global__ void __launch_bounds__(1024) k_tile_scan(uint32_t* __restrict__ cnt, int64_t n_tiles,
+                                                    uint32_t* __restrict__ tot) {
+  __shared__ uint32_t s_w[32];
+  __shared__ uint32_t s_carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* row = cnt + (int64_t)blockIdx.x * n_tiles;
+  if (threadIdx.x == 0) s_carry = 0u;
+  __syncthreads();
+  for (int64_t b0 = 0; b0 < n_tiles; b0 += 4 * 1024) {
+    // four consecutive entries per thread
+    const int64_t b = b0 + 4 * (int64_t)threadIdx.x;
+    uint32_t v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = (b + j < n_tiles) ? row[b + j] : 0u;
+    const uint32_t sum = v[0] + v[1] + v[2] + v[3];
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = s_w[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      s_w[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = s_carry + (warp ? s_w[warp - 1] : 0u) + x - sum;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (b + j < n_tiles) row[b + j] = run;
+      run += v[j];
+    }
+    __syncthreads();
+    if (threadIdx.x == 1023) s_carry += s_w[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) tot[blockIdx.x] = s_carry;
+}
+
+template <typename KeyT, int ITEMS = kItems>
+__global__ void __launch_bounds__(kThreads, ITEMS <= 8 ? 4 : 3) k_tile_sort(const KeyT* __restrict__ keys_in,
+                                                           const uint32_t* __restrict__ vals_in,
+                                                           KeyT* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+                                                           const uint32_t* __restrict__ n_dev, int shift, int rbits,
+                                                           const uint32_t* __restrict__ cnt, int64_t n_tiles_max,
+                                                           const uint32_t* __restrict__ tot) {
+  constexpr int TILE = kThreads * ITEMS;
+  __shared__ KeyT s_keys[TILE];
+  __shared__ uint32_t s_vals[TILE];
+  __shared__ uint16_t s_whist[kWarps][kR];   // per-warp digit counts, then prefixes (< 2^16)
+  __shared__ uint32_t s_gpos[kR];            // global position of local position 0 of digit d
+  __shared__ uint32_t s_lstart[kR];          // tile-local start of digit d
+  __shared__ uint32_t s_scan[kWarps];
+  __shared__ uint32_t s_total;
+
+  const int R = 1 << rbits;
+  const uint32_t mask = (uint32_t)R - 1u;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t n = *n_dev;
+  const int64_t tile = blockIdx.x;
+  const int64_t t0 = tile * TILE;
+  if (t0 >= n) return;   // uniform per CTA
+  const int tn = (int)min((int64_t)TILE, n - t0);
+  for (int i = threadIdx.x; i < kWarps * kR; i += kThreads) (&s_whist[0][0])[i] = 0;
+
+  uint32_t k[ITEMS], v[ITEMS];
+  uint16_t rank[ITEMS];
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const int li = warp * (ITEMS * 32) + i * 32 + lane;
+    if (li < tn) {
+      k[i] = (uint32_t)__ldcs(keys_in + t0 + li);
+      v[i] = __ldcs(vals_in + t0 + li);
+    } else {
+      k[i] = 0xffffffffu;   // sentinel: digit R, never counted
+      v[i] = 0u;
+    }
+  }
+  // global position of this tile's first key of digit d
+  const int d = threadIdx.x;
+  const uint32_t dbase = radix::block_excl_scan(d < R ? tot[d] : 0u, s_scan, &s_total);
+  const uint32_t gfirst = d < R ? dbase + cnt[(int64_t)d * n_tiles_max + tile] : 0u;
+
+  const unsigned lt_mask = (1u << lane) - 1u;
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const int dg = k[i] == 0xffffffffu ? R : (int)((k[i] >> shift) & mask);
+    const unsigned peers = __match_any_sync(0xffffffffu, dg);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (dg < R) base = s_whist[warp][dg];
+    rank[i] = (uint16_t)(base + __popc(peers & lt_mask));
+    __syncwarp();
+    if (lane == leader && dg < R) s_whist[warp][dg] = (uint16_t)(base + __popc(peers));
+    __syncwarp();
+  }
+  __syncthreads();
+  uint32_t c = 0;
+  if (d < R) {
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      const uint32_t x = s_whist[w][d];
+      s_whist[w][d] = (uint16_t)c;
+      c += x;
+    }
+  }
+  const uint32_t lstart = radix::block_excl_scan(d < R ? c : 0u, s_scan, &s_total);
+  if (d < R) {
+    s_lstart[d] = lstart;
+    s_gpos[d] = gfirst - lstart;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    if (k[i] != 0xffffffffu) {
+      const int dg = (int)((k[i] >> shift) & mask);
+      const uint32_t p = s_lstart[dg] + s_whist[warp][dg] + rank[i];
+      s_keys[p] = (KeyT)k[i];
+      s_vals[p] = v[i];
+    }
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < tn; p += kThreads) {
+    const KeyT key = s_keys[p];
+    const int dd = (int)(((uint32_t)key >> shift) & mask);
+    const uint32_t g = s_gpos[dd] + (uint32_t)p;
+    if (keys_out) keys_out[g] = key;
+    vals_out[g] = s_vals[p];
+  }
+}
+
+inline int64_t tiles_for(int64_t n, int tile = kTile) { return (n + tile - 1) / tile; }
+
+// Scratch words: per-tile digit counters and the digit totals.
+inline size_t scratch_words(int64_t n_max, int tile = kTile) {
+  const int64_t nt = tiles_for(n_max, tile);
+  return (size_t)kR * (size_t)(nt > 0 ? nt : 1) + kR;
+}
+
+// Stable sort of the first n (device count) pairs on bits [0, bits).  Buffers ping-pong
+// between (k0, v0) and (k1, v1); returns 0 if the result is in (k0, v0), 1 if in (k1, v1).
+// n_max bounds the count (grid sizes and scratch).
+template <typename KeyT, int ITEMS = kItems>
+inline int sort_pairs(KeyT* k0, uint32_t* v0, KeyT* k1, uint32_t* v1, const uint32_t* n_dev, int64_t n_max, int bits,
+                      uint32_t* scratch, cudaStream_t s, bool write_last_keys = true) {
+  constexpr int TILE = kThreads * ITEMS;
+  const int passes = radix::sort_passes(bits);
+  const int rbits = (bits + passes - 1) / passes;
+  const int64_t nt = tiles_for(n_max, TILE) > 0 ? tiles_for(n_max, TILE) : 1;
+  uint32_t* cnt = scratch;
+  uint32_t* tot = scratch + (size_t)kR * nt;
+  int cur = 0;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = p * rbits;
+    const int rb = (shift + rbits <= bits) ? rbits : bits - shift;
+    KeyT* ki = cur ? k1 : k0;
+    uint32_t* vi = cur ? v1 : v0;
+    KeyT* ko = cur ? k0 : k1;
+    uint32_t* vo = cur ? v0 : v1;
+    const bool last = (p == passes - 1);
+    {
+      prof::Scope ps("k_tile_hist", s);
+      k_tile_hist<KeyT, TILE><<<(unsigned)nt, kThreads, 0, s>>>(ki, n_dev, shift, rb, nt, cnt);
+    }
+    {
+      prof::Scope ps("k_tile_scan", s);
+      k_tile_scan<<<1 << rb, 1024, 0, s>>>(cnt, nt, tot);
+    }
+    prof::Scope ps("k_tile_sort", s);
+    k_tile_sort<KeyT, ITEMS><<<(unsigned)nt, kThreads, 0, s>>>(
+        ki, vi, (last && !write_last_keys) ? nullptr : ko, vo, n_dev, shift, rb, cnt, nt, tot);
+    cur ^= 1;
+  }
+  return cur;
+}
+
+}  // namespace tiles
+}  // namespace rs

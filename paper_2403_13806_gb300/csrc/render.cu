@@ -14,6 +14,7 @@
 #include <math.h>
 
 #include "blend.cuh"
+#include "profile.cuh"
 #include "radsplat.h"
 #include "rs_common.cuh"
 
@@ -156,6 +157,7 @@ __global__ void __launch_bounds__(TW* TH / 2) k_render(RenderArgs a) {
 template <int TW, int TH>
 static void launch_render(const RenderArgs& a, int n_tiles, bool image, bool imp, cudaStream_t s) {
   constexpr int NT = TW * TH / 2;
+  prof::Scope ps(imp ? "k_render_importance" : "k_render", s);
   if (image && imp) k_render<TW, TH, true, true><<<n_tiles, NT, 0, s>>>(a);
   else if (image) k_render<TW, TH, true, false><<<n_tiles, NT, 0, s>>>(a);
   else if (imp) k_render<TW, TH, false, true><<<n_tiles, NT, 0, s>>>(a);

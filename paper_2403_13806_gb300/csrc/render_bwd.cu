@@ -19,6 +19,7 @@
 //   (including the view-direction term of the mean).
 #include <math.h>
 
+#include "profile.cuh"
 #include "radsplat.h"
 #include "blend.cuh"
 #include "rs_common.cuh"
@@ -520,6 +521,7 @@ size_t backward_ws_bytes(const rs_view_batch* batch) { return bwd_ws_layout(null
 
 template <int TW, int TH>
 static void launch_bwd_blend(const BwdBlendArgs& a, int n_tiles, cudaStream_t s) {
+  prof::Scope ps("k_render_bwd", s);
   k_render_bwd<TW, TH><<<n_tiles, TW * TH / 2, 0, s>>>(a);
 }
 
@@ -578,6 +580,7 @@ extern "C" rs_status rs_render_backward(const rs_gaussians* g, const rs_view_bat
   p.gc = w.gc;
   p.out = *grads;
   const int threads = 128;
+  prof::Scope ps("k_project_bwd", s);
   if (!batch->subset_idx) {
     const unsigned blocks = (unsigned)((g->n + threads - 1) / threads);
     switch (g->sh_degree) {
