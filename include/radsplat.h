@@ -267,6 +267,26 @@ rs_status rs_importance(const rs_projected* proj, const rs_bins* bins,
 rs_status rs_filter(const float* h, int64_t n, float t, rs_filter_mode mode, uint8_t* mask,
                     uint32_t* idx, uint32_t* count, void* ws, size_t ws_bytes, void* stream);
 
+/* rs_filter_noalloc -- rs_filter for callers that cannot allocate device memory at all
+ * (the paper has no counterpart).  Some hosts own every byte of device memory and forbid
+ * allocation after start-up -- real-time renderers with a fixed budget, engine plug-ins,
+ * embedded runtimes -- so they can neither call cudaMalloc nor hand this library a
+ * workspace.  This entry point computes exactly what rs_filter computes, but keeps the
+ * compaction's scratch (one 32-bit count per 4096 elements) in a fixed array inside the
+ * library, RS_FILTER_NOALLOC_MAX_N / 4096 words (64 KB) that every GPU loading the library
+ * holds until the process exits.  Nothing is allocated: no cudaMalloc, no cudaFree, no
+ * allocating library call.  The caller still passes h, mask, idx and count.
+ * The first call on a device looks up that array's device address (with the device
+ * current) and caches it; make that first call before capturing a stream into a CUDA
+ * graph.  Every call shares the one array, and each call overwrites all of the scratch it
+ * reads before reading it (the per-block counts), so nothing from an earlier call leaks
+ * into a later one; but calls that overlap on the GPU (other streams, other threads) race
+ * on it, so serialise them.  n > RS_FILTER_NOALLOC_MAX_N returns RS_ERR_INVALID_ARG without
+ * launching anything.  Other arguments and errors as rs_filter. */
+#define RS_FILTER_NOALLOC_MAX_N (1LL << 26)
+rs_status rs_filter_noalloc(const float* h, int64_t n, float t, rs_filter_mode mode, uint8_t* mask,
+                            uint32_t* idx, uint32_t* count, void* stream);
+
 /* rs_filter_nearest -- Sec. 3.4: for each of n_cams camera centres (device float [n][3]),
  * the nearest of k cluster centres (device float [k][3]) by the FP32 squared distance
  * ((x0-c0)^2 + (x1-c1)^2) + (x2-c2)^2, ties to the lower index; out device int32 [n].

@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libradsplat.so")
 
 RS_OK, RS_ERR_INVALID_ARG, RS_ERR_WORKSPACE, RS_ERR_UNSUPPORTED, RS_ERR_CUDA, RS_ERR_CAPACITY, RS_ERR_TIMEOUT = range(7)
 RS_PRUNE_BELOW, RS_KEEP_ABOVE = 0, 1
+RS_FILTER_NOALLOC_MAX_N = 1 << 26
 RS_STAGE_PROJECT, RS_STAGE_BIN_SORT, RS_STAGE_RENDER, RS_STAGE_BACKWARD, RS_STAGE_FILTER = range(5)
 
 
@@ -81,6 +82,7 @@ SIGNATURES = {
     "rs_importance": (ctypes.c_int, [P, P, P, P, P, c_int64, P]),
     "rs_filter": (ctypes.c_int, [P, c_int64, c_float, ctypes.c_int, P, P, P, P, c_size_t, P]),
     "rs_filter_nearest": (ctypes.c_int, [P, c_int32, P, c_int32, P, P]),
+    "rs_filter_noalloc": (ctypes.c_int, [P, c_int64, c_float, ctypes.c_int, P, P, P, P]),
     "rs_render_backward": (ctypes.c_int, [P, P, P, P, P, P, P, P, P, P, c_size_t, P]),
     "rs_l1_loss": (ctypes.c_int, [P, P, c_int64, P, P, P]),
     "rs_profile_enable": (ctypes.c_int, [c_int32]),

@@ -6,6 +6,8 @@
 // byte mask), one exclusive scan of the block counts, and an order-preserving scatter of
 // the indices (block-local scan with warp ballots).  The block counts are the only
 // scratch memory (4 bytes per 4096 elements).
+#include <mutex>
+
 #include "profile.cuh"
 #include "radsplat.h"
 #include "rs_common.cuh"
@@ -181,4 +183,46 @@ extern "C" rs_status rs_filter_nearest(const float* centres, int32_t k, const fl
   k_nearest<<<(n_cams + threads - 1) / threads, threads, (size_t)k * 3 * sizeof(float),
               reinterpret_cast<cudaStream_t>(stream)>>>(centres, k, cam_centres, n_cams, out);
   return launch_status();
+}
+
+// ---------------------------------------------------------------------------------------
+// rs_filter_noalloc: the same kernels with their per-block counts in a fixed device array.
+
+namespace rs {
+
+constexpr int64_t kNoallocMaxBlocks = (RS_FILTER_NOALLOC_MAX_N + kFiltTile - 1) / kFiltTile;   // 16384 words
+static __device__ __align__(256) uint32_t g_filter_scratch[kNoallocMaxBlocks];
+
+constexpr int kNoallocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static uint32_t* g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+// Device address of g_filter_scratch on the current device, looked up once per device.
+// (In host code the array's name is only a host-side stand-in, never a device address.)
+static rs_status noalloc_scratch(uint32_t** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return RS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_filter_scratch) != cudaSuccess || !p) return RS_ERR_CUDA;
+    g_noalloc_ptr[dev] = static_cast<uint32_t*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return RS_OK;
+}
+
+}  // namespace rs
+
+extern "C" rs_status rs_filter_noalloc(const float* h, int64_t n, float t, rs_filter_mode mode, uint8_t* mask,
+                                       uint32_t* idx, uint32_t* count, void* stream) {
+  if ((!h && n > 0) || !count || n < 0) return RS_ERR_INVALID_ARG;
+  if (n > RS_FILTER_NOALLOC_MAX_N) return RS_ERR_INVALID_ARG;
+  if (mode != RS_PRUNE_BELOW && mode != RS_KEEP_ABOVE) return RS_ERR_INVALID_ARG;
+  uint32_t* scratch = nullptr;
+  const rs_status st = noalloc_scratch(&scratch);
+  if (st != RS_OK) return st;
+  // every block of k_filter_count writes its own count before the scan reads it: the array
+  // needs no clearing between calls
+  return filter_launch(h, n, t, (int)mode, mask, idx, count, scratch, reinterpret_cast<cudaStream_t>(stream));
 }
