@@ -7,7 +7,7 @@
 #include "rs_common.cuh"
 
 namespace rs {
-size_t bin_sort_ws_bytes(int64_t n_items, int64_t capacity);
+size_t bin_sort_ws_bytes(const rs_view_batch* batch, int64_t capacity);
 size_t filter_ws_bytes(int64_t n);
 size_t backward_ws_bytes(const rs_view_batch* batch);
 }  // namespace rs
@@ -89,7 +89,7 @@ extern "C" size_t rs_workspace_size(rs_stage stage, const rs_view_batch* batch, 
   if (!batch) return 0;
   switch (stage) {
     case RS_STAGE_PROJECT: return 0;
-    case RS_STAGE_BIN_SORT: return bin_sort_ws_bytes(batch->n_items, capacity);
+    case RS_STAGE_BIN_SORT: return bin_sort_ws_bytes(batch, capacity);
     case RS_STAGE_RENDER: return 0;
     case RS_STAGE_BACKWARD: return backward_ws_bytes(batch);
     case RS_STAGE_FILTER: return filter_ws_bytes(batch->n_items);

@@ -1,67 +1,88 @@
-// rs_bin_sort: duplicated (tile | depth) keys and a device radix sort.
+// rs_bin_sort: tile binning by duplicated 64-bit (tile | depth) keys and a device radix sort.
 //
-// The 64-bit key of an instance is (global tile id) << 32 | float bits of the item's depth.
-// An LSD radix sort processes the least significant digits first; the low 32 bits depend
-// on the item only, so their passes are run over the N items before duplication (four
-// 8-bit passes), and the expansion then emits every item's tiles in that depth order.  The
-// remaining passes sort the K instances stably on the tile id alone, over only the
-// ceil(log2(tiles)) significant bits.  The result -- permutation and keys -- is exactly
-// that of a stable sort of the 64-bit keys emitted in item order.
+// The order to produce, per tile, is that of a stable sort of the keys
+// (global tile id) << 32 | float bits of the item's depth, emitted item by item.  It is an
+// LSD radix sort taken in three groups of digits:
+//   1. the low 32 bits (the depth) are constant per item, so their four 8-bit passes run
+//      over the N items before any duplication;
+//   2. the tile id is split into a coarse digit -- the super-tile of 4 x 4 tiles that holds
+//      the tile -- and a fine one.  Items are duplicated once per super-tile their rect
+//      touches (about 7x fewer instances than tiles at the workload sizes) and those
+//      instances are radix-sorted stably on the super-tile id (one pass per 8 bits);
+//   3. the fine digit is one stable counting pass per super-tile: 8 CTAs share each
+//      super-tile's depth-ordered list in equal segments and, for each of its 4 x 4 tiles,
+//      keep the items whose rect covers that tile -- once to count them (exclusive scans over
+//      the segments and over all tiles then give every tile its range and every segment its
+//      first position in it), once to write them, contiguously and in order.
+// Every tile's list therefore holds its items by depth, ties to the lower item: exactly the
+// order of the stable 64-bit sort.  The 64-bit keys are written only on request.
 //
-// Pipeline (one stream, no host synchronisation; K lives in device memory):
-//   k_depth_keys -> 4 depth passes (reduce-then-scan radix over the N items)
-//   -> k_count_blocks -> k_count_top (K, capacity check)
-//   -> k_emit (warp-cooperative expansion, coalesced stores)
-//   -> tile passes (per-tile histogram, per-digit scan, per-tile stable scatter, per 8-bit digit)
-//   -> memset(ranges) -> k_ranges -> [k_keys]
-#include "radix_tiles.cuh"
-#include "radix.cuh"
+// Pipeline (one stream, no host synchronisation; counts live in device memory):
+//   k_super_layout (super-tile bases per view); k_depth_keys, 4 depth passes (items);
+//   k_count_blocks, k_count_top (super total); k_emit (super instances); super passes
+//   (radix_tiles); k_ranges (super ranges); k_fine_count; k_fine_seg_scan; k_fine_scan
+//   (ranges, K, capacity check); k_fine_scatter (vals, optional keys).
 #include "profile.cuh"
+#include "radix.cuh"
+#include "radix_tiles.cuh"
 #include "radsplat.h"
 #include "rs_common.cuh"
 
 namespace rs {
 
 constexpr int kEmitThreads = 256;
+constexpr int kSuper = 4;           // tiles per super-tile side
+constexpr int kFineThreads = 256;   // threads of a fine-binning CTA
+constexpr int kSegs = 8;            // CTAs per super-tile list (equal segments) in the fine binning
+constexpr int kNF = kSuper * kSuper;
 
 struct BinWs {
   uint32_t* dkeys[2];
   uint32_t* dvals[2];
-  unsigned long long* bsum;   // per emission block: instances, then exclusive prefix
-  char* tkeys[2];
-  uint32_t* tvals;
-  uint32_t* hist;
-  uint32_t* sweep;            // per-tile digit counters of the instance sort
-  uint32_t* counters;         // [0] = instances written (min(K, capacity))
-  int grid_depth, grid_tile;
+  unsigned long long* bsum;   // per emission block: super instances, then exclusive prefix
+  char* skeys[2];             // super-tile ids (uint16 or uint32)
+  uint32_t* svals[2];         // items
+  uint32_t* hist;             // item radix scratch
+  uint32_t* sweep;            // per-tile digit counters of the super-instance sort
+  uint32_t* sranges;          // [n_tiles][2]: super-tile ranges (super-tiles never outnumber tiles)
+  uint32_t* super_base;       // [n_views + 1]
+  uint32_t* fine_tot;         // [n_tiles]: instances per tile, then first position
+  uint32_t* seg_cnt;          // [n_tiles][kSegs][16]: per (super-tile, segment, tile) counts, then prefixes
+  uint32_t* counters;         // [0] super instances written, [2] instances written
+  int grid_depth;
   size_t bytes;
 };
 
-static BinWs bin_ws_layout(void* base, int64_t n_items, int64_t capacity) {
+static BinWs bin_ws_layout(void* base, int64_t n_items, int64_t capacity, int n_tiles, int n_views) {
   BinWs w{};
   size_t off = 0;
   auto take = [&](size_t bytes) -> char* {
     char* p = base ? static_cast<char*>(base) + off : nullptr;
-    off += align_up(bytes, 256);
+    off += align_up(bytes > 0 ? bytes : 1, 256);
     return p;
   };
   const size_t ni = (size_t)(n_items > 0 ? n_items : 1);
-  const size_t cap = (size_t)(capacity > 0 ? capacity : 1);
+  const size_t cap = (size_t)(capacity > 0 ? capacity : 1);   // super instances <= instances
   const int64_t nblk = (n_items + kEmitThreads - 1) / kEmitThreads;
   w.grid_depth = radix::grid_for(n_items);
-  w.grid_tile = radix::grid_for(capacity);
-  const int hist_grid = w.grid_depth > w.grid_tile ? w.grid_depth : w.grid_tile;
   for (int i = 0; i < 2; ++i) w.dkeys[i] = reinterpret_cast<uint32_t*>(take(ni * 4));
   for (int i = 0; i < 2; ++i) w.dvals[i] = reinterpret_cast<uint32_t*>(take(ni * 4));
   w.bsum = reinterpret_cast<unsigned long long*>(take((size_t)(nblk > 0 ? nblk : 1) * 8));
-  for (int i = 0; i < 2; ++i) w.tkeys[i] = take(cap * 4);   // uint16 or uint32 tile ids
-  w.tvals = reinterpret_cast<uint32_t*>(take(cap * 4));
-  w.hist = reinterpret_cast<uint32_t*>(take(radix::scratch_words(hist_grid) * 4));
+  for (int i = 0; i < 2; ++i) w.skeys[i] = take(cap * 4);
+  for (int i = 0; i < 2; ++i) w.svals[i] = reinterpret_cast<uint32_t*>(take(cap * 4));
+  w.hist = reinterpret_cast<uint32_t*>(take(radix::scratch_words(w.grid_depth) * 4));
   w.sweep = reinterpret_cast<uint32_t*>(take(tiles::scratch_words(capacity) * 4));
+  w.sranges = reinterpret_cast<uint32_t*>(take((size_t)(n_tiles > 0 ? n_tiles : 1) * 8));
+  w.super_base = reinterpret_cast<uint32_t*>(take((size_t)(n_views + 1) * 4));
+  w.fine_tot = reinterpret_cast<uint32_t*>(take((size_t)(n_tiles > 0 ? n_tiles : 1) * 4));
+  w.seg_cnt = reinterpret_cast<uint32_t*>(take((size_t)(n_tiles > 0 ? n_tiles : 1) * kSegs * kNF * 4));
   w.counters = reinterpret_cast<uint32_t*>(take(64));
   w.bytes = off;
   return w;
 }
+
+__device__ __forceinline__ int super_w(const rs_view& v) { return (v.tiles_x + kSuper - 1) / kSuper; }
+__device__ __forceinline__ int super_h(const rs_view& v) { return (v.tiles_y + kSuper - 1) / kSuper; }
 
 __global__ void k_depth_keys(const float4* __restrict__ rgb_d, int64_t n, uint32_t* __restrict__ keys,
                              uint32_t* __restrict__ vals) {
@@ -71,13 +92,34 @@ __global__ void k_depth_keys(const float4* __restrict__ rgb_d, int64_t n, uint32
   vals[i] = (uint32_t)i;
 }
 
-// Instances per block of kEmitThreads depth-sorted items.
+// First super-tile id of every view (exclusive prefix of the views' super-tile counts).
+__global__ void k_super_layout(const rs_view* __restrict__ views, int n_views, uint32_t* __restrict__ super_base) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  uint32_t run = 0;
+  for (int v = 0; v < n_views; ++v) {
+    super_base[v] = run;
+    run += (uint32_t)(super_w(views[v]) * super_h(views[v]));
+  }
+  super_base[n_views] = run;
+}
+
+// Super-tile rect of an item's tile rect (both half-open).
+__device__ __forceinline__ ushort4 super_rect(ushort4 r) {
+  if (r.z <= r.x || r.w <= r.y) return make_ushort4(0, 0, 0, 0);
+  return make_ushort4(r.x / kSuper, r.y / kSuper, (r.z - 1) / kSuper + 1, (r.w - 1) / kSuper + 1);
+}
+
+// Super instances per block of kEmitThreads depth-sorted items.
 __global__ void __launch_bounds__(kEmitThreads) k_count_blocks(const uint32_t* __restrict__ order, int64_t n,
-                                                               const uint32_t* __restrict__ n_tiles,
+                                                               const ushort4* __restrict__ rect,
                                                                unsigned long long* __restrict__ bsum) {
   __shared__ unsigned long long s[kEmitThreads / 32];
   const int64_t i = (int64_t)blockIdx.x * kEmitThreads + threadIdx.x;
-  unsigned long long c = i < n ? (unsigned long long)n_tiles[order[i]] : 0ull;
+  unsigned long long c = 0;
+  if (i < n) {
+    const ushort4 sr = super_rect(rect[order[i]]);
+    c = (unsigned long long)(sr.z - sr.x) * (unsigned long long)(sr.w - sr.y);
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
   if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = c;
@@ -89,8 +131,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_count_blocks(const uint32_t* _
   }
 }
 
-// Exclusive prefix over the block counts (one block), the instance total K, and the
-// capacity check.
+// Exclusive prefix over the block counts (one block) and the super-instance total.
 __global__ void __launch_bounds__(1024) k_count_top(unsigned long long* __restrict__ bsum, int64_t nblk,
                                                     int64_t capacity, uint32_t* __restrict__ counters,
                                                     rs_device_status* st) {
@@ -128,42 +169,38 @@ __global__ void __launch_bounds__(1024) k_count_top(unsigned long long* __restri
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    const unsigned long long K = s_carry;
-    const unsigned long long written = K < (unsigned long long)capacity ? K : (unsigned long long)capacity;
-    counters[0] = (uint32_t)written;
-    if (st) {
-      atomicMax(reinterpret_cast<unsigned long long*>(&st->required), K);
-      st->n_instances = (int64_t)written;
-      if (K > (unsigned long long)capacity) atomicCAS(&st->code, 0, (int)RS_ERR_CAPACITY);
-    }
+    // super instances never outnumber instances: more than the capacity means the instances
+    // overflow too (k_fine_scan records the required count)
+    const unsigned long long Ks = s_carry;
+    counters[0] = (uint32_t)(Ks < (unsigned long long)capacity ? Ks : (unsigned long long)capacity);
+    if (st && Ks > (unsigned long long)capacity) atomicCAS(&st->code, 0, (int)RS_ERR_CAPACITY);
   }
 }
 
-// Expansion: each warp takes 32 consecutive depth-sorted items and writes their
-// instances contiguously (tile ids row-major inside each rect); lanes locate the item of
-// their instance by a binary search over the warp's inclusive prefix.
+// Expansion into super instances: each warp takes 32 consecutive depth-sorted items and
+// writes their super-tile ids contiguously (row-major inside each super rect); lanes locate
+// the item of their instance by a binary search over the warp's inclusive prefix.
 template <typename KeyT>
 __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restrict__ order, int64_t n,
-                                                       const uint32_t* __restrict__ n_tiles,
                                                        const ushort4* __restrict__ rect,
                                                        const rs_view* __restrict__ views, int n_views,
-                                                       const unsigned long long* __restrict__ bpre,
-                                                       int64_t capacity, KeyT* __restrict__ tkeys,
-                                                       uint32_t* __restrict__ tvals) {
+                                                       const uint32_t* __restrict__ super_base,
+                                                       const unsigned long long* __restrict__ bpre, int64_t capacity,
+                                                       KeyT* __restrict__ skeys, uint32_t* __restrict__ svals) {
   __shared__ uint32_t s_wtot[kEmitThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t i = (int64_t)blockIdx.x * kEmitThreads + threadIdx.x;
   uint32_t item = 0, cnt = 0;
-  ushort4 rc = make_ushort4(0, 0, 0, 0);
-  int tile_base = 0, tiles_x = 0;
+  ushort4 sr = make_ushort4(0, 0, 0, 0);
+  int sbase = 0, sw = 0;
   if (i < n) {
     item = order[i];
-    cnt = n_tiles[item];
+    sr = super_rect(rect[item]);
+    cnt = (uint32_t)(sr.z - sr.x) * (uint32_t)(sr.w - sr.y);
     if (cnt) {
-      rc = rect[item];
       const int v = find_view_by_item(views, n_views, (int64_t)item);
-      tile_base = views[v].tile_base;
-      tiles_x = views[v].tiles_x;
+      sbase = (int)super_base[v];
+      sw = super_w(views[v]);
     }
   }
   uint32_t incl = cnt;
@@ -178,7 +215,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
   unsigned long long wbase = bpre[blockIdx.x];
   for (int w = 0; w < warp; ++w) wbase += s_wtot[w];
   const uint32_t excl = incl - cnt;
-  const int rw = (int)rc.z - (int)rc.x;
+  const int rw = (int)sr.z - (int)sr.x;
   for (uint32_t e0 = 0; e0 < wtot; e0 += 32) {
     const uint32_t e = e0 + lane;
     int lo = 0;
@@ -190,10 +227,10 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
     const int owner = lo < 31 ? lo : 31;
     const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, owner);
     const int o_rw = __shfl_sync(0xffffffffu, rw, owner);
-    const int o_x0 = __shfl_sync(0xffffffffu, (int)rc.x, owner);
-    const int o_y0 = __shfl_sync(0xffffffffu, (int)rc.y, owner);
-    const int o_tb = __shfl_sync(0xffffffffu, tile_base, owner);
-    const int o_tx = __shfl_sync(0xffffffffu, tiles_x, owner);
+    const int o_x0 = __shfl_sync(0xffffffffu, (int)sr.x, owner);
+    const int o_y0 = __shfl_sync(0xffffffffu, (int)sr.y, owner);
+    const int o_sb = __shfl_sync(0xffffffffu, sbase, owner);
+    const int o_sw = __shfl_sync(0xffffffffu, sw, owner);
     const uint32_t o_item = __shfl_sync(0xffffffffu, item, owner);
     if (e < wtot) {
       const uint32_t r = e - o_excl;
@@ -201,20 +238,18 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
       const uint32_t tx = r - ty * (uint32_t)o_rw;
       const unsigned long long pos = wbase + e;
       if (pos < (unsigned long long)capacity) {
-        tkeys[pos] = (KeyT)((uint32_t)o_tb + (uint32_t)(o_y0 + (int)ty) * (uint32_t)o_tx + (uint32_t)(o_x0 + (int)tx));
-        tvals[pos] = o_item;
+        skeys[pos] = (KeyT)((uint32_t)o_sb + (uint32_t)(o_y0 + (int)ty) * (uint32_t)o_sw + (uint32_t)(o_x0 + (int)tx));
+        svals[pos] = o_item;
       }
     }
   }
 }
 
-// Tile boundaries of the sorted tile ids: each thread owns 4 consecutive keys (one 16-byte
-// load) and compares across its neighbours.  A key outside [0, n_tiles) can only come from
-// a rect outside its view's tile grid and is ignored.
+// Range of every key value of a sorted key array (16-byte loads; keys >= n_keys ignored).
 template <typename KeyT>
-__global__ void k_ranges(const KeyT* __restrict__ tkeys, const uint32_t* __restrict__ counters,
-                         uint32_t n_tiles, uint32_t* __restrict__ ranges) {
-  constexpr int V = 16 / sizeof(KeyT);   // keys per 16-byte load
+__global__ void k_ranges(const KeyT* __restrict__ tkeys, const uint32_t* __restrict__ counters, uint32_t n_keys,
+                         uint32_t* __restrict__ ranges) {
+  constexpr int V = 16 / sizeof(KeyT);
   const int64_t K = counters[0];
   const int64_t nq = (K + V - 1) / V;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
@@ -235,7 +270,7 @@ __global__ void k_ranges(const KeyT* __restrict__ tkeys, const uint32_t* __restr
       const int64_t k = k0 + j;
       if (k >= K) break;
       const uint32_t nx = (j < V - 1) ? ((k + 1 < K) ? t[j + 1] : 0xffffffffu) : next;
-      if (t[j] < n_tiles) {
+      if (t[j] < n_keys) {
         if (k == 0 || prev != t[j]) ranges[2 * (int64_t)t[j]] = (uint32_t)k;
         if (k == K - 1 || nx != t[j]) ranges[2 * (int64_t)t[j] + 1] = (uint32_t)(k + 1);
       }
@@ -244,13 +279,264 @@ __global__ void k_ranges(const KeyT* __restrict__ tkeys, const uint32_t* __restr
   }
 }
 
-template <typename KeyT>
-__global__ void k_keys(const KeyT* __restrict__ tkeys, const uint32_t* __restrict__ vals,
-                       const float4* __restrict__ rgb_d, const uint32_t* __restrict__ counters,
-                       unsigned long long* __restrict__ keys) {
-  const int64_t K = counters[0];
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x)
-    keys[k] = ((unsigned long long)tkeys[k] << 32) | (unsigned long long)__float_as_uint(rgb_d[vals[k]].w);
+// The super-tile a CTA works on: its view, its first tile, the extent of its block of tiles
+// (up to kSuper x kSuper), and its range of sorted super instances.
+struct SuperTile {
+  int v;
+  int tx0, ty0, nx, ny;
+  uint32_t s0, s1;
+  bool valid;
+};
+
+__device__ __forceinline__ SuperTile super_tile(uint32_t S, const rs_view* views, int n_views,
+                                                const uint32_t* super_base, const uint32_t* sranges) {
+  SuperTile t;
+  t.valid = S < super_base[n_views];
+  if (!t.valid) return t;
+  int lo = 0, hi = n_views - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (super_base[mid] <= S) lo = mid; else hi = mid - 1;
+  }
+  t.v = lo;
+  const rs_view& cam = views[t.v];
+  const int local = (int)(S - super_base[t.v]);
+  const int sw = super_w(cam);
+  const int sy = local / sw, sx = local - sy * sw;
+  t.tx0 = sx * kSuper;
+  t.ty0 = sy * kSuper;
+  t.nx = min(kSuper, cam.tiles_x - t.tx0);
+  t.ny = min(kSuper, cam.tiles_y - t.ty0);
+  t.s0 = sranges[2 * (int64_t)S];
+  t.s1 = sranges[2 * (int64_t)S + 1];
+  return t;
+}
+
+// Bit (fy * kSuper + fx) set for every tile of the super-tile's block the rect covers.
+__device__ __forceinline__ uint32_t cover_mask(ushort4 r, const SuperTile& t) {
+  const int x0 = max((int)r.x - t.tx0, 0), x1 = min((int)r.z - t.tx0, t.nx);
+  const int y0 = max((int)r.y - t.ty0, 0), y1 = min((int)r.w - t.ty0, t.ny);
+  if (x0 >= x1 || y0 >= y1) return 0u;
+  const uint32_t row = ((1u << x1) - 1u) & ~((1u << x0) - 1u);
+  uint32_t m = 0u;
+  for (int fy = y0; fy < y1; ++fy) m |= row << (fy * kSuper);
+  return m;
+}
+
+// Segment j of super-tile S's list: kSegs CTAs share each list in equal parts.
+__device__ __forceinline__ void segment(const SuperTile& t, int j, uint32_t& a, uint32_t& b) {
+  const uint32_t len = t.s1 - t.s0;
+  const uint32_t L = (len + kSegs - 1) / kSegs;
+  a = min(t.s0 + (uint32_t)j * L, t.s1);
+  b = min(a + L, t.s1);
+}
+
+// Instances per (super-tile, segment, tile): each CTA reads one segment of its super-tile's
+// depth-ordered list once and counts, for each of the 4 x 4 tiles, the items covering it.
+__global__ void __launch_bounds__(kFineThreads) k_fine_count(const uint32_t* __restrict__ svals,
+                                                             const ushort4* __restrict__ rect,
+                                                             const rs_view* __restrict__ views, int n_views,
+                                                             const uint32_t* __restrict__ super_base,
+                                                             const uint32_t* __restrict__ sranges,
+                                                             uint32_t* __restrict__ seg_cnt) {
+  constexpr int NW = kFineThreads / 32;
+  __shared__ uint32_t s_cnt[NW][kNF];
+  const uint32_t S = blockIdx.x / kSegs;
+  const int j = blockIdx.x % kSegs;
+  const SuperTile t = super_tile(S, views, n_views, super_base, sranges);
+  if (!t.valid) return;   // uniform per CTA
+  uint32_t a, b;
+  segment(t, j, a, b);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t c[kNF];
+#pragma unroll
+  for (int f = 0; f < kNF; ++f) c[f] = 0u;
+  for (uint32_t e0 = a; e0 < b; e0 += kFineThreads) {
+    const uint32_t e = e0 + threadIdx.x;
+    const uint32_t m = e < b ? cover_mask(rect[svals[e]], t) : 0u;
+#pragma unroll
+    for (int f = 0; f < kNF; ++f) c[f] += __popc(__ballot_sync(0xffffffffu, (m >> f) & 1u));
+  }
+  if (lane < kNF) {
+    uint32_t mine = 0;
+#pragma unroll
+    for (int f = 0; f < kNF; ++f) mine = (lane == f) ? c[f] : mine;
+    s_cnt[warp][lane] = mine;
+  }
+  __syncthreads();
+  if (threadIdx.x < kNF) {
+    uint32_t tot = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) tot += s_cnt[w][threadIdx.x];
+    seg_cnt[((int64_t)S * kSegs + j) * kNF + threadIdx.x] = tot;
+  }
+}
+
+// One thread per tile: exclusive prefix of its counts over its super-tile's segments (in
+// place) and the tile's total.
+__global__ void k_fine_seg_scan(uint32_t* __restrict__ seg_cnt, const rs_view* __restrict__ views, int n_views,
+                                const uint32_t* __restrict__ super_base, int n_tiles, uint32_t* __restrict__ fine_tot) {
+  const int T = blockIdx.x * blockDim.x + threadIdx.x;
+  if (T >= n_tiles) return;
+  const int v = find_view_by_tile(views, n_views, T);
+  const rs_view& cam = views[v];
+  const int local = T - cam.tile_base;
+  const int ty = local / cam.tiles_x, tx = local - ty * cam.tiles_x;
+  const uint32_t S = super_base[v] + (uint32_t)((ty / kSuper) * super_w(cam) + tx / kSuper);
+  const int f = (ty % kSuper) * kSuper + tx % kSuper;
+  uint32_t run = 0;
+#pragma unroll
+  for (int j = 0; j < kSegs; ++j) {
+    uint32_t* c = seg_cnt + ((int64_t)S * kSegs + j) * kNF + f;
+    const uint32_t x = *c;
+    *c = run;
+    run += x;
+  }
+  fine_tot[T] = run;
+}
+
+// Exclusive scan of the per-tile totals (one CTA): first position of every tile (in place,
+// saturated to 32 bits), ranges clamped to the capacity, K, and the capacity check.
+__global__ void __launch_bounds__(1024) k_fine_scan(uint32_t* __restrict__ tot, int n_tiles, int64_t capacity,
+                                                    uint32_t* __restrict__ ranges, uint32_t* __restrict__ counters,
+                                                    rs_device_status* st) {
+  __shared__ unsigned long long s_w[32];
+  __shared__ unsigned long long s_carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned long long cap = (unsigned long long)capacity;
+  if (threadIdx.x == 0) s_carry = 0ull;
+  __syncthreads();
+  for (int b0 = 0; b0 < n_tiles; b0 += 4 * 1024) {
+    const int b = b0 + 4 * (int)threadIdx.x;
+    uint32_t v[4];
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      v[j] = (b + j < n_tiles) ? tot[b + j] : 0u;
+      sum += v[j];
+    }
+    unsigned long long x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      unsigned long long w = s_w[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      s_w[lane] = w;
+    }
+    __syncthreads();
+    unsigned long long run = s_carry + (warp ? s_w[warp - 1] : 0ull) + x - sum;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (b + j < n_tiles) {
+        const unsigned long long e = run + v[j];
+        tot[b + j] = (uint32_t)(run < 0xffffffffull ? run : 0xffffffffull);
+        ranges[2 * (int64_t)(b + j)] = (uint32_t)(run < cap ? run : cap);
+        ranges[2 * (int64_t)(b + j) + 1] = (uint32_t)(e < cap ? e : cap);
+        run = e;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 1023) s_carry += s_w[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const unsigned long long K = s_carry;
+    counters[2] = (uint32_t)(K < cap ? K : cap);
+    if (st) {
+      atomicMax(reinterpret_cast<unsigned long long*>(&st->required), K);
+      st->n_instances = (int64_t)(K < cap ? K : cap);
+      if (K > cap) atomicCAS(&st->code, 0, (int)RS_ERR_CAPACITY);
+    }
+  }
+}
+
+// Every tile's items, in its super-tile list order, written contiguously: each CTA takes one
+// segment of a super-tile's list and writes, for each of its tiles, the covering items from
+// that tile's first position plus the counts of the earlier segments (order-preserving
+// compaction with warp ballots).
+__global__ void __launch_bounds__(kFineThreads) k_fine_scatter(const uint32_t* __restrict__ svals,
+                                                               const ushort4* __restrict__ rect,
+                                                               const float4* __restrict__ rgb_d,
+                                                               const rs_view* __restrict__ views, int n_views,
+                                                               const uint32_t* __restrict__ super_base,
+                                                               const uint32_t* __restrict__ sranges,
+                                                               const uint32_t* __restrict__ fine_start,
+                                                               const uint32_t* __restrict__ seg_pre, int64_t capacity,
+                                                               uint32_t* __restrict__ vals,
+                                                               unsigned long long* __restrict__ keys) {
+  constexpr int NW = kFineThreads / 32;
+  __shared__ uint32_t s_bal[NW][kNF];     // per-warp ballot of each tile
+  __shared__ uint32_t s_base[NW][kNF];    // first position of each (warp, tile) in this chunk
+  __shared__ uint32_t s_run[kNF];         // next position of each tile
+  __shared__ uint32_t s_tile[kNF];        // global id of each tile
+  const uint32_t S = blockIdx.x / kSegs;
+  const int j = blockIdx.x % kSegs;
+  const SuperTile t = super_tile(S, views, n_views, super_base, sranges);
+  if (!t.valid) return;   // uniform per CTA
+  uint32_t a, b;
+  segment(t, j, a, b);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x < kNF) {
+    const int f = threadIdx.x, fx = f % kSuper, fy = f / kSuper;
+    const rs_view& cam = views[t.v];
+    const bool in = fx < t.nx && fy < t.ny;
+    const uint32_t T = in ? (uint32_t)(cam.tile_base + (t.ty0 + fy) * cam.tiles_x + t.tx0 + fx) : 0u;
+    s_tile[f] = T;
+    s_run[f] = in ? fine_start[T] + seg_pre[((int64_t)S * kSegs + j) * kNF + f] : 0u;
+  }
+  const uint32_t cap = (uint32_t)(capacity < 0xffffffffLL ? capacity : 0xffffffffLL);
+  const unsigned lt = (1u << lane) - 1u;
+  for (uint32_t e0 = a; e0 < b; e0 += kFineThreads) {
+    const uint32_t e = e0 + threadIdx.x;
+    uint32_t item = 0, m = 0u;
+    if (e < b) {
+      item = svals[e];
+      m = cover_mask(rect[item], t);
+    }
+    uint32_t my_bal = 0;
+#pragma unroll
+    for (int f = 0; f < kNF; ++f) {
+      const unsigned bl = __ballot_sync(0xffffffffu, (m >> f) & 1u);
+      my_bal = (lane == f) ? bl : my_bal;
+    }
+    if (lane < kNF) s_bal[warp][lane] = my_bal;
+    __syncthreads();
+    if (threadIdx.x < kNF) {
+      // per tile: warp offsets inside this chunk, then advance the tile's run
+      const int f = threadIdx.x;
+      uint32_t r = s_run[f];
+#pragma unroll
+      for (int w = 0; w < NW; ++w) {
+        s_base[w][f] = r;
+        r += __popc(s_bal[w][f]);
+      }
+      s_run[f] = r;
+    }
+    __syncthreads();
+    if (m) {
+      const uint32_t db = keys ? __float_as_uint(rgb_d[item].w) : 0u;
+      uint32_t mm = m;
+      while (mm) {
+        const int f = __ffs(mm) - 1;
+        mm &= mm - 1u;
+        const uint32_t pos = s_base[warp][f] + __popc(s_bal[warp][f] & lt);
+        if (pos < cap) {
+          vals[pos] = item;
+          if (keys) keys[pos] = ((unsigned long long)s_tile[f] << 32) | db;
+        }
+      }
+    }
+    __syncthreads();
+  }
 }
 
 static int bits_for(int64_t n) {
@@ -259,30 +545,30 @@ static int bits_for(int64_t n) {
   return b;
 }
 
-size_t bin_sort_ws_bytes(int64_t n_items, int64_t capacity) { return bin_ws_layout(nullptr, n_items, capacity).bytes; }
+size_t bin_sort_ws_bytes(const rs_view_batch* b, int64_t capacity) {
+  return bin_ws_layout(nullptr, b->n_items, capacity, b->n_tiles, b->n_views).bytes;
+}
 
-// Expansion, stable sort of the instances on the tile id, ranges and optional keys, with
-// tile ids held as KeyT (16-bit whenever every tile id fits).
+// Super instances: expansion, stable sort on the super-tile id (KeyT-wide), ranges.
+// Returns the sorted item array.
 template <typename KeyT>
-static void sort_instances(const BinWs& w, const uint32_t* order, int64_t n, const rs_projected* proj,
-                           const rs_view_batch* batch, const rs_bins* bins, int64_t cap, int64_t nblk,
-                           uint32_t* v_first, uint32_t* v_second, rs_device_status* status, cudaStream_t s) {
-  KeyT* k0 = reinterpret_cast<KeyT*>(w.tkeys[0]);
-  KeyT* k1 = reinterpret_cast<KeyT*>(w.tkeys[1]);
-  { prof::Scope ps("k_emit", s);
-  k_emit<KeyT><<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n, proj->n_tiles,
-                                                       reinterpret_cast<const ushort4*>(proj->rect), batch->views,
-                                                       batch->n_views, w.bsum, cap, k0, v_first); }
-  const int tbits = bits_for(batch->n_tiles);
-  const int cur = tiles::sort_pairs<KeyT>(k0, v_first, k1, v_second, w.counters, cap, tbits, w.sweep, s, true);
-  const KeyT* tk = cur ? k1 : k0;
-  const int rgrid = 4 * kNumSMs;
-  { prof::Scope ps("k_ranges", s);
-  k_ranges<KeyT><<<rgrid, 256, 0, s>>>(tk, w.counters, (uint32_t)batch->n_tiles, bins->ranges); }
-  prof::Scope ps("k_keys", s);
-  if (bins->keys)
-    k_keys<KeyT><<<rgrid, 256, 0, s>>>(tk, bins->vals, reinterpret_cast<const float4*>(proj->rgb_d), w.counters,
-                                       reinterpret_cast<unsigned long long*>(bins->keys));
+static const uint32_t* super_instances(const BinWs& w, const uint32_t* order, int64_t n, const rs_projected* proj,
+                                       const rs_view_batch* batch, int64_t cap, int64_t nblk, int n_super_max,
+                                       cudaStream_t s) {
+  KeyT* k0 = reinterpret_cast<KeyT*>(w.skeys[0]);
+  KeyT* k1 = reinterpret_cast<KeyT*>(w.skeys[1]);
+  {
+    prof::Scope ps("k_emit", s);
+    k_emit<KeyT><<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n, reinterpret_cast<const ushort4*>(proj->rect),
+                                                         batch->views, batch->n_views, w.super_base, w.bsum, cap, k0,
+                                                         w.svals[0]);
+  }
+  const int cur = tiles::sort_pairs<KeyT>(k0, w.svals[0], k1, w.svals[1], w.counters, cap, bits_for(n_super_max),
+                                          w.sweep, s, true);
+  const KeyT* sk = cur ? k1 : k0;
+  prof::Scope ps("k_ranges", s);
+  k_ranges<KeyT><<<4 * kNumSMs, 256, 0, s>>>(sk, w.counters, (uint32_t)n_super_max, w.sranges);
+  return cur ? w.svals[1] : w.svals[0];
 }
 
 }  // namespace rs
@@ -294,42 +580,69 @@ extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* 
   if (!proj || !batch || !bins) return RS_ERR_INVALID_ARG;
   if (!bins->vals || !bins->ranges || bins->capacity <= 0 || bins->capacity >= ((int64_t)1 << 32))
     return RS_ERR_INVALID_ARG;
-  if (batch->n_items < 0 || batch->n_items >= ((int64_t)1 << 32) || batch->n_tiles <= 0 || !batch->views)
+  if (batch->n_items < 0 || batch->n_items >= ((int64_t)1 << 32) || batch->n_tiles <= 0 || !batch->views ||
+      batch->n_views <= 0)
     return RS_ERR_INVALID_ARG;
   if (!proj->rgb_d || !proj->rect || !proj->n_tiles) return RS_ERR_INVALID_ARG;
-  const BinWs w = bin_ws_layout(ws, batch->n_items, bins->capacity);
+  const BinWs w = bin_ws_layout(ws, batch->n_items, bins->capacity, batch->n_tiles, batch->n_views);
   if (!ws || ws_bytes < w.bytes || !aligned<uint4>(ws, 256)) return RS_ERR_WORKSPACE;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int64_t n = batch->n_items;
   const int64_t cap = bins->capacity;
   const float4* rgb_d = reinterpret_cast<const float4*>(proj->rgb_d);
+  const ushort4* rect = reinterpret_cast<const ushort4*>(proj->rect);
+  // super-tiles never outnumber tiles: a bound for the super-tile key width and ranges
+  const int n_super_max = batch->n_tiles;
 
   if (cudaMemsetAsync(w.counters, 0, 64, s) != cudaSuccess) return RS_ERR_CUDA;
-  if (cudaMemsetAsync(bins->ranges, 0, (size_t)batch->n_tiles * 2 * sizeof(uint32_t), s) != cudaSuccess)
-    return RS_ERR_CUDA;
-  if (n == 0) {
-    k_count_top<<<1, 1024, 0, s>>>(w.bsum, 0, cap, w.counters, status);
-    return launch_status();
+  if (cudaMemsetAsync(w.sranges, 0, (size_t)n_super_max * 8, s) != cudaSuccess) return RS_ERR_CUDA;
+  {
+    prof::Scope ps("k_super_layout", s);
+    k_super_layout<<<1, 32, 0, s>>>(batch->views, batch->n_views, w.super_base);
   }
-  // 1) items by depth (four 8-bit passes; even count leaves the result in buffer 0)
-  { prof::Scope ps("k_depth_keys", s);
-  k_depth_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rgb_d, n, w.dkeys[0], w.dvals[0]); }
-  radix::sort_pairs(w.dkeys[0], w.dvals[0], w.dkeys[1], w.dvals[1], n, nullptr, 32, w.hist, w.grid_depth, s, false);
-  const uint32_t* order = w.dvals[0];
-  // 2) instance offsets in depth order and K
-  const int64_t nblk = (n + kEmitThreads - 1) / kEmitThreads;
-  { prof::Scope ps("k_count_blocks", s);
-  k_count_blocks<<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n, proj->n_tiles, w.bsum); }
-  { prof::Scope ps("k_count_top", s);
-  k_count_top<<<1, 1024, 0, s>>>(w.bsum, nblk, cap, w.counters, status); }
-  // 3) expansion; the tile passes then ping-pong so that the final values land in bins->vals
-  const int tbits = bits_for(batch->n_tiles);
-  const int passes = radix::sort_passes(tbits);
-  uint32_t* v_first = (passes % 2 == 0) ? bins->vals : w.tvals;
-  uint32_t* v_second = (passes % 2 == 0) ? w.tvals : bins->vals;
-  if (batch->n_tiles <= 65536)
-    sort_instances<uint16_t>(w, order, n, proj, batch, bins, cap, nblk, v_first, v_second, status, s);
-  else
-    sort_instances<uint32_t>(w, order, n, proj, batch, bins, cap, nblk, v_first, v_second, status, s);
+  const uint32_t* svals = w.svals[0];
+  if (n > 0) {
+    // 1) items by depth (four 8-bit passes; an even count leaves the result in buffer 0)
+    {
+      prof::Scope ps("k_depth_keys", s);
+      k_depth_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rgb_d, n, w.dkeys[0], w.dvals[0]);
+    }
+    radix::sort_pairs(w.dkeys[0], w.dvals[0], w.dkeys[1], w.dvals[1], n, nullptr, 32, w.hist, w.grid_depth, s, false);
+    const uint32_t* order = w.dvals[0];
+    // 2) super instances in depth order, sorted stably on the super-tile id
+    const int64_t nblk = (n + kEmitThreads - 1) / kEmitThreads;
+    {
+      prof::Scope ps("k_count_blocks", s);
+      k_count_blocks<<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n, rect, w.bsum);
+    }
+    {
+      prof::Scope ps("k_count_top", s);
+      k_count_top<<<1, 1024, 0, s>>>(w.bsum, nblk, cap, w.counters, status);
+    }
+    svals = (n_super_max <= 65536) ? super_instances<uint16_t>(w, order, n, proj, batch, cap, nblk, n_super_max, s)
+                                   : super_instances<uint32_t>(w, order, n, proj, batch, cap, nblk, n_super_max, s);
+  }
+  // 3) per tile: count (per super-tile segment), scans (ranges and K), scatter
+  const unsigned fgrid = (unsigned)((int64_t)batch->n_tiles * kSegs);
+  {
+    prof::Scope ps("k_fine_count", s);
+    k_fine_count<<<fgrid, kFineThreads, 0, s>>>(svals, rect, batch->views, batch->n_views, w.super_base, w.sranges,
+                                                 w.seg_cnt);
+  }
+  {
+    prof::Scope ps("k_fine_seg_scan", s);
+    k_fine_seg_scan<<<(unsigned)((batch->n_tiles + 255) / 256), 256, 0, s>>>(w.seg_cnt, batch->views, batch->n_views,
+                                                                            w.super_base, batch->n_tiles, w.fine_tot);
+  }
+  {
+    prof::Scope ps("k_fine_scan", s);
+    k_fine_scan<<<1, 1024, 0, s>>>(w.fine_tot, batch->n_tiles, cap, bins->ranges, w.counters, status);
+  }
+  {
+    prof::Scope ps("k_fine_scatter", s);
+    k_fine_scatter<<<fgrid, kFineThreads, 0, s>>>(svals, rect, rgb_d, batch->views, batch->n_views, w.super_base,
+                                                   w.sranges, w.fine_tot, w.seg_cnt, cap, bins->vals,
+                                                   reinterpret_cast<unsigned long long*>(bins->keys));
+  }
   return launch_status();
 }

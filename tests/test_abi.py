@@ -120,10 +120,12 @@ def test_workspace_sizes_grow_with_the_problem(native):
     L = native.lib()
     b = native.RsViewBatch()
     b.n_items = 1000
+    b.n_views = 1
+    b.n_tiles = 64
     small = L.rs_workspace_size(native.RS_STAGE_BIN_SORT, ctypes.byref(b), 10_000)
     big = L.rs_workspace_size(native.RS_STAGE_BIN_SORT, ctypes.byref(b), 1_000_000)
     assert 0 < small < big
-    assert big >= 3 * 4 * 1_000_000           # two key buffers and one value buffer per instance
+    assert big >= 4 * 4 * 1_000_000           # two key and two value buffers of super instances
     b.n_items = 10_000_000
     assert L.rs_workspace_size(native.RS_STAGE_FILTER, ctypes.byref(b), 0) >= 4 * (10_000_000 // 4096)
     assert L.rs_workspace_size(native.RS_STAGE_BACKWARD, ctypes.byref(b), 0) >= 36 * 10_000_000
