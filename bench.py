@@ -10,7 +10,9 @@ better); the same views looped one at a time through plain launches ("plain") an
 forward-only FPS of one view are reported beside it.
 
 `--impl reference` times the FP64 CPU oracle on a bounded sample of the same workload.
-Under torchrun every rank renders its own views (weak scaling, no collective).
+Under torchrun every rank renders its own views of the same Gaussians (weak scaling); the
+step then ends with the two reductions over views: an all-reduce MAX of the importance and
+an all-reduce SUM of the parameter gradients (NCCL), before the pruning filter.
 """
 from __future__ import annotations
 
@@ -41,6 +43,7 @@ def parse():
     ap.add_argument("--views", type=int, default=4, help="views per rank per step")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--sample-pixels", type=int, default=0, help="reference arm: pixels per step (0: auto)")
     return ap.parse_args()
 
@@ -122,6 +125,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
     from paper_2403_13806_gb300 import api, synth, _native as N
+    from paper_2403_13806_gb300 import dist as rd
 
     world, rank, local = dist_env()
     if world > 1:
@@ -161,21 +165,30 @@ def run_ours(args):
     h = torch.zeros(scene.n, dtype=torch.int32, device=dev)
     dL = torch.empty_like(img)
     loss = torch.zeros(1, dtype=torch.float64, device=dev)
-    grads = [torch.zeros_like(t) for t in g.tensors()]
+    gbuf = rd.GradBuffer(g.tensors())
+    grads = gbuf.views
     mask = torch.empty(scene.n, dtype=torch.uint8, device=dev)
     idx = torch.empty(scene.n, dtype=torch.int32, device=dev)
     del probe
 
-    def step(stream=None):
+    def views_part():
         h.zero_()
-        for t in grads:
-            t.zero_()
+        gbuf.zero_()
         api.project(g, vb, cfg, st, out=proj)
         api.bin_sort(proj, vb, bins, ws_sort, st)
         api.render(proj, bins, vb, cfg, image=img, T_final=T, last=L, importance=h)
         api.l1_loss(img, target, dL, loss)
         api.render_backward(g, vb, proj, bins, T, L, dL, grads, ws_bwd, cfg)
+
+    def prune():
         api.filter(h, 0.01, N.RS_PRUNE_BELOW, ws_f, mask=mask, idx=idx)
+
+    # N = 1: the whole step is one graph.  N > 1: the per-view part is the graph, then the
+    # reductions over views (NCCL) and the filter on the reduced importance.
+    def step_body():
+        views_part()
+        if world == 1:
+            prune()
 
     # capture the batched step in a CUDA graph
     torch.cuda.synchronize()
@@ -183,13 +196,20 @@ def run_ours(args):
     s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
         for _ in range(2):
-            step()
+            step_body()
     torch.cuda.current_stream().wait_stream(s)
     torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
-        step()
+        step_body()
     torch.cuda.synchronize()
+
+    def run_step():
+        graph.replay()
+        if world > 1:
+            rd.allreduce_importance(h)
+            rd.allreduce_grads(gbuf)
+            prune()
 
     def barrier():
         if world > 1:
@@ -197,7 +217,7 @@ def run_ours(args):
         torch.cuda.synchronize()
 
     for _ in range(max(args.warmup, 3)):
-        graph.replay()
+        run_step()
     st.zero_()
     barrier()
     with ClockSampler(local) as clk:
@@ -206,14 +226,14 @@ def run_ours(args):
         t_end = time.perf_counter() + 1.0
         while time.perf_counter() < t_end:
             for _ in range(8):
-                graph.replay()
+                run_step()
             torch.cuda.synchronize()
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(args.steps):
-            graph.replay()
+            run_step()
         e1.record()
         barrier()
     ms = e0.elapsed_time(e1)
@@ -232,6 +252,13 @@ def run_ours(args):
     stage_ms, kernel_ms = stage_times(api, N, g, vb, cfg, st, proj, bins, ws_sort, img, T, L, h, target, dL, loss,
                                       grads, ws_bwd, ws_f, mask, idx, reps=max(3, min(args.steps, 10)))
     pairs = int(L.to(torch.int64).sum().item())   # entries walked by the backward (sum of last over pixels)
+    # super-tile instances (4 x 4 tiles per super-tile) of the batch, for the binning byte counts
+    r = proj.rect[:vb.n_items].to(torch.int64) & 0xffff
+    nonempty = (r[:, 2] > r[:, 0]) & (r[:, 3] > r[:, 1])
+    sw = torch.where(nonempty, (r[:, 2] - 1) // 4 - r[:, 0] // 4 + 1, torch.zeros_like(r[:, 0]))
+    sh_ = torch.where(nonempty, (r[:, 3] - 1) // 4 - r[:, 1] // 4 + 1, torch.zeros_like(r[:, 0]))
+    n_super = int((sw * sh_).sum().item())
+    del r, nonempty, sw, sh_
 
     # plain: the same views one at a time, no graph
     plain = None
@@ -240,30 +267,39 @@ def run_ours(args):
         plain, fps = plain_loop(api, N, torch, g, vb1, cfg, target, cams, reps=max(3, min(args.steps, 10)), dev=dev)
 
     # end to end through the public API: host parameters and targets in pinned memory
-    e2e = e2e_run(api, N, torch, scene, vb, cfg, target, cap, reps=max(3, min(args.steps, 5)), dev=dev)
+    e2e = e2e_run(api, N, torch, scene, vb, cfg, target, cap, reps=max(3, min(args.steps, 5)), dev=dev, world=world)
 
     # roofline of the dominant kernel
     hbm, peak_kind, pk = peaks()
-    roof = roofline(kernel_ms, vb, sres, hbm, peak_kind, pairs)
+    work = kernel_work(vb, sres, pairs, n_super)
+    roof = roofline(kernel_ms, work, hbm, peak_kind, V)
+    per_kernel = {k: kernel_frac(k, kernel_ms[k], work, hbm) for k in kernel_ms if k in work}
     launches = int(round(sum(v["launches_per_step"] for v in kernel_ms.values()))) * args.steps
 
     if rank == 0:
-        cpu = cpu_baseline(args)
+        cpu = None if args.no_cpu else cpu_baseline(args)
         line = {
             "metric": METRIC, "value": round(value, 5), "unit": "ms/view (fwd+bwd)", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded 360-capture scene; target = render of a perturbed copy)",
-            "config": dict(workload_config(V, world), parallelism=f"views sharded over {world} GPU(s), no collective"),
+            "config": dict(workload_config(V, world),
+                           parallelism=(f"views sharded over {world} GPUs; all-reduce MAX of importance and SUM "
+                                        f"of gradients per step" if world > 1 else "1 GPU, no collective")),
             "batched_ms_per_view": round(value, 5),
             "plain_ms_per_view": round(plain, 5) if plain else None,
             "batched_over_plain_speedup": round(plain / value, 3) if plain else None,
             "fps_forward_single_view": round(fps, 1) if fps else None,
             "instances_per_view": int(sres["n_instances"] / V),
+            "super_instances_per_view": int(n_super / V),
+            "pairs_per_pixel": round(pairs / vb.n_pixels, 2),
+            "blends_per_s_forward": round(pairs / (kernel_ms["k_render_importance"]["ms_per_launch"] / 1e3), 0)
+            if "k_render_importance" in kernel_ms else None,
             "stage_ms_per_step": {k: round(v, 5) for k, v in stage_ms.items()},
             "kernel_ms_per_step": {k: round(v["ms_per_step"], 5) for k, v in
                                    sorted(kernel_ms.items(), key=lambda kv: -kv[1]["ms_per_step"])},
-            "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
+            "e2e": e2e, "roofline": roof, "roofline_per_kernel": per_kernel, "cpu_baseline": cpu,
+            "clocks": clk.summary(),
             "gpu_launches": launches,
         }
         print(json.dumps(line))
@@ -369,9 +405,11 @@ def plain_loop(api, N, torch, g, vb1, cfg, target, cams, reps, dev):
     return plain, fps
 
 
-def e2e_run(api, N, torch, scene, vb, cfg, target, cap, reps, dev):
+def e2e_run(api, N, torch, scene, vb, cfg, target, cap, reps, dev, world=1):
     """Same batched step through the public API, parameters and targets copied from pinned
-    host memory each step, the loss read back to the host."""
+    host memory each step, the loss read back to the host (with the reductions over ranks
+    when world > 1)."""
+    from paper_2403_13806_gb300 import dist as rd
     host = [torch.from_numpy(np.ascontiguousarray(a, np.float32)).pin_memory() for a in scene.arrays()]
     tgt_h = target.cpu().pin_memory()
     dev_p = [torch.empty_like(t, device=dev) for t in host]
@@ -382,7 +420,8 @@ def e2e_run(api, N, torch, scene, vb, cfg, target, cap, reps, dev):
     bins = api.Bins.empty(cap, vb.n_tiles, device=dev)
     ws_sort, ws_bwd, ws_f = api.Workspace(dev), api.Workspace(dev), api.Workspace(dev)
     h = torch.zeros(scene.n, dtype=torch.int32, device=dev)
-    grads = [torch.zeros_like(t) for t in dev_p]
+    gbuf = rd.GradBuffer(dev_p)
+    grads = gbuf.views
     loss_h = torch.zeros(1, dtype=torch.float64).pin_memory()
 
     def step():
@@ -390,13 +429,15 @@ def e2e_run(api, N, torch, scene, vb, cfg, target, cap, reps, dev):
             d.copy_(s, non_blocking=True)
         tgt_d.copy_(tgt_h, non_blocking=True)
         h.zero_()
-        for t in grads:
-            t.zero_()
+        gbuf.zero_()
         api.project(g, vb, cfg, st, out=proj)
         api.bin_sort(proj, vb, bins, ws_sort, st)
         img, T, L = api.render(proj, bins, vb, cfg, importance=h)
         loss, dl = api.l1_loss(img, tgt_d)
         api.render_backward(g, vb, proj, bins, T, L, dl, grads, ws_bwd, cfg)
+        if world > 1:
+            rd.allreduce_importance(h)
+            rd.allreduce_grads(gbuf)
         api.filter(h, 0.01, N.RS_PRUNE_BELOW, ws_f)
         loss_h.copy_(loss, non_blocking=True)
         torch.cuda.current_stream().synchronize()
@@ -420,30 +461,99 @@ ALU_PEAK_OPS = 152 * 128 * 2070e6
 # transmittance 3, weight 1, colour 3, bookkeeping 1); backward 46.
 OPS_PER_PAIR = {"k_render_importance": 22, "k_render": 22, "k_render_bwd": 46}
 
+# DRAM bytes (read + write) per launch of a kernel, per view of the benchmark workload, from
+# one ncu capture of a one-view run (command and figures under profiles/), with the hashes
+# of the sources the kernel was built from.  A capture stays valid only while those sources
+# are unchanged; otherwise the roofline reports traffic as null.
+NCU_TRAFFIC = {
+    "k_render_bwd": {"bytes_per_view": 25160960, "files": ['render_bwd.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "f1149114a9ca0344",
+                "profile": "k_render_bwd_1M_1view.md"},
+    "k_render_importance": {"bytes_per_view": 6874368, "files": ['render.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "ef776bd49ca59be4",
+                "profile": "k_render_1M_1view.md"},
+    "k_fine_scatter": {"bytes_per_view": 24204032, "files": ['binsort.cu', 'rs_common.cuh'], "sha": "a64b3191aaf884f5",
+                "profile": "k_fine_scatter_1M_1view.md"},
+}
 
-def roofline(kernel_ms, vb, sres, hbm, peak_kind, pairs):
-    """Roofline of the kernel with the largest share of the step (library launch events).
 
-    Algorithmic work per launch: the instance sort pass moves 2 x K x (key + value bytes);
-    the projection 288 B per item; the emission 6 or 8 B per instance; the blend kernels
-    FP32 operations per evaluated pair (pairs = sum over pixels of entries walked)."""
+def _src_hash(files):
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2403_13806_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(name, views):
+    rec = NCU_TRAFFIC.get(name)
+    if not rec or _src_hash(rec["files"]) != rec["sha"]:
+        return None
+    return int(rec["bytes_per_view"] * views)
+
+
+def kernel_work(vb, sres, pairs, n_super):
+    """Algorithmic work per launch of each library kernel: DRAM bytes the method must move
+    (bound "hbm") or FP32 lane operations (bound "alu").
+
+    Items M (view, Gaussian) pairs, instances K, super-tile instances Ks, pixels P:
+    projection reads 236 B of parameters and writes 52 B per item; the depth sort moves
+    8 B per item and pass (read key+value, write key+value = 16 B in the scatter, 4 B read in
+    the count); the super-tile sort moves 2 x (2 + 4) B per super instance and pass (count:
+    2 B); the fine partition reads 4 B index + 8 B rect per super instance (twice: count and
+    scatter) and writes 4 B per instance; the projection backward reads 236 + 36 B and writes
+    236 B per item; the blend kernels count FP32 operations per evaluated pair."""
+    M, K, Ks, P = vb.n_items, sres["n_instances"], n_super, vb.n_pixels
+    kb = 2 if vb.n_tiles <= 65536 else 4
+    hbm = {
+        "k_project": M * (236 + 52),
+        "k_depth_keys": M * (4 + 8),
+        "k_upsweep": M * 4,
+        "k_downsweep": M * 16,
+        "k_count_blocks": M * (4 + 8),
+        "k_emit": M * (4 + 8) + Ks * (kb + 4),
+        "k_tile_hist": Ks * kb,
+        "k_tile_sort": Ks * 2 * (kb + 4),
+        "k_ranges": Ks * kb,
+        "k_fine_count": Ks * (4 + 8),
+        "k_fine_scatter": Ks * (4 + 8) + K * 4,
+        "k_l1": P * 3 * 4 * 3,
+        "k_project_bwd": M * (236 + 36 + 236),
+        "k_filter_count": vb.n_gaussians * 4,
+        "k_filter_scatter": vb.n_gaussians * (4 + 1) + vb.n_gaussians * 4,
+    }
+    out = {k: ("hbm", v) for k, v in hbm.items()}
+    for k, ops in OPS_PER_PAIR.items():
+        out[k] = ("alu", pairs * ops)
+    return out
+
+
+def kernel_frac(name, rec, work, hbm_peak):
+    bound, w = work[name]
+    t = rec["ms_per_launch"] / 1000.0
+    if bound == "hbm":
+        a = w / t / 1e9
+        return {"bound": "hbm", "achieved_gbs": round(a, 1), "frac": round(a / hbm_peak, 4)}
+    a = w / t / 1e12
+    return {"bound": "alu", "achieved_tops": round(a, 2), "frac": round(a / (ALU_PEAK_OPS / 1e12), 4)}
+
+
+def roofline(kernel_ms, work, hbm, peak_kind, views):
+    """Roofline of the kernel with the largest share of the step (library launch events)."""
     name, rec = max(kernel_ms.items(), key=lambda kv: kv[1]["ms_per_step"])
     t = rec["ms_per_launch"] / 1000.0
-    K = sres["n_instances"]
-    kb = 2 if vb.n_tiles <= 65536 else 4
-    hbm_bytes = {"k_onesweep": 2 * K * (kb + 4), "k_project": vb.n_items * (236 + 52), "k_emit": K * (kb + 4),
-                 "k_ranges": K * kb, "k_project_bwd": vb.n_items * (236 + 36 + 236)}
-    if name in hbm_bytes:
-        a = hbm_bytes[name] / t / 1e9
+    bound, w = work.get(name, ("hbm", 0))
+    traffic = ncu_traffic(name, views)
+    if bound == "hbm":
+        a = w / t / 1e9
         return {"kernel": name, "bound": "hbm", "achieved": round(a, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(a / hbm, 4), "traffic": None, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                "work_per_launch": int(hbm_bytes[name]), "ms_per_launch": round(rec["ms_per_launch"], 5)}
-    ops = pairs * OPS_PER_PAIR.get(name, 0)
-    a = ops / t / 1e12
+                "frac": round(a / hbm, 4), "traffic": traffic,
+                "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "work_per_launch": int(w), "ms_per_launch": round(rec["ms_per_launch"], 5)}
+    a = w / t / 1e12
     peak = ALU_PEAK_OPS / 1e12
-    return {"kernel": name, "bound": "alu", "achieved": round(a, 2), "peak": round(peak, 2), "unit": "TOP/s (FP32 lane ops)",
-            "frac": round(a / peak, 4), "traffic": None,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz", "work_per_launch": int(ops),
+    return {"kernel": name, "bound": "alu", "achieved": round(a, 2), "peak": round(peak, 2),
+            "unit": "TOP/s (FP32 lane ops)", "frac": round(a / peak, 4), "traffic": traffic,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz", "work_per_launch": int(w),
             "ms_per_launch": round(rec["ms_per_launch"], 5)}
 
 
