@@ -1,6 +1,11 @@
-// Blend-ready Gaussian records shared by the forward and backward blend kernels.
+// Blend-ready Gaussian records and the per-pixel-pair arithmetic shared by the forward and
+// backward blend kernels.
 //
-// Both kernels stage and evaluate a record with the same explicitly rounded operations
+// Each thread owns pixels of one column, taken two at a time: the two pixels of a pair share
+// the horizontal offset dx and differ in dy, so the quadratic form, the opacity product,
+// the transmittance update and the colour sums run as packed two-lane FP32 instructions
+// (__ffma2_rn / __fmul2_rn / __fadd2_rn, one rounding per lane, identical to the scalar
+// operations).  Both kernels evaluate a record with the same explicitly rounded operations
 // (no compiler contraction), so the backward pass replays every skip decision of the
 // forward pass bit for bit.
 #pragma once
@@ -9,24 +14,78 @@
 
 namespace rs {
 
-// Record of one Gaussian: g = (x, y, A, B), g2 = (C, cut, o, 0), col = (r, g, b, 0) with
-// A, B, C = conic (a, b, c) times (-log2(e)/2, -log2(e), -log2(e)/2), so that
-// p2 = A dx^2 + B dx dy + C dy^2 = log2(e) * power, and cut = log2(1/(255 o)) - 1e-3: below
-// it alpha = o 2^p2 < 1/255 for sure, and only pairs above it take the exact test.
+// Record of one Gaussian in shared memory.  Every value a pixel pair uses on both lanes is
+// stored twice so that a packed instruction reads it as one register pair.  A, B, C are the
+// conic (a, b, c) times (-log2(e)/2, -log2(e), -log2(e)/2), so that
+// p2 = A dx^2 + B dx dy + C dy^2 = log2(e) * power; cut = log2(1/(255 o)) - 1e-3: below it
+// alpha = o 2^p2 < 1/255 for sure, and only pairs above it take the exact test.
+struct BlendRec {
+  float4 xy;    // (x, x, y, y)
+  float4 ab;    // (A, A, B, B)
+  float4 co;    // (C, C, o, o)
+  float4 rg;    // (r, r, g, g)
+  float4 bc;    // (b, b, cut, cut)
+};
+
 __device__ __forceinline__ void stage_record(const float2* xy, const float4* conic_o, const float4* rgb_d,
-                                             uint32_t item, float4& g, float4& g2, float4& col) {
+                                             uint32_t item, BlendRec& r) {
   const float2 p = __ldg(xy + item);
   const float4 co = __ldg(conic_o + item);
   const float4 cd = __ldg(rgb_d + item);
-  g = make_float4(p.x, p.y, __fmul_rn(-0.5f * kLog2e, co.x), __fmul_rn(-kLog2e, co.y));
-  g2 = make_float4(__fmul_rn(-0.5f * kLog2e, co.z), __fsub_rn(log2f(__fdiv_rn(kAlphaMin, co.w)), 1e-3f), co.w, 0.f);
-  col = make_float4(cd.x, cd.y, cd.z, 0.f);
+  const float A = __fmul_rn(-0.5f * kLog2e, co.x), B = __fmul_rn(-kLog2e, co.y), C = __fmul_rn(-0.5f * kLog2e, co.z);
+  const float cut = __fsub_rn(log2f(__fdiv_rn(kAlphaMin, co.w)), 1e-3f);
+  r.xy = make_float4(p.x, p.x, p.y, p.y);
+  r.ab = make_float4(A, A, B, B);
+  r.co = make_float4(C, C, co.w, co.w);
+  r.rg = make_float4(cd.x, cd.x, cd.y, cd.y);
+  r.bc = make_float4(cd.z, cd.z, cut, cut);
 }
 
-// p2 = log2(e) * power at pixel (fu, fv), with dx = x - u, dy = y - v.
-__device__ __forceinline__ float blend_power(const float4& g, const float4& g2, float fu, float fv) {
-  const float dx = __fsub_rn(g.x, fu), dy = __fsub_rn(g.y, fv);
-  return __fmaf_rn(dx, __fmaf_rn(g.z, dx, __fmul_rn(g.w, dy)), __fmul_rn(__fmul_rn(g2.x, dy), dy));
+__device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
+
+// 2^x by the hardware approximation (ex2.approx.ftz: relative error below 2^-22 for the
+// arguments used here, x in [-8.1, 0], whose results are normal numbers).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// (x - u, x - u) for the thread's column u (nu = (-u, -u)).
+__device__ __forceinline__ float2 pair_dx(const BlendRec& r, float2 nu) { return __fadd2_rn(lo2(r.xy), nu); }
+
+// (y - v0, y - v1) for a pixel pair in rows v0, v1 (nv = (-v0, -v1)).
+__device__ __forceinline__ float2 pair_dy(const BlendRec& r, float2 nv) { return __fadd2_rn(hi2(r.xy), nv); }
+
+// p2 = log2(e) * power for both pixels of a pair: dx (A dx + B dy) + (C dy) dy.
+__device__ __forceinline__ float2 pair_power(const BlendRec& r, float2 dx, float2 dy) {
+  return __ffma2_rn(dx, __ffma2_rn(lo2(r.ab), dx, __fmul2_rn(hi2(r.ab), dy)),
+                    __fmul2_rn(__fmul2_rn(lo2(r.co), dy), dy));
+}
+
+// Per-pixel outcome of the blend rule's tests on one record.
+struct PairAlpha {
+  float2 ex;      // 2^min(p2, 0)
+  float2 raw;     // o 2^min(p2, 0) (before the 0.99 clamp)
+  float2 alpha;   // min(0.99, raw)
+  bool in0, in1;  // cut <= p2 <= 0 and alpha >= 1/255
+};
+
+__device__ __forceinline__ PairAlpha pair_alpha(const BlendRec& r, float2 p2) {
+  PairAlpha a;
+  a.ex = make_float2(ex2_approx(fminf(p2.x, 0.f)), ex2_approx(fminf(p2.y, 0.f)));
+  a.raw = __fmul2_rn(hi2(r.co), a.ex);
+  a.alpha = make_float2(fminf(kAlphaMax, a.raw.x), fminf(kAlphaMax, a.raw.y));
+  const float cut = r.bc.z;
+  a.in0 = p2.x <= 0.f && p2.x >= cut && a.alpha.x >= kAlphaMin;
+  a.in1 = p2.y <= 0.f && p2.y >= cut && a.alpha.y >= kAlphaMin;
+  return a;
+}
+
+// 1 - alpha on both lanes (one rounding, as the scalar subtraction).
+__device__ __forceinline__ float2 one_minus(float2 a) {
+  return __ffma2_rn(a, make_float2(-1.f, -1.f), make_float2(1.f, 1.f));
 }
 
 }  // namespace rs

@@ -1,13 +1,14 @@
 // rs_render / rs_importance: per-tile front-to-back compositing, Eq. (render-gs), with the
 // importance max of Eq. (importance-score) fused in.
 //
-// One CTA per (view, tile); each thread owns two vertically adjacent pixels, so every
-// Gaussian record read from shared memory serves two pixel evaluations.  The tile's sorted
-// list is consumed in batches of two records per thread, staged into shared memory in
-// blend-ready form (conic pre-scaled to the log2 domain), so the inner loop per
-// (pixel, Gaussian) pair is FP32 arithmetic plus one ex2.  A CTA stops fetching batches
-// once every pixel is done (__syncthreads_count), and a warp leaves a batch early once all
-// of its pixels are done.
+// One CTA per (view, tile); each thread owns PX vertically adjacent pixels of one column
+// (PX = 4, or 2 for 8x8 tiles), evaluated as PX/2 pixel pairs with packed two-lane FP32
+// instructions, so every Gaussian record read from shared memory serves PX pixel
+// evaluations.  The tile's sorted list is consumed in batches of two records per thread,
+// staged into shared memory in blend-ready form (conic pre-scaled to the log2 domain); the
+// per-pixel decisions are predicated, not branched.  A warp skips a record that none of
+// its pixels' alpha-support tests accept, leaves a batch once all of its pixels are done,
+// and the CTA stops fetching batches once every pixel is done (__syncthreads_count).
 // Importance: composited alpha*T values are max-reduced across the warp (redux.sync on the
 // float bits, which order like the values for non-negative floats), then across the CTA in
 // shared memory, then one global atomicMax per (tile, Gaussian).
@@ -37,42 +38,12 @@ struct RenderArgs {
   int64_t n_gaussians;
 };
 
-struct PixelState {
-  float T, c0, c1, c2;
-  int last;
-  bool done;
-};
-
-// One (pixel, Gaussian) step of the blend rule; returns the composited weight alpha*T
-// (0 if the entry was skipped or compositing stopped here).
-__device__ __forceinline__ float blend_step(PixelState& s, const float4& g, const float4& g2, const float4& col,
-                                            float fu, float fv, int pos) {
-  if (s.done) return 0.f;
-  const float p2 = blend_power(g, g2, fu, fv);
-  if (!(p2 <= 0.f && p2 >= g2.y)) return 0.f;
-  const float alpha = fminf(kAlphaMax, __fmul_rn(g2.z, exp2f(p2)));
-  if (alpha < kAlphaMin) return 0.f;
-  const float Tn = s.T * (1.f - alpha);
-  if (Tn < kTMin) {
-    s.done = true;
-    return 0.f;
-  }
-  const float w = alpha * s.T;
-  s.c0 = fmaf(w, col.x, s.c0);
-  s.c1 = fmaf(w, col.y, s.c1);
-  s.c2 = fmaf(w, col.z, s.c2);
-  s.T = Tn;
-  s.last = pos + 1;
-  return w;
-}
-
-template <int TW, int TH, bool IMAGE, bool IMPORTANCE>
-__global__ void __launch_bounds__(TW* TH / 2) k_render(RenderArgs a) {
-  constexpr int NT = TW * TH / 2;   // threads; each owns pixels (x, 2r) and (x, 2r + 1)
-  constexpr int NB = 2 * NT;        // records per batch
-  __shared__ float4 s_geo[NB];
-  __shared__ float4 s_geo2[NB];
-  __shared__ float4 s_col[NB];
+template <int TW, int TH, int PX, bool IMAGE, bool IMPORTANCE>
+__global__ void __launch_bounds__(TW* TH / PX) k_render(RenderArgs a) {
+  constexpr int NT = TW * TH / PX;   // threads; each owns pixels (x, PX r + k), k < PX
+  constexpr int NP = PX / 2;         // pixel pairs per thread
+  constexpr int NB = 2 * NT;         // records per batch
+  __shared__ BlendRec s_rec[NB];
   __shared__ uint32_t s_h[IMPORTANCE ? NB : 1];
   __shared__ uint32_t s_gid[IMPORTANCE ? NB : 1];
 
@@ -85,25 +56,41 @@ __global__ void __launch_bounds__(TW* TH / 2) k_render(RenderArgs a) {
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int pu = txi * TW + (tid % TW);
-  const int pv0 = tyi * TH + 2 * (tid / TW);
-  const bool in0 = pu < cam.width && pv0 < cam.height;
-  const bool in1 = pu < cam.width && pv0 + 1 < cam.height;
-  const float fu = (float)pu, fv0 = (float)pv0, fv1 = (float)(pv0 + 1);
+  const int pv0 = tyi * TH + PX * (tid / TW);
+  const float2 nu = make_float2(-(float)pu, -(float)pu);
   const uint2 rg = a.ranges[tile];
   const uint32_t start = rg.x, end = rg.y;
 
-  PixelState s0{1.f, 0.f, 0.f, 0.f, 0, !in0};
-  PixelState s1{1.f, 0.f, 0.f, 0.f, 0, !in1};
+  float2 nv[NP], T[NP], cr[NP], cg[NP], cb[NP];
+  int last[PX];
+  bool done[PX];
+#pragma unroll
+  for (int k = 0; k < PX; ++k) {
+    last[k] = 0;
+    done[k] = !(pu < cam.width && pv0 + k < cam.height);
+  }
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    nv[q] = make_float2(-(float)(pv0 + 2 * q), -(float)(pv0 + 2 * q + 1));
+    T[q] = make_float2(1.f, 1.f);
+    cr[q] = cg[q] = cb[q] = make_float2(0.f, 0.f);
+  }
+  auto all_done = [&]() {
+    bool d = true;
+#pragma unroll
+    for (int k = 0; k < PX; ++k) d = d && done[k];
+    return d;
+  };
 
   for (uint32_t b0 = start; b0 < end; b0 += NB) {
-    if (__syncthreads_count(!(s0.done && s1.done)) == 0) break;
+    if (__syncthreads_count(!all_done()) == 0) break;
     const int nb = (int)min((uint32_t)NB, end - b0);
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const int slot = tid + k * NT;
       if (slot < nb) {
         const uint32_t item = __ldg(a.vals + b0 + slot);
-        stage_record(a.xy, a.conic_o, a.rgb_d, item, s_geo[slot], s_geo2[slot], s_col[slot]);
+        stage_record(a.xy, a.conic_o, a.rgb_d, item, s_rec[slot]);
         if (IMPORTANCE) {
           s_h[slot] = 0u;
           s_gid[slot] = a.subset ? __ldg(a.subset + item) : (uint32_t)((int64_t)item - cam.item_base);
@@ -113,16 +100,45 @@ __global__ void __launch_bounds__(TW* TH / 2) k_render(RenderArgs a) {
     __syncthreads();
     const int base = (int)(b0 - start);
     for (int j = 0; j < nb; ++j) {
-      const float4 g = s_geo[j];
-      const float4 g2 = s_geo2[j];
-      const float4 col = s_col[j];
-      const float w0 = blend_step(s0, g, g2, col, fu, fv0, base + j);
-      const float w1 = blend_step(s1, g, g2, col, fu, fv1, base + j);
-      if (IMPORTANCE) {
-        const uint32_t m = __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(w0, w1)));
-        if (lane == 0 && m) atomicMax(&s_h[j], m);
+      const BlendRec r = s_rec[j];
+      const float2 dx = pair_dx(r, nu);
+      float2 p2[NP];
+      bool any = false;
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        p2[q] = pair_power(r, dx, pair_dy(r, nv[q]));
+        any |= (!done[2 * q] && p2[q].x <= 0.f && p2[q].x >= r.bc.z) ||
+               (!done[2 * q + 1] && p2[q].y <= 0.f && p2[q].y >= r.bc.z);
       }
-      if (__all_sync(0xffffffffu, s0.done && s1.done)) break;
+      if (!__any_sync(0xffffffffu, any)) continue;   // no pixel of the warp is in this record's support
+      float m = 0.f;
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        const PairAlpha al = pair_alpha(r, p2[q]);
+        bool ok0 = al.in0 && !done[2 * q], ok1 = al.in1 && !done[2 * q + 1];
+        const float2 Tn = __fmul2_rn(T[q], one_minus(al.alpha));
+        const bool st0 = ok0 && Tn.x < kTMin, st1 = ok1 && Tn.y < kTMin;   // stop before compositing
+        done[2 * q] |= st0;
+        done[2 * q + 1] |= st1;
+        ok0 &= !st0;
+        ok1 &= !st1;
+        float2 w = __fmul2_rn(al.alpha, T[q]);
+        w.x = ok0 ? w.x : 0.f;
+        w.y = ok1 ? w.y : 0.f;
+        T[q].x = ok0 ? Tn.x : T[q].x;
+        T[q].y = ok1 ? Tn.y : T[q].y;
+        cr[q] = __ffma2_rn(w, lo2(r.rg), cr[q]);
+        cg[q] = __ffma2_rn(w, hi2(r.rg), cg[q]);
+        cb[q] = __ffma2_rn(w, lo2(r.bc), cb[q]);
+        last[2 * q] = ok0 ? base + j + 1 : last[2 * q];
+        last[2 * q + 1] = ok1 ? base + j + 1 : last[2 * q + 1];
+        if (IMPORTANCE) m = fmaxf(m, fmaxf(w.x, w.y));
+      }
+      if (IMPORTANCE) {
+        const uint32_t mm = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+        if (lane == 0 && mm) atomicMax(&s_h[j], mm);
+      }
+      if (__all_sync(0xffffffffu, all_done())) break;
     }
     __syncthreads();
     if (IMPORTANCE) {
@@ -130,8 +146,8 @@ __global__ void __launch_bounds__(TW* TH / 2) k_render(RenderArgs a) {
       for (int k = 0; k < 2; ++k) {
         const int slot = tid + k * NT;
         if (slot < nb) {
-          const uint32_t m = s_h[slot];
-          if (m && (int64_t)s_gid[slot] < a.n_gaussians) atomicMax(a.importance + s_gid[slot], m);
+          const uint32_t mm = s_h[slot];
+          if (mm && (int64_t)s_gid[slot] < a.n_gaussians) atomicMax(a.importance + s_gid[slot], mm);
         }
       }
     }
@@ -139,29 +155,31 @@ __global__ void __launch_bounds__(TW* TH / 2) k_render(RenderArgs a) {
 
   const int64_t HW = (int64_t)cam.width * cam.height;
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const PixelState& s = k ? s1 : s0;
-    if (k ? !in1 : !in0) continue;
+  for (int k = 0; k < PX; ++k) {
+    if (!(pu < cam.width && pv0 + k < cam.height)) continue;
+    const int q = k >> 1;
+    const bool hi = k & 1;
+    const float Tk = hi ? T[q].y : T[q].x;
     const int64_t pix = (int64_t)(pv0 + k) * cam.width + pu;
     if (IMAGE) {
       float* img = a.image + 3 * cam.pixel_base;
-      img[pix] = s.c0 + s.T * a.bg0;
-      img[HW + pix] = s.c1 + s.T * a.bg1;
-      img[2 * HW + pix] = s.c2 + s.T * a.bg2;
+      img[pix] = (hi ? cr[q].y : cr[q].x) + Tk * a.bg0;
+      img[HW + pix] = (hi ? cg[q].y : cg[q].x) + Tk * a.bg1;
+      img[2 * HW + pix] = (hi ? cb[q].y : cb[q].x) + Tk * a.bg2;
     }
-    if (a.T_final) a.T_final[cam.pixel_base + pix] = s.T;
-    if (a.last) a.last[cam.pixel_base + pix] = s.last;
+    if (a.T_final) a.T_final[cam.pixel_base + pix] = Tk;
+    if (a.last) a.last[cam.pixel_base + pix] = last[k];
   }
 }
 
-template <int TW, int TH>
+template <int TW, int TH, int PX>
 static void launch_render(const RenderArgs& a, int n_tiles, bool image, bool imp, cudaStream_t s) {
-  constexpr int NT = TW * TH / 2;
+  constexpr int NT = TW * TH / PX;
   prof::Scope ps(imp ? "k_render_importance" : "k_render", s);
-  if (image && imp) k_render<TW, TH, true, true><<<n_tiles, NT, 0, s>>>(a);
-  else if (image) k_render<TW, TH, true, false><<<n_tiles, NT, 0, s>>>(a);
-  else if (imp) k_render<TW, TH, false, true><<<n_tiles, NT, 0, s>>>(a);
-  else k_render<TW, TH, false, false><<<n_tiles, NT, 0, s>>>(a);
+  if (image && imp) k_render<TW, TH, PX, true, true><<<n_tiles, NT, 0, s>>>(a);
+  else if (image) k_render<TW, TH, PX, true, false><<<n_tiles, NT, 0, s>>>(a);
+  else if (imp) k_render<TW, TH, PX, false, true><<<n_tiles, NT, 0, s>>>(a);
+  else k_render<TW, TH, PX, false, false><<<n_tiles, NT, 0, s>>>(a);
 }
 
 rs_status render_dispatch(const rs_projected* proj, const rs_bins* bins, const rs_view_batch* batch,
@@ -185,9 +203,9 @@ rs_status render_dispatch(const rs_projected* proj, const rs_bins* bins, const r
   a.importance = importance;
   a.n_gaussians = n_gaussians;
   const bool img = image != nullptr, imp = importance != nullptr;
-  if (batch->tile_w == 16 && batch->tile_h == 16) launch_render<16, 16>(a, batch->n_tiles, img, imp, s);
-  else if (batch->tile_w == 32 && batch->tile_h == 8) launch_render<32, 8>(a, batch->n_tiles, img, imp, s);
-  else if (batch->tile_w == 8 && batch->tile_h == 8) launch_render<8, 8>(a, batch->n_tiles, img, imp, s);
+  if (batch->tile_w == 16 && batch->tile_h == 16) launch_render<16, 16, 4>(a, batch->n_tiles, img, imp, s);
+  else if (batch->tile_w == 32 && batch->tile_h == 8) launch_render<32, 8, 4>(a, batch->n_tiles, img, imp, s);
+  else if (batch->tile_w == 8 && batch->tile_h == 8) launch_render<8, 8, 2>(a, batch->n_tiles, img, imp, s);
   else return RS_ERR_UNSUPPORTED;
   return launch_status();
 }

@@ -1,14 +1,15 @@
 // rs_render_backward: derivative of Eq. (render-gs) (training loss of Sec. 3.2), in two
 // kernels.
 //
-// k_render_bwd -- one CTA per (view, tile), two pixels per thread, the tile list walked back
+// k_render_bwd -- one CTA per (view, tile), four pixels of a column per thread (two for 8x8
+//   tiles) evaluated as pixel pairs with packed FP32 instructions, the tile list walked back
 //   to front from the largest `last` of the tile.  Each pixel recovers T_j = T_{j+1}/(1-a_j)
 //   from its T_final and accumulates, per composited entry j,
 //     dL/dc_j     = a_j T_j dL/dC
 //     dL/da_j     = T_j (c_j . dL/dC) - (S_j . dL/dC + T_final bg . dL/dC) / (1 - a_j)
 //   (S_j: colour composited behind j), and through a = o exp(power) (no gradient where the
 //   0.99 clamp is active) the image-space gradients of the mean, conic and opacity.  The
-//   nine values of a thread's two pixels are summed in registers, across the warp by
+//   nine values of a thread's pixels are summed in registers, across the warp by
 //   recursive halving (16 shuffles, only for entries some lane composited), across the
 //   CTA through per-warp shared-memory slots, and added to per-item buffers with two
 //   float4 and one float atomic per (tile, entry).
@@ -48,52 +49,6 @@ struct BwdBlendArgs {
   Grad2D g;
 };
 
-// Per-pixel state of the back-to-front walk.
-struct BwdPixel {
-  float T;      // transmittance after the current entry (T_final at the start)
-  float G0, G1, G2;
-  float bgG;    // T_final * (bg . dL/dC)
-  float SG;     // (colour composited behind the current entry) . dL/dC
-  int last;     // entries at positions >= last were not composited
-};
-
-// Adds the nine image-space gradient terms of entry e of one pixel into r (slots 0..8:
-// d/dx, d/dy, d/da, d/db, d/dc, d/do, d/dr, d/dg, d/db(lue)); returns whether the entry was
-// composited for this pixel.  The skip decisions replay the forward ones exactly.
-__device__ __forceinline__ bool bwd_step(BwdPixel& p, const float4& g, const float4& g2, const float4& col, float fu,
-                                         float fv, int e, float* r) {
-  if (e >= p.last) return false;
-  const float p2 = blend_power(g, g2, fu, fv);
-  if (!(p2 <= 0.f && p2 >= g2.y)) return false;
-  const float ex = exp2f(p2);
-  const float raw = __fmul_rn(g2.z, ex);
-  const float alpha = fminf(kAlphaMax, raw);
-  if (alpha < kAlphaMin) return false;
-  const float inv = __fdividef(1.f, 1.f - alpha);
-  const float Tj = p.T * inv;
-  const float w = alpha * Tj;
-  const float cG = col.x * p.G0 + col.y * p.G1 + col.z * p.G2;
-  const float dLda = Tj * cG - (p.SG + p.bgG) * inv;
-  r[6] += w * p.G0;
-  r[7] += w * p.G1;
-  r[8] += w * p.G2;
-  if (raw < kAlphaMax) {
-    const float dLdpow = dLda * alpha;          // d alpha / d power = alpha
-    r[5] += dLda * ex;                          // d alpha / d o = exp(power)
-    // power = p2 ln 2, p2 = A dx^2 + B dx dy + C dy^2 with dx = mean - pixel
-    const float dx = g.x - fu, dy = g.y - fv;
-    const float k = dLdpow * 0.6931471805599453f;
-    r[0] += k * (2.f * g.z * dx + g.w * dy);
-    r[1] += k * (g.w * dx + 2.f * g2.x * dy);
-    r[2] += -0.5f * dLdpow * dx * dx;
-    r[3] += -dLdpow * dx * dy;
-    r[4] += -0.5f * dLdpow * dy * dy;
-  }
-  p.SG = fmaf(w, cG, p.SG);
-  p.T = Tj;
-  return true;
-}
-
 // Sums v[0..15] over the warp by recursive halving: at each step a lane keeps half of its
 // values and trades the other half with its partner, so the 16 sums take 16 shuffles.
 // On return lanes 2c and 2c + 1 hold the warp total of component c.
@@ -112,15 +67,27 @@ __device__ __forceinline__ float warp_transpose_sum16(float (&v)[16]) {
   return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW* TH / 2) k_render_bwd(BwdBlendArgs a) {
-  constexpr int NT = TW * TH / 2;   // threads; each owns pixels (x, 2r) and (x, 2r + 1)
+__device__ __forceinline__ float2 sel2(bool a, bool b, float2 x) {
+  return make_float2(a ? x.x : 0.f, b ? x.y : 0.f);
+}
+
+// Back-to-front walk of one tile.  Per pixel pair q (lanes = the two pixels): T[q] is the
+// transmittance after the current entry (T_final at the start), G*[q] = dL/dC per channel,
+// bgG[q] = T_final (bg . dL/dC), SG[q] = (colour composited behind the current entry) .
+// dL/dC; entries at positions >= last[k] were not composited for pixel k.  Per entry e the
+// thread's pixels add up, with a = alpha_e and T_e = T/(1 - a):
+//   d/dcolour = a T_e dL/dC,  dL/da = T_e (c . dL/dC) - (SG + bgG)/(1 - a),
+// and, unless the 0.99 clamp was active, d/do = dL/da 2^p2 and with q = dL/da * a (the
+// derivative with respect to the power) the moments sum(q), sum(q dy), sum(q dy^2); the
+// column's common dx turns them into the mean and conic gradients.
+template <int TW, int TH, int PX>
+__global__ void __launch_bounds__(TW* TH / PX) k_render_bwd(BwdBlendArgs a) {
+  constexpr int NT = TW * TH / PX;  // threads; each owns pixels (x, PX r + k), k < PX
+  constexpr int NP = PX / 2;
   constexpr int NW = NT / 32;
-  constexpr int NB = NT;            // records per batch (one per thread: keeps shared memory < 48 KB)
+  constexpr int NB = NT;            // records per batch
   constexpr int PS = NB + 1;        // padded stride: the nine components land in distinct banks
-  __shared__ float4 s_geo[NB];
-  __shared__ float4 s_geo2[NB];
-  __shared__ float4 s_col[NB];
+  __shared__ BlendRec s_rec[NB];
   __shared__ uint32_t s_item[NB];
   __shared__ float s_part[NW][9 * PS];
   __shared__ int s_maxlast[NW];
@@ -133,31 +100,43 @@ __global__ void __launch_bounds__(TW* TH / 2) k_render_bwd(BwdBlendArgs a) {
   const int txi = local - tyi * cam.tiles_x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int pu = txi * TW + (tid % TW);
-  const int pv0 = tyi * TH + 2 * (tid / TW);
-  const float fu = (float)pu;
+  const int pv0 = tyi * TH + PX * (tid / TW);
+  const float2 nu = make_float2(-(float)pu, -(float)pu);
   const uint2 rg = a.ranges[tile];
   const uint32_t start = rg.x;
 
-  BwdPixel px[2];
+  float2 nv[NP], T[NP], Gr[NP], Gg[NP], Gb[NP], bgG[NP], SG[NP];
+  int last[PX];
   const int64_t HW = (int64_t)cam.width * cam.height;
   const float* gi = a.dL_dimage + 3 * cam.pixel_base;
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    BwdPixel& p = px[k];
-    p.T = 1.f;
-    p.G0 = p.G1 = p.G2 = p.bgG = p.SG = 0.f;
-    p.last = 0;
-    if (pu < cam.width && pv0 + k < cam.height) {
-      const int64_t pix = (int64_t)(pv0 + k) * cam.width + pu;
-      p.G0 = gi[pix];
-      p.G1 = gi[HW + pix];
-      p.G2 = gi[2 * HW + pix];
-      p.T = a.T_final[cam.pixel_base + pix];
-      p.last = a.last[cam.pixel_base + pix];
-      p.bgG = p.T * (a.bg0 * p.G0 + a.bg1 * p.G1 + a.bg2 * p.G2);
+  for (int q = 0; q < NP; ++q) {
+    nv[q] = make_float2(-(float)(pv0 + 2 * q), -(float)(pv0 + 2 * q + 1));
+    float t[2] = {1.f, 1.f}, g0[2] = {0.f, 0.f}, g1[2] = {0.f, 0.f}, g2[2] = {0.f, 0.f};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = 2 * q + h;
+      last[k] = 0;
+      if (pu < cam.width && pv0 + k < cam.height) {
+        const int64_t pix = (int64_t)(pv0 + k) * cam.width + pu;
+        g0[h] = gi[pix];
+        g1[h] = gi[HW + pix];
+        g2[h] = gi[2 * HW + pix];
+        t[h] = a.T_final[cam.pixel_base + pix];
+        last[k] = a.last[cam.pixel_base + pix];
+      }
     }
+    T[q] = make_float2(t[0], t[1]);
+    Gr[q] = make_float2(g0[0], g0[1]);
+    Gg[q] = make_float2(g1[0], g1[1]);
+    Gb[q] = make_float2(g2[0], g2[1]);
+    bgG[q] = make_float2(t[0] * (a.bg0 * g0[0] + a.bg1 * g1[0] + a.bg2 * g2[0]),
+                         t[1] * (a.bg0 * g0[1] + a.bg1 * g1[1] + a.bg2 * g2[1]));
+    SG[q] = make_float2(0.f, 0.f);
   }
-  const int my_last = max(px[0].last, px[1].last);
+  int my_last = 0;
+#pragma unroll
+  for (int k = 0; k < PX; ++k) my_last = max(my_last, last[k]);
   int wl = my_last;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
@@ -173,27 +152,76 @@ __global__ void __launch_bounds__(TW* TH / 2) k_render_bwd(BwdBlendArgs a) {
     __syncthreads();
     if (tid < nb) {
       const uint32_t item = __ldg(a.vals + start + lo + tid);
-      stage_record(a.xy, a.conic_o, a.rgb_d, item, s_geo[tid], s_geo2[tid], s_col[tid]);
+      stage_record(a.xy, a.conic_o, a.rgb_d, item, s_rec[tid]);
       s_item[tid] = item;
     }
     __syncthreads();
     float* part = s_part[warp];
     for (int j = nb - 1; j >= 0; --j) {
       const int e = lo + j;
-      if (!__any_sync(0xffffffffu, e < my_last)) {
+      const BlendRec r = s_rec[j];
+      const float2 dx = pair_dx(r, nu);
+      float2 dy[NP], p2[NP];
+      bool any = false;
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        dy[q] = pair_dy(r, nv[q]);
+        p2[q] = pair_power(r, dx, dy[q]);
+        any |= (e < last[2 * q] && p2[q].x <= 0.f && p2[q].x >= r.bc.z) ||
+               (e < last[2 * q + 1] && p2[q].y <= 0.f && p2[q].y >= r.bc.z);
+      }
+      if (!__any_sync(0xffffffffu, any)) {
         if (lane < 9) part[lane * PS + j] = 0.f;
         continue;
       }
-      const float4 g = s_geo[j];
-      const float4 g2 = s_geo2[j];
-      const float4 col = s_col[j];
-      float r[16];
+      float2 acc_r = make_float2(0.f, 0.f), acc_g = acc_r, acc_b = acc_r, acc_o = acc_r;
+      float2 acc_q = acc_r, acc_qy = acc_r, acc_qyy = acc_r;
+      bool act = false;
 #pragma unroll
-      for (int c = 0; c < 16; ++c) r[c] = 0.f;
-      bool act = bwd_step(px[0], g, g2, col, fu, (float)pv0, e, r);
-      act |= bwd_step(px[1], g, g2, col, fu, (float)(pv0 + 1), e, r);
+      for (int q = 0; q < NP; ++q) {
+        const PairAlpha al = pair_alpha(r, p2[q]);
+        const bool ok0 = al.in0 && e < last[2 * q], ok1 = al.in1 && e < last[2 * q + 1];
+        act |= ok0 || ok1;
+        const float2 om = one_minus(al.alpha);
+        const float2 inv = make_float2(__fdividef(1.f, om.x), __fdividef(1.f, om.y));
+        const float2 Tj = __fmul2_rn(T[q], inv);
+        const float2 w = sel2(ok0, ok1, __fmul2_rn(al.alpha, Tj));
+        const float2 cG = __ffma2_rn(lo2(r.rg), Gr[q], __ffma2_rn(hi2(r.rg), Gg[q], __fmul2_rn(lo2(r.bc), Gb[q])));
+        const float2 X = __fmul2_rn(__fadd2_rn(SG[q], bgG[q]), inv);
+        const float2 dLda = __ffma2_rn(Tj, cG, make_float2(-X.x, -X.y));
+        const float2 dl = sel2(ok0 && al.raw.x < kAlphaMax, ok1 && al.raw.y < kAlphaMax, dLda);
+        acc_r = __ffma2_rn(w, Gr[q], acc_r);
+        acc_g = __ffma2_rn(w, Gg[q], acc_g);
+        acc_b = __ffma2_rn(w, Gb[q], acc_b);
+        acc_o = __ffma2_rn(dl, al.ex, acc_o);
+        const float2 qp = __fmul2_rn(dl, al.alpha);   // d alpha / d power = alpha
+        const float2 qy = __fmul2_rn(qp, dy[q]);
+        acc_q = __fadd2_rn(acc_q, qp);
+        acc_qy = __fadd2_rn(acc_qy, qy);
+        acc_qyy = __ffma2_rn(qy, dy[q], acc_qyy);
+        SG[q] = __ffma2_rn(w, cG, SG[q]);
+        T[q].x = ok0 ? Tj.x : T[q].x;
+        T[q].y = ok1 ? Tj.y : T[q].y;
+      }
       if (__any_sync(0xffffffffu, act)) {
-        const float tot = warp_transpose_sum16(r);
+        // power = p2 ln 2, p2 = A dx^2 + B dx dy + C dy^2 with dx = x - u, dy = y - v
+        const float Q = acc_q.x + acc_q.y, Qy = acc_qy.x + acc_qy.y, Qyy = acc_qyy.x + acc_qyy.y;
+        const float d = dx.x;
+        const float A = r.ab.x, B = r.ab.z, C = r.co.x;
+        const float kl = 0.6931471805599453f;
+        float rr[16];
+        rr[0] = kl * (2.f * A * d * Q + B * Qy);
+        rr[1] = kl * (B * d * Q + 2.f * C * Qy);
+        rr[2] = -0.5f * d * d * Q;
+        rr[3] = -d * Qy;
+        rr[4] = -0.5f * Qyy;
+        rr[5] = acc_o.x + acc_o.y;
+        rr[6] = acc_r.x + acc_r.y;
+        rr[7] = acc_g.x + acc_g.y;
+        rr[8] = acc_b.x + acc_b.y;
+#pragma unroll
+        for (int c = 9; c < 16; ++c) rr[c] = 0.f;
+        const float tot = warp_transpose_sum16(rr);
         if ((lane & 1) == 0 && lane < 18) part[(lane >> 1) * PS + j] = tot;
       } else if (lane < 9) {
         part[lane * PS + j] = 0.f;
@@ -519,10 +547,10 @@ static BwdWs bwd_ws_layout(void* base, int64_t n_items) {
 
 size_t backward_ws_bytes(const rs_view_batch* batch) { return bwd_ws_layout(nullptr, batch->n_items).bytes; }
 
-template <int TW, int TH>
+template <int TW, int TH, int PX>
 static void launch_bwd_blend(const BwdBlendArgs& a, int n_tiles, cudaStream_t s) {
   prof::Scope ps("k_render_bwd", s);
-  k_render_bwd<TW, TH><<<n_tiles, TW * TH / 2, 0, s>>>(a);
+  k_render_bwd<TW, TH, PX><<<n_tiles, TW * TH / PX, 0, s>>>(a);
 }
 
 }  // namespace rs
@@ -562,9 +590,9 @@ extern "C" rs_status rs_render_backward(const rs_gaussians* g, const rs_view_bat
   b.g.ga = w.ga;
   b.g.gb = w.gb;
   b.g.gc = w.gc;
-  if (batch->tile_w == 16 && batch->tile_h == 16) launch_bwd_blend<16, 16>(b, batch->n_tiles, s);
-  else if (batch->tile_w == 32 && batch->tile_h == 8) launch_bwd_blend<32, 8>(b, batch->n_tiles, s);
-  else if (batch->tile_w == 8 && batch->tile_h == 8) launch_bwd_blend<8, 8>(b, batch->n_tiles, s);
+  if (batch->tile_w == 16 && batch->tile_h == 16) launch_bwd_blend<16, 16, 4>(b, batch->n_tiles, s);
+  else if (batch->tile_w == 32 && batch->tile_h == 8) launch_bwd_blend<32, 8, 4>(b, batch->n_tiles, s);
+  else if (batch->tile_w == 8 && batch->tile_h == 8) launch_bwd_blend<8, 8, 2>(b, batch->n_tiles, s);
   else return RS_ERR_UNSUPPORTED;
 
   BwdProjArgs p;
