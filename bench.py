@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--tile", default="auto", help="tile shape WxH with all views in one launch, or 'auto' "
+                                                   "(autotuner: tile shape and views per launch)")
     ap.add_argument("--sample-pixels", type=int, default=0, help="reference arm: pixels per step (0: auto)")
     return ap.parse_args()
 
@@ -55,11 +57,12 @@ def dist_env():
     return ws, rank, local
 
 
-def workload_config(views, world):
+def workload_config(views, world, tile=(16, 16), per_launch=None):
     return {"workload": "360-capture synthetic scene, 1M Gaussians SH3, 1280x832 ring views, "
                         "project+bin/sort+blend+importance+L1+backward+prune",
             "gaussians": N_GAUSSIANS, "width": WIDTH, "height": HEIGHT, "views_per_step": views * world,
-            "views_per_rank": views, "sh_degree": 3, "tile": "16x16", "seed": 2,
+            "views_per_rank": views, "views_per_launch": per_launch or views, "sh_degree": 3,
+            "tile": f"{tile[0]}x{tile[1]}", "seed": 2,
             "l2": "inputs larger than L2 (236 MB of parameters, ~0.5 GB of instances per view)"}
 
 
@@ -139,46 +142,64 @@ def run_ours(args):
     all_cams = synth.ring_cameras(V * world, width=WIDTH, height=HEIGHT, f=1200.0)
     cams = all_cams[rank * V:(rank + 1) * V]
     g = api.Gaussians.from_scene(scene, device=dev)
-    vb = api.ViewBatch(cams, scene.n, device=dev)
     vb1 = [api.ViewBatch([c], scene.n, device=dev) for c in cams]
     cfg = api.config()
+
+    # tile shape and views per launch from the autotuner (setup, untimed; cached per workload)
+    if args.tile == "auto":
+        tune = api.autotune(g, cams, cfg=cfg, backward=True)
+        tile, B = tune["tile"], tune["batch"]
+    else:
+        tune = None
+        tile, B = tuple(int(x) for x in args.tile.split("x")), V
+    vbs = [api.ViewBatch(cams[i:i + B], scene.n, tile=tile, device=dev) for i in range(0, V, B)]
 
     # synthetic targets: renders of a perturbed copy (setup, untimed)
     tscene = synth.perturbed_copy(scene, 12)
     tg = api.Gaussians.from_scene(tscene, device=dev)
     trast = api.Rasterizer(device=dev)
-    target = trast.forward(tg, vb)["image"].clone()
+    targets = [trast.forward(tg, vb)["image"].clone() for vb in vbs]
     del trast, tg
 
-    # capacity from a first (plain) forward of every view configuration
+    # capacity from a first (plain) forward of every chunk
     rast = api.Rasterizer(device=dev)
-    probe = rast.forward(g, vb)
-    K_batch = rast.status.read()["required"]
-    cap = int(K_batch * 1.05) + 4096
+    K_max = 0
+    for vb in vbs:
+        rast.forward(g, vb)
+        K_max = max(K_max, rast.status.read()["required"])
+    del rast
+    cap = int(K_max * 1.05) + 4096
+    M = max(vb.n_items for vb in vbs)
+    P = max(vb.n_pixels for vb in vbs)
+    NTI = max(vb.n_tiles for vb in vbs)
     st = api.DeviceStatus(dev)
-    proj = api.Projected.empty(vb.n_items, dev)
-    bins = api.Bins.empty(cap, vb.n_tiles, device=dev)
+    proj = api.Projected.empty(M, dev)
+    bins_all = api.Bins.empty(cap, NTI, device=dev)
+    bins_of = [api.Bins(bins_all.vals, bins_all.ranges[:vb.n_tiles], None, cap) for vb in vbs]
     ws_sort, ws_bwd, ws_f = api.Workspace(dev), api.Workspace(dev), api.Workspace(dev)
-    img = torch.empty(3 * vb.n_pixels, device=dev)
-    T = torch.empty(vb.n_pixels, device=dev)
-    L = torch.empty(vb.n_pixels, dtype=torch.int32, device=dev)
+    img_all = torch.empty(3 * P, device=dev)
+    T_all = torch.empty(P, device=dev)
+    L_all = torch.empty(P, dtype=torch.int32, device=dev)
+    dL_all = torch.empty_like(img_all)
+    bufs = [(img_all[:3 * vb.n_pixels], T_all[:vb.n_pixels], L_all[:vb.n_pixels], dL_all[:3 * vb.n_pixels])
+            for vb in vbs]
     h = torch.zeros(scene.n, dtype=torch.int32, device=dev)
-    dL = torch.empty_like(img)
     loss = torch.zeros(1, dtype=torch.float64, device=dev)
     gbuf = rd.GradBuffer(g.tensors())
     grads = gbuf.views
     mask = torch.empty(scene.n, dtype=torch.uint8, device=dev)
     idx = torch.empty(scene.n, dtype=torch.int32, device=dev)
-    del probe
+    chunks = list(zip(vbs, bins_of, bufs, targets))
 
     def views_part():
         h.zero_()
         gbuf.zero_()
-        api.project(g, vb, cfg, st, out=proj)
-        api.bin_sort(proj, vb, bins, ws_sort, st)
-        api.render(proj, bins, vb, cfg, image=img, T_final=T, last=L, importance=h)
-        api.l1_loss(img, target, dL, loss)
-        api.render_backward(g, vb, proj, bins, T, L, dL, grads, ws_bwd, cfg)
+        for vb, bins, (img, T, L, dL), target in chunks:
+            api.project(g, vb, cfg, st, out=proj)
+            api.bin_sort(proj, vb, bins, ws_sort, st)
+            api.render(proj, bins, vb, cfg, image=img, T_final=T, last=L, importance=h)
+            api.l1_loss(img, target, dL, loss)
+            api.render_backward(g, vb, proj, bins, T, L, dL, grads, ws_bwd, cfg)
 
     def prune():
         api.filter(h, 0.01, N.RS_PRUNE_BELOW, ws_f, mask=mask, idx=idx)
@@ -248,31 +269,26 @@ def run_ours(args):
     views_total = V * world
     value = ms_per_step / views_total   # whole job: all ranks' views in the max-over-ranks step time
 
-    # per-stage times of the same batched step (plain launches, events on this stream)
-    stage_ms, kernel_ms = stage_times(api, N, g, vb, cfg, st, proj, bins, ws_sort, img, T, L, h, target, dL, loss,
-                                      grads, ws_bwd, ws_f, mask, idx, reps=max(3, min(args.steps, 10)))
-    pairs = int(L.to(torch.int64).sum().item())   # entries walked by the backward (sum of last over pixels)
-    # super-tile instances (4 x 4 tiles per super-tile) of the batch, for the binning byte counts
-    r = proj.rect[:vb.n_items].to(torch.int64) & 0xffff
-    nonempty = (r[:, 2] > r[:, 0]) & (r[:, 3] > r[:, 1])
-    sw = torch.where(nonempty, (r[:, 2] - 1) // 4 - r[:, 0] // 4 + 1, torch.zeros_like(r[:, 0]))
-    sh_ = torch.where(nonempty, (r[:, 3] - 1) // 4 - r[:, 1] // 4 + 1, torch.zeros_like(r[:, 0]))
-    n_super = int((sw * sh_).sum().item())
-    del r, nonempty, sw, sh_
+    # per-stage times of the same batched step (plain launches, events on this stream), and
+    # the work counts of each launch (pairs walked, super-tile instances)
+    stage_ms, kernel_ms, work_counts = stage_times(api, N, torch, g, chunks, cfg, st, proj, h, gbuf, loss, ws_sort,
+                                                   ws_bwd, ws_f, mask, idx, reps=max(3, min(args.steps, 10)))
+    pairs, n_super = work_counts["pairs"], work_counts["super_instances"]
 
     # plain: the same views one at a time, no graph
     plain = None
     fps = None
     if not args.no_plain:
-        plain, fps = plain_loop(api, N, torch, g, vb1, cfg, target, cams, reps=max(3, min(args.steps, 10)), dev=dev)
+        plain, fps = plain_loop(api, N, torch, g, vb1, cfg, torch.cat(targets), cams, reps=max(3, min(args.steps, 10)),
+                                dev=dev)
 
     # end to end through the public API: host parameters and targets in pinned memory
-    e2e = e2e_run(api, N, torch, scene, vb, cfg, target, cap, reps=max(3, min(args.steps, 5)), dev=dev, world=world)
+    e2e = e2e_run(api, N, torch, scene, vbs, cfg, targets, cap, reps=max(3, min(args.steps, 5)), dev=dev, world=world)
 
     # roofline of the dominant kernel
     hbm, peak_kind, pk = peaks()
-    work = kernel_work(vb, sres, pairs, n_super)
-    roof = roofline(kernel_ms, work, hbm, peak_kind, V)
+    work = kernel_work(vbs, sres, pairs, n_super)
+    roof = roofline(kernel_ms, work, hbm, peak_kind, B)
     per_kernel = {k: kernel_frac(k, kernel_ms[k], work, hbm) for k in kernel_ms if k in work}
     launches = int(round(sum(v["launches_per_step"] for v in kernel_ms.values()))) * args.steps
 
@@ -283,18 +299,21 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded 360-capture scene; target = render of a perturbed copy)",
-            "config": dict(workload_config(V, world),
+            "config": dict(workload_config(V, world, tile, B),
                            parallelism=(f"views sharded over {world} GPUs; all-reduce MAX of importance and SUM "
                                         f"of gradients per step" if world > 1 else "1 GPU, no collective")),
             "batched_ms_per_view": round(value, 5),
             "plain_ms_per_view": round(plain, 5) if plain else None,
             "batched_over_plain_speedup": round(plain / value, 3) if plain else None,
             "fps_forward_single_view": round(fps, 1) if fps else None,
-            "instances_per_view": int(sres["n_instances"] / V),
+            "instances_per_view": int(sres["n_instances"] / B),
             "super_instances_per_view": int(n_super / V),
-            "pairs_per_pixel": round(pairs / vb.n_pixels, 2),
-            "blends_per_s_forward": round(pairs / (kernel_ms["k_render_importance"]["ms_per_launch"] / 1e3), 0)
+            "pairs_per_pixel": round(pairs / sum(vb.n_pixels for vb in vbs), 2),
+            "blends_per_s_forward": round(pairs / (kernel_ms["k_render_importance"]["ms_per_step"] / 1e3), 0)
             if "k_render_importance" in kernel_ms else None,
+            "autotune": None if tune is None else {
+                "tile": f"{tile[0]}x{tile[1]}", "views_per_launch": B, "ms_per_view": round(tune["ms_per_view"], 5),
+                "candidates_ms_per_view": {f"{a}x{b}/{c}": round(v, 5) for (a, b, c), v in tune["candidates"].items()}},
             "stage_ms_per_step": {k: round(v, 5) for k, v in stage_ms.items()},
             "kernel_ms_per_step": {k: round(v["ms_per_step"], 5) for k, v in
                                    sorted(kernel_ms.items(), key=lambda kv: -kv[1]["ms_per_step"])},
@@ -308,33 +327,41 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def stage_times(api, N, g, vb, cfg, st, proj, bins, ws_sort, img, T, L, h, target, dL, loss, grads, ws_bwd, ws_f,
-                mask, idx, reps):
-    """Per-stage times (CUDA events around each C-ABI call) and per-kernel times (the
-    library's own launch events, rs_profile_*) of the same step with plain launches."""
-    import torch
+def stage_times(api, N, torch, g, chunks, cfg, st, proj, h, gbuf, loss, ws_sort, ws_bwd, ws_f, mask, idx, reps):
+    """Per-stage times (CUDA events around each C-ABI call, summed over the launches of a
+    step) and per-kernel times (the library's own launch events, rs_profile_*) of the same
+    step with plain launches; then, in an untimed pass, the work counts: pairs walked by the
+    backward (sum of `last` over pixels) and super-tile instances (4 x 4 tiles) of every
+    launch."""
     names = ["project", "bin_sort", "render_importance", "l1", "backward", "filter"]
     acc = {k: 0.0 for k in names}
     kern = {}
     for r in range(reps + 1):
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)]
         h.zero_()
-        for t in grads:
-            t.zero_()
+        gbuf.zero_()
         if r == 1:
             N.profile_enable(True)
-        ev[0].record()
-        api.project(g, vb, cfg, st, out=proj); ev[1].record()
-        api.bin_sort(proj, vb, bins, ws_sort, st); ev[2].record()
-        api.render(proj, bins, vb, cfg, image=img, T_final=T, last=L, importance=h); ev[3].record()
-        api.l1_loss(img, target, dL, loss); ev[4].record()
-        api.render_backward(g, vb, proj, bins, T, L, dL, grads, ws_bwd, cfg); ev[5].record()
-        api.filter(h, 0.01, N.RS_PRUNE_BELOW, ws_f, mask=mask, idx=idx); ev[6].record()
+        evs = []
+        for vb, bins, (img, T, L, dL), target in chunks:
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+            ev[0].record()
+            api.project(g, vb, cfg, st, out=proj); ev[1].record()
+            api.bin_sort(proj, vb, bins, ws_sort, st); ev[2].record()
+            api.render(proj, bins, vb, cfg, image=img, T_final=T, last=L, importance=h); ev[3].record()
+            api.l1_loss(img, target, dL, loss); ev[4].record()
+            api.render_backward(g, vb, proj, bins, T, L, dL, gbuf.views, ws_bwd, cfg); ev[5].record()
+            evs.append(ev)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        api.filter(h, 0.01, N.RS_PRUNE_BELOW, ws_f, mask=mask, idx=idx)
+        f1.record()
         torch.cuda.synchronize()
         if r == 0:
             continue   # warm-up pass
-        for i, k in enumerate(names):
-            acc[k] += ev[i].elapsed_time(ev[i + 1]) / reps
+        for ev in evs:
+            for i, k in enumerate(names[:5]):
+                acc[k] += ev[i].elapsed_time(ev[i + 1]) / reps
+        acc["filter"] += f0.elapsed_time(f1) / reps
     for name, ms in N.profile_records():
         c = kern.setdefault(name, [0, 0.0])
         c[0] += 1
@@ -342,7 +369,21 @@ def stage_times(api, N, g, vb, cfg, st, proj, bins, ws_sort, img, T, L, h, targe
     N.profile_enable(False)
     kernels = {k: {"launches_per_step": v[0] / reps, "ms_per_step": v[1] / reps, "ms_per_launch": v[1] / v[0]}
                for k, v in kern.items()}
-    return acc, kernels
+    pairs, n_super = 0, 0
+    for vb, bins, (img, T, L, dL), target in chunks:
+        api.project(g, vb, cfg, st, out=proj)
+        api.bin_sort(proj, vb, bins, ws_sort, st)
+        api.render(proj, bins, vb, cfg, image=img, T_final=T, last=L)
+        pairs += int(L.to(torch.int64).sum().item())
+        r = proj.rect[:vb.n_items].to(torch.int64) & 0xffff
+        nonempty = (r[:, 2] > r[:, 0]) & (r[:, 3] > r[:, 1])
+        zero = torch.zeros_like(r[:, 0])
+        sw = torch.where(nonempty, (r[:, 2] - 1) // 4 - r[:, 0] // 4 + 1, zero)
+        sh = torch.where(nonempty, (r[:, 3] - 1) // 4 - r[:, 1] // 4 + 1, zero)
+        n_super += int((sw * sh).sum().item())
+        del r, nonempty, zero, sw, sh
+    torch.cuda.synchronize()
+    return acc, kernels, {"pairs": pairs, "super_instances": n_super}
 
 
 def plain_loop(api, N, torch, g, vb1, cfg, target, cams, reps, dev):
@@ -405,43 +446,46 @@ def plain_loop(api, N, torch, g, vb1, cfg, target, cams, reps, dev):
     return plain, fps
 
 
-def e2e_run(api, N, torch, scene, vb, cfg, target, cap, reps, dev, world=1):
+def e2e_run(api, N, torch, scene, vbs, cfg, targets, cap, reps, dev, world=1):
     """Same batched step through the public API, parameters and targets copied from pinned
     host memory each step, the loss read back to the host (with the reductions over ranks
     when world > 1)."""
     from paper_2403_13806_gb300 import dist as rd
     host = [torch.from_numpy(np.ascontiguousarray(a, np.float32)).pin_memory() for a in scene.arrays()]
-    tgt_h = target.cpu().pin_memory()
+    tgt_h = [t.cpu().pin_memory() for t in targets]
     dev_p = [torch.empty_like(t, device=dev) for t in host]
-    tgt_d = torch.empty_like(target)
+    tgt_d = [torch.empty_like(t) for t in targets]
     g = api.Gaussians(*dev_p, scene.sh_degree)
     st = api.DeviceStatus(dev)
-    proj = api.Projected.empty(vb.n_items, dev)
-    bins = api.Bins.empty(cap, vb.n_tiles, device=dev)
+    proj = api.Projected.empty(max(vb.n_items for vb in vbs), dev)
+    bins_all = api.Bins.empty(cap, max(vb.n_tiles for vb in vbs), device=dev)
     ws_sort, ws_bwd, ws_f = api.Workspace(dev), api.Workspace(dev), api.Workspace(dev)
     h = torch.zeros(scene.n, dtype=torch.int32, device=dev)
     gbuf = rd.GradBuffer(dev_p)
-    grads = gbuf.views
-    loss_h = torch.zeros(1, dtype=torch.float64).pin_memory()
+    loss_h = torch.zeros(len(vbs), dtype=torch.float64).pin_memory()
+    loss_d = torch.zeros(len(vbs), dtype=torch.float64, device=dev)
 
     def step():
         for d, s in zip(dev_p, host):
             d.copy_(s, non_blocking=True)
-        tgt_d.copy_(tgt_h, non_blocking=True)
+        for d, s in zip(tgt_d, tgt_h):
+            d.copy_(s, non_blocking=True)
         h.zero_()
         gbuf.zero_()
-        api.project(g, vb, cfg, st, out=proj)
-        api.bin_sort(proj, vb, bins, ws_sort, st)
-        img, T, L = api.render(proj, bins, vb, cfg, importance=h)
-        loss, dl = api.l1_loss(img, tgt_d)
-        api.render_backward(g, vb, proj, bins, T, L, dl, grads, ws_bwd, cfg)
+        for i, vb in enumerate(vbs):
+            bins = api.Bins(bins_all.vals, bins_all.ranges[:vb.n_tiles], None, cap)
+            api.project(g, vb, cfg, st, out=proj)
+            api.bin_sort(proj, vb, bins, ws_sort, st)
+            img, T, L = api.render(proj, bins, vb, cfg, importance=h)
+            loss, dl = api.l1_loss(img, tgt_d[i], loss=loss_d[i:i + 1])
+            api.render_backward(g, vb, proj, bins, T, L, dl, gbuf.views, ws_bwd, cfg)
         if world > 1:
             rd.allreduce_importance(h)
             rd.allreduce_grads(gbuf)
         api.filter(h, 0.01, N.RS_PRUNE_BELOW, ws_f)
-        loss_h.copy_(loss, non_blocking=True)
+        loss_h.copy_(loss_d, non_blocking=True)
         torch.cuda.current_stream().synchronize()
-        return float(loss_h[0])
+        return float(loss_h.mean())
 
     for _ in range(2):
         step()
@@ -449,9 +493,10 @@ def e2e_run(api, N, torch, scene, vb, cfg, target, cap, reps, dev, world=1):
     for _ in range(reps):
         step()
     dt = (time.perf_counter() - t0) / reps * 1000.0
-    h2d = sum(t.numel() * 4 for t in host) + target.numel() * 4
-    return {"value": round(dt / vb.n_views, 4), "unit": "ms/view (fwd+bwd)", "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": 8}
+    h2d = sum(t.numel() * 4 for t in host) + sum(t.numel() * 4 for t in targets)
+    n_views = sum(vb.n_views for vb in vbs)
+    return {"value": round(dt / n_views, 4), "unit": "ms/view (fwd+bwd)", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": 8 * len(vbs)}
 
 
 # FP32 lane-operations per second of the GB300: 152 SMs x 128 FP32 lanes x 2070 MHz.
@@ -491,7 +536,19 @@ def ncu_traffic(name, views):
     return int(rec["bytes_per_view"] * views)
 
 
-def kernel_work(vb, sres, pairs, n_super):
+class _PerLaunch:
+    """Averages of a step's launches (all launches of a step cover equal view chunks)."""
+
+    def __init__(self, vbs):
+        c = len(vbs)
+        self.n_items = sum(vb.n_items for vb in vbs) / c
+        self.n_pixels = sum(vb.n_pixels for vb in vbs) / c
+        self.n_tiles = max(vb.n_tiles for vb in vbs)
+        self.n_gaussians = vbs[0].n_gaussians
+        self.launches = c
+
+
+def kernel_work(vbs, sres, pairs, n_super):
     """Algorithmic work per launch of each library kernel: DRAM bytes the method must move
     (bound "hbm") or FP32 lane operations (bound "alu").
 
@@ -502,7 +559,10 @@ def kernel_work(vb, sres, pairs, n_super):
     2 B); the fine partition reads 4 B index + 8 B rect per super instance (twice: count and
     scatter) and writes 4 B per instance; the projection backward reads 236 + 36 B and writes
     236 B per item; the blend kernels count FP32 operations per evaluated pair."""
-    M, K, Ks, P = vb.n_items, sres["n_instances"], n_super, vb.n_pixels
+    vb = _PerLaunch(vbs)
+    c = vb.launches
+    M, K, Ks, P = vb.n_items, sres["n_instances"], n_super / c, vb.n_pixels
+    pairs = pairs / c
     kb = 2 if vb.n_tiles <= 65536 else 4
     hbm = {
         "k_project": M * (236 + 52),

@@ -200,7 +200,7 @@ size_t rs_workspace_size(rs_stage stage, const rs_view_batch* batch, int64_t cap
 
 /* Sizes of the ABI structs, for bindings that mirror them: writes up to n entries in the
  * order rs_gaussians, rs_camera, rs_view, rs_view_batch, rs_config, rs_projected, rs_bins,
- * rs_gaussian_grads, rs_device_status; returns how many it wrote. */
+ * rs_gaussian_grads, rs_device_status, rs_tune_result; returns how many it wrote. */
 int32_t rs_struct_sizes(int64_t* out, int32_t n);
 
 /* ---- hot path ---------------------------------------------------------------------- */
@@ -315,6 +315,49 @@ rs_status rs_render_backward(const rs_gaussians* g, const rs_view_batch* batch,
  * Errors: RS_ERR_INVALID_ARG, RS_ERR_CUDA. */
 rs_status rs_l1_loss(const float* image, const float* target, int64_t n, float* dL_dimage,
                      double* loss, void* stream);
+
+/* ---- batched execution: autotuner --------------------------------------------------- */
+
+/* Choice of rs_autotune. */
+typedef struct rs_tune_result {
+  int32_t tile_w, tile_h;   /* tile shape: 16x16, 32x8 or 8x8 */
+  int32_t batch;            /* views per launch (consecutive chunks of the view list) */
+  int32_t cached;           /* 1: taken from the cache without measuring */
+  float ms_per_view;        /* measured device time per view of the choice */
+  int32_t n_candidates;     /* candidates measured by this call (0 if cached) */
+  int32_t reserved[2];
+} rs_tune_result;
+
+#define RS_TUNE_BACKWARD 1  /* time render_backward too (training), else the forward only */
+#define RS_TUNE_FORCE 2     /* measure even when the workload is cached */
+
+/* rs_autotune -- chooses the tile shape and the views per launch for rendering the given
+ * views (the paper has no counterpart: it serves the batched execution of many views,
+ * the training views of Sec. 3.2 and the per-cluster view sets of Sec. 3.4).  Times the
+ * library's own project -> bin_sort -> render (with importance) [-> render_backward] on
+ * every candidate (tile shapes 16x16, 32x8, 8x8 x batch sizes 1, 2, 4, ... and n_views) over
+ * the first min(n_views, max(batch, 16)) views (one untimed pass, three timed passes,
+ * CUDA events on `stream`), keeps the fastest per view, and caches it under the workload
+ * (view sizes, n_items, g->n, sh_degree, subset use, RS_TUNE_BACKWARD).  A later call with
+ * the same workload returns the cached choice without device work unless RS_TUNE_FORCE.
+ * g, subset_idx (device, may be NULL) and n_items (host [n_views]) as in a batch of all the
+ * views; cams: host [n_views]; cand_ms (host, may be NULL): rs_autotune_candidates(n_views)
+ * floats, ms per view of each candidate in the order (16x16, 32x8, 8x8) x ascending batch,
+ * -1 where a candidate was not measured.  Not a hot call: it allocates and frees device
+ * memory (cudaMalloc / cudaFree), synchronises the stream, and must not run during stream
+ * capture.  The importance and gradient buffers it renders into are its own.  Candidates
+ * needing 2^32 or more instances, or more device memory than is free, are skipped.
+ * Errors: RS_ERR_INVALID_ARG, RS_ERR_UNSUPPORTED (sh_degree), RS_ERR_CAPACITY (no
+ * candidate fits), RS_ERR_CUDA, or a device status the pipeline reported. */
+rs_status rs_autotune(const rs_gaussians* g, const rs_camera* cams, int32_t n_views,
+                      const int64_t* n_items, const uint32_t* subset_idx, const rs_config* cfg,
+                      int32_t flags, rs_tune_result* out, float* cand_ms, void* stream);
+
+/* Number of candidates rs_autotune considers for n_views views (length of cand_ms). */
+int32_t rs_autotune_candidates(int32_t n_views);
+
+/* Empties the autotuner's cache (host state, guarded by a mutex). */
+void rs_autotune_clear(void);
 
 /* ---- tracing ------------------------------------------------------------------------ */
 

@@ -65,7 +65,15 @@ class RsDeviceStatus(ctypes.Structure):
                 ("reserved", c_int64)]
 
 
-STRUCTS = [RsGaussians, RsCamera, RsView, RsViewBatch, RsConfig, RsProjected, RsBins, RsGaussianGrads, RsDeviceStatus]
+class RsTuneResult(ctypes.Structure):
+    _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("batch", c_int32), ("cached", c_int32),
+                ("ms_per_view", c_float), ("n_candidates", c_int32), ("reserved", c_int32 * 2)]
+
+
+RS_TUNE_BACKWARD, RS_TUNE_FORCE = 1, 2
+
+STRUCTS = [RsGaussians, RsCamera, RsView, RsViewBatch, RsConfig, RsProjected, RsBins, RsGaussianGrads, RsDeviceStatus,
+           RsTuneResult]
 
 # every function include/radsplat.h declares, with its ctypes signature
 P = c_void_p
@@ -85,6 +93,9 @@ SIGNATURES = {
     "rs_filter_noalloc": (ctypes.c_int, [P, c_int64, c_float, ctypes.c_int, P, P, P, P]),
     "rs_render_backward": (ctypes.c_int, [P, P, P, P, P, P, P, P, P, P, c_size_t, P]),
     "rs_l1_loss": (ctypes.c_int, [P, P, c_int64, P, P, P]),
+    "rs_autotune": (ctypes.c_int, [P, P, c_int32, P, P, P, c_int32, P, P, P]),
+    "rs_autotune_candidates": (c_int32, [c_int32]),
+    "rs_autotune_clear": (None, []),
     "rs_profile_enable": (ctypes.c_int, [c_int32]),
     "rs_profile_count": (c_int32, []),
     "rs_profile_read": (ctypes.c_int, [c_int32, P, P]),

@@ -17,7 +17,9 @@ from . import _native as N
 
 __all__ = ["Gaussians", "ViewBatch", "Projected", "Bins", "DeviceStatus", "Workspace", "config", "project",
            "bin_sort", "render", "importance", "filter", "nearest", "render_backward", "Rasterizer",
-           "RadSplatFunction", "split_images", "importance_as_float"]
+           "RadSplatFunction", "split_images", "importance_as_float", "autotune", "TILE_SHAPES"]
+
+TILE_SHAPES = ((16, 16), (32, 8), (8, 8))
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -280,6 +282,44 @@ def render_backward(g: Gaussians, vb: ViewBatch, proj: Projected, bins: Bins, T_
     N.call("rs_render_backward", N.ref(g.struct()), N.ref(vb.batch), N.ref(cfg), N.ref(proj.struct()),
            N.ref(bins.struct()), _ptr(T_final), _ptr(last), _ptr(dL_dimage), N.ref(gs), _ptr(w), w.numel(),
            _stream(stream))
+
+
+def autotune(g: Gaussians, cams: Sequence[dict], subsets: Optional[Sequence] = None, cfg=None,
+             backward: bool = True, force: bool = False, stream=None) -> dict:
+    """rs_autotune: tile shape and views per launch for rendering `cams` (cached per workload).
+
+    Returns {"tile": (w, h), "batch": views per launch, "cached", "ms_per_view",
+    "n_candidates", "candidates": {(w, h, batch): ms per view}}."""
+    cfg = cfg or config()
+    V = len(cams)
+    if subsets is not None and len(subsets) != V:
+        raise ValueError("one subset per view")
+    n_items = np.array([len(x) for x in subsets] if subsets is not None else [g.n] * V, dtype=np.int64)
+    sub = None
+    if subsets is not None:
+        sub = torch.as_tensor(np.concatenate([np.asarray(x, dtype=np.uint32) for x in subsets]).view(np.int32),
+                              device=g.means.device)
+    cam_arr = (N.RsCamera * V)(*[_camera_struct(c) for c in cams])
+    res = N.RsTuneResult()
+    nc = N.lib().rs_autotune_candidates(V)
+    cand = (ctypes.c_float * nc)()
+    flags = (N.RS_TUNE_BACKWARD if backward else 0) | (N.RS_TUNE_FORCE if force else 0)
+    N.call("rs_autotune", N.ref(g.struct()), cam_arr, V, n_items.ctypes.data_as(ctypes.c_void_p), _ptr(sub),
+           N.ref(cfg), flags, N.ref(res), cand, _stream(stream))
+    batches = []
+    b = 1
+    while b < V:
+        batches.append(b)
+        b *= 2
+    batches.append(V)
+    cands = {}
+    for si, (tw, th) in enumerate(TILE_SHAPES):
+        for bi, bb in enumerate(batches):
+            ms = cand[si * len(batches) + bi]
+            if ms >= 0:
+                cands[(tw, th, bb)] = float(ms)
+    return {"tile": (res.tile_w, res.tile_h), "batch": res.batch, "cached": bool(res.cached),
+            "ms_per_view": float(res.ms_per_view), "n_candidates": res.n_candidates, "candidates": cands}
 
 
 def split_images(flat: torch.Tensor, vb: ViewBatch) -> List[torch.Tensor]:

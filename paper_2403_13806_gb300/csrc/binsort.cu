@@ -351,11 +351,20 @@ __global__ void __launch_bounds__(kFineThreads) k_fine_count(const uint32_t* __r
   uint32_t c[kNF];
 #pragma unroll
   for (int f = 0; f < kNF; ++f) c[f] = 0u;
-  for (uint32_t e0 = a; e0 < b; e0 += kFineThreads) {
-    const uint32_t e = e0 + threadIdx.x;
-    const uint32_t m = e < b ? cover_mask(rect[svals[e]], t) : 0u;
+  constexpr int U = 4;   // independent loads in flight per thread
+  for (uint32_t e0 = a; e0 < b; e0 += U * kFineThreads) {
+    ushort4 rr[U];
 #pragma unroll
-    for (int f = 0; f < kNF; ++f) c[f] += __popc(__ballot_sync(0xffffffffu, (m >> f) & 1u));
+    for (int u = 0; u < U; ++u) {
+      const uint32_t e = e0 + u * kFineThreads + threadIdx.x;
+      rr[u] = e < b ? rect[svals[e]] : make_ushort4(0, 0, 0, 0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t m = cover_mask(rr[u], t);
+#pragma unroll
+      for (int f = 0; f < kNF; ++f) c[f] += __popc(__ballot_sync(0xffffffffu, (m >> f) & 1u));
+    }
   }
   if (lane < kNF) {
     uint32_t mine = 0;
@@ -495,12 +504,22 @@ __global__ void __launch_bounds__(kFineThreads) k_fine_scatter(const uint32_t* _
   }
   const uint32_t cap = (uint32_t)(capacity < 0xffffffffLL ? capacity : 0xffffffffLL);
   const unsigned lt = (1u << lane) - 1u;
+  // the next chunk's item and rect are fetched while the current one is placed
+  uint32_t n_item = 0;
+  ushort4 n_rect = make_ushort4(0, 0, 0, 0);
+  if (a + threadIdx.x < b) {
+    n_item = svals[a + threadIdx.x];
+    n_rect = rect[n_item];
+  }
   for (uint32_t e0 = a; e0 < b; e0 += kFineThreads) {
-    const uint32_t e = e0 + threadIdx.x;
-    uint32_t item = 0, m = 0u;
-    if (e < b) {
-      item = svals[e];
-      m = cover_mask(rect[item], t);
+    const uint32_t item = n_item;
+    const uint32_t m = cover_mask(n_rect, t);
+    const uint32_t en = e0 + kFineThreads + threadIdx.x;
+    n_item = 0;
+    n_rect = make_ushort4(0, 0, 0, 0);   // past the segment: covers nothing
+    if (en < b) {
+      n_item = svals[en];
+      n_rect = rect[n_item];
     }
     uint32_t my_bal = 0;
 #pragma unroll
@@ -522,13 +541,15 @@ __global__ void __launch_bounds__(kFineThreads) k_fine_scatter(const uint32_t* _
       s_run[f] = r;
     }
     __syncthreads();
-    if (m) {
-      const uint32_t db = keys ? __float_as_uint(rgb_d[item].w) : 0u;
-      uint32_t mm = m;
-      while (mm) {
-        const int f = __ffs(mm) - 1;
-        mm &= mm - 1u;
-        const uint32_t pos = s_base[warp][f] + __popc(s_bal[warp][f] & lt);
+    // one store per tile, all lanes together: the lanes covering tile f write consecutive
+    // positions of its list
+    const uint32_t db = (keys && m) ? __float_as_uint(rgb_d[item].w) : 0u;
+#pragma unroll
+    for (int f = 0; f < kNF; ++f) {
+      const uint32_t bl = s_bal[warp][f];
+      if (bl == 0u) continue;   // uniform per warp
+      if ((m >> f) & 1u) {
+        const uint32_t pos = s_base[warp][f] + __popc(bl & lt);
         if (pos < cap) {
           vals[pos] = item;
           if (keys) keys[pos] = ((unsigned long long)s_tile[f] << 32) | db;

@@ -69,7 +69,7 @@ struct PairAlpha {
   float2 ex;      // 2^min(p2, 0)
   float2 raw;     // o 2^min(p2, 0) (before the 0.99 clamp)
   float2 alpha;   // min(0.99, raw)
-  bool in0, in1;  // cut <= p2 <= 0 and alpha >= 1/255
+  bool in0, in1;  // p2 <= 0 and alpha >= 1/255
 };
 
 __device__ __forceinline__ PairAlpha pair_alpha(const BlendRec& r, float2 p2) {
@@ -77,9 +77,11 @@ __device__ __forceinline__ PairAlpha pair_alpha(const BlendRec& r, float2 p2) {
   a.ex = make_float2(ex2_approx(fminf(p2.x, 0.f)), ex2_approx(fminf(p2.y, 0.f)));
   a.raw = __fmul2_rn(hi2(r.co), a.ex);
   a.alpha = make_float2(fminf(kAlphaMax, a.raw.x), fminf(kAlphaMax, a.raw.y));
-  const float cut = r.bc.z;
-  a.in0 = p2.x <= 0.f && p2.x >= cut && a.alpha.x >= kAlphaMin;
-  a.in1 = p2.y <= 0.f && p2.y >= cut && a.alpha.y >= kAlphaMin;
+  // alpha >= 1/255 implies p2 >= cut (the cut's 1e-3 margin exceeds the rounding of
+  // 2^p2, o 2^p2 and the cut itself), so the exact test needs no cut comparison; the cut
+  // only serves the warp-level pre-test of the kernels
+  a.in0 = p2.x <= 0.f && a.alpha.x >= kAlphaMin;
+  a.in1 = p2.y <= 0.f && a.alpha.y >= kAlphaMin;
   return a;
 }
 

@@ -43,9 +43,23 @@ def test_struct_layouts_match(native):
     L = native.lib()
     assert L.rs_abi_version() == 1
     assert ctypes.sizeof(native.RsView) == 128
-    sizes = (ctypes.c_int64 * 9)()
-    assert L.rs_struct_sizes(sizes, 9) == 9
+    n = len(native.STRUCTS)
+    sizes = (ctypes.c_int64 * n)()
+    assert L.rs_struct_sizes(sizes, n) == n
     assert list(sizes) == [ctypes.sizeof(c) for c in native.STRUCTS]
+    assert ctypes.sizeof(native.RsTuneResult) == 32
+
+
+def test_autotune_host_checks(native):
+    L = native.lib()
+    assert L.rs_autotune_candidates(0) == 0
+    assert L.rs_autotune_candidates(1) == 3          # three tile shapes x batch 1
+    assert L.rs_autotune_candidates(4) == 9          # batches 1, 2, 4
+    assert L.rs_autotune_candidates(5) == 12         # batches 1, 2, 4, 5
+    res = native.RsTuneResult()
+    # argument checks happen before any device work
+    assert L.rs_autotune(None, None, 1, None, None, None, 0, ctypes.byref(res), None, None) == native.RS_ERR_INVALID_ARG
+    L.rs_autotune_clear()
 
 
 def test_status_strings(native):

@@ -1,0 +1,91 @@
+"""The autotuner (rs_autotune): candidates measured, the fastest chosen and cached, and the
+chosen tile shape and views per launch render the same images as the default batch."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2403_13806_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2403_13806_gb300 import build
+    build.build()
+
+
+def three_views():
+    scene, (cam,) = synth.config0()
+    cams = []
+    for k in range(3):
+        vm = np.eye(3, 4, dtype=np.float32)
+        vm[0, 3] = 0.2 * (k - 1)
+        c = dict(cam)
+        c["viewmat"] = vm
+        cams.append(c)
+    return scene, cams
+
+
+def render_chunks(g, cams, tile, batch, subsets=None):
+    imgs = []
+    for s0 in range(0, len(cams), batch):
+        sub = subsets[s0:s0 + batch] if subsets is not None else None
+        vb = api.ViewBatch(cams[s0:s0 + batch], g.n, subsets=sub, tile=tile)
+        out = api.Rasterizer().forward(g, vb)
+        imgs += [x.cpu().numpy() for x in api.split_images(out["image"], vb)]
+    return imgs
+
+
+def test_autotune_measures_chooses_and_caches():
+    scene, cams = three_views()
+    g = api.Gaussians.from_scene(scene)
+    api.N.lib().rs_autotune_clear()
+    r = api.autotune(g, cams, backward=True)
+    assert not r["cached"]
+    assert r["n_candidates"] == 9 and len(r["candidates"]) == 9   # 3 shapes x batches 1, 2, 3
+    assert r["tile"] in api.TILE_SHAPES and r["batch"] in (1, 2, 3)
+    assert all(ms > 0 for ms in r["candidates"].values())
+    assert r["ms_per_view"] == pytest.approx(min(r["candidates"].values()), rel=1e-6)
+    assert r["candidates"][(*r["tile"], r["batch"])] == pytest.approx(r["ms_per_view"], rel=1e-6)
+    again = api.autotune(g, cams, backward=True)
+    assert again["cached"] and again["tile"] == r["tile"] and again["batch"] == r["batch"]
+    assert again["n_candidates"] == 0
+    # the forward-only workload is a different cache entry; forcing re-measures
+    fwd = api.autotune(g, cams, backward=False)
+    assert not fwd["cached"]
+    forced = api.autotune(g, cams, backward=True, force=True)
+    assert not forced["cached"] and forced["n_candidates"] == 9
+    # the choice renders the same images as one 16x16 batch of all views
+    ref = render_chunks(g, cams, (16, 16), 3)
+    got = render_chunks(g, cams, r["tile"], r["batch"])
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
+
+
+def test_autotune_with_visibility_lists():
+    scene, cams = three_views()
+    g = api.Gaussians.from_scene(scene)
+    rng = np.random.default_rng(5)
+    subsets = [np.sort(rng.choice(scene.n, size=n, replace=False)).astype(np.uint32) for n in (500, 1200, 800)]
+    r = api.autotune(g, cams, subsets=subsets, backward=True, force=True)
+    assert r["tile"] in api.TILE_SHAPES and r["batch"] in (1, 2, 3)
+    ref = render_chunks(g, cams, (16, 16), 3, subsets)
+    got = render_chunks(g, cams, r["tile"], r["batch"], subsets)
+    for a, b in zip(ref, got):
+        assert np.array_equal(a, b)
+
+
+def test_autotune_rejects_bad_arguments():
+    import ctypes
+    scene, cams = three_views()
+    g = api.Gaussians.from_scene(scene)
+    with pytest.raises(ValueError):
+        api.autotune(g, cams, subsets=[np.arange(10, dtype=np.uint32)] * 2)   # subsets != views
+    # without visibility lists every view must list all Gaussians
+    cam_arr = (api.N.RsCamera * 3)(*[api._camera_struct(c) for c in cams])
+    n_items = np.array([5, 5, 5], dtype=np.int64)
+    res = api.N.RsTuneResult()
+    rc = api.N.lib().rs_autotune(api.N.ref(g.struct()), cam_arr, 3, n_items.ctypes.data_as(ctypes.c_void_p), None,
+                                 api.N.ref(api.config()), 0, api.N.ref(res), None, None)
+    assert rc == api.N.RS_ERR_INVALID_ARG

@@ -59,26 +59,30 @@ def test_projection_matches_oracle():
             assert np.all(n_t == (rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1]))
 
 
-def synthetic_projected(rng, views, m_per_view):
-    """Seeded projected items (depth with ties, random rects) for the integer stages."""
+def synthetic_projected(rng, views, m_per_view, span=5):
+    """Seeded projected items (depth with ties, random rects up to span-1 tiles a side) for
+    the integer stages."""
     depth, rect = [], []
     for (tx, ty), m in zip(views, m_per_view):
         d = rng.choice(np.array([0.5, 1.25, 2.0, 3.5, 9.0], np.float32), m)
         cont = rng.random(m) < 0.5
         d[cont] = rng.uniform(0.3, 50.0, int(cont.sum())).astype(np.float32)
         x0 = rng.integers(0, tx, m); y0 = rng.integers(0, ty, m)
-        x1 = np.minimum(tx, x0 + rng.integers(0, 5, m)); y1 = np.minimum(ty, y0 + rng.integers(0, 5, m))
+        x1 = np.minimum(tx, x0 + rng.integers(0, span, m)); y1 = np.minimum(ty, y0 + rng.integers(0, span, m))
         depth.append(d.astype(np.float32))
         rect.append(np.stack([x0, y0, x1, y1], 1).astype(np.uint16))
     return np.concatenate(depth), np.concatenate(rect)
 
 
-@pytest.mark.parametrize("views,m", [([(8, 8)], [5000]), ([(80, 52)], [60000]), ([(5, 3), (12, 9), (1, 1)], [700, 3000, 5])])
-def test_bin_sort_bit_exact(views, m):
-    """Keys, values and ranges equal the oracle's stable sort of the duplicated keys."""
+@pytest.mark.parametrize("views,m,span", [([(8, 8)], [5000], 5), ([(80, 52)], [60000], 5),
+                                         ([(5, 3), (12, 9), (1, 1)], [700, 3000, 5], 5),
+                                         ([(8, 8)], [200003], 5), ([(30, 21), (7, 9)], [90001, 40000], 12)])
+def test_bin_sort_bit_exact(views, m, span):
+    """Keys, values and ranges equal the oracle's stable sort of the duplicated keys, also
+    where the per-super-tile lists span many 256-entry chunks with a ragged last chunk."""
     from paper_2403_13806_gb300 import api, _native as N
     rng = np.random.default_rng(len(m) * 7 + m[0])
-    depth, rect = synthetic_projected(rng, views, m)
+    depth, rect = synthetic_projected(rng, views, m, span)
     M = len(depth)
     item_view = np.repeat(np.arange(len(views)), m).astype(np.int32)
     tiles_x = np.array([v[0] for v in views], np.int32)
