@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--tile", default="auto", help="tile shape WxH with all views in one launch, or 'auto' "
-                                                   "(autotuner: tile shape and views per launch)")
+                                                   "(autotuner: tile shape, staging batch, views per launch)")
     ap.add_argument("--sample-pixels", type=int, default=0, help="reference arm: pixels per step (0: auto)")
     return ap.parse_args()
 
@@ -148,7 +148,8 @@ def run_ours(args):
     # tile shape and views per launch from the autotuner (setup, untimed; cached per workload)
     if args.tile == "auto":
         tune = api.autotune(g, cams, cfg=cfg, backward=True)
-        tile, B = tune["tile"], tune["batch"]
+        tile, B = tune["tile"], tune["views_per_launch"]
+        cfg = api.config(batch=tune["smem_batch"])
     else:
         tune = None
         tile, B = tuple(int(x) for x in args.tile.split("x")), V
@@ -312,8 +313,10 @@ def run_ours(args):
             "blends_per_s_forward": round(pairs / (kernel_ms["k_render_importance"]["ms_per_step"] / 1e3), 0)
             if "k_render_importance" in kernel_ms else None,
             "autotune": None if tune is None else {
-                "tile": f"{tile[0]}x{tile[1]}", "views_per_launch": B, "ms_per_view": round(tune["ms_per_view"], 5),
-                "candidates_ms_per_view": {f"{a}x{b}/{c}": round(v, 5) for (a, b, c), v in tune["candidates"].items()}},
+                "tile": f"{tile[0]}x{tile[1]}", "smem_batch": tune["smem_batch"], "views_per_launch": B,
+                "ms_per_view": round(tune["ms_per_view"], 5),
+                "stage1_ms_per_view": {f"{a}x{b}/{m}": round(v, 5) for (a, b, m), v in tune["stage1"].items()},
+                "stage2_ms_per_view": {str(k): round(v, 5) for k, v in tune["stage2"].items()}},
             "stage_ms_per_step": {k: round(v, 5) for k, v in stage_ms.items()},
             "kernel_ms_per_step": {k: round(v["ms_per_step"], 5) for k, v in
                                    sorted(kernel_ms.items(), key=lambda kv: -kv[1]["ms_per_step"])},

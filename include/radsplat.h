@@ -123,7 +123,10 @@ typedef struct rs_config {
   float eps2d;           /* dilation added to the diagonal of Sigma' (px^2), default 0.3 */
   float near_plane;      /* cull if the FP32 camera depth <= near_plane, default 0.2 */
   float bg[3];           /* background colour composited with T_final, default 0 */
-  int32_t batch;         /* Gaussians staged in shared memory per step of the blend (0: auto) */
+  int32_t batch;         /* Gaussian records staged in shared memory per batch of the blend
+                            kernels: 0 (default: 2 per thread forward, 1 per thread backward)
+                            or 1, 2 or 4 x the CTA's threads (64 for 16x16 and 32x8 tiles,
+                            32 for 8x8); other values give RS_ERR_UNSUPPORTED */
   int32_t reserved[2];
 } rs_config;
 
@@ -320,33 +323,40 @@ rs_status rs_l1_loss(const float* image, const float* target, int64_t n, float* 
 
 /* Choice of rs_autotune. */
 typedef struct rs_tune_result {
-  int32_t tile_w, tile_h;   /* tile shape: 16x16, 32x8 or 8x8 */
-  int32_t batch;            /* views per launch (consecutive chunks of the view list) */
-  int32_t cached;           /* 1: taken from the cache without measuring */
-  float ms_per_view;        /* measured device time per view of the choice */
-  int32_t n_candidates;     /* candidates measured by this call (0 if cached) */
-  int32_t reserved[2];
+  int32_t tile_w, tile_h;     /* tile shape: 16x16, 32x8 or 8x8 */
+  int32_t smem_batch;         /* rs_config.batch: records staged per blend batch */
+  int32_t views_per_launch;   /* views per launch (consecutive chunks of the view list) */
+  float ms_per_view;          /* measured device time per view of the choice */
+  int32_t cached;             /* 1: taken from the cache without measuring */
+  int32_t n_candidates;       /* candidates measured by this call (0 if cached) */
+  int32_t reserved;
 } rs_tune_result;
 
 #define RS_TUNE_BACKWARD 1  /* time render_backward too (training), else the forward only */
 #define RS_TUNE_FORCE 2     /* measure even when the workload is cached */
 
-/* rs_autotune -- chooses the tile shape and the views per launch for rendering the given
- * views (the paper has no counterpart: it serves the batched execution of many views,
- * the training views of Sec. 3.2 and the per-cluster view sets of Sec. 3.4).  Times the
- * library's own project -> bin_sort -> render (with importance) [-> render_backward] on
- * every candidate (tile shapes 16x16, 32x8, 8x8 x batch sizes 1, 2, 4, ... and n_views) over
- * the first min(n_views, max(batch, 16)) views (one untimed pass, three timed passes,
- * CUDA events on `stream`), keeps the fastest per view, and caches it under the workload
- * (view sizes, n_items, g->n, sh_degree, subset use, RS_TUNE_BACKWARD).  A later call with
- * the same workload returns the cached choice without device work unless RS_TUNE_FORCE.
+/* rs_autotune -- chooses the tile shape, the Gaussians staged per shared-memory batch of
+ * the blend kernels and the views per launch for rendering the given views (the paper has
+ * no counterpart: it serves the batched execution of many views, the training views of
+ * Sec. 3.2 and the per-cluster view sets of Sec. 3.4).  It times the library's own
+ * project -> bin_sort -> render (with importance) [-> render_backward] in two stages:
+ * (1) every tile shape (16x16, 32x8, 8x8) x staging batch (1, 2, 4 records per thread),
+ * all of the first min(n_views, 16) views in one launch per stage; (2) with the winner of
+ * (1), views per launch 1, 2, 4, ... and n_views over the first min(n_views,
+ * max(views per launch, 16)) views.  Each candidate gets one untimed pass and three timed
+ * passes (CUDA events on `stream`); the score is device milliseconds per view.  The choice
+ * is cached under the workload (view sizes, n_items, g->n, sh_degree, subset use,
+ * RS_TUNE_BACKWARD, cfg apart from batch); a later call with the same workload returns it
+ * without device work unless RS_TUNE_FORCE.
  * g, subset_idx (device, may be NULL) and n_items (host [n_views]) as in a batch of all the
- * views; cams: host [n_views]; cand_ms (host, may be NULL): rs_autotune_candidates(n_views)
- * floats, ms per view of each candidate in the order (16x16, 32x8, 8x8) x ascending batch,
- * -1 where a candidate was not measured.  Not a hot call: it allocates and frees device
- * memory (cudaMalloc / cudaFree), synchronises the stream, and must not run during stream
- * capture.  The importance and gradient buffers it renders into are its own.  Candidates
- * needing 2^32 or more instances, or more device memory than is free, are skipped.
+ * views; cams: host [n_views]; cfg: its batch field is ignored; cand_ms (host, may be
+ * NULL): rs_autotune_candidates(n_views) floats, device ms per view of each candidate in
+ * the order of stage (1) (tile shape major, then 1, 2, 4 records per thread) followed by
+ * stage (2) (ascending views per launch), -1 where a candidate was not measured.
+ * Not a hot call: it allocates and frees device memory (cudaMalloc / cudaFree),
+ * synchronises the stream, and must not run during stream capture.  The importance and
+ * gradient buffers it renders into are its own.  Candidates needing 2^32 or more
+ * instances, or more device memory than is free, are skipped.
  * Errors: RS_ERR_INVALID_ARG, RS_ERR_UNSUPPORTED (sh_degree), RS_ERR_CAPACITY (no
  * candidate fits), RS_ERR_CUDA, or a device status the pipeline reported. */
 rs_status rs_autotune(const rs_gaussians* g, const rs_camera* cams, int32_t n_views,

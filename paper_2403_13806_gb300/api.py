@@ -17,7 +17,7 @@ from . import _native as N
 
 __all__ = ["Gaussians", "ViewBatch", "Projected", "Bins", "DeviceStatus", "Workspace", "config", "project",
            "bin_sort", "render", "importance", "filter", "nearest", "render_backward", "Rasterizer",
-           "RadSplatFunction", "split_images", "importance_as_float", "autotune", "TILE_SHAPES"]
+           "RadSplatFunction", "split_images", "importance_as_float", "autotune", "TILE_SHAPES", "blend_threads"]
 
 TILE_SHAPES = ((16, 16), (32, 8), (8, 8))
 
@@ -33,10 +33,12 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def config(eps2d: float = 0.3, near_plane: float = 0.2, bg=(0.0, 0.0, 0.0)) -> N.RsConfig:
+def config(eps2d: float = 0.3, near_plane: float = 0.2, bg=(0.0, 0.0, 0.0), batch: int = 0) -> N.RsConfig:
+    """rs_config; batch = Gaussian records staged per blend batch (0: default)."""
     c = N.lib().rs_config_default()
     c.eps2d = eps2d
     c.near_plane = near_plane
+    c.batch = int(batch)
     for i in range(3):
         c.bg[i] = float(bg[i])
     return c
@@ -284,12 +286,19 @@ def render_backward(g: Gaussians, vb: ViewBatch, proj: Projected, bins: Bins, T_
            _stream(stream))
 
 
+def blend_threads(tile) -> int:
+    """Threads of a blend CTA for a tile shape (four pixels per thread, two for 8x8)."""
+    return 32 if tuple(tile) == (8, 8) else tile[0] * tile[1] // 4
+
+
 def autotune(g: Gaussians, cams: Sequence[dict], subsets: Optional[Sequence] = None, cfg=None,
              backward: bool = True, force: bool = False, stream=None) -> dict:
-    """rs_autotune: tile shape and views per launch for rendering `cams` (cached per workload).
+    """rs_autotune: tile shape, records staged per blend batch and views per launch for
+    rendering `cams` (cached per workload).
 
-    Returns {"tile": (w, h), "batch": views per launch, "cached", "ms_per_view",
-    "n_candidates", "candidates": {(w, h, batch): ms per view}}."""
+    Returns {"tile": (w, h), "smem_batch": rs_config.batch, "views_per_launch", "cached",
+    "ms_per_view", "n_candidates", "stage1": {(w, h, records per thread): ms per view},
+    "stage2": {views per launch: ms per view}}."""
     cfg = cfg or config()
     V = len(cams)
     if subsets is not None and len(subsets) != V:
@@ -312,14 +321,19 @@ def autotune(g: Gaussians, cams: Sequence[dict], subsets: Optional[Sequence] = N
         batches.append(b)
         b *= 2
     batches.append(V)
-    cands = {}
+    stage1, stage2 = {}, {}
     for si, (tw, th) in enumerate(TILE_SHAPES):
-        for bi, bb in enumerate(batches):
-            ms = cand[si * len(batches) + bi]
+        for pi, m in enumerate((1, 2, 4)):
+            ms = cand[si * 3 + pi]
             if ms >= 0:
-                cands[(tw, th, bb)] = float(ms)
-    return {"tile": (res.tile_w, res.tile_h), "batch": res.batch, "cached": bool(res.cached),
-            "ms_per_view": float(res.ms_per_view), "n_candidates": res.n_candidates, "candidates": cands}
+                stage1[(tw, th, m)] = float(ms)
+    for bi, bb in enumerate(batches):
+        ms = cand[9 + bi]
+        if ms >= 0:
+            stage2[bb] = float(ms)
+    return {"tile": (res.tile_w, res.tile_h), "smem_batch": res.smem_batch, "views_per_launch": res.views_per_launch,
+            "cached": bool(res.cached), "ms_per_view": float(res.ms_per_view), "n_candidates": res.n_candidates,
+            "stage1": stage1, "stage2": stage2}
 
 
 def split_images(flat: torch.Tensor, vb: ViewBatch) -> List[torch.Tensor]:

@@ -12,7 +12,10 @@
 //                   reordered by digit in shared memory, and each digit run is stored
 //                   contiguously.
 // The per-tile counters cost 2 x 1 KB per 2048 keys of extra traffic per pass and make
-// every tile independent, so the scatter runs at full occupancy.
+// every tile independent, so the scatter runs at full occupancy.  The count lives on the
+// device; the histogram and scatter kernels stride over its tiles with grids capped at a
+// few waves, and the scan covers only its tiles, so a generous bound n_max (the instance
+// capacity) costs no empty work.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -20,6 +23,7 @@
 
 #include "profile.cuh"
 #include "radix.cuh"
+#include "rs_common.cuh"
 
 namespace rs {
 namespace tiles {
@@ -36,13 +40,14 @@ __global__ void __launch_bounds__(kThreads) k_tile_hist(const KeyT* __restrict__
                                                         uint32_t* __restrict__ cnt) {
   __shared__ uint32_t s[kWarps][kR];
   const int warp = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < kWarps * kR; i += kThreads) (&s[0][0])[i] = 0u;
-  __syncthreads();
   const int64_t n = *n_dev;
-  const int64_t tile = blockIdx.x;
-  const int64_t t0 = tile * TILE;
+  const int64_t n_tiles = (n + TILE - 1) / TILE;
   const uint32_t mask = (1u << rbits) - 1u;
-  if (t0 < n) {
+  // grid-stride over the tiles the device count needs (the grid is sized for the bound)
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    for (int i = threadIdx.x; i < kWarps * kR; i += kThreads) (&s[0][0])[i] = 0u;
+    __syncthreads();
+    const int64_t t0 = tile * TILE;
     const int tn = (int)min((int64_t)TILE, n - t0);
     constexpr int kVec = 16 / sizeof(KeyT);
     if (tn == TILE) {
@@ -57,22 +62,26 @@ __global__ void __launch_bounds__(kThreads) k_tile_hist(const KeyT* __restrict__
       for (int i = threadIdx.x; i < tn; i += kThreads)
         atomicAdd(&s[warp][((uint32_t)keys[t0 + i] >> shift) & mask], 1u);
     }
-  }
-  __syncthreads();
-  const int d = threadIdx.x;
-  uint32_t c = 0;
+    __syncthreads();
+    const int d = threadIdx.x;
+    uint32_t c = 0;
 #pragma unroll
-  for (int w = 0; w < kWarps; ++w) c += s[w][d];
-  cnt[(int64_t)d * n_tiles_max + tile] = c;   // zero for tiles past the count
+    for (int w = 0; w < kWarps; ++w) c += s[w][d];
+    cnt[(int64_t)d * n_tiles_max + tile] = c;
+    __syncthreads();
+  }
 }
 
-// One CTA per digit d: exclusive prefix of cnt[d][0 .. n_tiles) in place; tot[d] = total.
-__global__ void __launch_bounds__(1024) k_tile_scan(uint32_t* __restrict__ cnt, int64_t n_tiles,
-                                                    uint32_t* __restrict__ tot) {
+// One CTA per digit d: exclusive prefix of cnt[d][0 .. n_tiles) in place, n_tiles the
+// tiles of the device count (rows have stride n_tiles_max); tot[d] = total.
+template <int TILE>
+__global__ void __launch_bounds__(1024) k_tile_scan(uint32_t* __restrict__ cnt, const uint32_t* __restrict__ n_dev,
+                                                    int64_t n_tiles_max, uint32_t* __restrict__ tot) {
   __shared__ uint32_t s_w[32];
   __shared__ uint32_t s_carry;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t* row = cnt + (int64_t)blockIdx.x * n_tiles;
+  const int64_t n_tiles = ((int64_t)*n_dev + TILE - 1) / TILE;
+  uint32_t* row = cnt + (int64_t)blockIdx.x * n_tiles_max;
   if (threadIdx.x == 0) s_carry = 0u;
   __syncthreads();
   for (int64_t b0 = 0; b0 < n_tiles; b0 += 4 * 1024) {
@@ -133,75 +142,82 @@ __global__ void __launch_bounds__(kThreads, ITEMS <= 8 ? 4 : 3) k_tile_sort(cons
   const uint32_t mask = (uint32_t)R - 1u;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t n = *n_dev;
-  const int64_t tile = blockIdx.x;
-  const int64_t t0 = tile * TILE;
-  if (t0 >= n) return;   // uniform per CTA
-  const int tn = (int)min((int64_t)TILE, n - t0);
-  for (int i = threadIdx.x; i < kWarps * kR; i += kThreads) (&s_whist[0][0])[i] = 0;
-
-  uint32_t k[ITEMS], v[ITEMS];
-  uint16_t rank[ITEMS];
-#pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
-    const int li = warp * (ITEMS * 32) + i * 32 + lane;
-    if (li < tn) {
-      k[i] = (uint32_t)__ldcs(keys_in + t0 + li);
-      v[i] = __ldcs(vals_in + t0 + li);
-    } else {
-      k[i] = 0xffffffffu;   // sentinel: digit R, never counted
-      v[i] = 0u;
-    }
-  }
-  // global position of this tile's first key of digit d
+  const int64_t n_tiles = (n + TILE - 1) / TILE;
+  if ((int64_t)blockIdx.x >= n_tiles) return;   // uniform per CTA
+  // global position of the first key of digit d over all tiles (exclusive prefix of totals)
   const int d = threadIdx.x;
   const uint32_t dbase = radix::block_excl_scan(d < R ? tot[d] : 0u, s_scan, &s_total);
-  const uint32_t gfirst = d < R ? dbase + cnt[(int64_t)d * n_tiles_max + tile] : 0u;
-
   const unsigned lt_mask = (1u << lane) - 1u;
+
+  // grid-stride over the tiles the device count needs (the grid is sized for the bound)
+  for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int64_t t0 = tile * TILE;
+    const int tn = (int)min((int64_t)TILE, n - t0);
+    __syncthreads();   // the previous tile's shared-memory reads are done
+    for (int i = threadIdx.x; i < kWarps * kR; i += kThreads) (&s_whist[0][0])[i] = 0;
+
+    uint32_t k[ITEMS], v[ITEMS];
+    uint16_t rank[ITEMS];
 #pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
-    const int dg = k[i] == 0xffffffffu ? R : (int)((k[i] >> shift) & mask);
-    const unsigned peers = __match_any_sync(0xffffffffu, dg);
-    const int leader = __ffs(peers) - 1;
-    uint32_t base = 0;
-    if (dg < R) base = s_whist[warp][dg];
-    rank[i] = (uint16_t)(base + __popc(peers & lt_mask));
-    __syncwarp();
-    if (lane == leader && dg < R) s_whist[warp][dg] = (uint16_t)(base + __popc(peers));
-    __syncwarp();
-  }
-  __syncthreads();
-  uint32_t c = 0;
-  if (d < R) {
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) {
-      const uint32_t x = s_whist[w][d];
-      s_whist[w][d] = (uint16_t)c;
-      c += x;
+    for (int i = 0; i < ITEMS; ++i) {
+      const int li = warp * (ITEMS * 32) + i * 32 + lane;
+      if (li < tn) {
+        k[i] = (uint32_t)__ldcs(keys_in + t0 + li);
+        v[i] = __ldcs(vals_in + t0 + li);
+      } else {
+        k[i] = 0xffffffffu;   // sentinel: digit R, never counted
+        v[i] = 0u;
+      }
     }
-  }
-  const uint32_t lstart = radix::block_excl_scan(d < R ? c : 0u, s_scan, &s_total);
-  if (d < R) {
-    s_lstart[d] = lstart;
-    s_gpos[d] = gfirst - lstart;
-  }
-  __syncthreads();
+    // global position of this tile's first key of digit d
+    const uint32_t gfirst = d < R ? dbase + cnt[(int64_t)d * n_tiles_max + tile] : 0u;
+    __syncthreads();   // counters zeroed
+
 #pragma unroll
-  for (int i = 0; i < ITEMS; ++i) {
-    if (k[i] != 0xffffffffu) {
-      const int dg = (int)((k[i] >> shift) & mask);
-      const uint32_t p = s_lstart[dg] + s_whist[warp][dg] + rank[i];
-      s_keys[p] = (KeyT)k[i];
-      s_vals[p] = v[i];
+    for (int i = 0; i < ITEMS; ++i) {
+      const int dg = k[i] == 0xffffffffu ? R : (int)((k[i] >> shift) & mask);
+      const unsigned peers = __match_any_sync(0xffffffffu, dg);
+      const int leader = __ffs(peers) - 1;
+      uint32_t base = 0;
+      if (dg < R) base = s_whist[warp][dg];
+      rank[i] = (uint16_t)(base + __popc(peers & lt_mask));
+      __syncwarp();
+      if (lane == leader && dg < R) s_whist[warp][dg] = (uint16_t)(base + __popc(peers));
+      __syncwarp();
     }
-  }
-  __syncthreads();
-  for (int p = threadIdx.x; p < tn; p += kThreads) {
-    const KeyT key = s_keys[p];
-    const int dd = (int)(((uint32_t)key >> shift) & mask);
-    const uint32_t g = s_gpos[dd] + (uint32_t)p;
-    if (keys_out) keys_out[g] = key;
-    vals_out[g] = s_vals[p];
+    __syncthreads();
+    uint32_t c = 0;
+    if (d < R) {
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) {
+        const uint32_t x = s_whist[w][d];
+        s_whist[w][d] = (uint16_t)c;
+        c += x;
+      }
+    }
+    const uint32_t lstart = radix::block_excl_scan(d < R ? c : 0u, s_scan, &s_total);
+    if (d < R) {
+      s_lstart[d] = lstart;
+      s_gpos[d] = gfirst - lstart;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      if (k[i] != 0xffffffffu) {
+        const int dg = (int)((k[i] >> shift) & mask);
+        const uint32_t p = s_lstart[dg] + s_whist[warp][dg] + rank[i];
+        s_keys[p] = (KeyT)k[i];
+        s_vals[p] = v[i];
+      }
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < tn; p += kThreads) {
+      const KeyT key = s_keys[p];
+      const int dd = (int)(((uint32_t)key >> shift) & mask);
+      const uint32_t g = s_gpos[dd] + (uint32_t)p;
+      if (keys_out) keys_out[g] = key;
+      vals_out[g] = s_vals[p];
+    }
   }
 }
 
@@ -225,6 +241,10 @@ inline int sort_pairs(KeyT* k0, uint32_t* v0, KeyT* k1, uint32_t* v1, const uint
   const int64_t nt = tiles_for(n_max, TILE) > 0 ? tiles_for(n_max, TILE) : 1;
   uint32_t* cnt = scratch;
   uint32_t* tot = scratch + (size_t)kR * nt;
+  // grids sized for the bound n_max but capped at a few waves: the kernels stride over the
+  // tiles of the device count, so an over-provisioned bound costs no empty CTAs
+  const unsigned grid_hist = (unsigned)(nt < 8 * kNumSMs ? nt : 8 * kNumSMs);
+  const unsigned grid_sort = (unsigned)(nt < 4 * kNumSMs ? nt : 4 * kNumSMs);
   int cur = 0;
   for (int p = 0; p < passes; ++p) {
     const int shift = p * rbits;
@@ -236,14 +256,14 @@ inline int sort_pairs(KeyT* k0, uint32_t* v0, KeyT* k1, uint32_t* v1, const uint
     const bool last = (p == passes - 1);
     {
       prof::Scope ps("k_tile_hist", s);
-      k_tile_hist<KeyT, TILE><<<(unsigned)nt, kThreads, 0, s>>>(ki, n_dev, shift, rb, nt, cnt);
+      k_tile_hist<KeyT, TILE><<<grid_hist, kThreads, 0, s>>>(ki, n_dev, shift, rb, nt, cnt);
     }
     {
       prof::Scope ps("k_tile_scan", s);
-      k_tile_scan<<<1 << rb, 1024, 0, s>>>(cnt, nt, tot);
+      k_tile_scan<TILE><<<1 << rb, 1024, 0, s>>>(cnt, n_dev, nt, tot);
     }
     prof::Scope ps("k_tile_sort", s);
-    k_tile_sort<KeyT, ITEMS><<<(unsigned)nt, kThreads, 0, s>>>(
+    k_tile_sort<KeyT, ITEMS><<<grid_sort, kThreads, 0, s>>>(
         ki, vi, (last && !write_last_keys) ? nullptr : ko, vo, n_dev, shift, rb, cnt, nt, tot);
     cur ^= 1;
   }

@@ -4,7 +4,8 @@
 // One CTA per (view, tile); each thread owns PX vertically adjacent pixels of one column
 // (PX = 4, or 2 for 8x8 tiles), evaluated as PX/2 pixel pairs with packed two-lane FP32
 // instructions, so every Gaussian record read from shared memory serves PX pixel
-// evaluations.  The tile's sorted list is consumed in batches of two records per thread,
+// evaluations.  The tile's sorted list is consumed in batches of NBM records per thread
+// (rs_config.batch = NBM x threads with NBM one of 1, 2, 4; the autotuner picks it),
 // staged into shared memory in blend-ready form (conic pre-scaled to the log2 domain); the
 // per-pixel decisions are predicated, not branched.  A warp skips a record that none of
 // its pixels' alpha-support tests accept, leaves a batch once all of its pixels are done,
@@ -38,11 +39,11 @@ struct RenderArgs {
   int64_t n_gaussians;
 };
 
-template <int TW, int TH, int PX, bool IMAGE, bool IMPORTANCE>
+template <int TW, int TH, int PX, int NBM, bool IMPORTANCE>
 __global__ void __launch_bounds__(TW* TH / PX) k_render(RenderArgs a) {
   constexpr int NT = TW * TH / PX;   // threads; each owns pixels (x, PX r + k), k < PX
   constexpr int NP = PX / 2;         // pixel pairs per thread
-  constexpr int NB = 2 * NT;         // records per batch
+  constexpr int NB = NBM * NT;       // records per batch (NBM per thread)
   __shared__ BlendRec s_rec[NB];
   __shared__ uint32_t s_h[IMPORTANCE ? NB : 1];
   __shared__ uint32_t s_gid[IMPORTANCE ? NB : 1];
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(TW* TH / PX) k_render(RenderArgs a) {
     if (__syncthreads_count(!all_done()) == 0) break;
     const int nb = (int)min((uint32_t)NB, end - b0);
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < NBM; ++k) {
       const int slot = tid + k * NT;
       if (slot < nb) {
         const uint32_t item = __ldg(a.vals + b0 + slot);
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(TW* TH / PX) k_render(RenderArgs a) {
     __syncthreads();
     if (IMPORTANCE) {
 #pragma unroll
-      for (int k = 0; k < 2; ++k) {
+      for (int k = 0; k < NBM; ++k) {
         const int slot = tid + k * NT;
         if (slot < nb) {
           const uint32_t mm = s_h[slot];
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(TW* TH / PX) k_render(RenderArgs a) {
     const bool hi = k & 1;
     const float Tk = hi ? T[q].y : T[q].x;
     const int64_t pix = (int64_t)(pv0 + k) * cam.width + pu;
-    if (IMAGE) {
+    if (a.image) {
       float* img = a.image + 3 * cam.pixel_base;
       img[pix] = (hi ? cr[q].y : cr[q].x) + Tk * a.bg0;
       img[HW + pix] = (hi ? cg[q].y : cg[q].x) + Tk * a.bg1;
@@ -172,14 +173,24 @@ __global__ void __launch_bounds__(TW* TH / PX) k_render(RenderArgs a) {
   }
 }
 
-template <int TW, int TH, int PX>
-static void launch_render(const RenderArgs& a, int n_tiles, bool image, bool imp, cudaStream_t s) {
+template <int TW, int TH, int PX, int NBM>
+static void launch_render(const RenderArgs& a, int n_tiles, bool imp, cudaStream_t s) {
   constexpr int NT = TW * TH / PX;
   prof::Scope ps(imp ? "k_render_importance" : "k_render", s);
-  if (image && imp) k_render<TW, TH, PX, true, true><<<n_tiles, NT, 0, s>>>(a);
-  else if (image) k_render<TW, TH, PX, true, false><<<n_tiles, NT, 0, s>>>(a);
-  else if (imp) k_render<TW, TH, PX, false, true><<<n_tiles, NT, 0, s>>>(a);
-  else k_render<TW, TH, PX, false, false><<<n_tiles, NT, 0, s>>>(a);
+  if (imp) k_render<TW, TH, PX, NBM, true><<<n_tiles, NT, 0, s>>>(a);
+  else k_render<TW, TH, PX, NBM, false><<<n_tiles, NT, 0, s>>>(a);
+}
+
+// Records staged per thread and batch: cfg->batch / threads, one of 1, 2, 4 (0: 2).
+template <int TW, int TH, int PX>
+static rs_status launch_render_nb(const RenderArgs& a, int n_tiles, bool imp, int batch, cudaStream_t s) {
+  constexpr int NT = TW * TH / PX;
+  const int m = batch == 0 ? 2 : (batch % NT == 0 ? batch / NT : 0);
+  if (m == 1) launch_render<TW, TH, PX, 1>(a, n_tiles, imp, s);
+  else if (m == 2) launch_render<TW, TH, PX, 2>(a, n_tiles, imp, s);
+  else if (m == 4) launch_render<TW, TH, PX, 4>(a, n_tiles, imp, s);
+  else return RS_ERR_UNSUPPORTED;
+  return RS_OK;
 }
 
 rs_status render_dispatch(const rs_projected* proj, const rs_bins* bins, const rs_view_batch* batch,
@@ -202,11 +213,15 @@ rs_status render_dispatch(const rs_projected* proj, const rs_bins* bins, const r
   a.last = last;
   a.importance = importance;
   a.n_gaussians = n_gaussians;
-  const bool img = image != nullptr, imp = importance != nullptr;
-  if (batch->tile_w == 16 && batch->tile_h == 16) launch_render<16, 16, 4>(a, batch->n_tiles, img, imp, s);
-  else if (batch->tile_w == 32 && batch->tile_h == 8) launch_render<32, 8, 4>(a, batch->n_tiles, img, imp, s);
-  else if (batch->tile_w == 8 && batch->tile_h == 8) launch_render<8, 8, 2>(a, batch->n_tiles, img, imp, s);
-  else return RS_ERR_UNSUPPORTED;
+  const bool imp = importance != nullptr;
+  rs_status st = RS_ERR_UNSUPPORTED;
+  if (batch->tile_w == 16 && batch->tile_h == 16)
+    st = launch_render_nb<16, 16, 4>(a, batch->n_tiles, imp, cfg->batch, s);
+  else if (batch->tile_w == 32 && batch->tile_h == 8)
+    st = launch_render_nb<32, 8, 4>(a, batch->n_tiles, imp, cfg->batch, s);
+  else if (batch->tile_w == 8 && batch->tile_h == 8)
+    st = launch_render_nb<8, 8, 2>(a, batch->n_tiles, imp, cfg->batch, s);
+  if (st != RS_OK) return st;
   return launch_status();
 }
 
@@ -216,6 +231,7 @@ static rs_status check_render_args(const rs_projected* proj, const rs_bins* bins
   if (!proj->xy || !proj->conic_o || !proj->rgb_d || !bins->vals || !bins->ranges || !batch->views)
     return RS_ERR_INVALID_ARG;
   if (batch->n_tiles < 0 || batch->n_views <= 0) return RS_ERR_INVALID_ARG;
+  if (!blend_batch_ok(batch->tile_w, batch->tile_h, cfg->batch)) return RS_ERR_UNSUPPORTED;
   if (!aligned<float4>(proj->conic_o, 16) || !aligned<float4>(proj->rgb_d, 16) || !aligned<float2>(proj->xy, 8) ||
       !aligned<uint2>(bins->ranges, 8))
     return RS_ERR_INVALID_ARG;

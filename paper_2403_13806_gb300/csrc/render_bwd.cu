@@ -80,12 +80,12 @@ __device__ __forceinline__ float2 sel2(bool a, bool b, float2 x) {
 // and, unless the 0.99 clamp was active, d/do = dL/da 2^p2 and with q = dL/da * a (the
 // derivative with respect to the power) the moments sum(q), sum(q dy), sum(q dy^2); the
 // column's common dx turns them into the mean and conic gradients.
-template <int TW, int TH, int PX>
+template <int TW, int TH, int PX, int NBM>
 __global__ void __launch_bounds__(TW* TH / PX) k_render_bwd(BwdBlendArgs a) {
   constexpr int NT = TW * TH / PX;  // threads; each owns pixels (x, PX r + k), k < PX
   constexpr int NP = PX / 2;
   constexpr int NW = NT / 32;
-  constexpr int NB = NT;            // records per batch
+  constexpr int NB = NBM * NT;      // records per batch (NBM per thread)
   constexpr int PS = NB + 1;        // padded stride: the nine components land in distinct banks
   __shared__ BlendRec s_rec[NB];
   __shared__ uint32_t s_item[NB];
@@ -150,10 +150,14 @@ __global__ void __launch_bounds__(TW* TH / PX) k_render_bwd(BwdBlendArgs a) {
     const int lo = max(hi - NB, 0);
     const int nb = hi - lo;
     __syncthreads();
-    if (tid < nb) {
-      const uint32_t item = __ldg(a.vals + start + lo + tid);
-      stage_record(a.xy, a.conic_o, a.rgb_d, item, s_rec[tid]);
-      s_item[tid] = item;
+#pragma unroll
+    for (int k = 0; k < NBM; ++k) {
+      const int slot = tid + k * NT;
+      if (slot < nb) {
+        const uint32_t item = __ldg(a.vals + start + lo + slot);
+        stage_record(a.xy, a.conic_o, a.rgb_d, item, s_rec[slot]);
+        s_item[slot] = item;
+      }
     }
     __syncthreads();
     float* part = s_part[warp];
@@ -228,8 +232,9 @@ __global__ void __launch_bounds__(TW* TH / PX) k_render_bwd(BwdBlendArgs a) {
       }
     }
     __syncthreads();
-    {
-      const int slot = tid;
+#pragma unroll
+    for (int k = 0; k < NBM; ++k) {
+      const int slot = tid + k * NT;
       if (slot < nb) {
         float c[9];
 #pragma unroll
@@ -547,10 +552,17 @@ static BwdWs bwd_ws_layout(void* base, int64_t n_items) {
 
 size_t backward_ws_bytes(const rs_view_batch* batch) { return bwd_ws_layout(nullptr, batch->n_items).bytes; }
 
+// Records staged per thread and batch: cfg->batch / threads, one of 1, 2, 4 (0: 1).
 template <int TW, int TH, int PX>
-static void launch_bwd_blend(const BwdBlendArgs& a, int n_tiles, cudaStream_t s) {
+static rs_status launch_bwd_blend(const BwdBlendArgs& a, int n_tiles, int batch, cudaStream_t s) {
+  constexpr int NT = TW * TH / PX;
+  const int m = batch == 0 ? 1 : (batch % NT == 0 ? batch / NT : 0);
+  if (m != 1 && m != 2 && m != 4) return RS_ERR_UNSUPPORTED;
   prof::Scope ps("k_render_bwd", s);
-  k_render_bwd<TW, TH, PX><<<n_tiles, TW * TH / PX, 0, s>>>(a);
+  if (m == 1) k_render_bwd<TW, TH, PX, 1><<<n_tiles, NT, 0, s>>>(a);
+  else if (m == 2) k_render_bwd<TW, TH, PX, 2><<<n_tiles, NT, 0, s>>>(a);
+  else k_render_bwd<TW, TH, PX, 4><<<n_tiles, NT, 0, s>>>(a);
+  return RS_OK;
 }
 
 }  // namespace rs
@@ -567,6 +579,7 @@ extern "C" rs_status rs_render_backward(const rs_gaussians* g, const rs_view_bat
     return RS_ERR_INVALID_ARG;
   if (!batch->views || batch->n_views <= 0 || batch->n_items < 0 || g->n <= 0) return RS_ERR_INVALID_ARG;
   if (!batch->subset_idx && batch->n_items != (int64_t)batch->n_views * g->n) return RS_ERR_INVALID_ARG;
+  if (!blend_batch_ok(batch->tile_w, batch->tile_h, cfg->batch)) return RS_ERR_UNSUPPORTED;
   const BwdWs w = bwd_ws_layout(ws, batch->n_items);
   if (!ws || ws_bytes < w.bytes || !aligned<float4>(ws, 256)) return RS_ERR_WORKSPACE;
   if (batch->n_items == 0 || batch->n_tiles == 0) return RS_OK;
@@ -590,10 +603,11 @@ extern "C" rs_status rs_render_backward(const rs_gaussians* g, const rs_view_bat
   b.g.ga = w.ga;
   b.g.gb = w.gb;
   b.g.gc = w.gc;
-  if (batch->tile_w == 16 && batch->tile_h == 16) launch_bwd_blend<16, 16, 4>(b, batch->n_tiles, s);
-  else if (batch->tile_w == 32 && batch->tile_h == 8) launch_bwd_blend<32, 8, 4>(b, batch->n_tiles, s);
-  else if (batch->tile_w == 8 && batch->tile_h == 8) launch_bwd_blend<8, 8, 2>(b, batch->n_tiles, s);
-  else return RS_ERR_UNSUPPORTED;
+  rs_status bst = RS_ERR_UNSUPPORTED;
+  if (batch->tile_w == 16 && batch->tile_h == 16) bst = launch_bwd_blend<16, 16, 4>(b, batch->n_tiles, cfg->batch, s);
+  else if (batch->tile_w == 32 && batch->tile_h == 8) bst = launch_bwd_blend<32, 8, 4>(b, batch->n_tiles, cfg->batch, s);
+  else if (batch->tile_w == 8 && batch->tile_h == 8) bst = launch_bwd_blend<8, 8, 2>(b, batch->n_tiles, cfg->batch, s);
+  if (bst != RS_OK) return bst;
 
   BwdProjArgs p;
   p.g = *g;

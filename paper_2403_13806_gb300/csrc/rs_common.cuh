@@ -53,4 +53,16 @@ inline bool aligned(const void* p, size_t a) {
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Threads of a blend CTA: four pixels of a column per thread (two for 8x8 tiles).
+inline int blend_threads(int tile_w, int tile_h) { return (tile_w == 8 && tile_h == 8) ? 32 : tile_w * tile_h / 4; }
+
+// rs_config.batch (records staged per blend batch): 0 (default) or 1, 2 or 4 per thread.
+inline bool blend_batch_ok(int tile_w, int tile_h, int batch) {
+  if (batch == 0) return true;
+  const int nt = blend_threads(tile_w, tile_h);
+  if (batch < 0 || batch % nt != 0) return false;
+  const int m = batch / nt;
+  return m == 1 || m == 2 || m == 4;
+}
+
 }  // namespace rs

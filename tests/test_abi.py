@@ -53,9 +53,10 @@ def test_struct_layouts_match(native):
 def test_autotune_host_checks(native):
     L = native.lib()
     assert L.rs_autotune_candidates(0) == 0
-    assert L.rs_autotune_candidates(1) == 3          # three tile shapes x batch 1
-    assert L.rs_autotune_candidates(4) == 9          # batches 1, 2, 4
-    assert L.rs_autotune_candidates(5) == 12         # batches 1, 2, 4, 5
+    # stage 1: three tile shapes x 1, 2, 4 staged records per thread; stage 2: views per launch
+    assert L.rs_autotune_candidates(1) == 9 + 1
+    assert L.rs_autotune_candidates(4) == 9 + 3      # 1, 2, 4
+    assert L.rs_autotune_candidates(5) == 9 + 4      # 1, 2, 4, 5
     res = native.RsTuneResult()
     # argument checks happen before any device work
     assert L.rs_autotune(None, None, 1, None, None, None, 0, ctypes.byref(res), None, None) == native.RS_ERR_INVALID_ARG

@@ -27,14 +27,27 @@ def three_views():
     return scene, cams
 
 
-def render_chunks(g, cams, tile, batch, subsets=None):
+def render_chunks(g, cams, tile, batch, subsets=None, smem_batch=0):
     imgs = []
+    cfg = api.config(batch=smem_batch)
     for s0 in range(0, len(cams), batch):
         sub = subsets[s0:s0 + batch] if subsets is not None else None
         vb = api.ViewBatch(cams[s0:s0 + batch], g.n, subsets=sub, tile=tile)
-        out = api.Rasterizer().forward(g, vb)
+        out = api.Rasterizer(cfg=cfg).forward(g, vb)
         imgs += [x.cpu().numpy() for x in api.split_images(out["image"], vb)]
     return imgs
+
+
+def check_choice(r, n_views):
+    n_batches = len(r["stage2"])
+    assert len(r["stage1"]) == 9 and all(ms > 0 for ms in r["stage1"].values())
+    assert r["n_candidates"] == 9 + n_batches
+    # stage 1 picks the fastest tile shape and staging batch, stage 2 the fastest views per launch
+    tw, th, m = min(r["stage1"], key=r["stage1"].get)
+    assert r["tile"] == (tw, th) and r["smem_batch"] == m * api.blend_threads((tw, th))
+    assert r["views_per_launch"] == min(r["stage2"], key=r["stage2"].get)
+    assert r["ms_per_view"] == pytest.approx(min(r["stage2"].values()), rel=1e-6)
+    assert set(r["stage2"]) <= set([1, 2, 4, 8, 16, 32, 64, 128, n_views])
 
 
 def test_autotune_measures_chooses_and_caches():
@@ -43,22 +56,20 @@ def test_autotune_measures_chooses_and_caches():
     api.N.lib().rs_autotune_clear()
     r = api.autotune(g, cams, backward=True)
     assert not r["cached"]
-    assert r["n_candidates"] == 9 and len(r["candidates"]) == 9   # 3 shapes x batches 1, 2, 3
-    assert r["tile"] in api.TILE_SHAPES and r["batch"] in (1, 2, 3)
-    assert all(ms > 0 for ms in r["candidates"].values())
-    assert r["ms_per_view"] == pytest.approx(min(r["candidates"].values()), rel=1e-6)
-    assert r["candidates"][(*r["tile"], r["batch"])] == pytest.approx(r["ms_per_view"], rel=1e-6)
+    check_choice(r, 3)
+    assert sorted(r["stage2"]) == [1, 2, 3]
     again = api.autotune(g, cams, backward=True)
-    assert again["cached"] and again["tile"] == r["tile"] and again["batch"] == r["batch"]
-    assert again["n_candidates"] == 0
+    assert again["cached"] and again["n_candidates"] == 0
+    assert (again["tile"], again["smem_batch"], again["views_per_launch"]) == \
+        (r["tile"], r["smem_batch"], r["views_per_launch"])
     # the forward-only workload is a different cache entry; forcing re-measures
     fwd = api.autotune(g, cams, backward=False)
     assert not fwd["cached"]
     forced = api.autotune(g, cams, backward=True, force=True)
-    assert not forced["cached"] and forced["n_candidates"] == 9
+    assert not forced["cached"] and forced["n_candidates"] == 12
     # the choice renders the same images as one 16x16 batch of all views
     ref = render_chunks(g, cams, (16, 16), 3)
-    got = render_chunks(g, cams, r["tile"], r["batch"])
+    got = render_chunks(g, cams, r["tile"], r["views_per_launch"], smem_batch=r["smem_batch"])
     for a, b in zip(ref, got):
         assert np.array_equal(a, b)
 
@@ -69,9 +80,9 @@ def test_autotune_with_visibility_lists():
     rng = np.random.default_rng(5)
     subsets = [np.sort(rng.choice(scene.n, size=n, replace=False)).astype(np.uint32) for n in (500, 1200, 800)]
     r = api.autotune(g, cams, subsets=subsets, backward=True, force=True)
-    assert r["tile"] in api.TILE_SHAPES and r["batch"] in (1, 2, 3)
+    check_choice(r, 3)
     ref = render_chunks(g, cams, (16, 16), 3, subsets)
-    got = render_chunks(g, cams, r["tile"], r["batch"], subsets)
+    got = render_chunks(g, cams, r["tile"], r["views_per_launch"], subsets, smem_batch=r["smem_batch"])
     for a, b in zip(ref, got):
         assert np.array_equal(a, b)
 

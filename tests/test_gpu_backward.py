@@ -138,3 +138,23 @@ def test_autograd_function_l1_step():
     assert abs(l.item() - ref_l) <= 1e-6
     d = img.detach().cpu().numpy() - tgt.astype(np.float32).ravel()
     np.testing.assert_array_equal(gl.cpu().numpy(), (np.sign(d) / np.float32(n)).astype(np.float32))
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (8, 8)])
+def test_backward_staging_batches_agree_with_oracle(tile):
+    """Every staging batch (1, 2, 4 records per thread) gives the oracle's gradient."""
+    from paper_2403_13806_gb300 import api
+    scene, cams = synth.fd_crop()
+    cam = cams[0]
+    w = unambiguous_weights(scene, cam, 4)
+    ref = og.gradients(scene, cam, w)
+    dL = torch.as_tensor(w.astype(np.float32).ravel(), device="cuda")
+    nt = api.blend_threads(tile)
+    for m in (1, 2, 4):
+        out = gpu_forward(scene, cams, tile=tile, importance=False)
+        g = out["g"]
+        grads = [torch.zeros_like(t) for t in g.tensors()]
+        api.render_backward(g, out["vb"], out["proj"], out["bins"], out["T_final"], out["last"], dL, grads,
+                            out["rast"].ws_bwd, api.config(batch=m * nt))
+        torch.cuda.synchronize()
+        compare_groups({k: t.cpu().numpy() for k, t in zip(KEYS, grads)}, ref)

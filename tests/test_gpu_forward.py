@@ -131,6 +131,32 @@ def test_images_identical_across_tile_shapes():
     assert np.array_equal(imgs[0], imgs[1]) and np.array_equal(imgs[0], imgs[2])
 
 
+@pytest.mark.parametrize("tile", [(16, 16), (32, 8), (8, 8)])
+def test_staging_batch_changes_nothing(tile):
+    """rs_config.batch (records staged per blend batch) leaves image, T_final, last and
+    importance bit-identical; values that are not 1, 2 or 4 per thread are rejected."""
+    from paper_2403_13806_gb300 import api, _native as N
+    scene, cams = synth.config1(n=20000, n_views=2, width=320, height=208)
+    g = api.Gaussians.from_scene(scene)
+    vb = api.ViewBatch(cams, scene.n, tile=tile)
+    nt = api.blend_threads(tile)
+    outs = []
+    for m in (1, 2, 4):
+        h = torch.zeros(scene.n, dtype=torch.int32, device="cuda")
+        out = api.Rasterizer(cfg=api.config(batch=m * nt)).forward(g, vb, importance=h)
+        torch.cuda.synchronize()
+        outs.append([out["image"].cpu().numpy(), out["T_final"].cpu().numpy(), out["last"].cpu().numpy(),
+                     h.cpu().numpy()])
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            assert np.array_equal(a, b)
+    rast = api.Rasterizer()
+    out = rast.forward(g, vb)
+    with pytest.raises(N.RadsplatError) as e:
+        api.render(out["proj"], out["bins"], vb, api.config(batch=3 * nt))
+    assert e.value.code == N.RS_ERR_UNSUPPORTED
+
+
 def check_importance(h_gpu, h, h_amb, min_strict=0.8):
     """h: max alpha*T over entries no near-threshold decision precedes; h_amb: over the
     others.  Flipping an alpha decision rescales later T by at most 1/(1 - 1/255), and a
