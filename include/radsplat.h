@@ -226,10 +226,12 @@ rs_status rs_project(const rs_gaussians* g, const rs_view_batch* batch, const rs
 
 /* rs_bin_sort -- tile binning with duplicated 64-bit (tile | depth) keys and a device
  * radix sort (the front-to-back order Eq. render-gs needs, per tile).  Every item is
- * duplicated once per tile of its rect; the instances are sorted by
- * key = (global tile id) << 32 | float bits of depth, stably with respect to item order
- * (an LSD radix sort whose low 32 bits, constant per item, are sorted over the items
- * before duplication).  Writes vals, ranges, and keys if non-NULL.
+ * duplicated once per tile of its rect; the instances come out sorted by
+ * key = (global tile id) << 32 | float bits of depth, stably with respect to item order.
+ * The sort runs in levels that give exactly that order: the items by depth (radix), their
+ * instances per 4 x 4-tile super-tile by super-tile id (stable radix), then each
+ * super-tile list partitioned in order into its tile lists.  Writes vals, ranges, and
+ * keys if non-NULL.
  * If the instance count K exceeds bins->capacity, status->code = RS_ERR_CAPACITY,
  * status->required = K, and only the first capacity instances are written (the lists
  * are then incomplete; re-run with capacity >= required).
