@@ -48,7 +48,8 @@ struct BinWs {
   uint32_t* super_base;       // [n_views + 1]
   uint32_t* fine_tot;         // [n_tiles]: instances per tile, then first position
   uint32_t* seg_cnt;          // [n_tiles][kSegs][16]: per (super-tile, segment, tile) counts, then prefixes
-  uint32_t* counters;         // [0] super instances written, [2] instances written
+  uint32_t* counters;         // [0] super instances written, [2] instances written,
+                              // [4], [5] work counters of the fine count and scatter
   int grid_depth;
   size_t bytes;
 };
@@ -331,53 +332,67 @@ __device__ __forceinline__ void segment(const SuperTile& t, int j, uint32_t& a, 
   b = min(a + L, t.s1);
 }
 
-// Instances per (super-tile, segment, tile): each CTA reads one segment of its super-tile's
-// depth-ordered list once and counts, for each of the 4 x 4 tiles, the items covering it.
+// Work items of the fine kernels are (super-tile, segment) pairs, handed out in order from a
+// device counter to a grid of at most a few CTAs per SM (the number of super-tiles is only
+// known on the device).  Every thread of the CTA receives the same item.
+__device__ __forceinline__ uint32_t next_work(uint32_t* ctr, uint32_t* s_slot) {
+  __syncthreads();   // the previous item's use of shared memory is over
+  if (threadIdx.x == 0) *s_slot = atomicAdd(ctr, 1u);
+  __syncthreads();
+  return *s_slot;
+}
+
+// Instances per (super-tile, segment, tile): each work item reads one segment of its
+// super-tile's depth-ordered list once and counts, for each of the 4 x 4 tiles, the items
+// covering it.
 __global__ void __launch_bounds__(kFineThreads) k_fine_count(const uint32_t* __restrict__ svals,
                                                              const ushort4* __restrict__ rect,
                                                              const rs_view* __restrict__ views, int n_views,
                                                              const uint32_t* __restrict__ super_base,
                                                              const uint32_t* __restrict__ sranges,
-                                                             uint32_t* __restrict__ seg_cnt) {
+                                                             uint32_t* __restrict__ seg_cnt, uint32_t* __restrict__ ctr) {
   constexpr int NW = kFineThreads / 32;
   __shared__ uint32_t s_cnt[NW][kNF];
-  const uint32_t S = blockIdx.x / kSegs;
-  const int j = blockIdx.x % kSegs;
-  const SuperTile t = super_tile(S, views, n_views, super_base, sranges);
-  if (!t.valid) return;   // uniform per CTA
-  uint32_t a, b;
-  segment(t, j, a, b);
+  __shared__ uint32_t s_w;
+  const uint32_t n_work = super_base[n_views] * (uint32_t)kSegs;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t c[kNF];
+  for (uint32_t wi = next_work(ctr, &s_w); wi < n_work; wi = next_work(ctr, &s_w)) {
+    const uint32_t S = wi / kSegs;
+    const int j = wi % kSegs;
+    const SuperTile t = super_tile(S, views, n_views, super_base, sranges);
+    uint32_t a, b;
+    segment(t, j, a, b);
+    uint32_t c[kNF];
 #pragma unroll
-  for (int f = 0; f < kNF; ++f) c[f] = 0u;
-  constexpr int U = 4;   // independent loads in flight per thread
-  for (uint32_t e0 = a; e0 < b; e0 += U * kFineThreads) {
-    ushort4 rr[U];
+    for (int f = 0; f < kNF; ++f) c[f] = 0u;
+    constexpr int U = 4;   // independent loads in flight per thread
+    for (uint32_t e0 = a; e0 < b; e0 += U * kFineThreads) {
+      ushort4 rr[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const uint32_t e = e0 + u * kFineThreads + threadIdx.x;
-      rr[u] = e < b ? rect[svals[e]] : make_ushort4(0, 0, 0, 0);
+      for (int u = 0; u < U; ++u) {
+        const uint32_t e = e0 + u * kFineThreads + threadIdx.x;
+        rr[u] = e < b ? rect[svals[e]] : make_ushort4(0, 0, 0, 0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const uint32_t m = cover_mask(rr[u], t);
+#pragma unroll
+        for (int f = 0; f < kNF; ++f) c[f] += __popc(__ballot_sync(0xffffffffu, (m >> f) & 1u));
+      }
     }
+    if (lane < kNF) {
+      uint32_t mine = 0;
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const uint32_t m = cover_mask(rr[u], t);
-#pragma unroll
-      for (int f = 0; f < kNF; ++f) c[f] += __popc(__ballot_sync(0xffffffffu, (m >> f) & 1u));
+      for (int f = 0; f < kNF; ++f) mine = (lane == f) ? c[f] : mine;
+      s_cnt[warp][lane] = mine;
     }
-  }
-  if (lane < kNF) {
-    uint32_t mine = 0;
+    __syncthreads();
+    if (threadIdx.x < kNF) {
+      uint32_t tot = 0;
 #pragma unroll
-    for (int f = 0; f < kNF; ++f) mine = (lane == f) ? c[f] : mine;
-    s_cnt[warp][lane] = mine;
-  }
-  __syncthreads();
-  if (threadIdx.x < kNF) {
-    uint32_t tot = 0;
-#pragma unroll
-    for (int w = 0; w < NW; ++w) tot += s_cnt[w][threadIdx.x];
-    seg_cnt[((int64_t)S * kSegs + j) * kNF + threadIdx.x] = tot;
+      for (int w = 0; w < NW; ++w) tot += s_cnt[w][threadIdx.x];
+      seg_cnt[((int64_t)S * kSegs + j) * kNF + threadIdx.x] = tot;
+    }
   }
 }
 
@@ -481,82 +496,86 @@ __global__ void __launch_bounds__(kFineThreads) k_fine_scatter(const uint32_t* _
                                                                const uint32_t* __restrict__ fine_start,
                                                                const uint32_t* __restrict__ seg_pre, int64_t capacity,
                                                                uint32_t* __restrict__ vals,
-                                                               unsigned long long* __restrict__ keys) {
+                                                               unsigned long long* __restrict__ keys,
+                                                               uint32_t* __restrict__ ctr) {
   constexpr int NW = kFineThreads / 32;
   __shared__ uint32_t s_bal[NW][kNF];     // per-warp ballot of each tile
   __shared__ uint32_t s_base[NW][kNF];    // first position of each (warp, tile) in this chunk
   __shared__ uint32_t s_run[kNF];         // next position of each tile
   __shared__ uint32_t s_tile[kNF];        // global id of each tile
-  const uint32_t S = blockIdx.x / kSegs;
-  const int j = blockIdx.x % kSegs;
-  const SuperTile t = super_tile(S, views, n_views, super_base, sranges);
-  if (!t.valid) return;   // uniform per CTA
-  uint32_t a, b;
-  segment(t, j, a, b);
+  __shared__ uint32_t s_w;
+  const uint32_t n_work = super_base[n_views] * (uint32_t)kSegs;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x < kNF) {
-    const int f = threadIdx.x, fx = f % kSuper, fy = f / kSuper;
-    const rs_view& cam = views[t.v];
-    const bool in = fx < t.nx && fy < t.ny;
-    const uint32_t T = in ? (uint32_t)(cam.tile_base + (t.ty0 + fy) * cam.tiles_x + t.tx0 + fx) : 0u;
-    s_tile[f] = T;
-    s_run[f] = in ? fine_start[T] + seg_pre[((int64_t)S * kSegs + j) * kNF + f] : 0u;
-  }
-  const uint32_t cap = (uint32_t)(capacity < 0xffffffffLL ? capacity : 0xffffffffLL);
-  const unsigned lt = (1u << lane) - 1u;
-  // the next chunk's item and rect are fetched while the current one is placed
-  uint32_t n_item = 0;
-  ushort4 n_rect = make_ushort4(0, 0, 0, 0);
-  if (a + threadIdx.x < b) {
-    n_item = svals[a + threadIdx.x];
-    n_rect = rect[n_item];
-  }
-  for (uint32_t e0 = a; e0 < b; e0 += kFineThreads) {
-    const uint32_t item = n_item;
-    const uint32_t m = cover_mask(n_rect, t);
-    const uint32_t en = e0 + kFineThreads + threadIdx.x;
-    n_item = 0;
-    n_rect = make_ushort4(0, 0, 0, 0);   // past the segment: covers nothing
-    if (en < b) {
-      n_item = svals[en];
+  for (uint32_t wi = next_work(ctr, &s_w); wi < n_work; wi = next_work(ctr, &s_w)) {
+    const uint32_t S = wi / kSegs;
+    const int j = wi % kSegs;
+    const SuperTile t = super_tile(S, views, n_views, super_base, sranges);
+    uint32_t a, b;
+    segment(t, j, a, b);
+    if (threadIdx.x < kNF) {
+      const int f = threadIdx.x, fx = f % kSuper, fy = f / kSuper;
+      const rs_view& cam = views[t.v];
+      const bool in = fx < t.nx && fy < t.ny;
+      const uint32_t T = in ? (uint32_t)(cam.tile_base + (t.ty0 + fy) * cam.tiles_x + t.tx0 + fx) : 0u;
+      s_tile[f] = T;
+      s_run[f] = in ? fine_start[T] + seg_pre[((int64_t)S * kSegs + j) * kNF + f] : 0u;
+    }
+    const uint32_t cap = (uint32_t)(capacity < 0xffffffffLL ? capacity : 0xffffffffLL);
+    const unsigned lt = (1u << lane) - 1u;
+    // the next chunk's item and rect are fetched while the current one is placed
+    uint32_t n_item = 0;
+    ushort4 n_rect = make_ushort4(0, 0, 0, 0);
+    if (a + threadIdx.x < b) {
+      n_item = svals[a + threadIdx.x];
       n_rect = rect[n_item];
     }
-    uint32_t my_bal = 0;
-#pragma unroll
-    for (int f = 0; f < kNF; ++f) {
-      const unsigned bl = __ballot_sync(0xffffffffu, (m >> f) & 1u);
-      my_bal = (lane == f) ? bl : my_bal;
-    }
-    if (lane < kNF) s_bal[warp][lane] = my_bal;
-    __syncthreads();
-    if (threadIdx.x < kNF) {
-      // per tile: warp offsets inside this chunk, then advance the tile's run
-      const int f = threadIdx.x;
-      uint32_t r = s_run[f];
-#pragma unroll
-      for (int w = 0; w < NW; ++w) {
-        s_base[w][f] = r;
-        r += __popc(s_bal[w][f]);
+    for (uint32_t e0 = a; e0 < b; e0 += kFineThreads) {
+      const uint32_t item = n_item;
+      const uint32_t m = cover_mask(n_rect, t);
+      const uint32_t en = e0 + kFineThreads + threadIdx.x;
+      n_item = 0;
+      n_rect = make_ushort4(0, 0, 0, 0);   // past the segment: covers nothing
+      if (en < b) {
+        n_item = svals[en];
+        n_rect = rect[n_item];
       }
-      s_run[f] = r;
-    }
-    __syncthreads();
-    // one store per tile, all lanes together: the lanes covering tile f write consecutive
-    // positions of its list
-    const uint32_t db = (keys && m) ? __float_as_uint(rgb_d[item].w) : 0u;
-#pragma unroll
-    for (int f = 0; f < kNF; ++f) {
-      const uint32_t bl = s_bal[warp][f];
-      if (bl == 0u) continue;   // uniform per warp
-      if ((m >> f) & 1u) {
-        const uint32_t pos = s_base[warp][f] + __popc(bl & lt);
-        if (pos < cap) {
-          vals[pos] = item;
-          if (keys) keys[pos] = ((unsigned long long)s_tile[f] << 32) | db;
+      uint32_t my_bal = 0;
+  #pragma unroll
+      for (int f = 0; f < kNF; ++f) {
+        const unsigned bl = __ballot_sync(0xffffffffu, (m >> f) & 1u);
+        my_bal = (lane == f) ? bl : my_bal;
+      }
+      if (lane < kNF) s_bal[warp][lane] = my_bal;
+      __syncthreads();
+      if (threadIdx.x < kNF) {
+        // per tile: warp offsets inside this chunk, then advance the tile's run
+        const int f = threadIdx.x;
+        uint32_t r = s_run[f];
+  #pragma unroll
+        for (int w = 0; w < NW; ++w) {
+          s_base[w][f] = r;
+          r += __popc(s_bal[w][f]);
+        }
+        s_run[f] = r;
+      }
+      __syncthreads();
+      // one store per tile, all lanes together: the lanes covering tile f write consecutive
+      // positions of its list
+      const uint32_t db = (keys && m) ? __float_as_uint(rgb_d[item].w) : 0u;
+  #pragma unroll
+      for (int f = 0; f < kNF; ++f) {
+        const uint32_t bl = s_bal[warp][f];
+        if (bl == 0u) continue;   // uniform per warp
+        if ((m >> f) & 1u) {
+          const uint32_t pos = s_base[warp][f] + __popc(bl & lt);
+          if (pos < cap) {
+            vals[pos] = item;
+            if (keys) keys[pos] = ((unsigned long long)s_tile[f] << 32) | db;
+          }
         }
       }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 
@@ -644,11 +663,14 @@ extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* 
                                    : super_instances<uint32_t>(w, order, n, proj, batch, cap, nblk, n_super_max, s);
   }
   // 3) per tile: count (per super-tile segment), scans (ranges and K), scatter
-  const unsigned fgrid = (unsigned)((int64_t)batch->n_tiles * kSegs);
+  // at most 8 resident CTAs per SM; the work items (super-tiles x segments) come from a
+  // device counter, so a generous bound on the number of super-tiles costs nothing
+  const int64_t fwork = (int64_t)batch->n_tiles * kSegs;
+  const unsigned fgrid = (unsigned)(fwork < 8 * kNumSMs ? fwork : 8 * kNumSMs);
   {
     prof::Scope ps("k_fine_count", s);
     k_fine_count<<<fgrid, kFineThreads, 0, s>>>(svals, rect, batch->views, batch->n_views, w.super_base, w.sranges,
-                                                 w.seg_cnt);
+                                                 w.seg_cnt, w.counters + 4);
   }
   {
     prof::Scope ps("k_fine_seg_scan", s);
@@ -663,7 +685,7 @@ extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* 
     prof::Scope ps("k_fine_scatter", s);
     k_fine_scatter<<<fgrid, kFineThreads, 0, s>>>(svals, rect, rgb_d, batch->views, batch->n_views, w.super_base,
                                                    w.sranges, w.fine_tot, w.seg_cnt, cap, bins->vals,
-                                                   reinterpret_cast<unsigned long long*>(bins->keys));
+                                                   reinterpret_cast<unsigned long long*>(bins->keys), w.counters + 5);
   }
   return launch_status();
 }
