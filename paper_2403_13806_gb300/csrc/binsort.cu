@@ -18,12 +18,12 @@
 // order of the stable 64-bit sort.  The 64-bit keys are written only on request.
 //
 // Pipeline (one stream, no host synchronisation; counts live in device memory):
-//   k_super_layout (super-tile bases per view); k_depth_keys, 4 depth passes (items);
+//   k_super_layout (super-tile bases per view); k_depth_keys, 4 depth passes over the items
+//   (radix_tiles, 31-bit keys);
 //   k_count_blocks, k_count_top (super total); k_emit (super instances); super passes
 //   (radix_tiles); k_ranges (super ranges); k_fine_count; k_fine_seg_scan; k_fine_scan
 //   (ranges, K, capacity check); k_fine_scatter (vals, optional keys).
 #include "profile.cuh"
-#include "radix.cuh"
 #include "radix_tiles.cuh"
 #include "radsplat.h"
 #include "rs_common.cuh"
@@ -42,15 +42,15 @@ struct BinWs {
   unsigned long long* bsum;   // per emission block: super instances, then exclusive prefix
   char* skeys[2];             // super-tile ids (uint16 or uint32)
   uint32_t* svals[2];         // items
-  uint32_t* hist;             // item radix scratch
+  uint32_t* hist;             // per-tile digit counters of the item (depth) sort
   uint32_t* sweep;            // per-tile digit counters of the super-instance sort
   uint32_t* sranges;          // [n_tiles][2]: super-tile ranges (super-tiles never outnumber tiles)
   uint32_t* super_base;       // [n_views + 1]
   uint32_t* fine_tot;         // [n_tiles]: instances per tile, then first position
   uint32_t* seg_cnt;          // [n_tiles][kSegs][16]: per (super-tile, segment, tile) counts, then prefixes
   uint32_t* counters;         // [0] super instances written, [2] instances written,
-                              // [4], [5] work counters of the fine count and scatter
-  int grid_depth;
+                              // [4], [5] work counters of the fine count and scatter,
+                              // [6] item count (the depth sort's device count)
   size_t bytes;
 };
 
@@ -65,13 +65,12 @@ static BinWs bin_ws_layout(void* base, int64_t n_items, int64_t capacity, int n_
   const size_t ni = (size_t)(n_items > 0 ? n_items : 1);
   const size_t cap = (size_t)(capacity > 0 ? capacity : 1);   // super instances <= instances
   const int64_t nblk = (n_items + kEmitThreads - 1) / kEmitThreads;
-  w.grid_depth = radix::grid_for(n_items);
   for (int i = 0; i < 2; ++i) w.dkeys[i] = reinterpret_cast<uint32_t*>(take(ni * 4));
   for (int i = 0; i < 2; ++i) w.dvals[i] = reinterpret_cast<uint32_t*>(take(ni * 4));
   w.bsum = reinterpret_cast<unsigned long long*>(take((size_t)(nblk > 0 ? nblk : 1) * 8));
   for (int i = 0; i < 2; ++i) w.skeys[i] = take(cap * 4);
   for (int i = 0; i < 2; ++i) w.svals[i] = reinterpret_cast<uint32_t*>(take(cap * 4));
-  w.hist = reinterpret_cast<uint32_t*>(take(radix::scratch_words(w.grid_depth) * 4));
+  w.hist = reinterpret_cast<uint32_t*>(take(tiles::scratch_words(n_items) * 4));
   w.sweep = reinterpret_cast<uint32_t*>(take(tiles::scratch_words(capacity) * 4));
   w.sranges = reinterpret_cast<uint32_t*>(take((size_t)(n_tiles > 0 ? n_tiles : 1) * 8));
   w.super_base = reinterpret_cast<uint32_t*>(take((size_t)(n_views + 1) * 4));
@@ -85,17 +84,24 @@ static BinWs bin_ws_layout(void* base, int64_t n_items, int64_t capacity, int n_
 __device__ __forceinline__ int super_w(const rs_view& v) { return (v.tiles_x + kSuper - 1) / kSuper; }
 __device__ __forceinline__ int super_h(const rs_view& v) { return (v.tiles_y + kSuper - 1) / kSuper; }
 
+// Depth sort keys: the FP32 depth bits with the sign bit cleared.  Every item that emits
+// instances has depth > near_plane > 0, whose bits order like the value and are unchanged;
+// culled items (any depth, possibly negative or NaN) emit nothing, so their place in the
+// order is irrelevant, and no key can equal the sort's all-ones padding sentinel.
 __global__ void k_depth_keys(const float4* __restrict__ rgb_d, int64_t n, uint32_t* __restrict__ keys,
                              uint32_t* __restrict__ vals) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  keys[i] = __float_as_uint(rgb_d[i].w);
+  keys[i] = __float_as_uint(rgb_d[i].w) & 0x7fffffffu;
   vals[i] = (uint32_t)i;
 }
 
-// First super-tile id of every view (exclusive prefix of the views' super-tile counts).
-__global__ void k_super_layout(const rs_view* __restrict__ views, int n_views, uint32_t* __restrict__ super_base) {
+// First super-tile id of every view (exclusive prefix of the views' super-tile counts), and
+// the item count as the depth sort's device count.
+__global__ void k_super_layout(const rs_view* __restrict__ views, int n_views, uint32_t* __restrict__ super_base,
+                               int64_t n_items, uint32_t* __restrict__ n_dev) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  *n_dev = (uint32_t)n_items;
   uint32_t run = 0;
   for (int v = 0; v < n_views; ++v) {
     super_base[v] = run;
@@ -638,7 +644,7 @@ extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* 
   if (cudaMemsetAsync(w.sranges, 0, (size_t)n_super_max * 8, s) != cudaSuccess) return RS_ERR_CUDA;
   {
     prof::Scope ps("k_super_layout", s);
-    k_super_layout<<<1, 32, 0, s>>>(batch->views, batch->n_views, w.super_base);
+    k_super_layout<<<1, 32, 0, s>>>(batch->views, batch->n_views, w.super_base, n, w.counters + 6);
   }
   const uint32_t* svals = w.svals[0];
   if (n > 0) {
@@ -647,8 +653,9 @@ extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* 
       prof::Scope ps("k_depth_keys", s);
       k_depth_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rgb_d, n, w.dkeys[0], w.dvals[0]);
     }
-    radix::sort_pairs(w.dkeys[0], w.dvals[0], w.dkeys[1], w.dvals[1], n, nullptr, 32, w.hist, w.grid_depth, s, false);
-    const uint32_t* order = w.dvals[0];
+    const int dcur = tiles::sort_pairs<uint32_t>(w.dkeys[0], w.dvals[0], w.dkeys[1], w.dvals[1], w.counters + 6, n, 31,
+                                                 w.hist, s, false);
+    const uint32_t* order = w.dvals[dcur];
     // 2) super instances in depth order, sorted stably on the super-tile id
     const int64_t nblk = (n + kEmitThreads - 1) / kEmitThreads;
     {

@@ -1,6 +1,7 @@
-// Stable LSD radix sort of (key, uint32 value) pairs for large inputs such as the
-// duplicated tile instances: one CTA per tile of 2048 keys in every kernel, and no waits
-// between CTAs.  Keys are 16-bit when every key fits (fewer bytes per pass), else 32-bit.
+// Stable LSD radix sort of (key, uint32 value) pairs -- the items by depth and the
+// super-tile instances by super-tile id: CTAs work on tiles of 2048 keys in every kernel,
+// with no waits between CTAs.  Keys are 16-bit when every key fits (fewer bytes per pass),
+// else 32-bit (all-ones is reserved as the padding sentinel).
 //
 // A pass over one digit (<= 8 bits) is three kernels:
 //   k_tile_hist  -- per tile: its digit histogram, stored digit-major cnt[d][tile];
@@ -22,7 +23,6 @@
 #include <stdint.h>
 
 #include "profile.cuh"
-#include "radix.cuh"
 #include "rs_common.cuh"
 
 namespace rs {
@@ -33,6 +33,38 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kItems = 8;
 constexpr int kTile = kThreads * kItems;   // 2048
 constexpr int kR = 256;
+
+// Exclusive scan of v over the block (kThreads values, one per thread); the block total is
+// written to *total (shared).  Contains barriers: every thread must call it.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp, uint32_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < kWarps ? s_warp[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < kWarps) s_warp[lane] = w;   // inclusive warp prefix
+    if (lane == kWarps - 1) *total = w;
+  }
+  __syncthreads();
+  const uint32_t wbase = warp ? s_warp[warp - 1] : 0u;
+  const uint32_t r = wbase + x - v;
+  __syncthreads();
+  return r;
+}
+
+// Passes of at most 8 bits for a sort on `bits` key bits.
+inline int sort_passes(int bits) { return bits < 1 ? 1 : (bits + 7) / 8; }
 
 template <typename KeyT, int TILE = kTile>
 __global__ void __launch_bounds__(kThreads) k_tile_hist(const KeyT* __restrict__ keys, const uint32_t* __restrict__ n_dev,
@@ -146,7 +178,7 @@ __global__ void __launch_bounds__(kThreads, ITEMS <= 8 ? 4 : 3) k_tile_sort(cons
   if ((int64_t)blockIdx.x >= n_tiles) return;   // uniform per CTA
   // global position of the first key of digit d over all tiles (exclusive prefix of totals)
   const int d = threadIdx.x;
-  const uint32_t dbase = radix::block_excl_scan(d < R ? tot[d] : 0u, s_scan, &s_total);
+  const uint32_t dbase = block_excl_scan(d < R ? tot[d] : 0u, s_scan, &s_total);
   const unsigned lt_mask = (1u << lane) - 1u;
 
   // grid-stride over the tiles the device count needs (the grid is sized for the bound)
@@ -195,7 +227,7 @@ __global__ void __launch_bounds__(kThreads, ITEMS <= 8 ? 4 : 3) k_tile_sort(cons
         c += x;
       }
     }
-    const uint32_t lstart = radix::block_excl_scan(d < R ? c : 0u, s_scan, &s_total);
+    const uint32_t lstart = block_excl_scan(d < R ? c : 0u, s_scan, &s_total);
     if (d < R) {
       s_lstart[d] = lstart;
       s_gpos[d] = gfirst - lstart;
@@ -236,7 +268,7 @@ template <typename KeyT, int ITEMS = kItems>
 inline int sort_pairs(KeyT* k0, uint32_t* v0, KeyT* k1, uint32_t* v1, const uint32_t* n_dev, int64_t n_max, int bits,
                       uint32_t* scratch, cudaStream_t s, bool write_last_keys = true) {
   constexpr int TILE = kThreads * ITEMS;
-  const int passes = radix::sort_passes(bits);
+  const int passes = sort_passes(bits);
   const int rbits = (bits + passes - 1) / passes;
   const int64_t nt = tiles_for(n_max, TILE) > 0 ? tiles_for(n_max, TILE) : 1;
   uint32_t* cnt = scratch;
