@@ -7,8 +7,9 @@ nothing from the product library.  The arithmetic lives in ``radsplat_oracle.c``
 this module only marshals numpy arrays through ctypes.
 
 Pinned functions (see tests/test_oracle_*.py): projection, SH basis, per-pixel
-compositing, importance, integer binning stages, filter and nearest centre, and the
-FP64 gradient.  No function here is unpinned.
+compositing, importance, integer binning stages, filter and nearest centre, the FP64
+gradient, and (``optim.py``) the Adam step and the compaction of pruned parameters.
+No function here is unpinned.
 """
 from __future__ import annotations
 
@@ -165,11 +166,12 @@ def tile_ranges(keys, n_tiles: int) -> np.ndarray:
     return ranges
 
 
-PRUNE_BELOW, KEEP_ABOVE = 0, 1
+PRUNE_BELOW, KEEP_ABOVE, PRUNE_KEEP = 0, 1, 2
 
 
 def filter_mask(h, t: float, mode: int):
-    """Sec. 3.3 (mode PRUNE_BELOW: h < t) / Eq. (importance-score-vis) (KEEP_ABOVE: h > t)."""
+    """Sec. 3.3 (mode PRUNE_BELOW: h < t; PRUNE_KEEP: h >= t, the survivors) /
+    Eq. (importance-score-vis) (KEEP_ABOVE: h > t)."""
     h = _c(h, np.float32)
     mask = np.zeros(h.shape[0], dtype=np.uint8)
     idx = np.zeros(h.shape[0], dtype=np.uint32)

@@ -505,7 +505,9 @@ void or_tile_ranges(int64_t K, const uint64_t* keys, int64_t n_tiles, uint32_t* 
 int64_t or_filter(int64_t n, const float* h, float t, int mode, uint8_t* mask, uint32_t* idx) {
   int64_t cnt = 0;
   for (int64_t i = 0; i < n; ++i) {
-    int on = mode == 0 ? (h[i] < t) : (h[i] > t);
+    /* mode 0: the pruning mask 1(h < t) (Sec. 3.3); 1: the visibility indicator 1(h > t)
+     * (Eq. importance-score-vis); 2: the points pruning keeps, 1(h >= t) = 1 - mode 0 */
+    int on = mode == 0 ? (h[i] < t) : mode == 1 ? (h[i] > t) : (h[i] >= t);
     mask[i] = (uint8_t)on;
     if (on) idx[cnt++] = (uint32_t)i;
   }
