@@ -288,6 +288,7 @@ def run_ours(args):
 
     # roofline of the dominant kernel
     hbm, peak_kind, pk = peaks()
+    optim = optimizer_bench(api, N, torch, g, gbuf, h, hbm, reps=10)
     work = kernel_work(vbs, sres, pairs, n_super)
     roof = roofline(kernel_ms, work, hbm, peak_kind, B)
     per_kernel = {k: kernel_frac(k, kernel_ms[k], work, hbm) for k in kernel_ms if k in work}
@@ -320,7 +321,7 @@ def run_ours(args):
             "stage_ms_per_step": {k: round(v, 5) for k, v in stage_ms.items()},
             "kernel_ms_per_step": {k: round(v["ms_per_step"], 5) for k, v in
                                    sorted(kernel_ms.items(), key=lambda kv: -kv[1]["ms_per_step"])},
-            "e2e": e2e, "roofline": roof, "roofline_per_kernel": per_kernel, "cpu_baseline": cpu,
+            "e2e": e2e, "roofline": roof, "roofline_per_kernel": per_kernel, "optimizer": optim, "cpu_baseline": cpu,
             "clocks": clk.summary(),
             "gpu_launches": launches,
         }
@@ -387,6 +388,50 @@ def stage_times(api, N, torch, g, chunks, cfg, st, proj, h, gbuf, loss, ws_sort,
         del r, nonempty, zero, sw, sh
     torch.cuda.synchronize()
     return acc, kernels, {"pairs": pairs, "super_instances": n_super}
+
+
+def optimizer_bench(api, N, torch, g, gbuf, h, hbm, reps):
+    """The optimisation step around the path on the 1M-Gaussian parameters: one Adam step over
+    all 59 floats per Gaussian (28 B moved per float: p, g, m, v read, p, m, v written), and
+    the pruning compaction with the step's importance at its median as threshold (about half
+    the points survive; at the paper's t_prune = 0.01 this synthetic scene keeps ~0.2 %, too
+    few to measure bandwidth) -- the survivors' columns of the parameters and both moments:
+    2 x 4 B per float moved, plus 4 B of index per survivor."""
+    m = [torch.zeros_like(t) for t in g.tensors()]
+    v = [torch.zeros_like(t) for t in g.tensors()]
+    groups = [(p, gr, mm, vv, 1e-3) for p, gr, mm, vv in zip(g.tensors(), gbuf.views, m, v)]
+    n_float = sum(t.numel() for t in g.tensors())
+    api.adam_step(groups, 1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for k in range(reps):
+        api.adam_step(groups, 2 + k)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_adam = e0.elapsed_time(e1) / reps
+    gbs = 28.0 * n_float / (ms_adam / 1e3) / 1e9
+    t_med = float(h.view(torch.float32).median().item())
+    _, idx, cnt = api.filter(h, t_med, N.RS_PRUNE_KEEP, mask=False)
+    kept = int(cnt.item())
+    src = list(g.tensors()) + m + v
+    dst = [torch.empty(t.shape[:-1] + (max(kept, 1),), device=t.device) for t in src]
+    pairs = list(zip(src, dst))
+    api.gather_columns(pairs, idx, cnt, max(kept, 1))
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        api.gather_columns(pairs, idx, cnt, max(kept, 1))
+    e1.record()
+    torch.cuda.synchronize()
+    ms_g = e0.elapsed_time(e1) / reps
+    moved = kept * (3 * (n_float // g.n) * 8 + 4)
+    ggbs = moved / (ms_g / 1e3) / 1e9
+    del m, v, dst, pairs
+    return {"adam": {"floats": int(n_float), "ms": round(ms_adam, 4), "achieved_gbs": round(gbs, 1),
+                     "frac": round(gbs / hbm, 4)},
+            "prune_gather": {"t": t_med, "kept": kept, "of": int(g.n), "arrays": 15, "ms": round(ms_g, 4),
+                             "achieved_gbs": round(ggbs, 1), "frac": round(ggbs / hbm, 4)}}
 
 
 def plain_loop(api, N, torch, g, vb1, cfg, target, cams, reps, dev):

@@ -167,7 +167,9 @@ typedef struct rs_gaussian_grads {
 
 typedef enum rs_filter_mode {
   RS_PRUNE_BELOW = 0,    /* mask = h < t: points the pruning step removes (Sec. 3.3) */
-  RS_KEEP_ABOVE = 1      /* mask = h > t: points active for a cluster (Eq. importance-score-vis) */
+  RS_KEEP_ABOVE = 1,     /* mask = h > t: points active for a cluster (Eq. importance-score-vis) */
+  RS_PRUNE_KEEP = 2      /* mask = h >= t: the points pruning keeps (1 - RS_PRUNE_BELOW), whose
+                            ascending list drives rs_gather_columns (Sec. 3.3) */
 } rs_filter_mode;
 
 typedef enum rs_stage {
@@ -203,7 +205,8 @@ size_t rs_workspace_size(rs_stage stage, const rs_view_batch* batch, int64_t cap
 
 /* Sizes of the ABI structs, for bindings that mirror them: writes up to n entries in the
  * order rs_gaussians, rs_camera, rs_view, rs_view_batch, rs_config, rs_projected, rs_bins,
- * rs_gaussian_grads, rs_device_status, rs_tune_result; returns how many it wrote. */
+ * rs_gaussian_grads, rs_device_status, rs_tune_result, rs_adam_group, rs_gather_desc;
+ * returns how many it wrote. */
 int32_t rs_struct_sizes(int64_t* out, int32_t n);
 
 /* ---- hot path ---------------------------------------------------------------------- */
@@ -320,6 +323,49 @@ rs_status rs_render_backward(const rs_gaussians* g, const rs_view_batch* batch,
  * Errors: RS_ERR_INVALID_ARG, RS_ERR_CUDA. */
 rs_status rs_l1_loss(const float* image, const float* target, int64_t n, float* dL_dimage,
                      double* loss, void* stream);
+
+/* ---- optimisation step (Sec. 3.2 optimiser, Sec. 3.3 pruning) ----------------------- */
+
+/* One parameter array of an Adam step (all device pointers, FP32, n elements). */
+typedef struct rs_adam_group {
+  float* param;          /* updated in place */
+  const float* grad;
+  float* m;              /* first moment, updated in place (zero before step 1) */
+  float* v;              /* second moment, updated in place (zero before step 1) */
+  int64_t n;
+  float lr;              /* learning rate of this array */
+  int32_t reserved;
+} rs_adam_group;
+
+/* rs_adam_step -- one step of Adam (Kingma & Ba, Algorithm 1), the optimiser 3D Gaussian
+ * Splatting optimises phi with (Sec. 3.2), on up to 8 arrays in one launch:
+ *   m <- b1 m + (1 - b1) g,  v <- b2 v + (1 - b2) g^2,
+ *   p <- p - lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps),
+ * in FP32 with correctly rounded division and square root.  groups: HOST array of
+ * n_groups (1..8) descriptors; step >= 1 counts the steps taken including this one.
+ * Arrays of a group must not overlap.  Errors: RS_ERR_INVALID_ARG (counts, step, betas in
+ * [0, 1), eps >= 0, null pointers with n > 0), RS_ERR_CUDA. */
+rs_status rs_adam_step(const rs_adam_group* groups, int32_t n_groups, float beta1, float beta2,
+                       float eps, int32_t step, void* stream);
+
+/* One structure-of-arrays array to compact: rows x src_stride source, rows x dst_stride
+ * destination (device, FP32, non-overlapping). */
+typedef struct rs_gather_desc {
+  const float* src;
+  float* dst;
+  int64_t rows;
+  int64_t src_stride;    /* columns of src (the point count before pruning) */
+  int64_t dst_stride;    /* columns of dst, >= max_count */
+} rs_gather_desc;
+
+/* rs_gather_columns -- removes pruned points from every parameter array (Sec. 3.3, "we
+ * remove all Gaussians ... that have a mask value of one"): dst[r][k] = src[r][idx[k]] for
+ * k < min(*count, max_count) and every row r of each of the n_desc (1..16) arrays.  idx and
+ * count (device) are rs_filter's outputs for RS_PRUNE_KEEP: the survivors in ascending
+ * order, so the points keep their relative order.  descs: HOST array.
+ * Errors: RS_ERR_INVALID_ARG, RS_ERR_CUDA. */
+rs_status rs_gather_columns(const rs_gather_desc* descs, int32_t n_desc, const uint32_t* idx,
+                            const uint32_t* count, int64_t max_count, void* stream);
 
 /* ---- batched execution: autotuner --------------------------------------------------- */
 

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libradsplat.so")
 
 RS_OK, RS_ERR_INVALID_ARG, RS_ERR_WORKSPACE, RS_ERR_UNSUPPORTED, RS_ERR_CUDA, RS_ERR_CAPACITY, RS_ERR_TIMEOUT = range(7)
-RS_PRUNE_BELOW, RS_KEEP_ABOVE = 0, 1
+RS_PRUNE_BELOW, RS_KEEP_ABOVE, RS_PRUNE_KEEP = 0, 1, 2
 RS_FILTER_NOALLOC_MAX_N = 1 << 26
 RS_STAGE_PROJECT, RS_STAGE_BIN_SORT, RS_STAGE_RENDER, RS_STAGE_BACKWARD, RS_STAGE_FILTER = range(5)
 
@@ -72,8 +72,18 @@ class RsTuneResult(ctypes.Structure):
 
 RS_TUNE_BACKWARD, RS_TUNE_FORCE = 1, 2
 
+
+class RsAdamGroup(ctypes.Structure):
+    _fields_ = [("param", c_void_p), ("grad", c_void_p), ("m", c_void_p), ("v", c_void_p), ("n", c_int64),
+                ("lr", c_float), ("reserved", c_int32)]
+
+
+class RsGatherDesc(ctypes.Structure):
+    _fields_ = [("src", c_void_p), ("dst", c_void_p), ("rows", c_int64), ("src_stride", c_int64),
+                ("dst_stride", c_int64)]
+
 STRUCTS = [RsGaussians, RsCamera, RsView, RsViewBatch, RsConfig, RsProjected, RsBins, RsGaussianGrads, RsDeviceStatus,
-           RsTuneResult]
+           RsTuneResult, RsAdamGroup, RsGatherDesc]
 
 # every function include/radsplat.h declares, with its ctypes signature
 P = c_void_p
@@ -94,6 +104,8 @@ SIGNATURES = {
     "rs_render_backward": (ctypes.c_int, [P, P, P, P, P, P, P, P, P, P, c_size_t, P]),
     "rs_l1_loss": (ctypes.c_int, [P, P, c_int64, P, P, P]),
     "rs_autotune": (ctypes.c_int, [P, P, c_int32, P, P, P, c_int32, P, P, P]),
+    "rs_adam_step": (ctypes.c_int, [P, c_int32, c_float, c_float, c_float, c_int32, P]),
+    "rs_gather_columns": (ctypes.c_int, [P, c_int32, P, P, c_int64, P]),
     "rs_autotune_candidates": (c_int32, [c_int32]),
     "rs_autotune_clear": (None, []),
     "rs_profile_enable": (ctypes.c_int, [c_int32]),

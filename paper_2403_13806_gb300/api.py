@@ -17,7 +17,8 @@ from . import _native as N
 
 __all__ = ["Gaussians", "ViewBatch", "Projected", "Bins", "DeviceStatus", "Workspace", "config", "project",
            "bin_sort", "render", "importance", "filter", "nearest", "render_backward", "Rasterizer",
-           "RadSplatFunction", "split_images", "importance_as_float", "autotune", "TILE_SHAPES", "blend_threads"]
+           "RadSplatFunction", "split_images", "importance_as_float", "autotune", "TILE_SHAPES", "blend_threads", "adam_step",
+           "gather_columns"]
 
 TILE_SHAPES = ((16, 16), (32, 8), (8, 8))
 
@@ -334,6 +335,30 @@ def autotune(g: Gaussians, cams: Sequence[dict], subsets: Optional[Sequence] = N
     return {"tile": (res.tile_w, res.tile_h), "smem_batch": res.smem_batch, "views_per_launch": res.views_per_launch,
             "cached": bool(res.cached), "ms_per_view": float(res.ms_per_view), "n_candidates": res.n_candidates,
             "stage1": stage1, "stage2": stage2}
+
+
+def adam_step(groups: Sequence[tuple], step: int, betas=(0.9, 0.999), eps: float = 1e-15, stream=None):
+    """rs_adam_step: groups of (param, grad, m, v, lr) float32 tensors updated in place."""
+    arr = (N.RsAdamGroup * len(groups))()
+    for i, (p, g, m, v, lr) in enumerate(groups):
+        for t in (p, g, m, v):
+            if t.dtype != torch.float32 or not t.is_contiguous() or t.numel() != p.numel():
+                raise ValueError("Adam arrays must be contiguous float32 tensors of one size")
+        arr[i] = N.RsAdamGroup(p.data_ptr(), g.data_ptr(), m.data_ptr(), v.data_ptr(), p.numel(), float(lr), 0)
+    N.call("rs_adam_step", arr, len(groups), float(betas[0]), float(betas[1]), float(eps), int(step), _stream(stream))
+
+
+def gather_columns(pairs: Sequence[tuple], idx: torch.Tensor, count: torch.Tensor, max_count: int, stream=None):
+    """rs_gather_columns: for each (src [rows, n] or [n], dst [rows, >= max_count] or [>= max_count])
+    float32 pair, dst[:, k] = src[:, idx[k]] for k < count (device)."""
+    arr = (N.RsGatherDesc * len(pairs))()
+    for i, (src, dst) in enumerate(pairs):
+        if src.dtype != torch.float32 or dst.dtype != torch.float32 or not src.is_contiguous() \
+                or not dst.is_contiguous():
+            raise ValueError("gather arrays must be contiguous float32 tensors")
+        rows = src.shape[0] if src.dim() == 2 else 1
+        arr[i] = N.RsGatherDesc(src.data_ptr(), dst.data_ptr(), rows, src.shape[-1], dst.shape[-1])
+    N.call("rs_gather_columns", arr, len(pairs), _ptr(idx), _ptr(count), int(max_count), _stream(stream))
 
 
 def split_images(flat: torch.Tensor, vb: ViewBatch) -> List[torch.Tensor]:

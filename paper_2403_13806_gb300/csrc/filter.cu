@@ -18,7 +18,9 @@ constexpr int kFiltThreads = 256;
 constexpr int kFiltItems = 16;
 constexpr int kFiltTile = kFiltThreads * kFiltItems;
 
-__device__ __forceinline__ bool filter_pred(float h, float t, int mode) { return mode == 0 ? (h < t) : (h > t); }
+__device__ __forceinline__ bool filter_pred(float h, float t, int mode) {
+  return mode == 0 ? (h < t) : mode == 1 ? (h > t) : !(h < t);
+}
 
 // Per block: mask bytes and the number of selected elements in its tile (warp-striped).
 __global__ void __launch_bounds__(kFiltThreads) k_filter_count(const float* __restrict__ h, int64_t n, float t,
@@ -168,7 +170,7 @@ using namespace rs;
 extern "C" rs_status rs_filter(const float* h, int64_t n, float t, rs_filter_mode mode, uint8_t* mask,
                                uint32_t* idx, uint32_t* count, void* ws, size_t ws_bytes, void* stream) {
   if ((!h && n > 0) || !count || n < 0 || n >= ((int64_t)1 << 32)) return RS_ERR_INVALID_ARG;
-  if (mode != RS_PRUNE_BELOW && mode != RS_KEEP_ABOVE) return RS_ERR_INVALID_ARG;
+  if (mode != RS_PRUNE_BELOW && mode != RS_KEEP_ABOVE && mode != RS_PRUNE_KEEP) return RS_ERR_INVALID_ARG;
   if (!ws || ws_bytes < filter_ws_bytes(n)) return RS_ERR_WORKSPACE;
   return filter_launch(h, n, t, (int)mode, mask, idx, count, static_cast<uint32_t*>(ws),
                        reinterpret_cast<cudaStream_t>(stream));
@@ -218,7 +220,7 @@ extern "C" rs_status rs_filter_noalloc(const float* h, int64_t n, float t, rs_fi
                                        uint32_t* idx, uint32_t* count, void* stream) {
   if ((!h && n > 0) || !count || n < 0) return RS_ERR_INVALID_ARG;
   if (n > RS_FILTER_NOALLOC_MAX_N) return RS_ERR_INVALID_ARG;
-  if (mode != RS_PRUNE_BELOW && mode != RS_KEEP_ABOVE) return RS_ERR_INVALID_ARG;
+  if (mode != RS_PRUNE_BELOW && mode != RS_KEEP_ABOVE && mode != RS_PRUNE_KEEP) return RS_ERR_INVALID_ARG;
   uint32_t* scratch = nullptr;
   const rs_status st = noalloc_scratch(&scratch);
   if (st != RS_OK) return st;

@@ -1,0 +1,161 @@
+// The optimisation step around the hot path (Sec. 3.2, Sec. 3.3):
+//
+// rs_adam_step -- one Adam step (Kingma & Ba, Algorithm 1) over up to eight parameter
+//   arrays with their own learning rates, in one launch: m <- b1 m + (1 - b1) g,
+//   v <- b2 v + (1 - b2) g^2, p <- p - lr (m / bc1) / (sqrt(v / bc2) + eps) with
+//   bc = 1 - b^t.  Every element is read once (p, g, m, v) and written once (p, m, v):
+//   28 bytes, HBM-bound.  Threads take four consecutive elements (16-byte loads when all
+//   four arrays of the group are 16-byte aligned) over the concatenation of the groups.
+// rs_gather_columns -- the compaction after pruning: for every structure-of-arrays
+//   parameter (and optimiser moment) dst[r][k] = src[r][idx[k]] for k < count, count and
+//   idx being the device outputs of rs_filter (the survivors, ascending).  One thread per
+//   surviving column k walks every row of every array, so idx is read once; the stores of
+//   a warp are contiguous and its loads follow the ascending indices.
+#include <math.h>
+
+#include "profile.cuh"
+#include "radsplat.h"
+#include "rs_common.cuh"
+
+namespace rs {
+
+constexpr int kMaxAdamGroups = 8;
+constexpr int kMaxGather = 16;
+
+struct AdamArgs {
+  float* p[kMaxAdamGroups];
+  const float* g[kMaxAdamGroups];
+  float* m[kMaxAdamGroups];
+  float* v[kMaxAdamGroups];
+  int64_t n[kMaxAdamGroups];
+  int64_t unit0[kMaxAdamGroups + 1];   // first 4-element unit of each group
+  float lr[kMaxAdamGroups];
+  int32_t vec[kMaxAdamGroups];         // 1: 16-byte loads and stores
+  int32_t n_groups;
+  float b1, b2, eps, bc1, bc2;
+};
+
+__device__ __forceinline__ void adam_one(float& p, float g, float& m, float& v, float lr, const AdamArgs& a) {
+  m = __fmaf_rn(a.b1, m, __fmul_rn(1.f - a.b1, g));
+  v = __fmaf_rn(a.b2, v, __fmul_rn(__fmul_rn(1.f - a.b2, g), g));
+  const float mhat = __fdiv_rn(m, a.bc1);
+  const float vhat = __fdiv_rn(v, a.bc2);
+  p = __fsub_rn(p, __fdiv_rn(__fmul_rn(lr, mhat), __fadd_rn(__fsqrt_rn(vhat), a.eps)));
+}
+
+__global__ void __launch_bounds__(256) k_adam(AdamArgs a) {
+  const int64_t total = a.unit0[a.n_groups];
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < total; u += (int64_t)gridDim.x * blockDim.x) {
+    int gi = 0;
+    while (gi + 1 < a.n_groups && u >= a.unit0[gi + 1]) ++gi;   // at most 8 groups
+    const int64_t e = 4 * (u - a.unit0[gi]);
+    const int64_t n = a.n[gi];
+    const float lr = a.lr[gi];
+    if (a.vec[gi] && e + 4 <= n) {
+      float4 p = *reinterpret_cast<const float4*>(a.p[gi] + e);
+      const float4 g = __ldcs(reinterpret_cast<const float4*>(a.g[gi] + e));
+      float4 m = *reinterpret_cast<const float4*>(a.m[gi] + e);
+      float4 v = *reinterpret_cast<const float4*>(a.v[gi] + e);
+      adam_one(p.x, g.x, m.x, v.x, lr, a);
+      adam_one(p.y, g.y, m.y, v.y, lr, a);
+      adam_one(p.z, g.z, m.z, v.z, lr, a);
+      adam_one(p.w, g.w, m.w, v.w, lr, a);
+      *reinterpret_cast<float4*>(a.p[gi] + e) = p;
+      *reinterpret_cast<float4*>(a.m[gi] + e) = m;
+      *reinterpret_cast<float4*>(a.v[gi] + e) = v;
+    } else {
+      for (int64_t k = e; k < e + 4 && k < n; ++k) {
+        float p = a.p[gi][k], m = a.m[gi][k], v = a.v[gi][k];
+        adam_one(p, a.g[gi][k], m, v, lr, a);
+        a.p[gi][k] = p;
+        a.m[gi][k] = m;
+        a.v[gi][k] = v;
+      }
+    }
+  }
+}
+
+struct GatherArgs {
+  const float* src[kMaxGather];
+  float* dst[kMaxGather];
+  int64_t rows[kMaxGather];
+  int64_t src_stride[kMaxGather];
+  int64_t dst_stride[kMaxGather];
+  int32_t n_desc;
+};
+
+__global__ void __launch_bounds__(256) k_gather_columns(GatherArgs a, const uint32_t* __restrict__ idx,
+                                                        const uint32_t* __restrict__ count, int64_t max_count) {
+  const int64_t cnt = min((int64_t)*count, max_count);
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx[k];
+    for (int d = 0; d < a.n_desc; ++d) {
+      const float* s = a.src[d] + i;
+      float* o = a.dst[d] + k;
+      for (int64_t r = 0; r < a.rows[d]; ++r) o[r * a.dst_stride[d]] = __ldg(s + r * a.src_stride[d]);
+    }
+  }
+}
+
+}  // namespace rs
+
+using namespace rs;
+
+extern "C" rs_status rs_adam_step(const rs_adam_group* groups, int32_t n_groups, float beta1, float beta2, float eps,
+                                  int32_t step, void* stream) {
+  if (!groups || n_groups < 1 || n_groups > kMaxAdamGroups || step < 1) return RS_ERR_INVALID_ARG;
+  if (!(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps >= 0.f)) return RS_ERR_INVALID_ARG;
+  AdamArgs a{};
+  a.n_groups = n_groups;
+  a.b1 = beta1;
+  a.b2 = beta2;
+  a.eps = eps;
+  a.bc1 = (float)(1.0 - pow((double)beta1, (double)step));
+  a.bc2 = (float)(1.0 - pow((double)beta2, (double)step));
+  int64_t units = 0;
+  for (int32_t i = 0; i < n_groups; ++i) {
+    const rs_adam_group& g = groups[i];
+    if (g.n < 0 || (g.n > 0 && (!g.param || !g.grad || !g.m || !g.v))) return RS_ERR_INVALID_ARG;
+    a.p[i] = g.param;
+    a.g[i] = g.grad;
+    a.m[i] = g.m;
+    a.v[i] = g.v;
+    a.n[i] = g.n;
+    a.lr[i] = g.lr;
+    a.vec[i] = aligned<float4>(g.param, 16) && aligned<float4>(g.grad, 16) && aligned<float4>(g.m, 16) &&
+               aligned<float4>(g.v, 16);
+    a.unit0[i] = units;
+    units += (g.n + 3) / 4;
+  }
+  a.unit0[n_groups] = units;
+  if (units == 0) return RS_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t blocks = (units + 255) / 256;
+  const unsigned grid = (unsigned)(blocks < 16 * kNumSMs ? blocks : 16 * kNumSMs);
+  prof::Scope ps("k_adam", s);
+  k_adam<<<grid, 256, 0, s>>>(a);
+  return launch_status();
+}
+
+extern "C" rs_status rs_gather_columns(const rs_gather_desc* descs, int32_t n_desc, const uint32_t* idx,
+                                       const uint32_t* count, int64_t max_count, void* stream) {
+  if (!descs || n_desc < 1 || n_desc > kMaxGather || !idx || !count || max_count < 0) return RS_ERR_INVALID_ARG;
+  GatherArgs a{};
+  a.n_desc = n_desc;
+  for (int32_t d = 0; d < n_desc; ++d) {
+    const rs_gather_desc& g = descs[d];
+    if (!g.src || !g.dst || g.rows < 0 || g.dst_stride < max_count || g.src_stride < 0) return RS_ERR_INVALID_ARG;
+    a.src[d] = g.src;
+    a.dst[d] = g.dst;
+    a.rows[d] = g.rows;
+    a.src_stride[d] = g.src_stride;
+    a.dst_stride[d] = g.dst_stride;
+  }
+  if (max_count == 0) return RS_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t blocks = (max_count + 255) / 256;
+  const unsigned grid = (unsigned)(blocks < 8 * kNumSMs ? blocks : 8 * kNumSMs);
+  prof::Scope ps("k_gather_columns", s);
+  k_gather_columns<<<grid, 256, 0, s>>>(a, idx, count, max_count);
+  return launch_status();
+}
