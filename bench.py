@@ -44,10 +44,23 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--loss", default="paper", choices=["paper", "l1"],
+                    help="paper: (1 - 0.2) MSE + 0.2 (1 - SSIM) of Sec. 3.2; l1: mean absolute error")
     ap.add_argument("--tile", default="auto", help="tile shape WxH with all views in one launch, or 'auto' "
                                                    "(autotuner: tile shape, staging batch, views per launch)")
     ap.add_argument("--sample-pixels", type=int, default=0, help="reference arm: pixels per step (0: auto)")
     return ap.parse_args()
+
+
+def make_loss(api, kind, width, height, dev):
+    """The step's photometric loss: 'paper' = (1 - 0.2) MSE + 0.2 (1 - SSIM) (Sec. 3.2), or L1."""
+    ws = api.Workspace(dev)
+
+    def loss_fn(img, target, dL=None, loss=None):
+        if kind == "paper":
+            return api.ssim_loss(img, target, width, height, api.PAPER_LAMBDA, dL_dimage=dL, loss=loss, ws=ws)
+        return api.l1_loss(img, target, dL, loss)
+    return loss_fn
 
 
 def dist_env():
@@ -57,9 +70,10 @@ def dist_env():
     return ws, rank, local
 
 
-def workload_config(views, world, tile=(16, 16), per_launch=None):
+def workload_config(views, world, tile=(16, 16), per_launch=None, loss="paper"):
     return {"workload": "360-capture synthetic scene, 1M Gaussians SH3, 1280x832 ring views, "
-                        "project+bin/sort+blend+importance+L1+backward+prune",
+                        "project+bin/sort+blend+importance+loss+backward+prune",
+            "loss": "0.8 MSE + 0.2 (1 - SSIM)" if loss == "paper" else "L1",
             "gaussians": N_GAUSSIANS, "width": WIDTH, "height": HEIGHT, "views_per_step": views * world,
             "views_per_rank": views, "views_per_launch": per_launch or views, "sh_degree": 3,
             "tile": f"{tile[0]}x{tile[1]}", "seed": 2,
@@ -144,6 +158,7 @@ def run_ours(args):
     g = api.Gaussians.from_scene(scene, device=dev)
     vb1 = [api.ViewBatch([c], scene.n, device=dev) for c in cams]
     cfg = api.config()
+    loss_fn = make_loss(api, args.loss, WIDTH, HEIGHT, dev)
 
     # tile shape and views per launch from the autotuner (setup, untimed; cached per workload)
     if args.tile == "auto":
@@ -199,7 +214,7 @@ def run_ours(args):
             api.project(g, vb, cfg, st, out=proj)
             api.bin_sort(proj, vb, bins, ws_sort, st)
             api.render(proj, bins, vb, cfg, image=img, T_final=T, last=L, importance=h)
-            api.l1_loss(img, target, dL, loss)
+            loss_fn(img, target, dL, loss)
             api.render_backward(g, vb, proj, bins, T, L, dL, grads, ws_bwd, cfg)
 
     def prune():
@@ -273,7 +288,8 @@ def run_ours(args):
     # per-stage times of the same batched step (plain launches, events on this stream), and
     # the work counts of each launch (pairs walked, super-tile instances)
     stage_ms, kernel_ms, work_counts = stage_times(api, N, torch, g, chunks, cfg, st, proj, h, gbuf, loss, ws_sort,
-                                                   ws_bwd, ws_f, mask, idx, reps=max(3, min(args.steps, 10)))
+                                                   ws_bwd, ws_f, mask, idx, reps=max(3, min(args.steps, 10)),
+                                                   loss_fn=loss_fn)
     pairs, n_super = work_counts["pairs"], work_counts["super_instances"]
 
     # plain: the same views one at a time, no graph
@@ -281,10 +297,11 @@ def run_ours(args):
     fps = None
     if not args.no_plain:
         plain, fps = plain_loop(api, N, torch, g, vb1, cfg, torch.cat(targets), cams, reps=max(3, min(args.steps, 10)),
-                                dev=dev)
+                                dev=dev, loss_fn=loss_fn)
 
     # end to end through the public API: host parameters and targets in pinned memory
-    e2e = e2e_run(api, N, torch, scene, vbs, cfg, targets, cap, reps=max(3, min(args.steps, 5)), dev=dev, world=world)
+    e2e = e2e_run(api, N, torch, scene, vbs, cfg, targets, cap, reps=max(3, min(args.steps, 5)), dev=dev, world=world,
+                  loss_fn=loss_fn)
 
     # roofline of the dominant kernel
     hbm, peak_kind, pk = peaks()
@@ -301,7 +318,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded 360-capture scene; target = render of a perturbed copy)",
-            "config": dict(workload_config(V, world, tile, B),
+            "config": dict(workload_config(V, world, tile, B, args.loss),
                            parallelism=(f"views sharded over {world} GPUs; all-reduce MAX of importance and SUM "
                                         f"of gradients per step" if world > 1 else "1 GPU, no collective")),
             "batched_ms_per_view": round(value, 5),
@@ -331,13 +348,14 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def stage_times(api, N, torch, g, chunks, cfg, st, proj, h, gbuf, loss, ws_sort, ws_bwd, ws_f, mask, idx, reps):
+def stage_times(api, N, torch, g, chunks, cfg, st, proj, h, gbuf, loss, ws_sort, ws_bwd, ws_f, mask, idx, reps,
+                loss_fn):
     """Per-stage times (CUDA events around each C-ABI call, summed over the launches of a
     step) and per-kernel times (the library's own launch events, rs_profile_*) of the same
     step with plain launches; then, in an untimed pass, the work counts: pairs walked by the
     backward (sum of `last` over pixels) and super-tile instances (4 x 4 tiles) of every
     launch."""
-    names = ["project", "bin_sort", "render_importance", "l1", "backward", "filter"]
+    names = ["project", "bin_sort", "render_importance", "loss", "backward", "filter"]
     acc = {k: 0.0 for k in names}
     kern = {}
     for r in range(reps + 1):
@@ -352,7 +370,7 @@ def stage_times(api, N, torch, g, chunks, cfg, st, proj, h, gbuf, loss, ws_sort,
             api.project(g, vb, cfg, st, out=proj); ev[1].record()
             api.bin_sort(proj, vb, bins, ws_sort, st); ev[2].record()
             api.render(proj, bins, vb, cfg, image=img, T_final=T, last=L, importance=h); ev[3].record()
-            api.l1_loss(img, target, dL, loss); ev[4].record()
+            loss_fn(img, target, dL, loss); ev[4].record()
             api.render_backward(g, vb, proj, bins, T, L, dL, gbuf.views, ws_bwd, cfg); ev[5].record()
             evs.append(ev)
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -434,7 +452,7 @@ def optimizer_bench(api, N, torch, g, gbuf, h, hbm, reps):
                              "achieved_gbs": round(ggbs, 1), "frac": round(ggbs / hbm, 4)}}
 
 
-def plain_loop(api, N, torch, g, vb1, cfg, target, cams, reps, dev):
+def plain_loop(api, N, torch, g, vb1, cfg, target, cams, reps, dev, loss_fn):
     """The same views one at a time with plain launches (no graph): fwd+bwd ms/view, and
     forward-only FPS of one view (project + bin/sort + blend)."""
     rasts = []
@@ -457,7 +475,7 @@ def plain_loop(api, N, torch, g, vb1, cfg, target, cams, reps, dev):
         proj = api.project(g, vb, r.cfg, st)
         api.bin_sort(proj, vb, bins, r.ws_sort, st)
         img, T, L = api.render(proj, bins, vb, r.cfg, importance=h)
-        l, dl = api.l1_loss(img, tg[i])
+        l, dl = loss_fn(img, tg[i])
         api.render_backward(g, vb, proj, bins, T, L, dl, grads, r.ws_bwd, r.cfg)
         api.filter(h, 0.01, N.RS_PRUNE_BELOW, ws_f)
 
@@ -494,7 +512,7 @@ def plain_loop(api, N, torch, g, vb1, cfg, target, cams, reps, dev):
     return plain, fps
 
 
-def e2e_run(api, N, torch, scene, vbs, cfg, targets, cap, reps, dev, world=1):
+def e2e_run(api, N, torch, scene, vbs, cfg, targets, cap, reps, dev, world=1, loss_fn=None):
     """Same batched step through the public API, parameters and targets copied from pinned
     host memory each step, the loss read back to the host (with the reductions over ranks
     when world > 1)."""
@@ -525,7 +543,7 @@ def e2e_run(api, N, torch, scene, vbs, cfg, targets, cap, reps, dev, world=1):
             api.project(g, vb, cfg, st, out=proj)
             api.bin_sort(proj, vb, bins, ws_sort, st)
             img, T, L = api.render(proj, bins, vb, cfg, importance=h)
-            loss, dl = api.l1_loss(img, tgt_d[i], loss=loss_d[i:i + 1])
+            loss, dl = loss_fn(img, tgt_d[i], loss=loss_d[i:i + 1])
             api.render_backward(g, vb, proj, bins, T, L, dl, gbuf.views, ws_bwd, cfg)
         if world > 1:
             rd.allreduce_importance(h)
@@ -625,6 +643,8 @@ def kernel_work(vbs, sres, pairs, n_super):
         "k_fine_count": Ks * (4 + 8),
         "k_fine_scatter": Ks * (4 + 8) + K * 4,
         "k_l1": P * 3 * 4 * 3,
+        "k_ssim_stats": P * 3 * (8 + 12),
+        "k_ssim_grad": P * 3 * (12 + 8 + 4),
         "k_project_bwd": M * (236 + 36 + 236),
         "k_filter_count": vb.n_gaussians * 4,
         "k_filter_scatter": vb.n_gaussians * (4 + 1) + vb.n_gaussians * 4,

@@ -324,6 +324,22 @@ rs_status rs_render_backward(const rs_gaussians* g, const rs_view_batch* batch,
 rs_status rs_l1_loss(const float* image, const float* target, int64_t n, float* dL_dimage,
                      double* loss, void* stream);
 
+/* rs_ssim_loss -- the training loss of Sec. 3.2,
+ *   L = (1 - lambda) mean((x - y)^2) + lambda (1 - mean SSIM(x, y)),  lambda = 0.2 in the paper,
+ * reading its SSIM term as the structural dissimilarity 1 - SSIM.  SSIM (Wang et al. 2004)
+ * per plane and pixel with a normalised 11 x 11 Gaussian window (sigma 1.5) over the
+ * zero-padded planes, C1 = 0.01^2, C2 = 0.03^2; means over all n = n_planes*H*W values.
+ * image (x, rendered), target (y): device float [n_planes][height][width] (the planar
+ * channels of one or more same-sized views).  dL_dimage: device float, same layout,
+ * overwritten with dL/dx.  loss: device double [1], overwritten (may be NULL).
+ * ws: rs_ssim_workspace_size(width, height, n_planes) bytes of device memory, 256-byte
+ * aligned.  Errors: RS_ERR_INVALID_ARG (sizes, lambda outside [0, 1], height above
+ * 1048560, n_planes above 65535), RS_ERR_WORKSPACE, RS_ERR_CUDA. */
+rs_status rs_ssim_loss(const float* image, const float* target, int32_t width, int32_t height,
+                       int32_t n_planes, float lambda, float* dL_dimage, double* loss, void* ws,
+                       size_t ws_bytes, void* stream);
+size_t rs_ssim_workspace_size(int32_t width, int32_t height, int32_t n_planes);
+
 /* ---- optimisation step (Sec. 3.2 optimiser, Sec. 3.3 pruning) ----------------------- */
 
 /* One parameter array of an Adam step (all device pointers, FP32, n elements). */

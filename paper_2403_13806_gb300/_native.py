@@ -105,6 +105,8 @@ SIGNATURES = {
     "rs_l1_loss": (ctypes.c_int, [P, P, c_int64, P, P, P]),
     "rs_autotune": (ctypes.c_int, [P, P, c_int32, P, P, P, c_int32, P, P, P]),
     "rs_adam_step": (ctypes.c_int, [P, c_int32, c_float, c_float, c_float, c_int32, P]),
+    "rs_ssim_loss": (ctypes.c_int, [P, P, c_int32, c_int32, c_int32, c_float, P, P, P, c_size_t, P]),
+    "rs_ssim_workspace_size": (c_size_t, [c_int32, c_int32, c_int32]),
     "rs_gather_columns": (ctypes.c_int, [P, c_int32, P, P, c_int64, P]),
     "rs_autotune_candidates": (c_int32, [c_int32]),
     "rs_autotune_clear": (None, []),

@@ -18,7 +18,9 @@ from . import _native as N
 __all__ = ["Gaussians", "ViewBatch", "Projected", "Bins", "DeviceStatus", "Workspace", "config", "project",
            "bin_sort", "render", "importance", "filter", "nearest", "render_backward", "Rasterizer",
            "RadSplatFunction", "split_images", "importance_as_float", "autotune", "TILE_SHAPES", "blend_threads", "adam_step",
-           "gather_columns"]
+           "gather_columns", "ssim_loss", "PAPER_LAMBDA"]
+
+PAPER_LAMBDA = 0.2   # weight of the SSIM term in the loss of Sec. 3.2
 
 TILE_SHAPES = ((16, 16), (32, 8), (8, 8))
 
@@ -335,6 +337,24 @@ def autotune(g: Gaussians, cams: Sequence[dict], subsets: Optional[Sequence] = N
     return {"tile": (res.tile_w, res.tile_h), "smem_batch": res.smem_batch, "views_per_launch": res.views_per_launch,
             "cached": bool(res.cached), "ms_per_view": float(res.ms_per_view), "n_candidates": res.n_candidates,
             "stage1": stage1, "stage2": stage2}
+
+
+def ssim_loss(image: torch.Tensor, target: torch.Tensor, width: int, height: int, lam: float = 0.2,
+              dL_dimage: Optional[torch.Tensor] = None, loss: Optional[torch.Tensor] = None,
+              ws: Optional[Workspace] = None, stream=None):
+    """rs_ssim_loss over planes [n_planes][height][width] (flat or shaped): the loss of
+    Sec. 3.2, (1 - lam) MSE + lam (1 - SSIM), float64 [1], and dL/dimage."""
+    n = image.numel()
+    if n % (width * height) != 0 or target.numel() != n:
+        raise ValueError("image and target must hold whole planes of width x height")
+    planes = n // (width * height)
+    g = torch.empty_like(image) if dL_dimage is None else dL_dimage
+    l = torch.empty(1, dtype=torch.float64, device=image.device) if loss is None else loss
+    ws = ws or Workspace(image.device)
+    w = ws.get(N.lib().rs_ssim_workspace_size(width, height, planes))
+    N.call("rs_ssim_loss", _ptr(image), _ptr(target), width, height, planes, float(lam), _ptr(g), _ptr(l), _ptr(w),
+           w.numel(), _stream(stream))
+    return l, g
 
 
 def adam_step(groups: Sequence[tuple], step: int, betas=(0.9, 0.999), eps: float = 1e-15, stream=None):

@@ -1,7 +1,8 @@
 """Optimisation of the point parameters on synthetic targets with importance pruning.
 
-Sec. 3.2 optimises phi = {(p, k, s, o, q)} with a photometric loss against target renders
-(here renders of a perturbed scene stand in for the radiance-field teacher's renders), the
+Sec. 3.2 optimises phi = {(p, k, s, o, q)} with the loss (1 - lambda) L2 + lambda (1 - SSIM)
+against target renders (here renders of a perturbed scene stand in for the radiance-field
+teacher's renders; an L1 loss is available too), the
 optimiser and learning rates of 3D Gaussian Splatting (Adam, eps 1e-15; SH rest at 1/20 of
 the DC rate), one training view drawn uniformly per step; Sec. 3.3 prunes the points whose
 importance h (Eq. importance-score, max over all training views) is below t_prune, twice
@@ -40,7 +41,7 @@ class Trainer:
     def __init__(self, g: api.Gaussians, cams: Sequence[dict], targets: Sequence[torch.Tensor],
                  prune_steps: Sequence[int] = (), t_prune: float = 0.01, lr: Optional[dict] = None,
                  extent: float = 1.0, betas=(0.9, 0.999), eps: float = 1e-15, seed: int = 0, tile=(16, 16),
-                 cfg=None):
+                 cfg=None, loss: str = "paper", lam: float = api.PAPER_LAMBDA):
         if len(cams) != len(targets):
             raise ValueError("one target per camera")
         self.g = g
@@ -55,6 +56,10 @@ class Trainer:
         self.tile = tuple(tile)
         self.cfg = cfg or api.config()
         self.rast = api.Rasterizer(cfg=self.cfg, device=g.means.device)
+        if loss not in ("paper", "l1"):
+            raise ValueError("loss is 'paper' ((1 - lam) MSE + lam (1 - SSIM)) or 'l1'")
+        self.loss_kind, self.lam = loss, float(lam)
+        self.ws_loss = api.Workspace(g.means.device)
         self.step_no = 0
         self.losses: List[float] = []
         self.prunes: List[PruneRecord] = []
@@ -86,7 +91,12 @@ class Trainer:
         i = int(self.rng.integers(0, len(self.cams)))
         vb = api.ViewBatch([self.cams[i]], self.g.n, tile=self.tile, device=self.g.means.device)
         out = self.rast.forward(self.g, vb)
-        loss, dl = api.l1_loss(out["image"], self.targets[i], loss=self._loss)
+        if self.loss_kind == "paper":
+            cam = self.cams[i]
+            loss, dl = api.ssim_loss(out["image"], self.targets[i], cam["width"], cam["height"], self.lam,
+                                     loss=self._loss, ws=self.ws_loss)
+        else:
+            loss, dl = api.l1_loss(out["image"], self.targets[i], loss=self._loss)
         for t in self.grads:
             t.zero_()
         api.render_backward(self.g, vb, out["proj"], out["bins"], out["T_final"], out["last"], dl, self.grads,

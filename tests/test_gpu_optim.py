@@ -92,7 +92,8 @@ def test_prune_filter_and_gather_bit_exact():
         assert np.array_equal(dst.cpu().numpy(), expect[name])
 
 
-def test_trainer_loss_decreases_and_pruning_keeps_h_at_least_t():
+@pytest.mark.parametrize("loss", ["paper", "l1"])
+def test_trainer_loss_decreases_and_pruning_keeps_h_at_least_t(loss):
     from paper_2403_13806_gb300.train import Trainer
     scene, (cam,) = synth.config0()
     cams = []
@@ -109,7 +110,7 @@ def test_trainer_loss_decreases_and_pruning_keeps_h_at_least_t():
         vb = api.ViewBatch([c], scene.n)
         targets.append(api.Rasterizer().forward(tg, vb)["image"].clone())
     g = api.Gaussians.from_scene(scene)
-    tr = Trainer(g, cams, targets, prune_steps=(), t_prune=0.01, extent=3.0, seed=3)
+    tr = Trainer(g, cams, targets, prune_steps=(), t_prune=0.01, extent=3.0, seed=3, loss=loss)
     for _ in range(50):
         tr.step()
     before = [t.clone() for t in tr.g.tensors()] + [t.clone() for t in tr.m] + [t.clone() for t in tr.v]
