@@ -302,6 +302,17 @@ rs_status rs_filter_noalloc(const float* h, int64_t n, float t, rs_filter_mode m
 rs_status rs_filter_nearest(const float* centres, int32_t k, const float* cam_centres,
                             int32_t n_cams, int32_t* out, void* stream);
 
+/* rs_kmeans -- Sec. 3.4 "Input Camera Clustering": Lloyd's k-means on the n camera
+ * locations (device float [n][3]) with k <= 256 initial centres (device float [k][3], the
+ * caller's choice; overwritten with the result) for `iterations` steps of: assign every
+ * point to its nearest centre (the rule of rs_filter_nearest), then move every centre that
+ * has points to their mean (summed in FP64, rounded to FP32); a centre without points stays.
+ * assign (device int32 [n]) receives the assignment to the final centres.  One CTA runs
+ * every iteration (meant for camera sets, up to some 1e5 points).
+ * Errors: RS_ERR_INVALID_ARG, RS_ERR_CUDA. */
+rs_status rs_kmeans(const float* points, int32_t n, float* centres, int32_t k, int32_t iterations,
+                    int32_t* assign, void* stream);
+
 /* rs_render_backward -- derivative of Eq. (render-gs) for the training loss of Sec. 3.2:
  * given dL/dimage (device, layout of rs_render's image) and the forward's T_final and
  * last, walks each pixel's list back to front from `last` (T_j recovered as

@@ -18,7 +18,7 @@ from . import _native as N
 __all__ = ["Gaussians", "ViewBatch", "Projected", "Bins", "DeviceStatus", "Workspace", "config", "project",
            "bin_sort", "render", "importance", "filter", "nearest", "render_backward", "Rasterizer",
            "RadSplatFunction", "split_images", "importance_as_float", "autotune", "TILE_SHAPES", "blend_threads", "adam_step",
-           "gather_columns", "ssim_loss", "PAPER_LAMBDA"]
+           "gather_columns", "ssim_loss", "PAPER_LAMBDA", "kmeans"]
 
 PAPER_LAMBDA = 0.2   # weight of the SSIM term in the loss of Sec. 3.2
 
@@ -93,7 +93,8 @@ class ViewBatch:
         V = len(cams)
         if subsets is not None and len(subsets) != V:
             raise ValueError("one subset per view")
-        n_items = np.array([len(s) for s in subsets] if subsets is not None else [n_gaussians] * V, dtype=np.int64)
+        n_items = np.array([(s.numel() if isinstance(s, torch.Tensor) else len(s)) for s in subsets]
+                           if subsets is not None else [n_gaussians] * V, dtype=np.int64)
         cam_arr = (N.RsCamera * V)(*[_camera_struct(c) for c in cams])
         host = (N.RsView * V)()
         b = N.RsViewBatch()
@@ -102,7 +103,10 @@ class ViewBatch:
         raw = np.frombuffer(bytes(host), dtype=np.uint8).copy()
         self.views_dev = torch.as_tensor(raw, device=device)
         self.views_host = host
-        if subsets is not None:
+        if subsets is not None and all(isinstance(s, torch.Tensor) for s in subsets):
+            # device index lists (int32 bits of uint32 ids), e.g. rs_filter outputs: no host copy
+            self.subset = torch.cat([s.to(device=device, dtype=torch.int32).reshape(-1) for s in subsets])
+        elif subsets is not None:
             sub = np.concatenate([np.asarray(s, dtype=np.uint32) for s in subsets]).view(np.int32)
             self.subset = torch.as_tensor(sub, device=device)
         else:
@@ -275,6 +279,16 @@ def nearest(centres: torch.Tensor, cam_centres: torch.Tensor, stream=None) -> to
     N.call("rs_filter_nearest", _ptr(centres), centres.shape[0], _ptr(cam_centres), cam_centres.shape[0], _ptr(out),
            _stream(stream))
     return out
+
+
+def kmeans(points: torch.Tensor, init: torch.Tensor, iterations: int = 50, stream=None):
+    """Sec. 3.4 camera clustering (rs_kmeans): returns (centres [k, 3], assignment [n])."""
+    pts = points.to(torch.float32).contiguous()
+    centres = init.to(device=pts.device, dtype=torch.float32).clone().contiguous()
+    assign = torch.empty(pts.shape[0], dtype=torch.int32, device=pts.device)
+    N.call("rs_kmeans", _ptr(pts), pts.shape[0], _ptr(centres), centres.shape[0], int(iterations), _ptr(assign),
+           _stream(stream))
+    return centres, assign
 
 
 def render_backward(g: Gaussians, vb: ViewBatch, proj: Projected, bins: Bins, T_final, last, dL_dimage,
