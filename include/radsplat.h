@@ -302,6 +302,17 @@ rs_status rs_filter_noalloc(const float* h, int64_t n, float t, rs_filter_mode m
 rs_status rs_filter_nearest(const float* centres, int32_t k, const float* cam_centres,
                             int32_t n_cams, int32_t* out, void* stream);
 
+/* rs_nn_distance -- Sec. 3.2 "Radiance Field-based Initialization": the isotropic initial
+ * scale s_i = min over the other points p of |p_i - p|_2, for every point of means (device
+ * float [3][n], the rs_gaussians layout); dist (device float [n]) receives it (0 for a
+ * duplicated point, +inf for a point with a non-finite coordinate).  Exact nearest
+ * neighbour over an implicit octree (points sorted by 30-bit Morton code); FP32 distances.
+ * ws: rs_nn_workspace_size(n) bytes of device memory, 256-byte aligned.  No host
+ * synchronisation.  Errors: RS_ERR_INVALID_ARG (n < 2 or n >= 2^31, null pointers),
+ * RS_ERR_WORKSPACE, RS_ERR_CUDA. */
+rs_status rs_nn_distance(const float* means, int64_t n, float* dist, void* ws, size_t ws_bytes, void* stream);
+size_t rs_nn_workspace_size(int64_t n);
+
 /* rs_kmeans -- Sec. 3.4 "Input Camera Clustering": Lloyd's k-means on the n camera
  * locations (device float [n][3]) with k <= 256 initial centres (device float [k][3], the
  * caller's choice; overwritten with the result) for `iterations` steps of: assign every

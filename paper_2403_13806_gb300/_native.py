@@ -101,6 +101,8 @@ SIGNATURES = {
     "rs_filter": (ctypes.c_int, [P, c_int64, c_float, ctypes.c_int, P, P, P, P, c_size_t, P]),
     "rs_filter_nearest": (ctypes.c_int, [P, c_int32, P, c_int32, P, P]),
     "rs_kmeans": (ctypes.c_int, [P, c_int32, P, c_int32, c_int32, P, P]),
+    "rs_nn_distance": (ctypes.c_int, [P, c_int64, P, P, c_size_t, P]),
+    "rs_nn_workspace_size": (c_size_t, [c_int64]),
     "rs_filter_noalloc": (ctypes.c_int, [P, c_int64, c_float, ctypes.c_int, P, P, P, P]),
     "rs_render_backward": (ctypes.c_int, [P, P, P, P, P, P, P, P, P, P, c_size_t, P]),
     "rs_l1_loss": (ctypes.c_int, [P, P, c_int64, P, P, P]),

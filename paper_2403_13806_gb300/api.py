@@ -18,7 +18,8 @@ from . import _native as N
 __all__ = ["Gaussians", "ViewBatch", "Projected", "Bins", "DeviceStatus", "Workspace", "config", "project",
            "bin_sort", "render", "importance", "filter", "nearest", "render_backward", "Rasterizer",
            "RadSplatFunction", "split_images", "importance_as_float", "autotune", "TILE_SHAPES", "blend_threads", "adam_step",
-           "gather_columns", "ssim_loss", "PAPER_LAMBDA", "kmeans"]
+           "gather_columns", "ssim_loss", "PAPER_LAMBDA", "kmeans", "nn_distance",
+           "init_log_scales"]
 
 PAPER_LAMBDA = 0.2   # weight of the SSIM term in the loss of Sec. 3.2
 
@@ -279,6 +280,23 @@ def nearest(centres: torch.Tensor, cam_centres: torch.Tensor, stream=None) -> to
     N.call("rs_filter_nearest", _ptr(centres), centres.shape[0], _ptr(cam_centres), cam_centres.shape[0], _ptr(out),
            _stream(stream))
     return out
+
+
+def nn_distance(means: torch.Tensor, ws: Optional[Workspace] = None, stream=None) -> torch.Tensor:
+    """rs_nn_distance: distance from each point (means [3, n]) to its nearest other point."""
+    m = means.to(torch.float32).contiguous()
+    n = m.shape[1]
+    d = torch.empty(n, dtype=torch.float32, device=m.device)
+    ws = ws or Workspace(m.device)
+    w = ws.get(N.lib().rs_nn_workspace_size(n))
+    N.call("rs_nn_distance", _ptr(m), n, _ptr(d), _ptr(w), w.numel(), _stream(stream))
+    return d
+
+
+def init_log_scales(means: torch.Tensor, floor: float = 1e-7) -> torch.Tensor:
+    """Sec. 3.2 initial scales: log of the nearest-neighbour distance (floored), on 3 rows."""
+    d = nn_distance(means)
+    return torch.log(torch.clamp(d, min=floor)).expand(3, -1).contiguous()
 
 
 def kmeans(points: torch.Tensor, init: torch.Tensor, iterations: int = 50, stream=None):
