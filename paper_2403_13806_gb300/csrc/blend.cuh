@@ -72,9 +72,14 @@ struct PairAlpha {
   bool in0, in1;  // p2 <= 0 and alpha >= 1/255
 };
 
+// CLAMP: evaluate 2^min(p2, 0) so that ex stays finite for every pair (the backward multiplies
+// it); the forward only uses alpha, where min(0.99, .) already bounds a large 2^p2, and the
+// decision (p2 <= 0 and alpha >= 1/255) is the same either way.
+template <bool CLAMP = true>
 __device__ __forceinline__ PairAlpha pair_alpha(const BlendRec& r, float2 p2) {
   PairAlpha a;
-  a.ex = make_float2(ex2_approx(fminf(p2.x, 0.f)), ex2_approx(fminf(p2.y, 0.f)));
+  a.ex = CLAMP ? make_float2(ex2_approx(fminf(p2.x, 0.f)), ex2_approx(fminf(p2.y, 0.f)))
+               : make_float2(ex2_approx(p2.x), ex2_approx(p2.y));
   a.raw = __fmul2_rn(hi2(r.co), a.ex);
   a.alpha = make_float2(fminf(kAlphaMax, a.raw.x), fminf(kAlphaMax, a.raw.y));
   // alpha >= 1/255 implies p2 >= cut (the cut's 1e-3 margin exceeds the rounding of

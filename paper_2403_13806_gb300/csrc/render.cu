@@ -62,29 +62,30 @@ __global__ void __launch_bounds__(TW* TH / PX) k_render(RenderArgs a) {
   const uint2 rg = a.ranges[tile];
   const uint32_t start = rg.x, end = rg.y;
 
+  // A pixel that is done (outside the image, or stopped by T(1 - alpha) < 1e-4) carries a NaN
+  // row offset: its p2 is NaN, every test on it is false, and it needs no flag of its own.
   float2 nv[NP], T[NP], cr[NP], cg[NP], cb[NP];
   int last[PX];
-  bool done[PX];
-#pragma unroll
-  for (int k = 0; k < PX; ++k) {
-    last[k] = 0;
-    done[k] = !(pu < cam.width && pv0 + k < cam.height);
-  }
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
-    nv[q] = make_float2(-(float)(pv0 + 2 * q), -(float)(pv0 + 2 * q + 1));
+    const bool in0 = pu < cam.width && pv0 + 2 * q < cam.height;
+    const bool in1 = pu < cam.width && pv0 + 2 * q + 1 < cam.height;
+    nv[q] = make_float2(in0 ? -(float)(pv0 + 2 * q) : __int_as_float(0x7fc00000),
+                        in1 ? -(float)(pv0 + 2 * q + 1) : __int_as_float(0x7fc00000));
     T[q] = make_float2(1.f, 1.f);
     cr[q] = cg[q] = cb[q] = make_float2(0.f, 0.f);
+    last[2 * q] = last[2 * q + 1] = 0;
   }
   auto all_done = [&]() {
     bool d = true;
 #pragma unroll
-    for (int k = 0; k < PX; ++k) d = d && done[k];
+    for (int q = 0; q < NP; ++q) d = d && isnan(nv[q].x) && isnan(nv[q].y);
     return d;
   };
+  bool my_done = all_done();
 
   for (uint32_t b0 = start; b0 < end; b0 += NB) {
-    if (__syncthreads_count(!all_done()) == 0) break;
+    if (__syncthreads_count(!my_done) == 0) break;
     const int nb = (int)min((uint32_t)NB, end - b0);
 #pragma unroll
     for (int k = 0; k < NBM; ++k) {
@@ -108,21 +109,20 @@ __global__ void __launch_bounds__(TW* TH / PX) k_render(RenderArgs a) {
 #pragma unroll
       for (int q = 0; q < NP; ++q) {
         p2[q] = pair_power(r, dx, pair_dy(r, nv[q]));
-        any |= (!done[2 * q] && p2[q].x <= 0.f && p2[q].x >= r.bc.z) ||
-               (!done[2 * q + 1] && p2[q].y <= 0.f && p2[q].y >= r.bc.z);
+        any |= p2[q].x >= r.bc.z || p2[q].y >= r.bc.z;   // NaN (done) compares false
       }
       if (!__any_sync(0xffffffffu, any)) continue;   // no pixel of the warp is in this record's support
       float m = 0.f;
+      bool stop = false;
+      bool st[PX];
 #pragma unroll
       for (int q = 0; q < NP; ++q) {
-        const PairAlpha al = pair_alpha(r, p2[q]);
-        bool ok0 = al.in0 && !done[2 * q], ok1 = al.in1 && !done[2 * q + 1];
+        const PairAlpha al = pair_alpha<false>(r, p2[q]);
         const float2 Tn = __fmul2_rn(T[q], one_minus(al.alpha));
-        const bool st0 = ok0 && Tn.x < kTMin, st1 = ok1 && Tn.y < kTMin;   // stop before compositing
-        done[2 * q] |= st0;
-        done[2 * q + 1] |= st1;
-        ok0 &= !st0;
-        ok1 &= !st1;
+        const bool ok0 = al.in0 && Tn.x >= kTMin, ok1 = al.in1 && Tn.y >= kTMin;
+        st[2 * q] = al.in0 && !ok0;   // stop before compositing this entry
+        st[2 * q + 1] = al.in1 && !ok1;
+        stop |= st[2 * q] | st[2 * q + 1];
         float2 w = __fmul2_rn(al.alpha, T[q]);
         w.x = ok0 ? w.x : 0.f;
         w.y = ok1 ? w.y : 0.f;
@@ -135,11 +135,19 @@ __global__ void __launch_bounds__(TW* TH / PX) k_render(RenderArgs a) {
         last[2 * q + 1] = ok1 ? base + j + 1 : last[2 * q + 1];
         if (IMPORTANCE) m = fmaxf(m, fmaxf(w.x, w.y));
       }
+      if (stop) {   // rare: retire the stopped pixels
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          if (st[2 * q]) nv[q].x = __int_as_float(0x7fc00000);
+          if (st[2 * q + 1]) nv[q].y = __int_as_float(0x7fc00000);
+        }
+        my_done = all_done();
+      }
       if (IMPORTANCE) {
         const uint32_t mm = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
         if (lane == 0 && mm) atomicMax(&s_h[j], mm);
       }
-      if (__all_sync(0xffffffffu, all_done())) break;
+      if (__all_sync(0xffffffffu, my_done)) break;
     }
     __syncthreads();
     if (IMPORTANCE) {

@@ -90,26 +90,36 @@ __global__ void __launch_bounds__(256) k_ssim_stats(SsimArgs a) {
       v[k] = make_float2(q.x, q.y);
       v[k + 1] = make_float2(q.z, q.w);
     }
-    float m[4][5];
+    // (mu_x, mu_y) and (E[x^2], E[y^2]) advance as packed pairs, E[xy] alone
+    float2 m1[4], m2[4];
+    float m3[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int q = 0; q < 5; ++q) m[j][q] = 0.f;
+    for (int j = 0; j < 4; ++j) {
+      m1[j] = m2[j] = make_float2(0.f, 0.f);
+      m3[j] = 0.f;
+    }
 #pragma unroll
     for (int k = 0; k < 4 + 2 * kSR; ++k) {
-      const float xv = v[k].x, yv = v[k].y;
-      const float xx = xv * xv, yy = yv * yv, xy = xv * yv;
+      const float2 sq = __fmul2_rn(v[k], v[k]);
+      const float xy = v[k].x * v[k].y;
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int tap = k - j;
         if (tap < 0 || tap > 2 * kSR) continue;   // resolved at compile time
-        const float wk = a.w[tap];
-        m[j][0] = fmaf(wk, xv, m[j][0]);
-        m[j][1] = fmaf(wk, yv, m[j][1]);
-        m[j][2] = fmaf(wk, xx, m[j][2]);
-        m[j][3] = fmaf(wk, yy, m[j][3]);
-        m[j][4] = fmaf(wk, xy, m[j][4]);
+        const float2 w2 = make_float2(a.w[tap], a.w[tap]);
+        m1[j] = __ffma2_rn(w2, v[k], m1[j]);
+        m2[j] = __ffma2_rn(w2, sq, m2[j]);
+        m3[j] = fmaf(a.w[tap], xy, m3[j]);
       }
+    }
+    float m[4][5];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      m[j][0] = m1[j].x;
+      m[j][1] = m1[j].y;
+      m[j][2] = m2[j].x;
+      m[j][3] = m2[j].y;
+      m[j][4] = m3[j];
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -124,11 +134,13 @@ __global__ void __launch_bounds__(256) k_ssim_stats(SsimArgs a) {
   float s_sum = 0.f, e_sum = 0.f;
   for (int t = threadIdx.x; t < kSTX * (kSTY / 2); t += blockDim.x) {
     const int c = t % kSTX, r0 = 2 * (t / kSTX);
-    float m[2][5];
+    float2 m1[2], m2[2];
+    float m3[2];
 #pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-      for (int q = 0; q < 5; ++q) m[j][q] = 0.f;
+    for (int j = 0; j < 2; ++j) {
+      m1[j] = m2[j] = make_float2(0.f, 0.f);
+      m3[j] = 0.f;
+    }
 #pragma unroll
     for (int k = 0; k < 2 + 2 * kSR; ++k) {
       const float4 hv = hq[r0 + k][c];
@@ -137,13 +149,20 @@ __global__ void __launch_bounds__(256) k_ssim_stats(SsimArgs a) {
       for (int j = 0; j < 2; ++j) {
         const int tap = k - j;
         if (tap < 0 || tap > 2 * kSR) continue;
-        const float wk = a.w[tap];
-        m[j][0] = fmaf(wk, hv.x, m[j][0]);
-        m[j][1] = fmaf(wk, hv.y, m[j][1]);
-        m[j][2] = fmaf(wk, hv.z, m[j][2]);
-        m[j][3] = fmaf(wk, hv.w, m[j][3]);
-        m[j][4] = fmaf(wk, hz, m[j][4]);
+        const float2 w2 = make_float2(a.w[tap], a.w[tap]);
+        m1[j] = __ffma2_rn(w2, make_float2(hv.x, hv.y), m1[j]);
+        m2[j] = __ffma2_rn(w2, make_float2(hv.z, hv.w), m2[j]);
+        m3[j] = fmaf(a.w[tap], hz, m3[j]);
       }
+    }
+    float m[2][5];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      m[j][0] = m1[j].x;
+      m[j][1] = m1[j].y;
+      m[j][2] = m2[j].x;
+      m[j][3] = m2[j].y;
+      m[j][4] = m3[j];
     }
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
@@ -224,9 +243,13 @@ __global__ void __launch_bounds__(256) k_ssim_grad(SsimArgs a) {
     const int t = threadIdx.x;
     const int r = (t & 7) + 8 * (t >> 6), c0 = 4 * ((t >> 3) & 7);
     if (r < kSHY) {
-    float m[4][3];
+    float2 mab[4];
+    float mc[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) m[j][0] = m[j][1] = m[j][2] = 0.f;
+    for (int j = 0; j < 4; ++j) {
+      mab[j] = make_float2(0.f, 0.f);
+      mc[j] = 0.f;
+    }
 #pragma unroll
     for (int k = 0; k < 4 + 2 * kSR; ++k) {
       const float4 v = sm[r][c0 + k];
@@ -234,11 +257,16 @@ __global__ void __launch_bounds__(256) k_ssim_grad(SsimArgs a) {
       for (int j = 0; j < 4; ++j) {
         const int tap = k - j;
         if (tap < 0 || tap > 2 * kSR) continue;
-        const float wk = a.w[tap];
-        m[j][0] = fmaf(wk, v.x, m[j][0]);
-        m[j][1] = fmaf(wk, v.y, m[j][1]);
-        m[j][2] = fmaf(wk, v.z, m[j][2]);
+        mab[j] = __ffma2_rn(make_float2(a.w[tap], a.w[tap]), make_float2(v.x, v.y), mab[j]);
+        mc[j] = fmaf(a.w[tap], v.z, mc[j]);
       }
+    }
+    float m[4][3];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      m[j][0] = mab[j].x;
+      m[j][1] = mab[j].y;
+      m[j][2] = mc[j];
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) hm[r][c0 + j] = make_float4(m[j][0], m[j][1], m[j][2], 0.f);
@@ -258,9 +286,13 @@ __global__ void __launch_bounds__(256) k_ssim_grad(SsimArgs a) {
       xv[j] = in ? __ldg(a.x + o) : 0.f;
       yv[j] = in ? __ldg(a.y + o) : 0.f;
     }
-    float m[2][3];
+    float2 mab[2];
+    float mc[2];
 #pragma unroll
-    for (int j = 0; j < 2; ++j) m[j][0] = m[j][1] = m[j][2] = 0.f;
+    for (int j = 0; j < 2; ++j) {
+      mab[j] = make_float2(0.f, 0.f);
+      mc[j] = 0.f;
+    }
 #pragma unroll
     for (int k = 0; k < 2 + 2 * kSR; ++k) {
       const float4 v = hm[r0 + k][c];
@@ -268,11 +300,16 @@ __global__ void __launch_bounds__(256) k_ssim_grad(SsimArgs a) {
       for (int j = 0; j < 2; ++j) {
         const int tap = k - j;
         if (tap < 0 || tap > 2 * kSR) continue;
-        const float wk = a.w[tap];
-        m[j][0] = fmaf(wk, v.x, m[j][0]);
-        m[j][1] = fmaf(wk, v.y, m[j][1]);
-        m[j][2] = fmaf(wk, v.z, m[j][2]);
+        mab[j] = __ffma2_rn(make_float2(a.w[tap], a.w[tap]), make_float2(v.x, v.y), mab[j]);
+        mc[j] = fmaf(a.w[tap], v.z, mc[j]);
       }
+    }
+    float m[2][3];
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      m[j][0] = mab[j].x;
+      m[j][1] = mab[j].y;
+      m[j][2] = mc[j];
     }
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
