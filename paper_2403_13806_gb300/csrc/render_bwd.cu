@@ -137,6 +137,15 @@ __global__ void __launch_bounds__(TW* TH / PX) k_render_bwd(BwdBlendArgs a) {
   int my_last = 0;
 #pragma unroll
   for (int k = 0; k < PX; ++k) my_last = max(my_last, last[k]);
+  // gate[q] = (0 or NaN) per pixel: NaN until the walk reaches the pixel's last composited
+  // entry (entry e is live for pixel k when e < last[k]); p2 + gate makes every test on a
+  // pixel that is not live false without a per-pixel comparison of e.  next_live is the
+  // largest entry at which a pixel still to be woken becomes live (-1: none).
+  const float kNaN = __int_as_float(0x7fc00000);
+  float2 gate[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) gate[q] = make_float2(kNaN, kNaN);
+  int next_live = my_last - 1;
   int wl = my_last;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) wl = max(wl, __shfl_xor_sync(0xffffffffu, wl, o));
@@ -163,6 +172,15 @@ __global__ void __launch_bounds__(TW* TH / PX) k_render_bwd(BwdBlendArgs a) {
     float* part = s_part[warp];
     for (int j = nb - 1; j >= 0; --j) {
       const int e = lo + j;
+      if (e <= next_live) {   // rare: wake the pixels whose walk starts here
+        int nl = -1;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          if (e < last[2 * q]) gate[q].x = 0.f; else nl = max(nl, last[2 * q] - 1);
+          if (e < last[2 * q + 1]) gate[q].y = 0.f; else nl = max(nl, last[2 * q + 1] - 1);
+        }
+        next_live = nl;
+      }
       const BlendRec r = s_rec[j];
       const float2 dx = pair_dx(r, nu);
       float2 dy[NP], p2[NP];
@@ -170,9 +188,8 @@ __global__ void __launch_bounds__(TW* TH / PX) k_render_bwd(BwdBlendArgs a) {
 #pragma unroll
       for (int q = 0; q < NP; ++q) {
         dy[q] = pair_dy(r, nv[q]);
-        p2[q] = pair_power(r, dx, dy[q]);
-        any |= (e < last[2 * q] && p2[q].x <= 0.f && p2[q].x >= r.bc.z) ||
-               (e < last[2 * q + 1] && p2[q].y <= 0.f && p2[q].y >= r.bc.z);
+        p2[q] = __fadd2_rn(pair_power(r, dx, dy[q]), gate[q]);
+        any |= p2[q].x >= r.bc.z || p2[q].y >= r.bc.z;   // NaN (not live) compares false
       }
       if (!__any_sync(0xffffffffu, any)) {
         if (lane < 9) part[lane * PS + j] = 0.f;
@@ -184,16 +201,17 @@ __global__ void __launch_bounds__(TW* TH / PX) k_render_bwd(BwdBlendArgs a) {
 #pragma unroll
       for (int q = 0; q < NP; ++q) {
         const PairAlpha al = pair_alpha(r, p2[q]);
-        const bool ok0 = al.in0 && e < last[2 * q], ok1 = al.in1 && e < last[2 * q + 1];
-        act |= ok0 || ok1;
-        const float2 om = one_minus(al.alpha);
+        act |= al.in0 || al.in1;
+        // a skipped entry gets alpha 0: its weight is 0 and T_j = T exactly (1/(1 - 0) = 1)
+        const float2 a_eff = sel2(al.in0, al.in1, al.alpha);
+        const float2 om = one_minus(a_eff);
         const float2 inv = make_float2(__fdividef(1.f, om.x), __fdividef(1.f, om.y));
         const float2 Tj = __fmul2_rn(T[q], inv);
-        const float2 w = sel2(ok0, ok1, __fmul2_rn(al.alpha, Tj));
+        const float2 w = __fmul2_rn(a_eff, Tj);
         const float2 cG = __ffma2_rn(lo2(r.rg), Gr[q], __ffma2_rn(hi2(r.rg), Gg[q], __fmul2_rn(lo2(r.bc), Gb[q])));
         const float2 X = __fmul2_rn(__fadd2_rn(SG[q], bgG[q]), inv);
         const float2 dLda = __ffma2_rn(Tj, cG, make_float2(-X.x, -X.y));
-        const float2 dl = sel2(ok0 && al.raw.x < kAlphaMax, ok1 && al.raw.y < kAlphaMax, dLda);
+        const float2 dl = sel2(al.in0 && al.raw.x < kAlphaMax, al.in1 && al.raw.y < kAlphaMax, dLda);
         acc_r = __ffma2_rn(w, Gr[q], acc_r);
         acc_g = __ffma2_rn(w, Gg[q], acc_g);
         acc_b = __ffma2_rn(w, Gb[q], acc_b);
@@ -204,8 +222,7 @@ __global__ void __launch_bounds__(TW* TH / PX) k_render_bwd(BwdBlendArgs a) {
         acc_qy = __fadd2_rn(acc_qy, qy);
         acc_qyy = __ffma2_rn(qy, dy[q], acc_qyy);
         SG[q] = __ffma2_rn(w, cG, SG[q]);
-        T[q].x = ok0 ? Tj.x : T[q].x;
-        T[q].y = ok1 ? Tj.y : T[q].y;
+        T[q] = Tj;
       }
       if (__any_sync(0xffffffffu, act)) {
         // power = p2 ln 2, p2 = A dx^2 + B dx dy + C dy^2 with dx = x - u, dy = y - v
