@@ -321,13 +321,13 @@ __device__ __forceinline__ SuperTile super_tile(uint32_t S, const rs_view* views
 
 // Bit (fy * kSuper + fx) set for every tile of the super-tile's block the rect covers.
 __device__ __forceinline__ uint32_t cover_mask(ushort4 r, const SuperTile& t) {
-  const int x0 = max((int)r.x - t.tx0, 0), x1 = min((int)r.z - t.tx0, t.nx);
-  const int y0 = max((int)r.y - t.ty0, 0), y1 = min((int)r.w - t.ty0, t.ny);
-  if (x0 >= x1 || y0 >= y1) return 0u;
-  const uint32_t row = ((1u << x1) - 1u) & ~((1u << x0) - 1u);
-  uint32_t m = 0u;
-  for (int fy = y0; fy < y1; ++fy) m |= row << (fy * kSuper);
-  return m;
+  // (x0, y0 clamped to the super-tile so that no shift exceeds its width)
+  const int x0 = min(max((int)r.x - t.tx0, 0), kSuper), x1 = min((int)r.z - t.tx0, t.nx);
+  const int y0 = min(max((int)r.y - t.ty0, 0), kSuper), y1 = min((int)r.w - t.ty0, t.ny);
+  const int k = y1 - y0;                                         // rows covered (<= 0: none)
+  const uint32_t row = (1u << max(x1, x0)) - (1u << x0);          // bits x0 .. x1-1 (0 if empty)
+  const uint32_t rep = k > 0 ? 0x1111u >> (kSuper * (kSuper - k)) : 0u;   // k rows, one bit each
+  return (row * rep) << (kSuper * y0);                            // row repeated on rows y0 .. y1-1
 }
 
 // Segment j of super-tile S's list: kSegs CTAs share each list in equal parts.

@@ -208,7 +208,20 @@ __global__ void __launch_bounds__(kThreads, ITEMS <= 8 ? 4 : 3) k_tile_sort(cons
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
       const int dg = k[i] == 0xffffffffu ? R : (int)((k[i] >> shift) & mask);
-      const unsigned peers = __match_any_sync(0xffffffffu, dg);
+      // lanes with the same digit: one match instruction for low-entropy digits (16-bit
+      // tile keys repeat a lot), rbits + 1 ballots for high-entropy ones (32-bit depth and
+      // Morton keys), where the match instruction's cost grows with the distinct values
+      unsigned peers;
+      if (sizeof(KeyT) == 2) {
+        peers = __match_any_sync(0xffffffffu, dg);
+      } else {
+        peers = 0xffffffffu;
+        for (int b = 0; b <= rbits; ++b) {   // bit rbits separates the padding digit R
+          const bool bit = (dg >> b) & 1;
+          const unsigned bal = __ballot_sync(0xffffffffu, bit);
+          peers &= bit ? bal : ~bal;
+        }
+      }
       const int leader = __ffs(peers) - 1;
       uint32_t base = 0;
       if (dg < R) base = s_whist[warp][dg];
