@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--step-only", action="store_true",
+                    help="time the step and stop (no per-stage pass, plain loop, end-to-end or optimiser "
+                         "measurements): the command for profiling the step's launches")
     ap.add_argument("--loss", default="paper", choices=["paper", "l1"],
                     help="paper: (1 - 0.2) MSE + 0.2 (1 - SSIM) of Sec. 3.2; l1: mean absolute error")
     ap.add_argument("--tile", default="auto", help="tile shape WxH with all views in one launch, or 'auto' "
@@ -284,6 +287,17 @@ def run_ours(args):
     ms_per_step = ms / args.steps
     views_total = V * world
     value = ms_per_step / views_total   # whole job: all ranks' views in the max-over-ranks step time
+
+    if args.step_only:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": round(value, 5), "unit": "ms/view (fwd+bwd)",
+                              "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                              "ms_per_step": round(ms_per_step, 5), "higher_is_better": False, "step_only": True,
+                              "config": dict(workload_config(V, world, tile, B, args.loss))}))
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
 
     # per-stage times of the same batched step (plain launches, events on this stream), and
     # the work counts of each launch (pairs walked, super-tile instances)
@@ -591,12 +605,14 @@ OPS_PER_PAIR = {"k_render_importance": 22, "k_render": 22, "k_render_bwd": 46}
 # of the sources the kernel was built from.  A capture stays valid only while those sources
 # are unchanged; otherwise the roofline reports traffic as null.
 NCU_TRAFFIC = {
-    "k_render_bwd": {"bytes_per_view": 25160960, "files": ['render_bwd.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "f1149114a9ca0344",
+    "k_render_bwd": {"bytes_per_view": 25175040, "files": ['render_bwd.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "f3925b9d4fc890bf",
                 "profile": "k_render_bwd_1M_1view.md"},
-    "k_render_importance": {"bytes_per_view": 6874368, "files": ['render.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "ef776bd49ca59be4",
+    "k_render_importance": {"bytes_per_view": 5254400, "files": ['render.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "ce077fcbd7e1da48",
                 "profile": "k_render_1M_1view.md"},
-    "k_fine_scatter": {"bytes_per_view": 24204032, "files": ['binsort.cu', 'rs_common.cuh'], "sha": "a64b3191aaf884f5",
+    "k_fine_scatter": {"bytes_per_view": 24176384, "files": ['binsort.cu', 'rs_common.cuh'], "sha": "4c469002ded06892",
                 "profile": "k_fine_scatter_1M_1view.md"},
+    "k_ssim_stats": {"bytes_per_view": 26043648, "files": ['ssim.cu', 'rs_common.cuh'], "sha": "964260dd02b43d8e",
+                "profile": "k_ssim_stats_1view.md"},
 }
 
 
