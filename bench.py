@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--smem-batch", type=int, default=0,
+                    help="with a fixed --tile: Gaussian records staged per blend batch (rs_config.batch, 0: default)")
     ap.add_argument("--step-only", action="store_true",
                     help="time the step and stop (no per-stage pass, plain loop, end-to-end or optimiser "
                          "measurements): the command for profiling the step's launches")
@@ -171,6 +173,7 @@ def run_ours(args):
     else:
         tune = None
         tile, B = tuple(int(x) for x in args.tile.split("x")), V
+        cfg = api.config(batch=args.smem_batch)
     vbs = [api.ViewBatch(cams[i:i + B], scene.n, tile=tile, device=dev) for i in range(0, V, B)]
 
     # synthetic targets: renders of a perturbed copy (setup, untimed)

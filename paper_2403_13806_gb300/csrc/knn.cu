@@ -12,8 +12,9 @@
 //   k_nn                   -- per point: an upper bound R from its 16 neighbours in Morton
 //                             order; the smallest level whose cell edge is >= 2R (at most two
 //                             cells per axis then cover the ball of radius R around the
-//                             point); a binary search for the start of each of those <= 8
-//                             cells; the minimum over every point in them.
+//                             point); the start and end of each of those <= 8 cells (a table
+//                             of the first index per 18-bit code prefix leaves at most a short
+//                             search inside one prefix bucket); the minimum over their points.
 // Exactness: the cell index floor((v - o)/h) is monotone in v, so every point within R of the
 // query on each axis (a superset of the ball) lies in a cell of the quantised range.
 // Distances are FP32 ((dx^2 + dy^2) + dz^2 with every operation rounded; square root
@@ -30,6 +31,8 @@ namespace rs {
 constexpr int kBBoxBlocks = 1024;
 constexpr int kMortonBits = 10;   // per axis
 constexpr int kWindow = 8;        // Morton neighbours on each side for the first bound
+constexpr int kPrefixShift = 12;  // index table over the top 18 code bits (octree level 4 cells)
+constexpr int kPrefixes = 1 << (3 * kMortonBits - kPrefixShift);
 
 struct CubeParams {
   float ox, oy, oz, h, inv_h;
@@ -43,6 +46,7 @@ struct NNWs {
   uint32_t* vals[2];
   uint32_t* scratch;
   float4* spts;         // [n]
+  uint32_t* first;      // [kPrefixes + 1]: first sorted index whose code has a prefix >= p
   size_t bytes;
 };
 
@@ -61,6 +65,7 @@ static NNWs nn_ws_layout(void* base, int64_t n) {
   for (int i = 0; i < 2; ++i) w.vals[i] = reinterpret_cast<uint32_t*>(take(nn * 4));
   w.scratch = reinterpret_cast<uint32_t*>(take(tiles::scratch_words(n) * 4));
   w.spts = reinterpret_cast<float4*>(take(nn * 16));
+  w.first = reinterpret_cast<uint32_t*>(take((size_t)(kPrefixes + 1) * 4));
   w.bytes = off;
   return w;
 }
@@ -172,9 +177,30 @@ __device__ __forceinline__ int64_t lower_bound(const uint32_t* __restrict__ sk, 
   return lo;
 }
 
+// first[p] = lower_bound(codes, p << kPrefixShift) for every prefix p (and first[kPrefixes] = n)
+__global__ void __launch_bounds__(256) k_prefix_table(const uint32_t* __restrict__ sk, int64_t n,
+                                                      uint32_t* __restrict__ first) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p > kPrefixes) return;
+  first[p] = p == kPrefixes ? (uint32_t)n : (uint32_t)lower_bound(sk, n, (uint32_t)p << kPrefixShift);
+}
+
+// lower_bound through the prefix table: a search only inside one prefix bucket
+__device__ __forceinline__ int64_t lower_bound_t(const uint32_t* __restrict__ sk, const uint32_t* __restrict__ first,
+                                                 uint32_t key) {
+  const uint32_t p = key >> kPrefixShift;
+  int64_t lo = first[p], hi = first[p + 1];
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (sk[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
 __global__ void __launch_bounds__(256) k_nn(const float4* __restrict__ spts, const uint32_t* __restrict__ sk,
                                             const uint32_t* __restrict__ sv, int64_t n,
-                                            const CubeParams* __restrict__ cp, float* __restrict__ dist) {
+                                            const CubeParams* __restrict__ cp, const uint32_t* __restrict__ first,
+                                            float* __restrict__ dist) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const CubeParams p = *cp;
@@ -200,9 +226,11 @@ __global__ void __launch_bounds__(256) k_nn(const float4* __restrict__ spts, con
   for (int z = z0; z <= z1; ++z)
     for (int y = y0; y <= y1; ++y)
       for (int x = x0; x <= x1; ++x) {
-        const uint32_t first = morton(x, y, z) << (3 * L);
-        const uint64_t last = (uint64_t)first + ((uint64_t)1 << (3 * L));   // exclusive
-        for (int64_t k = lower_bound(sk, n, first); k < n && (uint64_t)sk[k] < last; ++k)
+        const uint32_t c0 = morton(x, y, z) << (3 * L);
+        const uint64_t c1 = (uint64_t)c0 + ((uint64_t)1 << (3 * L));   // exclusive
+        const int64_t k0 = lower_bound_t(sk, first, c0);
+        const int64_t k1 = c1 >= ((uint64_t)1 << (3 * kMortonBits)) ? n : lower_bound_t(sk, first, (uint32_t)c1);
+        for (int64_t k = k0; k < k1; ++k)
           if (k != j) best = fminf(best, dist2(q, spts[k]));
       }
   dist[sv[j]] = __fsqrt_rn(best);
@@ -243,7 +271,11 @@ extern "C" rs_status rs_nn_distance(const float* means, int64_t n, float* dist, 
     prof::Scope ps("k_sorted_points", s);
     k_sorted_points<<<(unsigned)blocks, 256, 0, s>>>(means, n, w.vals[cur], w.spts);
   }
+  {
+    prof::Scope ps("k_prefix_table", s);
+    k_prefix_table<<<(kPrefixes + 256) / 256, 256, 0, s>>>(w.keys[cur], n, w.first);
+  }
   prof::Scope ps("k_nn", s);
-  k_nn<<<(unsigned)blocks, 256, 0, s>>>(w.spts, w.keys[cur], w.vals[cur], n, w.params, dist);
+  k_nn<<<(unsigned)blocks, 256, 0, s>>>(w.spts, w.keys[cur], w.vals[cur], n, w.params, w.first, dist);
   return launch_status();
 }
