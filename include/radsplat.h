@@ -124,9 +124,10 @@ typedef struct rs_config {
   float near_plane;      /* cull if the FP32 camera depth <= near_plane, default 0.2 */
   float bg[3];           /* background colour composited with T_final, default 0 */
   int32_t batch;         /* Gaussian records staged in shared memory per batch of the blend
-                            kernels: 0 (default: 2 per thread forward, 1 per thread backward)
-                            or 1, 2 or 4 x the CTA's threads (64 for 16x16 and 32x8 tiles,
-                            32 for 8x8); other values give RS_ERR_UNSUPPORTED */
+                            kernels: 0 (default: 128 in the forward, 64 in the backward) or
+                            1, 2 or 4 x 64 for 16x16 and 32x8 tiles (x 32 for 8x8); the forward
+                            runs 64 threads per tile (32 for 8x8), the backward one warp per
+                            tile; other values give RS_ERR_UNSUPPORTED */
   int32_t reserved[2];
 } rs_config;
 

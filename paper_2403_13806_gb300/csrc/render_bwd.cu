@@ -1,7 +1,7 @@
 // rs_render_backward: derivative of Eq. (render-gs) (training loss of Sec. 3.2), in two
 // kernels.
 //
-// k_render_bwd -- one CTA per (view, tile), four pixels of a column per thread (two for 8x8
+// k_render_bwd -- one warp per (view, tile): eight pixels of a column per thread (two for 8x8
 //   tiles) evaluated as pixel pairs with packed FP32 instructions, the tile list walked back
 //   to front from the largest `last` of the tile.  Each pixel recovers T_j = T_{j+1}/(1-a_j)
 //   from its T_final and accumulates, per composited entry j,
@@ -81,7 +81,7 @@ __device__ __forceinline__ float2 sel2(bool a, bool b, float2 x) {
 // derivative with respect to the power) the moments sum(q), sum(q dy), sum(q dy^2); the
 // column's common dx turns them into the mean and conic gradients.
 template <int TW, int TH, int PX, int NBM>
-__global__ void __launch_bounds__(TW* TH / PX) k_render_bwd(BwdBlendArgs a) {
+__global__ void __launch_bounds__(TW* TH / PX, 16) k_render_bwd(BwdBlendArgs a) {
   constexpr int NT = TW * TH / PX;  // threads; each owns pixels (x, PX r + k), k < PX
   constexpr int NP = PX / 2;
   constexpr int NW = NT / 32;
@@ -569,16 +569,21 @@ static BwdWs bwd_ws_layout(void* base, int64_t n_items) {
 
 size_t backward_ws_bytes(const rs_view_batch* batch) { return bwd_ws_layout(nullptr, batch->n_items).bytes; }
 
-// Records staged per thread and batch: cfg->batch / threads, one of 1, 2, 4 (0: 1).
+// One warp per tile (PX = 8 pixels per thread for 16x16 and 32x8 tiles, 2 for 8x8): the
+// per-entry warp reduction serves 256 (64) pixels and no cross-warp partials are needed.
+// Records staged per batch: cfg->batch (the same count as the forward stages), i.e.
+// cfg->batch / 32 per thread, one of 1, 2, 4, 8 (0: 64 records).
 template <int TW, int TH, int PX>
 static rs_status launch_bwd_blend(const BwdBlendArgs& a, int n_tiles, int batch, cudaStream_t s) {
   constexpr int NT = TW * TH / PX;
-  const int m = batch == 0 ? 1 : (batch % NT == 0 ? batch / NT : 0);
-  if (m != 1 && m != 2 && m != 4) return RS_ERR_UNSUPPORTED;
+  static_assert(NT == 32, "one warp per tile");
+  const int m = batch == 0 ? 2 : (batch % NT == 0 ? batch / NT : 0);
+  if (m != 1 && m != 2 && m != 4 && m != 8) return RS_ERR_UNSUPPORTED;
   prof::Scope ps("k_render_bwd", s);
   if (m == 1) k_render_bwd<TW, TH, PX, 1><<<n_tiles, NT, 0, s>>>(a);
   else if (m == 2) k_render_bwd<TW, TH, PX, 2><<<n_tiles, NT, 0, s>>>(a);
-  else k_render_bwd<TW, TH, PX, 4><<<n_tiles, NT, 0, s>>>(a);
+  else if (m == 4) k_render_bwd<TW, TH, PX, 4><<<n_tiles, NT, 0, s>>>(a);
+  else k_render_bwd<TW, TH, PX, 8><<<n_tiles, NT, 0, s>>>(a);
   return RS_OK;
 }
 
@@ -621,8 +626,8 @@ extern "C" rs_status rs_render_backward(const rs_gaussians* g, const rs_view_bat
   b.g.gb = w.gb;
   b.g.gc = w.gc;
   rs_status bst = RS_ERR_UNSUPPORTED;
-  if (batch->tile_w == 16 && batch->tile_h == 16) bst = launch_bwd_blend<16, 16, 4>(b, batch->n_tiles, cfg->batch, s);
-  else if (batch->tile_w == 32 && batch->tile_h == 8) bst = launch_bwd_blend<32, 8, 4>(b, batch->n_tiles, cfg->batch, s);
+  if (batch->tile_w == 16 && batch->tile_h == 16) bst = launch_bwd_blend<16, 16, 8>(b, batch->n_tiles, cfg->batch, s);
+  else if (batch->tile_w == 32 && batch->tile_h == 8) bst = launch_bwd_blend<32, 8, 8>(b, batch->n_tiles, cfg->batch, s);
   else if (batch->tile_w == 8 && batch->tile_h == 8) bst = launch_bwd_blend<8, 8, 2>(b, batch->n_tiles, cfg->batch, s);
   if (bst != RS_OK) return bst;
 
