@@ -656,8 +656,9 @@ def kernel_work(vbs, sres, pairs, n_super):
     8 B per item and pass (read key+value, write key+value = 16 B in the scatter, 4 B read in
     the count); the super-tile sort moves 2 x (2 + 4) B per super instance and pass (count:
     2 B); the fine partition reads 4 B index + 8 B rect per super instance (twice: count and
-    scatter) and writes 4 B per instance; the projection backward reads 236 + 36 B and writes
-    236 B per item; the blend kernels count FP32 operations per evaluated pair."""
+    scatter) and writes 4 B per instance; the projection backward reads 236 B and writes
+    236 B per Gaussian (read-modify-write) plus 52 B per item; the blend kernels count FP32
+    operations per evaluated pair."""
     vb = _PerLaunch(vbs)
     c = vb.launches
     M, K, Ks, P = vb.n_items, sres["n_instances"], n_super / c, vb.n_pixels
@@ -678,7 +679,9 @@ def kernel_work(vbs, sres, pairs, n_super):
         "k_l1": P * 3 * 4 * 3,
         "k_ssim_stats": P * 3 * (8 + 12),
         "k_ssim_grad": P * 3 * (12 + 8 + 4),
-        "k_project_bwd": M * (236 + 36 + 236),
+        # per Gaussian: parameters read once, gradients read and written once (all views
+        # summed in registers); per item: 36 B of image-space gradients + the 16 B colour row
+        "k_project_bwd": vb.n_gaussians * (236 + 2 * 236) + M * (36 + 16),
         "k_filter_count": vb.n_gaussians * 4,
         "k_filter_scatter": vb.n_gaussians * (4 + 1) + vb.n_gaussians * 4,
     }

@@ -287,6 +287,7 @@ struct BwdProjArgs {
   const float4* ga;
   const float4* gb;
   const float* gc;
+  const float4* rgb_d;   // forward colours: a clamped channel (max(0, .) = 0) has no gradient
   rs_gaussian_grads out;
 };
 
@@ -297,9 +298,23 @@ struct ParamGrad {
 };
 
 // Adds the parameter gradient of one item (view `cam`, Gaussian gid) into pg.
+// Where an item's SH gradient goes: the thread's registers (one item per thread), or a
+// per-thread column of a shared-memory array (all views of a Gaussian summed there, which
+// keeps 48 accumulators out of the registers).
 template <int D>
-__device__ __forceinline__ void item_backward(const BwdProjArgs& a, const rs_view& cam, int64_t gid, float4 ga,
-                                              float4 gb, float gcb, ParamGrad<D>& pg) {
+struct RegSH {
+  ParamGrad<D>& pg;
+  __device__ __forceinline__ void add(int k, int c, float v) { pg.sh[k][c] += v; }
+};
+struct SmemSH {
+  float* col;   // element (k, c) at col[(3 k + c) * stride]
+  int stride;
+  __device__ __forceinline__ void add(int k, int c, float v) { col[(3 * k + c) * stride] += v; }
+};
+
+template <int D, typename SH>
+__device__ __forceinline__ void item_backward(const BwdProjArgs& a, const rs_view& cam, int64_t gid, int64_t item,
+                                              float4 ga, float4 gb, float gcb, ParamGrad<D>& pg, SH& shg) {
   constexpr int NC = (D + 1) * (D + 1);
   const int64_t N = a.g.n;
   const float* W = cam.viewmat;
@@ -428,22 +443,16 @@ __device__ __forceinline__ void item_backward(const BwdProjArgs& a, const rs_vie
   dz *= dn;
   float Y[NC];
   sh::basis<D>(dx, dy, dz, Y);
-  const float grgb[3] = {gb.z, gb.w, gcb};
-  float gcol[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    float acc = 0.5f;
-#pragma unroll
-    for (int k = 0; k < NC; ++k) acc = fmaf(__ldg(a.g.sh + (int64_t)(k * 3 + c) * N + gid), Y[k], acc);
-    gcol[c] = acc > 0.f ? grgb[c] : 0.f;
-  }
+  // the forward stored max(0, 0.5 + sum k Y): a channel it clamped to 0 gets no gradient
+  const float4 fc = __ldg(a.rgb_d + item);
+  const float gcol[3] = {fc.x > 0.f ? gb.z : 0.f, fc.y > 0.f ? gb.w : 0.f, fc.z > 0.f ? gcb : 0.f};
   float gY[NC];
 #pragma unroll
   for (int k = 0; k < NC; ++k) {
     float t = 0.f;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      pg.sh[k][c] += gcol[c] * Y[k];
+      shg.add(k, c, gcol[c] * Y[k]);
       t += gcol[c] * __ldg(a.g.sh + (int64_t)(k * 3 + c) * N + gid);
     }
     gY[k] = t;
@@ -472,9 +481,10 @@ __device__ __forceinline__ bool any_grad(float4 ga, float4 gb, float gc) {
 template <int D>
 __global__ void __launch_bounds__(128) k_project_bwd_dense(BwdProjArgs a) {
   constexpr int NC = (D + 1) * (D + 1);
+  __shared__ float s_gsh[3 * NC][128];
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t N = a.g.n;
-  if (gid >= N) return;
+  if (gid >= N) return;   // no barrier below: each thread owns its column
   ParamGrad<D> pg;
 #pragma unroll
   for (int c = 0; c < 3; ++c) pg.m[c] = pg.ls[c] = 0.f;
@@ -482,9 +492,8 @@ __global__ void __launch_bounds__(128) k_project_bwd_dense(BwdProjArgs a) {
   for (int c = 0; c < 4; ++c) pg.q[c] = 0.f;
   pg.lg = 0.f;
 #pragma unroll
-  for (int k = 0; k < NC; ++k)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) pg.sh[k][c] = 0.f;
+  for (int k = 0; k < 3 * NC; ++k) s_gsh[k][threadIdx.x] = 0.f;
+  SmemSH shg{&s_gsh[0][threadIdx.x], 128};
   bool touched = false;
   for (int v = 0; v < a.n_views; ++v) {
     const rs_view& cam = a.views[v];
@@ -493,7 +502,7 @@ __global__ void __launch_bounds__(128) k_project_bwd_dense(BwdProjArgs a) {
     const float gc = a.gc[item];
     if (!any_grad(ga, gb, gc)) continue;
     touched = true;
-    item_backward<D>(a, cam, gid, ga, gb, gc, pg);
+    item_backward<D>(a, cam, gid, item, ga, gb, gc, pg, shg);
   }
   if (!touched) return;
   for (int c = 0; c < 3; ++c) {
@@ -503,9 +512,7 @@ __global__ void __launch_bounds__(128) k_project_bwd_dense(BwdProjArgs a) {
   for (int c = 0; c < 4; ++c) a.out.quats[c * N + gid] += pg.q[c];
   a.out.opacity_logit[gid] += pg.lg;
 #pragma unroll
-  for (int k = 0; k < NC; ++k)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) a.out.sh[(int64_t)(k * 3 + c) * N + gid] += pg.sh[k][c];
+  for (int k = 0; k < 3 * NC; ++k) a.out.sh[(int64_t)k * N + gid] += s_gsh[k][threadIdx.x];
 }
 
 // Visibility-list batches: one thread per item, atomic adds (items of one Gaussian can sit
@@ -531,7 +538,8 @@ __global__ void __launch_bounds__(128) k_project_bwd_subset(BwdProjArgs a) {
   for (int k = 0; k < NC; ++k)
 #pragma unroll
     for (int c = 0; c < 3; ++c) pg.sh[k][c] = 0.f;
-  item_backward<D>(a, a.views[v], gid, ga, gb, gc, pg);
+  RegSH<D> shg{pg};
+  item_backward<D>(a, a.views[v], gid, item, ga, gb, gc, pg, shg);
   for (int c = 0; c < 3; ++c) {
     atomicAdd(a.out.means + c * N + gid, pg.m[c]);
     atomicAdd(a.out.log_scales + c * N + gid, pg.ls[c]);
@@ -642,6 +650,7 @@ extern "C" rs_status rs_render_backward(const rs_gaussians* g, const rs_view_bat
   p.ga = w.ga;
   p.gb = w.gb;
   p.gc = w.gc;
+  p.rgb_d = reinterpret_cast<const float4*>(proj->rgb_d);
   p.out = *grads;
   const int threads = 128;
   prof::Scope ps("k_project_bwd", s);
