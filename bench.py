@@ -652,7 +652,8 @@ def kernel_work(vbs, sres, pairs, n_super):
     (bound "hbm") or FP32 lane operations (bound "alu").
 
     Items M (view, Gaussian) pairs, instances K, super-tile instances Ks, pixels P:
-    projection reads 236 B of parameters and writes 52 B per item; the depth sort moves
+    projection reads 236 B of parameters per Gaussian (per item for visibility lists) and
+    writes 52 B per item; the depth sort moves
     8 B per item and pass (read key+value, write key+value = 16 B in the scatter, 4 B read in
     the count); the super-tile sort moves 2 x (2 + 4) B per super instance and pass (count:
     2 B); the fine partition reads 4 B index + 8 B rect per super instance (twice: count and
@@ -665,7 +666,9 @@ def kernel_work(vbs, sres, pairs, n_super):
     pairs = pairs / c
     kb = 2 if vb.n_tiles <= 65536 else 4
     hbm = {
-        "k_project": M * (236 + 52),
+        # dense batches read each Gaussian's parameters once for all its views
+        "k_project": (vb.n_gaussians * 236 + M * 52) if (vbs[0].subset is None and vbs[0].n_views > 1)
+        else M * (236 + 52),
         "k_depth_keys": M * (4 + 8),
         "k_upsweep": M * 4,
         "k_downsweep": M * 16,

@@ -1,8 +1,10 @@
 // rs_project: EWA projection of every (view, Gaussian) item (Sec. 3.2 "Gaussian Splatting").
 //
-// One thread per item.  Reads are coalesced structure-of-arrays loads of the Gaussian
-// parameters (236 B per Gaussian at SH degree 3); writes are one float2, two float4, one
-// ushort4 and one uint32 per item.  The kernel is bound by HBM bandwidth.
+// Dense batches: one thread per Gaussian over all views (its parameters read from HBM once);
+// visibility-list batches: one thread per item.  Reads are coalesced structure-of-arrays
+// loads of the Gaussian parameters (236 B per Gaussian at SH degree 3); writes are one
+// float2, two float4, one ushort4 and one uint32 per item.  The kernel is bound by HBM
+// bandwidth.
 #include <math.h>
 
 #include "profile.cuh"
@@ -27,15 +29,11 @@ struct ProjectArgs {
   rs_device_status* status;
 };
 
+// One item: Gaussian gid seen from view cam, written at row `item`.
 template <int D>
-__global__ void __launch_bounds__(256) k_project(ProjectArgs a) {
+__device__ __forceinline__ void project_item(const ProjectArgs& a, const rs_view& cam, int64_t gid, int64_t item) {
   constexpr int NC = (D + 1) * (D + 1);
-  const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (item >= a.n_items) return;
-  const int v = find_view_by_item(a.views, a.n_views, item);
-  const rs_view& cam = a.views[v];
   const int64_t N = a.g.n;
-  const int64_t gid = a.subset ? (int64_t)__ldg(a.subset + item) : item - cam.item_base;
 
   const float* W = cam.viewmat;
   const float px = __ldg(a.g.means + gid), py = __ldg(a.g.means + N + gid), pz = __ldg(a.g.means + 2 * N + gid);
@@ -162,6 +160,31 @@ __global__ void __launch_bounds__(256) k_project(ProjectArgs a) {
   a.n_tiles[item] = o_n;
 }
 
+// Visibility-list batches: one thread per item.
+template <int D>
+__global__ void __launch_bounds__(256) k_project(ProjectArgs a) {
+  const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (item >= a.n_items) return;
+  const int v = find_view_by_item(a.views, a.n_views, item);
+  const rs_view& cam = a.views[v];
+  const int64_t gid = a.subset ? (int64_t)__ldg(a.subset + item) : item - cam.item_base;
+  project_item<D>(a, cam, gid, item);
+}
+
+// Dense batches (every view lists every Gaussian): one thread per Gaussian walks the views,
+// so the 236 bytes of its parameters come from HBM once (later views read them from L1)
+// instead of once per view.
+template <int D>
+__global__ void __launch_bounds__(256, 2) k_project_dense(ProjectArgs a) {
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gid >= a.g.n) return;
+#pragma unroll 1
+  for (int v = 0; v < a.n_views; ++v) {
+    const rs_view& cam = a.views[v];
+    project_item<D>(a, cam, gid, cam.item_base + gid);
+  }
+}
+
 }  // namespace rs
 
 using namespace rs;
@@ -196,15 +219,21 @@ extern "C" rs_status rs_project(const rs_gaussians* g, const rs_view_batch* batc
   a.n_tiles = out->n_tiles;
   a.status = status;
   const int threads = 256;
-  const int64_t blocks = (batch->n_items + threads - 1) / threads;
+  // one thread per Gaussian pays off once its parameters serve several views
+  const bool dense = !batch->subset_idx && batch->n_views > 1;
+  const int64_t blocks = ((dense ? g->n : batch->n_items) + threads - 1) / threads;
   if (blocks > 0x7fffffffLL) return RS_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   prof::Scope ps("k_project", s);
   switch (g->sh_degree) {
-    case 0: k_project<0><<<(unsigned)blocks, threads, 0, s>>>(a); break;
-    case 1: k_project<1><<<(unsigned)blocks, threads, 0, s>>>(a); break;
-    case 2: k_project<2><<<(unsigned)blocks, threads, 0, s>>>(a); break;
-    default: k_project<3><<<(unsigned)blocks, threads, 0, s>>>(a); break;
+    case 0: dense ? k_project_dense<0><<<(unsigned)blocks, threads, 0, s>>>(a)
+                  : k_project<0><<<(unsigned)blocks, threads, 0, s>>>(a); break;
+    case 1: dense ? k_project_dense<1><<<(unsigned)blocks, threads, 0, s>>>(a)
+                  : k_project<1><<<(unsigned)blocks, threads, 0, s>>>(a); break;
+    case 2: dense ? k_project_dense<2><<<(unsigned)blocks, threads, 0, s>>>(a)
+                  : k_project<2><<<(unsigned)blocks, threads, 0, s>>>(a); break;
+    default: dense ? k_project_dense<3><<<(unsigned)blocks, threads, 0, s>>>(a)
+                   : k_project<3><<<(unsigned)blocks, threads, 0, s>>>(a); break;
   }
   return launch_status();
 }
