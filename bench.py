@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--smem-batch", type=int, default=0,
                     help="with a fixed --tile: Gaussian records staged per blend batch (rs_config.batch, 0: default)")
+    ap.add_argument("--uneven-views", type=int, default=32,
+                    help="views of the uneven-batch leg (house-scale 3M scene, random resolutions, per-view "
+                         "visibility lists); 0 skips it")
     ap.add_argument("--step-only", action="store_true",
                     help="time the step and stop (no per-stage pass, plain loop, end-to-end or optimiser "
                          "measurements): the command for profiling the step's launches")
@@ -323,6 +326,7 @@ def run_ours(args):
     # roofline of the dominant kernel
     hbm, peak_kind, pk = peaks()
     optim = optimizer_bench(api, N, torch, g, gbuf, h, hbm, reps=10)
+    uneven = uneven_bench(api, N, torch, dev, args.uneven_views, reps=3) if args.uneven_views > 0 else None
     work = kernel_work(vbs, sres, pairs, n_super)
     roof = roofline(kernel_ms, work, hbm, peak_kind, B)
     per_kernel = {k: kernel_frac(k, kernel_ms[k], work, hbm) for k in kernel_ms if k in work}
@@ -355,7 +359,8 @@ def run_ours(args):
             "stage_ms_per_step": {k: round(v, 5) for k, v in stage_ms.items()},
             "kernel_ms_per_step": {k: round(v["ms_per_step"], 5) for k, v in
                                    sorted(kernel_ms.items(), key=lambda kv: -kv[1]["ms_per_step"])},
-            "e2e": e2e, "roofline": roof, "roofline_per_kernel": per_kernel, "optimizer": optim, "cpu_baseline": cpu,
+            "e2e": e2e, "roofline": roof, "roofline_per_kernel": per_kernel, "optimizer": optim,
+            "uneven_batch": uneven, "cpu_baseline": cpu,
             "clocks": clk.summary(),
             "gpu_launches": launches,
         }
@@ -423,6 +428,58 @@ def stage_times(api, N, torch, g, chunks, cfg, st, proj, h, gbuf, loss, ws_sort,
         del r, nonempty, zero, sw, sh
     torch.cuda.synchronize()
     return acc, kernels, {"pairs": pairs, "super_instances": n_super}
+
+
+def uneven_bench(api, N, torch, dev, n_views, reps):
+    """Uneven batch: views of random resolution (320-1920 x 240-1080) of the 3M-Gaussian
+    house-scale scene, each with its own ascending visibility list of 0.2M-2M Gaussians
+    (the first n_views of the 256-view set).  fwd+bwd ms/view (L1 loss per view, gradients
+    summed over views) with the autotuner's tile shape, staging batch and views per launch,
+    against a loop of plain single-view launches.  Includes every stage of the step but
+    the pruning filter."""
+    from paper_2403_13806_gb300 import synth
+    scene, _, _ = synth.config3()
+    cams, subsets = synth.config4(scene, n_views=n_views)   # the first n_views of the 256-view set
+    g = api.Gaussians.from_scene(scene, device=dev)
+    grads = [torch.zeros_like(t) for t in g.tensors()]
+    tune = api.autotune(g, cams, subsets=subsets, backward=True)
+    B = tune["views_per_launch"]
+    cfg = api.config(batch=tune["smem_batch"])
+
+    def make(chunks, tile, cfg_):
+        out = []
+        for i in range(0, len(cams), chunks):
+            vb = api.ViewBatch(cams[i:i + chunks], scene.n, subsets=subsets[i:i + chunks], tile=tile, device=dev)
+            r = api.Rasterizer(cfg=cfg_, device=dev)
+            r.forward(g, vb)   # sizes the capacity
+            out.append((vb, r))
+        return out
+
+    def run(plan):
+        for vb, r in plan:
+            o = r.forward(g, vb)
+            loss, dl = api.l1_loss(o["image"], torch.zeros_like(o["image"]))
+            api.render_backward(g, vb, o["proj"], o["bins"], o["T_final"], o["last"], dl, grads, r.ws_bwd, r.cfg)
+
+    def timed(plan):
+        run(plan)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            run(plan)
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / (reps * len(cams))
+
+    batched = timed(make(B, tune["tile"], cfg))
+    plain = timed(make(1, (16, 16), api.config()))
+    return {"views": len(cams), "pixels": int(sum(c["width"] * c["height"] for c in cams)),
+            "items": int(sum(len(s) for s in subsets)), "tile": f"{tune['tile'][0]}x{tune['tile'][1]}",
+            "smem_batch": tune["smem_batch"], "views_per_launch": B,
+            "batched_ms_per_view": round(batched, 4), "plain_ms_per_view": round(plain, 4),
+            "batched_over_plain_speedup": round(plain / batched, 3),
+            "note": "Rasterizer calls (one host read of the instance count per launch) on both sides"}
 
 
 def optimizer_bench(api, N, torch, g, gbuf, h, hbm, reps):
