@@ -727,12 +727,12 @@ def kernel_work(vbs, sres, pairs, n_super):
         "k_project": (vb.n_gaussians * 236 + M * 52) if (vbs[0].subset is None and vbs[0].n_views > 1)
         else M * (236 + 52),
         "k_depth_keys": M * (4 + 8),
-        "k_upsweep": M * 4,
-        "k_downsweep": M * 16,
         "k_count_blocks": M * (4 + 8),
         "k_emit": M * (4 + 8) + Ks * (kb + 4),
-        "k_tile_hist": Ks * kb,
-        "k_tile_sort": Ks * 2 * (kb + 4),
+        "k_depth_sort_hist": M * 4,
+        "k_depth_sort": M * 16,
+        "k_super_sort_hist": Ks * kb,
+        "k_super_sort": Ks * 2 * (kb + 4),
         "k_ranges": Ks * kb,
         "k_fine_count": Ks * (4 + 8),
         "k_fine_scatter": Ks * (4 + 8) + K * 4,

@@ -610,7 +610,8 @@ static const uint32_t* super_instances(const BinWs& w, const uint32_t* order, in
                                                          w.svals[0]);
   }
   const int cur = tiles::sort_pairs<KeyT>(k0, w.svals[0], k1, w.svals[1], w.counters, cap, bits_for(n_super_max),
-                                          w.sweep, s, true);
+                                          w.sweep, s, true,
+                                          {"k_super_sort_hist", "k_super_sort_scan", "k_super_sort"});
   const KeyT* sk = cur ? k1 : k0;
   prof::Scope ps("k_ranges", s);
   k_ranges<KeyT><<<4 * kNumSMs, 256, 0, s>>>(sk, w.counters, (uint32_t)n_super_max, w.sranges);
@@ -654,7 +655,8 @@ extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* 
       k_depth_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rgb_d, n, w.dkeys[0], w.dvals[0]);
     }
     const int dcur = tiles::sort_pairs<uint32_t>(w.dkeys[0], w.dvals[0], w.dkeys[1], w.dvals[1], w.counters + 6, n, 31,
-                                                 w.hist, s, false);
+                                                 w.hist, s, false,
+                                                 {"k_depth_sort_hist", "k_depth_sort_scan", "k_depth_sort"});
     const uint32_t* order = w.dvals[dcur];
     // 2) super instances in depth order, sorted stably on the super-tile id
     const int64_t nblk = (n + kEmitThreads - 1) / kEmitThreads;

@@ -266,7 +266,8 @@ extern "C" rs_status rs_nn_distance(const float* means, int64_t n, float* dist, 
     k_morton<<<(unsigned)blocks, 256, 0, s>>>(means, n, w.params, w.keys[0], w.vals[0]);
   }
   const int cur = tiles::sort_pairs<uint32_t>(w.keys[0], w.vals[0], w.keys[1], w.vals[1], &w.params->n, n,
-                                              3 * kMortonBits, w.scratch, s, true);
+                                              3 * kMortonBits, w.scratch, s, true,
+                                              {"k_morton_sort_hist", "k_morton_sort_scan", "k_morton_sort"});
   {
     prof::Scope ps("k_sorted_points", s);
     k_sorted_points<<<(unsigned)blocks, 256, 0, s>>>(means, n, w.vals[cur], w.spts);

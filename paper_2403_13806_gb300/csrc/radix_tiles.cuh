@@ -277,9 +277,16 @@ inline size_t scratch_words(int64_t n_max, int tile = kTile) {
 // Stable sort of the first n (device count) pairs on bits [0, bits).  Buffers ping-pong
 // between (k0, v0) and (k1, v1); returns 0 if the result is in (k0, v0), 1 if in (k1, v1).
 // n_max bounds the count (grid sizes and scratch).
+// Names under which the launch tracer records the three kernels of a use of the sort.
+struct SortNames {
+  const char* hist;
+  const char* scan;
+  const char* sort;
+};
+
 template <typename KeyT, int ITEMS = kItems>
 inline int sort_pairs(KeyT* k0, uint32_t* v0, KeyT* k1, uint32_t* v1, const uint32_t* n_dev, int64_t n_max, int bits,
-                      uint32_t* scratch, cudaStream_t s, bool write_last_keys = true) {
+                      uint32_t* scratch, cudaStream_t s, bool write_last_keys, const SortNames& names) {
   constexpr int TILE = kThreads * ITEMS;
   const int passes = sort_passes(bits);
   const int rbits = (bits + passes - 1) / passes;
@@ -300,14 +307,14 @@ inline int sort_pairs(KeyT* k0, uint32_t* v0, KeyT* k1, uint32_t* v1, const uint
     uint32_t* vo = cur ? v0 : v1;
     const bool last = (p == passes - 1);
     {
-      prof::Scope ps("k_tile_hist", s);
+      prof::Scope ps(names.hist, s);
       k_tile_hist<KeyT, TILE><<<grid_hist, kThreads, 0, s>>>(ki, n_dev, shift, rb, nt, cnt);
     }
     {
-      prof::Scope ps("k_tile_scan", s);
+      prof::Scope ps(names.scan, s);
       k_tile_scan<TILE><<<1 << rb, 1024, 0, s>>>(cnt, n_dev, nt, tot);
     }
-    prof::Scope ps("k_tile_sort", s);
+    prof::Scope ps(names.sort, s);
     k_tile_sort<KeyT, ITEMS><<<grid_sort, kThreads, 0, s>>>(
         ki, vi, (last && !write_last_keys) ? nullptr : ko, vo, n_dev, shift, rb, cnt, nt, tot);
     cur ^= 1;
