@@ -665,7 +665,7 @@ OPS_PER_PAIR = {"k_render_importance": 22, "k_render": 22, "k_render_bwd": 46}
 # of the sources the kernel was built from.  A capture stays valid only while those sources
 # are unchanged; otherwise the roofline reports traffic as null.
 NCU_TRAFFIC = {
-    "k_render_bwd": {"bytes_per_view": 25175040, "files": ['render_bwd.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "f3925b9d4fc890bf",
+    "k_render_bwd": {"bytes_per_view": 25184256, "files": ['render_bwd.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "f50bf20b9822d499",
                 "profile": "k_render_bwd_1M_1view.md"},
     "k_render_importance": {"bytes_per_view": 5254400, "files": ['render.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "ce077fcbd7e1da48",
                 "profile": "k_render_1M_1view.md"},
