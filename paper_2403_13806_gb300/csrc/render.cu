@@ -123,11 +123,11 @@ __global__ void __launch_bounds__(TW* TH / PX) k_render(RenderArgs a) {
         st[2 * q] = al.in0 && !ok0;   // stop before compositing this entry
         st[2 * q + 1] = al.in1 && !ok1;
         stop |= st[2 * q] | st[2 * q + 1];
-        float2 w = __fmul2_rn(al.alpha, T[q]);
-        w.x = ok0 ? w.x : 0.f;
-        w.y = ok1 ? w.y : 0.f;
-        T[q].x = ok0 ? Tn.x : T[q].x;
-        T[q].y = ok1 ? Tn.y : T[q].y;
+        // an entry that is not composited gets alpha 0: weight 0 and T(1 - 0) = T exactly, so
+        // one select per pixel replaces the weight and transmittance selects
+        const float2 a_eff = make_float2(ok0 ? al.alpha.x : 0.f, ok1 ? al.alpha.y : 0.f);
+        const float2 w = __fmul2_rn(a_eff, T[q]);
+        T[q] = __fmul2_rn(T[q], one_minus(a_eff));
         cr[q] = __ffma2_rn(w, lo2(r.rg), cr[q]);
         cg[q] = __ffma2_rn(w, hi2(r.rg), cg[q]);
         cb[q] = __ffma2_rn(w, lo2(r.bc), cb[q]);
