@@ -601,56 +601,102 @@ def plain_loop(api, N, torch, g, vb1, cfg, target, cams, reps, dev, loss_fn):
 
 
 def e2e_run(api, N, torch, scene, vbs, cfg, targets, cap, reps, dev, world=1, loss_fn=None):
-    """Same batched step through the public API, parameters and targets copied from pinned
-    host memory each step, the loss read back to the host (with the reductions over ranks
-    when world > 1)."""
+    """Same batched step through the public API (an api.StepGraph per input buffer set):
+    every step copies its parameters and targets from pinned host memory and reads its loss
+    back to the host.  The copies of step k+1 run on a copy stream while step k computes
+    (two device buffer sets, events order each buffer's reuse), as a training loop's input
+    pipeline would; with world > 1 the reductions over ranks follow each graph."""
     from paper_2403_13806_gb300 import dist as rd
     host = [torch.from_numpy(np.ascontiguousarray(a, np.float32)).pin_memory() for a in scene.arrays()]
     tgt_h = [t.cpu().pin_memory() for t in targets]
-    dev_p = [torch.empty_like(t, device=dev) for t in host]
-    tgt_d = [torch.empty_like(t) for t in targets]
-    g = api.Gaussians(*dev_p, scene.sh_degree)
     st = api.DeviceStatus(dev)
     proj = api.Projected.empty(max(vb.n_items for vb in vbs), dev)
     bins_all = api.Bins.empty(cap, max(vb.n_tiles for vb in vbs), device=dev)
     ws_sort, ws_bwd, ws_f = api.Workspace(dev), api.Workspace(dev), api.Workspace(dev)
     h = torch.zeros(scene.n, dtype=torch.int32, device=dev)
-    gbuf = rd.GradBuffer(dev_p)
     loss_h = torch.zeros(len(vbs), dtype=torch.float64).pin_memory()
     loss_d = torch.zeros(len(vbs), dtype=torch.float64, device=dev)
+    img_buf = [torch.empty(3 * vb.n_pixels, device=dev) for vb in vbs]
+    T_buf = [torch.empty(vb.n_pixels, device=dev) for vb in vbs]
+    L_buf = [torch.empty(vb.n_pixels, dtype=torch.int32, device=dev) for vb in vbs]
+    dl_buf = [torch.empty(3 * vb.n_pixels, device=dev) for vb in vbs]
+    mask = torch.empty(scene.n, dtype=torch.uint8, device=dev)
+    idx = torch.empty(scene.n, dtype=torch.int32, device=dev)
 
-    def step():
-        for d, s in zip(dev_p, host):
-            d.copy_(s, non_blocking=True)
-        for d, s in zip(tgt_d, tgt_h):
-            d.copy_(s, non_blocking=True)
-        h.zero_()
-        gbuf.zero_()
-        for i, vb in enumerate(vbs):
-            bins = api.Bins(bins_all.vals, bins_all.ranges[:vb.n_tiles], None, cap)
-            api.project(g, vb, cfg, st, out=proj)
-            api.bin_sort(proj, vb, bins, ws_sort, st)
-            img, T, L = api.render(proj, bins, vb, cfg, importance=h)
-            loss, dl = loss_fn(img, tgt_d[i], loss=loss_d[i:i + 1])
-            api.render_backward(g, vb, proj, bins, T, L, dl, gbuf.views, ws_bwd, cfg)
+    def make_set():
+        dev_p = [torch.empty_like(t, device=dev) for t in host]
+        tgt_d = [torch.empty_like(t) for t in targets]
+        for d, s_ in zip(dev_p, host):
+            d.copy_(s_)
+        for d, s_ in zip(tgt_d, tgt_h):
+            d.copy_(s_)
+        g = api.Gaussians(*dev_p, scene.sh_degree)
+        gbuf = rd.GradBuffer(dev_p)
+
+        def views_part():
+            h.zero_()
+            gbuf.zero_()
+            for i, vb in enumerate(vbs):
+                bins = api.Bins(bins_all.vals, bins_all.ranges[:vb.n_tiles], None, cap)
+                api.project(g, vb, cfg, st, out=proj)
+                api.bin_sort(proj, vb, bins, ws_sort, st)
+                img, T, L = api.render(proj, bins, vb, cfg, image=img_buf[i], T_final=T_buf[i], last=L_buf[i],
+                                       importance=h)
+                loss, dl = loss_fn(img, tgt_d[i], dL=dl_buf[i], loss=loss_d[i:i + 1])
+                api.render_backward(g, vb, proj, bins, T, L, dl, gbuf.views, ws_bwd, cfg)
+
+        def prune():
+            api.filter(h, 0.01, N.RS_PRUNE_BELOW, ws_f, mask=mask, idx=idx)
+
+        if world == 1:
+            sg = api.StepGraph(lambda: (views_part(), prune()), outputs=[(loss_d, loss_h)], device=dev)
+        else:
+            sg = api.StepGraph(views_part, device=dev)
+        return {"p": dev_p, "t": tgt_d, "sg": sg, "gbuf": gbuf, "prune": prune}
+
+    sets = [make_set(), make_set()]
+    copy_stream = torch.cuda.Stream(device=dev)
+    comp = torch.cuda.current_stream(dev)
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    used = [torch.cuda.Event(), torch.cuda.Event()]
+
+    def copy_in(k):
+        b = sets[k % 2]
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(used[k % 2])   # the previous step on this buffer set is done
+            for d, s_ in zip(b["p"], host):
+                d.copy_(s_, non_blocking=True)
+            for d, s_ in zip(b["t"], tgt_h):
+                d.copy_(s_, non_blocking=True)
+            copied[k % 2].record(copy_stream)
+
+    def step(k):
+        b = sets[k % 2]
+        copy_in(k + 1)                 # the next step's inputs, behind this step's compute
+        comp.wait_event(copied[k % 2])
+        b["sg"].launch()
         if world > 1:
             rd.allreduce_importance(h)
-            rd.allreduce_grads(gbuf)
-        api.filter(h, 0.01, N.RS_PRUNE_BELOW, ws_f)
-        loss_h.copy_(loss_d, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+            rd.allreduce_grads(b["gbuf"])
+            b["prune"]()
+            loss_h.copy_(loss_d, non_blocking=True)
+        used[k % 2].record(comp)
+        comp.synchronize()
         return float(loss_h.mean())
 
-    for _ in range(2):
-        step()
+    copy_in(0)
+    for k in range(2):
+        step(k)
     t0 = time.perf_counter()
-    for _ in range(reps):
-        step()
+    for k in range(2, 2 + reps):
+        step(k)
     dt = (time.perf_counter() - t0) / reps * 1000.0
+    torch.cuda.synchronize()
     h2d = sum(t.numel() * 4 for t in host) + sum(t.numel() * 4 for t in targets)
     n_views = sum(vb.n_views for vb in vbs)
     return {"value": round(dt / n_views, 4), "unit": "ms/view (fwd+bwd)", "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": 8 * len(vbs)}
+            "d2h_bytes_per_step": 8 * len(vbs),
+            "input_pipeline": "step k+1's copies overlap step k's compute (two device buffer sets)"}
 
 
 # FP32 lane-operations per second of the GB300: 152 SMs x 128 FP32 lanes x 2070 MHz.

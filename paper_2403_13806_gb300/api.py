@@ -19,7 +19,7 @@ __all__ = ["Gaussians", "ViewBatch", "Projected", "Bins", "DeviceStatus", "Works
            "bin_sort", "render", "importance", "filter", "nearest", "render_backward", "Rasterizer",
            "RadSplatFunction", "split_images", "importance_as_float", "autotune", "TILE_SHAPES", "blend_threads", "adam_step",
            "gather_columns", "ssim_loss", "PAPER_LAMBDA", "kmeans", "nn_distance",
-           "init_log_scales"]
+           "init_log_scales", "StepGraph"]
 
 PAPER_LAMBDA = 0.2   # weight of the SSIM term in the loss of Sec. 3.2
 
@@ -411,6 +411,56 @@ def gather_columns(pairs: Sequence[tuple], idx: torch.Tensor, count: torch.Tenso
         rows = src.shape[0] if src.dim() == 2 else 1
         arr[i] = N.RsGatherDesc(src.data_ptr(), dst.data_ptr(), rows, src.shape[-1], dst.shape[-1])
     N.call("rs_gather_columns", arr, len(pairs), _ptr(idx), _ptr(count), int(max_count), _stream(stream))
+
+
+class StepGraph:
+    """A step repeated with fixed buffers, captured once as a CUDA graph: the host-to-device
+    copies of its inputs from pinned host memory, the library calls `body` enqueues, and the
+    device-to-host copies of its outputs; `run()` replays it (one graph launch) and waits.
+
+    inputs: (pinned host tensor, device tensor) pairs copied in before the body;
+    outputs: (device tensor, pinned host tensor) pairs copied out after it.  The body must
+    not synchronise the host (every library hot call qualifies) and must use the current
+    stream.  Capacity-dependent calls (bin_sort) need their capacity sized beforehand."""
+
+    def __init__(self, body, inputs=(), outputs=(), warmup: int = 2, device=None):
+        self.body, self.inputs, self.outputs = body, list(inputs), list(outputs)
+        for h, d in self.inputs:
+            if not h.is_pinned():
+                raise ValueError("inputs must come from pinned host memory")
+        for d, h in self.outputs:
+            if not h.is_pinned():
+                raise ValueError("outputs must go to pinned host memory")
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        torch.cuda.synchronize(dev)
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            for _ in range(max(warmup, 1)):   # allocations and lazy initialisation happen here
+                self._enqueue()
+        torch.cuda.current_stream(dev).wait_stream(side)
+        torch.cuda.synchronize(dev)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self._enqueue()
+        torch.cuda.synchronize(dev)
+        self.device = dev
+
+    def _enqueue(self):
+        for h, d in self.inputs:
+            d.copy_(h, non_blocking=True)
+        self.body()
+        for d, h in self.outputs:
+            h.copy_(d, non_blocking=True)
+
+    def launch(self):
+        """Enqueue one replay on the current stream without waiting (for callers that
+        order it against their own streams, e.g. an input pipeline on a copy stream)."""
+        self.graph.replay()
+
+    def run(self):
+        self.launch()
+        torch.cuda.current_stream(self.device).synchronize()
 
 
 def split_images(flat: torch.Tensor, vb: ViewBatch) -> List[torch.Tensor]:
