@@ -758,11 +758,11 @@ def kernel_work(vbs, sres, pairs, n_super):
     projection reads 236 B of parameters per Gaussian (per item for visibility lists) and
     writes 52 B per item; the depth sort moves
     8 B per item and pass (read key+value, write key+value = 16 B in the scatter, 4 B read in
-    the count); the super-tile sort moves 2 x (2 + 4) B per super instance and pass (count:
-    2 B); the fine partition reads 4 B index + 8 B rect per super instance (twice: count and
-    scatter) and writes 4 B per instance; the projection backward reads 236 B and writes
-    236 B per Gaussian (read-modify-write) plus 52 B per item; the blend kernels count FP32
-    operations per evaluated pair."""
+    the count); the super-tile sort moves 2 x (2 + 4 + 1) B per super instance and pass
+    (count: 2 B); the fine partition reads the 1 B cover byte per super instance (count),
+    then 4 B item + 1 B cover byte per super instance and writes 4 B per instance (scatter);
+    the projection backward reads 236 B and writes 236 B per Gaussian (read-modify-write)
+    plus 52 B per item; the blend kernels count FP32 operations per evaluated pair."""
     vb = _PerLaunch(vbs)
     c = vb.launches
     M, K, Ks, P = vb.n_items, sres["n_instances"], n_super / c, vb.n_pixels
@@ -774,14 +774,14 @@ def kernel_work(vbs, sres, pairs, n_super):
         else M * (236 + 52),
         "k_depth_keys": M * (4 + 8),
         "k_count_blocks": M * (4 + 8),
-        "k_emit": M * (4 + 8) + Ks * (kb + 4),
+        "k_emit": M * (4 + 8) + Ks * (kb + 4 + 1),
         "k_depth_sort_hist": M * 4,
         "k_depth_sort": M * 16,
         "k_super_sort_hist": Ks * kb,
-        "k_super_sort": Ks * 2 * (kb + 4),
+        "k_super_sort": Ks * 2 * (kb + 4 + 1),
         "k_ranges": Ks * kb,
-        "k_fine_count": Ks * (4 + 8),
-        "k_fine_scatter": Ks * (4 + 8) + K * 4,
+        "k_fine_count": Ks * 1,
+        "k_fine_scatter": Ks * (4 + 1) + K * 4,
         "k_l1": P * 3 * 4 * 3,
         "k_ssim_stats": P * 3 * (8 + 12),
         "k_ssim_grad": P * 3 * (12 + 8 + 4),

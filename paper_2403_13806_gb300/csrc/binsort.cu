@@ -8,12 +8,16 @@
 //   2. the tile id is split into a coarse digit -- the super-tile of 4 x 4 tiles that holds
 //      the tile -- and a fine one.  Items are duplicated once per super-tile their rect
 //      touches (about 7x fewer instances than tiles at the workload sizes) and those
-//      instances are radix-sorted stably on the super-tile id (one pass per 8 bits);
-//   3. the fine digit is one stable counting pass per super-tile: 8 CTAs share each
-//      super-tile's depth-ordered list in equal segments and, for each of its 4 x 4 tiles,
-//      keep the items whose rect covers that tile -- once to count them (exclusive scans over
-//      the segments and over all tiles then give every tile its range and every segment its
-//      first position in it), once to write them, contiguously and in order.
+//      instances are radix-sorted stably on the super-tile id (one pass per 8 bits); each
+//      carries one byte, the part of the super-tile's 4 x 4 tiles its rect covers, so the
+//      fine kernels below read their lists sequentially and gather nothing;
+//   3. the fine digit is one stable counting pass per super-tile: each super-tile's
+//      depth-ordered list is cut into segments of kSegLen entries (work in proportion to the
+//      list, however unevenly the items fall on the super-tiles), and a CTA per segment
+//      keeps, for each of the 4 x 4 tiles, the items whose rect covers that tile -- once to
+//      count them (exclusive scans over the segments and over all tiles then give every tile
+//      its range and every segment its first position in it), once to write them,
+//      contiguously and in order.
 // Every tile's list therefore holds its items by depth, ties to the lower item: exactly the
 // order of the stable 64-bit sort.  The 64-bit keys are written only on request.
 //
@@ -21,8 +25,9 @@
 //   k_super_layout (super-tile bases per view); k_depth_keys, 4 depth passes over the items
 //   (radix_tiles, 31-bit keys);
 //   k_count_blocks, k_count_top (super total); k_emit (super instances); super passes
-//   (radix_tiles); k_ranges (super ranges); k_fine_count; k_fine_seg_scan; k_fine_scan
-//   (ranges, K, capacity check); k_fine_scatter (vals, optional keys).
+//   (radix_tiles); k_ranges (super ranges); k_fine_layout (segments); k_fine_count;
+//   k_fine_seg_scan; k_fine_scan (ranges, K, capacity check); k_fine_scatter (vals,
+//   optional keys).
 #include "profile.cuh"
 #include "radix_tiles.cuh"
 #include "radsplat.h"
@@ -33,7 +38,7 @@ namespace rs {
 constexpr int kEmitThreads = 256;
 constexpr int kSuper = 4;           // tiles per super-tile side
 constexpr int kFineThreads = 256;   // threads of a fine-binning CTA
-constexpr int kSegs = 8;            // CTAs per super-tile list (equal segments) in the fine binning
+constexpr int kSegLen = 2048;       // super-list entries per fine work item (segment)
 constexpr int kNF = kSuper * kSuper;
 
 struct BinWs {
@@ -42,15 +47,19 @@ struct BinWs {
   unsigned long long* bsum;   // per emission block: super instances, then exclusive prefix
   char* skeys[2];             // super-tile ids (uint16 or uint32)
   uint32_t* svals[2];         // items
+  uint8_t* saux[2];           // covered part of the super-tile (cover_byte)
   uint32_t* hist;             // per-tile digit counters of the item (depth) sort
   uint32_t* sweep;            // per-tile digit counters of the super-instance sort
   uint32_t* sranges;          // [n_tiles][2]: super-tile ranges (super-tiles never outnumber tiles)
   uint32_t* super_base;       // [n_views + 1]
   uint32_t* fine_tot;         // [n_tiles]: instances per tile, then first position
-  uint32_t* seg_cnt;          // [n_tiles][kSegs][16]: per (super-tile, segment, tile) counts, then prefixes
+  uint32_t* seg_off;          // [n_tiles + 1]: first segment of every super-tile, then the total
+  uint32_t* work_s;           // [n_work_max]: super-tile of every segment
+  uint32_t* seg_cnt;          // [n_work_max][16]: per (segment, tile) counts, then prefixes
+  int64_t n_work_max;         // segments: at most capacity / kSegLen + one per super-tile
   uint32_t* counters;         // [0] super instances written, [2] instances written,
                               // [4], [5] work counters of the fine count and scatter,
-                              // [6] item count (the depth sort's device count)
+                              // [6] item count (the depth sort's device count), [7] segments
   size_t bytes;
 };
 
@@ -70,12 +79,16 @@ static BinWs bin_ws_layout(void* base, int64_t n_items, int64_t capacity, int n_
   w.bsum = reinterpret_cast<unsigned long long*>(take((size_t)(nblk > 0 ? nblk : 1) * 8));
   for (int i = 0; i < 2; ++i) w.skeys[i] = take(cap * 4);
   for (int i = 0; i < 2; ++i) w.svals[i] = reinterpret_cast<uint32_t*>(take(cap * 4));
+  for (int i = 0; i < 2; ++i) w.saux[i] = reinterpret_cast<uint8_t*>(take(cap));
   w.hist = reinterpret_cast<uint32_t*>(take(tiles::scratch_words(n_items) * 4));
   w.sweep = reinterpret_cast<uint32_t*>(take(tiles::scratch_words(capacity) * 4));
   w.sranges = reinterpret_cast<uint32_t*>(take((size_t)(n_tiles > 0 ? n_tiles : 1) * 8));
   w.super_base = reinterpret_cast<uint32_t*>(take((size_t)(n_views + 1) * 4));
   w.fine_tot = reinterpret_cast<uint32_t*>(take((size_t)(n_tiles > 0 ? n_tiles : 1) * 4));
-  w.seg_cnt = reinterpret_cast<uint32_t*>(take((size_t)(n_tiles > 0 ? n_tiles : 1) * kSegs * kNF * 4));
+  w.n_work_max = (int64_t)(cap / kSegLen) + (n_tiles > 0 ? n_tiles : 1) + 1;
+  w.seg_off = reinterpret_cast<uint32_t*>(take((size_t)((n_tiles > 0 ? n_tiles : 1) + 1) * 4));
+  w.work_s = reinterpret_cast<uint32_t*>(take((size_t)w.n_work_max * 4));
+  w.seg_cnt = reinterpret_cast<uint32_t*>(take((size_t)w.n_work_max * kNF * 4));
   w.counters = reinterpret_cast<uint32_t*>(take(64));
   w.bytes = off;
   return w;
@@ -116,6 +129,24 @@ __device__ __forceinline__ ushort4 super_rect(ushort4 r) {
   return make_ushort4(r.x / kSuper, r.y / kSuper, (r.z - 1) / kSuper + 1, (r.w - 1) / kSuper + 1);
 }
 
+// The tiles of super-tile (sx, sy) that tile rect r covers, as one byte: first and last
+// covered column (bits 0-1, 2-3) and row (bits 4-5, 6-7) inside its 4 x 4 block.  The rect
+// touches the super-tile and lies inside the view's tile grid, so every field is in 0..3.
+__device__ __forceinline__ uint8_t cover_byte(ushort4 r, int sx, int sy) {
+  const int tx0 = kSuper * sx, ty0 = kSuper * sy;
+  const int lx0 = max((int)r.x - tx0, 0), lx1 = min((int)r.z - 1 - tx0, kSuper - 1);
+  const int ly0 = max((int)r.y - ty0, 0), ly1 = min((int)r.w - 1 - ty0, kSuper - 1);
+  return (uint8_t)(lx0 | (lx1 << 2) | (ly0 << 4) | (ly1 << 6));
+}
+
+// Bit (fy * kSuper + fx) set for every tile of the block that a cover byte covers.
+__device__ __forceinline__ uint32_t cover_mask(uint32_t c) {
+  const int x0 = c & 3, x1 = (c >> 2) & 3, y0 = (c >> 4) & 3, y1 = c >> 6;
+  const uint32_t row = (2u << x1) - (1u << x0);                      // bits x0 .. x1
+  const uint32_t rep = 0x1111u >> (kSuper * (kSuper - 1 - (y1 - y0)));   // y1 - y0 + 1 rows, one bit each
+  return (row * rep) << (kSuper * y0);                               // row repeated on rows y0 .. y1
+}
+
 // Super instances per block of kEmitThreads depth-sorted items.
 __global__ void __launch_bounds__(kEmitThreads) k_count_blocks(const uint32_t* __restrict__ order, int64_t n,
                                                                const ushort4* __restrict__ rect,
@@ -138,7 +169,10 @@ __global__ void __launch_bounds__(kEmitThreads) k_count_blocks(const uint32_t* _
   }
 }
 
-// Exclusive prefix over the block counts (one block) and the super-instance total.
+// Exclusive prefix over the block counts (one block, kScanPer consecutive counts per
+// thread) and the super-instance total.
+constexpr int kScanPer = 4;
+
 __global__ void __launch_bounds__(1024) k_count_top(unsigned long long* __restrict__ bsum, int64_t nblk,
                                                     int64_t capacity, uint32_t* __restrict__ counters,
                                                     rs_device_status* st) {
@@ -147,9 +181,14 @@ __global__ void __launch_bounds__(1024) k_count_top(unsigned long long* __restri
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) s_carry = 0ull;
   __syncthreads();
-  for (int64_t b0 = 0; b0 < nblk; b0 += 1024) {
-    const int64_t b = b0 + threadIdx.x;
-    const unsigned long long v = b < nblk ? bsum[b] : 0ull;
+  for (int64_t b0 = 0; b0 < nblk; b0 += 1024 * kScanPer) {
+    const int64_t b = b0 + (int64_t)threadIdx.x * kScanPer;
+    unsigned long long c[kScanPer], v = 0ull;
+#pragma unroll
+    for (int j = 0; j < kScanPer; ++j) {
+      c[j] = b + j < nblk ? bsum[b + j] : 0ull;
+      v += c[j];
+    }
     unsigned long long x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -169,8 +208,12 @@ __global__ void __launch_bounds__(1024) k_count_top(unsigned long long* __restri
     }
     __syncthreads();
     const unsigned long long carry = s_carry;
-    const unsigned long long excl = carry + (warp ? s_w[warp - 1] : 0ull) + x - v;
-    if (b < nblk) bsum[b] = excl;
+    unsigned long long run = carry + (warp ? s_w[warp - 1] : 0ull) + x - v;
+#pragma unroll
+    for (int j = 0; j < kScanPer; ++j) {
+      if (b + j < nblk) bsum[b + j] = run;
+      run += c[j];
+    }
     __syncthreads();
     if (threadIdx.x == 1023) s_carry = carry + s_w[31];
     __syncthreads();
@@ -185,24 +228,27 @@ __global__ void __launch_bounds__(1024) k_count_top(unsigned long long* __restri
 }
 
 // Expansion into super instances: each warp takes 32 consecutive depth-sorted items and
-// writes their super-tile ids contiguously (row-major inside each super rect); lanes locate
-// the item of their instance by a binary search over the warp's inclusive prefix.
+// writes their super-tile ids, items and cover bytes contiguously (row-major inside each
+// super rect); lanes locate the item of their instance by a binary search over the warp's
+// inclusive prefix.
 template <typename KeyT>
 __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restrict__ order, int64_t n,
                                                        const ushort4* __restrict__ rect,
                                                        const rs_view* __restrict__ views, int n_views,
                                                        const uint32_t* __restrict__ super_base,
                                                        const unsigned long long* __restrict__ bpre, int64_t capacity,
-                                                       KeyT* __restrict__ skeys, uint32_t* __restrict__ svals) {
+                                                       KeyT* __restrict__ skeys, uint32_t* __restrict__ svals,
+                                                       uint8_t* __restrict__ saux) {
   __shared__ uint32_t s_wtot[kEmitThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t i = (int64_t)blockIdx.x * kEmitThreads + threadIdx.x;
   uint32_t item = 0, cnt = 0;
-  ushort4 sr = make_ushort4(0, 0, 0, 0);
+  ushort4 sr = make_ushort4(0, 0, 0, 0), tr = sr;
   int sbase = 0, sw = 0;
   if (i < n) {
     item = order[i];
-    sr = super_rect(rect[item]);
+    tr = rect[item];
+    sr = super_rect(tr);
     cnt = (uint32_t)(sr.z - sr.x) * (uint32_t)(sr.w - sr.y);
     if (cnt) {
       const int v = find_view_by_item(views, n_views, (int64_t)item);
@@ -239,14 +285,20 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
     const int o_sb = __shfl_sync(0xffffffffu, sbase, owner);
     const int o_sw = __shfl_sync(0xffffffffu, sw, owner);
     const uint32_t o_item = __shfl_sync(0xffffffffu, item, owner);
+    const uint32_t o_r01 = __shfl_sync(0xffffffffu, (uint32_t)tr.x | ((uint32_t)tr.y << 16), owner);
+    const uint32_t o_r23 = __shfl_sync(0xffffffffu, (uint32_t)tr.z | ((uint32_t)tr.w << 16), owner);
     if (e < wtot) {
       const uint32_t r = e - o_excl;
       const uint32_t ty = r / (uint32_t)o_rw;
       const uint32_t tx = r - ty * (uint32_t)o_rw;
       const unsigned long long pos = wbase + e;
       if (pos < (unsigned long long)capacity) {
-        skeys[pos] = (KeyT)((uint32_t)o_sb + (uint32_t)(o_y0 + (int)ty) * (uint32_t)o_sw + (uint32_t)(o_x0 + (int)tx));
+        const int sx = o_x0 + (int)tx, sy = o_y0 + (int)ty;
+        skeys[pos] = (KeyT)((uint32_t)o_sb + (uint32_t)sy * (uint32_t)o_sw + (uint32_t)sx);
         svals[pos] = o_item;
+        const ushort4 orr = make_ushort4((unsigned short)(o_r01 & 0xffffu), (unsigned short)(o_r01 >> 16),
+                                         (unsigned short)(o_r23 & 0xffffu), (unsigned short)(o_r23 >> 16));
+        saux[pos] = cover_byte(orr, sx, sy);
       }
     }
   }
@@ -319,28 +371,74 @@ __device__ __forceinline__ SuperTile super_tile(uint32_t S, const rs_view* views
   return t;
 }
 
-// Bit (fy * kSuper + fx) set for every tile of the super-tile's block the rect covers.
-__device__ __forceinline__ uint32_t cover_mask(ushort4 r, const SuperTile& t) {
-  // (x0, y0 clamped to the super-tile so that no shift exceeds its width)
-  const int x0 = min(max((int)r.x - t.tx0, 0), kSuper), x1 = min((int)r.z - t.tx0, t.nx);
-  const int y0 = min(max((int)r.y - t.ty0, 0), kSuper), y1 = min((int)r.w - t.ty0, t.ny);
-  const int k = y1 - y0;                                         // rows covered (<= 0: none)
-  const uint32_t row = (1u << max(x1, x0)) - (1u << x0);          // bits x0 .. x1-1 (0 if empty)
-  const uint32_t rep = k > 0 ? 0x1111u >> (kSuper * (kSuper - k)) : 0u;   // k rows, one bit each
-  return (row * rep) << (kSuper * y0);                            // row repeated on rows y0 .. y1-1
+// Segment j of super-tile S's list: entries [s0 + j kSegLen, s0 + (j + 1) kSegLen) of it.
+__device__ __forceinline__ void segment(const SuperTile& t, uint32_t j, uint32_t& a, uint32_t& b) {
+  a = min(t.s0 + j * (uint32_t)kSegLen, t.s1);
+  b = min(a + (uint32_t)kSegLen, t.s1);
 }
 
-// Segment j of super-tile S's list: kSegs CTAs share each list in equal parts.
-__device__ __forceinline__ void segment(const SuperTile& t, int j, uint32_t& a, uint32_t& b) {
-  const uint32_t len = t.s1 - t.s0;
-  const uint32_t L = (len + kSegs - 1) / kSegs;
-  a = min(t.s0 + (uint32_t)j * L, t.s1);
-  b = min(a + L, t.s1);
+// Segments of the super-tile lists (one CTA): seg_off[S] = first segment of super-tile S
+// (exclusive prefix of ceil(len / kSegLen)), seg_off[n_super] = the total, work_s[w] = the
+// super-tile of segment w, counters[7] = the number of segments (the fine work items).
+__global__ void __launch_bounds__(1024) k_fine_layout(const uint32_t* __restrict__ super_base, int n_views,
+                                                      const uint32_t* __restrict__ sranges,
+                                                      uint32_t* __restrict__ seg_off, uint32_t* __restrict__ work_s,
+                                                      int64_t n_work_max, uint32_t* __restrict__ counters) {
+  __shared__ uint32_t s_w[32];
+  __shared__ uint32_t s_carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n_super = (int)super_base[n_views];
+  if (threadIdx.x == 0) s_carry = 0u;
+  __syncthreads();
+  for (int b0 = 0; b0 < n_super; b0 += 4 * 1024) {
+    const int b = b0 + 4 * (int)threadIdx.x;
+    uint32_t v[4], sum = 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      v[j] = (b + j < n_super) ? (sranges[2 * (b + j) + 1] - sranges[2 * (b + j)] + kSegLen - 1) / kSegLen : 0u;
+      sum += v[j];
+    }
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = s_w[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      s_w[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = s_carry + (warp ? s_w[warp - 1] : 0u) + x - sum;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (b + j < n_super) {
+        seg_off[b + j] = run;
+        for (uint32_t k = 0; k < v[j]; ++k)
+          if ((int64_t)(run + k) < n_work_max) work_s[run + k] = (uint32_t)(b + j);
+      }
+      run += v[j];
+    }
+    __syncthreads();
+    if (threadIdx.x == 1023) s_carry += s_w[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    seg_off[n_super] = s_carry;
+    counters[7] = (uint32_t)min((int64_t)s_carry, n_work_max);
+  }
 }
 
-// Work items of the fine kernels are (super-tile, segment) pairs, handed out in order from a
-// device counter to a grid of at most a few CTAs per SM (the number of super-tiles is only
-// known on the device).  Every thread of the CTA receives the same item.
+// Work items of the fine kernels are the segments, handed out in order from a device counter
+// to a grid of at most a few CTAs per SM (their number is only known on the device).  Every
+// thread of the CTA receives the same item.
 __device__ __forceinline__ uint32_t next_work(uint32_t* ctr, uint32_t* s_slot) {
   __syncthreads();   // the previous item's use of shared memory is over
   if (threadIdx.x == 0) *s_slot = atomicAdd(ctr, 1u);
@@ -348,64 +446,83 @@ __device__ __forceinline__ uint32_t next_work(uint32_t* ctr, uint32_t* s_slot) {
   return *s_slot;
 }
 
-// Instances per (super-tile, segment, tile): each work item reads one segment of its
+// Instances per (segment, tile): each work item reads the cover bytes of one segment of a
 // super-tile's depth-ordered list once and counts, for each of the 4 x 4 tiles, the items
-// covering it.
-__global__ void __launch_bounds__(kFineThreads) k_fine_count(const uint32_t* __restrict__ svals,
-                                                             const ushort4* __restrict__ rect,
+// covering it.  A thread keeps its counts as 16 four-bit fields in two words (it sees at
+// most kSegLen / kFineThreads < 16 entries of a segment) and adds one shared-memory table
+// row per entry -- the cover byte's tiles as ones in their fields -- so an entry costs a
+// load and two adds; the fields are unpacked and summed over the CTA once per segment.
+static_assert(kSegLen / kFineThreads < 16, "four-bit per-thread tile counts");
+
+__global__ void __launch_bounds__(kFineThreads) k_fine_count(const uint8_t* __restrict__ saux,
                                                              const rs_view* __restrict__ views, int n_views,
                                                              const uint32_t* __restrict__ super_base,
                                                              const uint32_t* __restrict__ sranges,
+                                                             const uint32_t* __restrict__ seg_off,
+                                                             const uint32_t* __restrict__ work_s,
+                                                             const uint32_t* __restrict__ n_work_dev,
                                                              uint32_t* __restrict__ seg_cnt, uint32_t* __restrict__ ctr) {
   constexpr int NW = kFineThreads / 32;
+  __shared__ uint2 s_tab[256];   // cover byte -> (tiles 0-7, tiles 8-15) as four-bit ones
   __shared__ uint32_t s_cnt[NW][kNF];
   __shared__ uint32_t s_w;
-  const uint32_t n_work = super_base[n_views] * (uint32_t)kSegs;
+  for (int c = threadIdx.x; c < 256; c += kFineThreads) {
+    const uint32_t m = cover_mask((uint32_t)c);
+    uint32_t lo = 0u, hi = 0u;
+#pragma unroll
+    for (int f = 0; f < 8; ++f) {
+      lo |= ((m >> f) & 1u) << (4 * f);
+      hi |= ((m >> (f + 8)) & 1u) << (4 * f);
+    }
+    s_tab[c] = make_uint2(lo, hi);
+  }
+  const uint32_t n_work = *n_work_dev;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint32_t wi = next_work(ctr, &s_w); wi < n_work; wi = next_work(ctr, &s_w)) {
-    const uint32_t S = wi / kSegs;
-    const int j = wi % kSegs;
+    const uint32_t S = work_s[wi];
+    const uint32_t j = wi - seg_off[S];
     const SuperTile t = super_tile(S, views, n_views, super_base, sranges);
     uint32_t a, b;
     segment(t, j, a, b);
-    uint32_t c[kNF];
+    uint32_t lo = 0u, hi = 0u;
+    constexpr int U = kSegLen / kFineThreads;   // every load of the segment in flight at once
+    uint32_t cb[U];
 #pragma unroll
-    for (int f = 0; f < kNF; ++f) c[f] = 0u;
-    constexpr int U = 4;   // independent loads in flight per thread
-    for (uint32_t e0 = a; e0 < b; e0 += U * kFineThreads) {
-      ushort4 rr[U];
+    for (int u = 0; u < U; ++u) {
+      const uint32_t e = a + u * kFineThreads + threadIdx.x;
+      cb[u] = e < b ? (uint32_t)__ldcs(saux + e) : 0x100u;   // 0x100: past the segment
+    }
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const uint32_t e = e0 + u * kFineThreads + threadIdx.x;
-        rr[u] = e < b ? rect[svals[e]] : make_ushort4(0, 0, 0, 0);
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const uint32_t m = cover_mask(rr[u], t);
-#pragma unroll
-        for (int f = 0; f < kNF; ++f) c[f] += __popc(__ballot_sync(0xffffffffu, (m >> f) & 1u));
+    for (int u = 0; u < U; ++u) {
+      if (cb[u] < 0x100u) {
+        const uint2 r = s_tab[cb[u]];
+        lo += r.x;
+        hi += r.y;
       }
     }
-    if (lane < kNF) {
-      uint32_t mine = 0;
+    uint32_t mine = 0u;
 #pragma unroll
-      for (int f = 0; f < kNF; ++f) mine = (lane == f) ? c[f] : mine;
-      s_cnt[warp][lane] = mine;
+    for (int f = 0; f < kNF; ++f) {
+      const uint32_t v = ((f < 8 ? lo : hi) >> (4 * (f & 7))) & 15u;
+      const uint32_t tot = __reduce_add_sync(0xffffffffu, v);
+      mine = (lane == f) ? tot : mine;
     }
+    if (lane < kNF) s_cnt[warp][lane] = mine;
     __syncthreads();
     if (threadIdx.x < kNF) {
       uint32_t tot = 0;
 #pragma unroll
       for (int w = 0; w < NW; ++w) tot += s_cnt[w][threadIdx.x];
-      seg_cnt[((int64_t)S * kSegs + j) * kNF + threadIdx.x] = tot;
+      seg_cnt[(int64_t)wi * kNF + threadIdx.x] = tot;
     }
   }
 }
 
 // One thread per tile: exclusive prefix of its counts over its super-tile's segments (in
-// place) and the tile's total.
+// place, four segments' loads at a time) and the tile's total.
 __global__ void k_fine_seg_scan(uint32_t* __restrict__ seg_cnt, const rs_view* __restrict__ views, int n_views,
-                                const uint32_t* __restrict__ super_base, int n_tiles, uint32_t* __restrict__ fine_tot) {
+                                const uint32_t* __restrict__ super_base, const uint32_t* __restrict__ seg_off,
+                                int n_tiles, uint32_t* __restrict__ fine_tot) {
   const int T = blockIdx.x * blockDim.x + threadIdx.x;
   if (T >= n_tiles) return;
   const int v = find_view_by_tile(views, n_views, T);
@@ -414,13 +531,17 @@ __global__ void k_fine_seg_scan(uint32_t* __restrict__ seg_cnt, const rs_view* _
   const int ty = local / cam.tiles_x, tx = local - ty * cam.tiles_x;
   const uint32_t S = super_base[v] + (uint32_t)((ty / kSuper) * super_w(cam) + tx / kSuper);
   const int f = (ty % kSuper) * kSuper + tx % kSuper;
+  const uint32_t w0 = seg_off[S], w1 = seg_off[S + 1];
   uint32_t run = 0;
+  for (uint32_t w = w0; w < w1; w += 4) {
+    uint32_t x[4];
 #pragma unroll
-  for (int j = 0; j < kSegs; ++j) {
-    uint32_t* c = seg_cnt + ((int64_t)S * kSegs + j) * kNF + f;
-    const uint32_t x = *c;
-    *c = run;
-    run += x;
+    for (int k = 0; k < 4; ++k) x[k] = w + k < w1 ? seg_cnt[(int64_t)(w + k) * kNF + f] : 0u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (w + k < w1) seg_cnt[(int64_t)(w + k) * kNF + f] = run;
+      run += x[k];
+    }
   }
   fine_tot[T] = run;
 }
@@ -436,12 +557,12 @@ __global__ void __launch_bounds__(1024) k_fine_scan(uint32_t* __restrict__ tot, 
   const unsigned long long cap = (unsigned long long)capacity;
   if (threadIdx.x == 0) s_carry = 0ull;
   __syncthreads();
-  for (int b0 = 0; b0 < n_tiles; b0 += 4 * 1024) {
-    const int b = b0 + 4 * (int)threadIdx.x;
-    uint32_t v[4];
+  for (int b0 = 0; b0 < n_tiles; b0 += kScanPer * 1024) {
+    const int b = b0 + kScanPer * (int)threadIdx.x;
+    uint32_t v[kScanPer];
     unsigned long long sum = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < kScanPer; ++j) {
       v[j] = (b + j < n_tiles) ? tot[b + j] : 0u;
       sum += v[j];
     }
@@ -465,7 +586,7 @@ __global__ void __launch_bounds__(1024) k_fine_scan(uint32_t* __restrict__ tot, 
     __syncthreads();
     unsigned long long run = s_carry + (warp ? s_w[warp - 1] : 0ull) + x - sum;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < kScanPer; ++j) {
       if (b + j < n_tiles) {
         const unsigned long long e = run + v[j];
         tot[b + j] = (uint32_t)(run < 0xffffffffull ? run : 0xffffffffull);
@@ -491,30 +612,47 @@ __global__ void __launch_bounds__(1024) k_fine_scan(uint32_t* __restrict__ tot, 
 
 // Every tile's items, in its super-tile list order, written contiguously: each CTA takes one
 // segment of a super-tile's list and writes, for each of its tiles, the covering items from
-// that tile's first position plus the counts of the earlier segments (order-preserving
-// compaction with warp ballots).
+// that tile's first position plus the counts of the earlier segments.  Per chunk of
+// kFineThreads entries, an entry's rank among the warp's entries covering tile f is byte f of
+// a warp-wide exclusive scan of 16-byte vectors (a shared-memory table row per cover byte:
+// byte f = 1 if the entry covers tile f; no byte exceeds 32), the warps' totals give each
+// (warp, tile) its first position, and each entry then stores its item once per tile it
+// covers.  KEYS: also write the 64-bit (tile << 32 | depth bits) keys.
+template <bool KEYS>
 __global__ void __launch_bounds__(kFineThreads) k_fine_scatter(const uint32_t* __restrict__ svals,
-                                                               const ushort4* __restrict__ rect,
+                                                               const uint8_t* __restrict__ saux,
                                                                const float4* __restrict__ rgb_d,
                                                                const rs_view* __restrict__ views, int n_views,
                                                                const uint32_t* __restrict__ super_base,
                                                                const uint32_t* __restrict__ sranges,
                                                                const uint32_t* __restrict__ fine_start,
+                                                               const uint32_t* __restrict__ seg_off,
+                                                               const uint32_t* __restrict__ work_s,
+                                                               const uint32_t* __restrict__ n_work_dev,
                                                                const uint32_t* __restrict__ seg_pre, int64_t capacity,
                                                                uint32_t* __restrict__ vals,
                                                                unsigned long long* __restrict__ keys,
                                                                uint32_t* __restrict__ ctr) {
   constexpr int NW = kFineThreads / 32;
-  __shared__ uint32_t s_bal[NW][kNF];     // per-warp ballot of each tile
-  __shared__ uint32_t s_base[NW][kNF];    // first position of each (warp, tile) in this chunk
-  __shared__ uint32_t s_run[kNF];         // next position of each tile
-  __shared__ uint32_t s_tile[kNF];        // global id of each tile
+  __shared__ uint4 s_tab[256];                       // cover byte -> byte f = covers tile f
+  __shared__ uint4 s_wtot[NW];                       // per warp: covering entries per tile (bytes)
+  __shared__ __align__(16) uint32_t s_base[NW][kNF];   // first position of each (warp, tile) in this chunk
+  __shared__ uint32_t s_run[kNF];                    // next position of each tile
+  __shared__ uint32_t s_tile[kNF];                   // global id of each tile
   __shared__ uint32_t s_w;
-  const uint32_t n_work = super_base[n_views] * (uint32_t)kSegs;
+  for (int c = threadIdx.x; c < 256; c += kFineThreads) {
+    const uint32_t m = cover_mask((uint32_t)c);
+    uint32_t wd[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int f = 0; f < kNF; ++f) wd[f >> 2] |= ((m >> f) & 1u) << (8 * (f & 3));
+    s_tab[c] = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+  }
+  const uint32_t n_work = *n_work_dev;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t cap = (uint32_t)(capacity < 0xffffffffLL ? capacity : 0xffffffffLL);
   for (uint32_t wi = next_work(ctr, &s_w); wi < n_work; wi = next_work(ctr, &s_w)) {
-    const uint32_t S = wi / kSegs;
-    const int j = wi % kSegs;
+    const uint32_t S = work_s[wi];
+    const uint32_t j = wi - seg_off[S];
     const SuperTile t = super_tile(S, views, n_views, super_base, sranges);
     uint32_t a, b;
     segment(t, j, a, b);
@@ -524,63 +662,77 @@ __global__ void __launch_bounds__(kFineThreads) k_fine_scatter(const uint32_t* _
       const bool in = fx < t.nx && fy < t.ny;
       const uint32_t T = in ? (uint32_t)(cam.tile_base + (t.ty0 + fy) * cam.tiles_x + t.tx0 + fx) : 0u;
       s_tile[f] = T;
-      s_run[f] = in ? fine_start[T] + seg_pre[((int64_t)S * kSegs + j) * kNF + f] : 0u;
+      s_run[f] = in ? fine_start[T] + seg_pre[(int64_t)wi * kNF + f] : 0u;
     }
-    const uint32_t cap = (uint32_t)(capacity < 0xffffffffLL ? capacity : 0xffffffffLL);
-    const unsigned lt = (1u << lane) - 1u;
-    // the next chunk's item and rect are fetched while the current one is placed
-    uint32_t n_item = 0;
-    ushort4 n_rect = make_ushort4(0, 0, 0, 0);
+    // the next chunk's item and cover byte are fetched while the current one is placed
+    uint32_t n_item = 0, n_cb = 0x100u;   // 0x100: past the segment, covers nothing
     if (a + threadIdx.x < b) {
-      n_item = svals[a + threadIdx.x];
-      n_rect = rect[n_item];
+      n_item = __ldcs(svals + a + threadIdx.x);
+      n_cb = __ldcs(saux + a + threadIdx.x);
     }
     for (uint32_t e0 = a; e0 < b; e0 += kFineThreads) {
       const uint32_t item = n_item;
-      const uint32_t m = cover_mask(n_rect, t);
+      const uint32_t cb = n_cb;
       const uint32_t en = e0 + kFineThreads + threadIdx.x;
       n_item = 0;
-      n_rect = make_ushort4(0, 0, 0, 0);   // past the segment: covers nothing
+      n_cb = 0x100u;
       if (en < b) {
-        n_item = svals[en];
-        n_rect = rect[n_item];
+        n_item = __ldcs(svals + en);
+        n_cb = __ldcs(saux + en);
       }
-      uint32_t my_bal = 0;
-  #pragma unroll
-      for (int f = 0; f < kNF; ++f) {
-        const unsigned bl = __ballot_sync(0xffffffffu, (m >> f) & 1u);
-        my_bal = (lane == f) ? bl : my_bal;
+      const uint4 own = cb < 0x100u ? s_tab[cb] : make_uint4(0u, 0u, 0u, 0u);
+      uint4 x = own;   // inclusive byte-wise scan over the warp
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y0 = __shfl_up_sync(0xffffffffu, x.x, o), y1 = __shfl_up_sync(0xffffffffu, x.y, o);
+        const uint32_t y2 = __shfl_up_sync(0xffffffffu, x.z, o), y3 = __shfl_up_sync(0xffffffffu, x.w, o);
+        if (lane >= o) {
+          x.x += y0;
+          x.y += y1;
+          x.z += y2;
+          x.w += y3;
+        }
       }
-      if (lane < kNF) s_bal[warp][lane] = my_bal;
+      if (lane == 31) s_wtot[warp] = x;
+      // exclusive ranks (no byte borrows: the inclusive bytes are at least the own ones)
+      const uint32_t ex[4] = {x.x - own.x, x.y - own.y, x.z - own.z, x.w - own.w};
+      const uint32_t ow[4] = {own.x, own.y, own.z, own.w};
       __syncthreads();
       if (threadIdx.x < kNF) {
         // per tile: warp offsets inside this chunk, then advance the tile's run
         const int f = threadIdx.x;
         uint32_t r = s_run[f];
-  #pragma unroll
+#pragma unroll
         for (int w = 0; w < NW; ++w) {
           s_base[w][f] = r;
-          r += __popc(s_bal[w][f]);
+          const uint4 tw = s_wtot[w];
+          const uint32_t word = (f >> 2) == 0 ? tw.x : (f >> 2) == 1 ? tw.y : (f >> 2) == 2 ? tw.z : tw.w;
+          r += (word >> (8 * (f & 3))) & 0xffu;
         }
         s_run[f] = r;
       }
       __syncthreads();
-      // one store per tile, all lanes together: the lanes covering tile f write consecutive
-      // positions of its list
-      const uint32_t db = (keys && m) ? __float_as_uint(rgb_d[item].w) : 0u;
-  #pragma unroll
-      for (int f = 0; f < kNF; ++f) {
-        const uint32_t bl = s_bal[warp][f];
-        if (bl == 0u) continue;   // uniform per warp
-        if ((m >> f) & 1u) {
-          const uint32_t pos = s_base[warp][f] + __popc(bl & lt);
-          if (pos < cap) {
-            vals[pos] = item;
-            if (keys) keys[pos] = ((unsigned long long)s_tile[f] << 32) | db;
+      if (cb < 0x100u) {
+        uint32_t db = 0u;
+        if (KEYS) db = __float_as_uint(rgb_d[item].w);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint4 bq = *reinterpret_cast<const uint4*>(&s_base[warp][4 * q]);
+          const uint32_t bs[4] = {bq.x, bq.y, bq.z, bq.w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            if ((ow[q] >> (8 * k)) & 1u) {
+              const uint32_t pos = bs[k] + ((ex[q] >> (8 * k)) & 0xffu);
+              if (pos < cap) {
+                vals[pos] = item;
+                if (KEYS) keys[pos] = ((unsigned long long)s_tile[4 * q + k] << 32) | db;
+              }
+            }
           }
         }
       }
-      __syncthreads();
+      // (the next chunk rewrites s_wtot before its first barrier and s_base after it: both
+      // are read only between this chunk's two barriers or after the second by their writer)
     }
   }
 }
@@ -596,26 +748,26 @@ size_t bin_sort_ws_bytes(const rs_view_batch* b, int64_t capacity) {
 }
 
 // Super instances: expansion, stable sort on the super-tile id (KeyT-wide), ranges.
-// Returns the sorted item array.
+// Returns which buffer set (0 or 1) holds the sorted items and cover bytes.
 template <typename KeyT>
-static const uint32_t* super_instances(const BinWs& w, const uint32_t* order, int64_t n, const rs_projected* proj,
-                                       const rs_view_batch* batch, int64_t cap, int64_t nblk, int n_super_max,
-                                       cudaStream_t s) {
+static int super_instances(const BinWs& w, const uint32_t* order, int64_t n, const rs_projected* proj,
+                           const rs_view_batch* batch, int64_t cap, int64_t nblk, int n_super_max, cudaStream_t s) {
   KeyT* k0 = reinterpret_cast<KeyT*>(w.skeys[0]);
   KeyT* k1 = reinterpret_cast<KeyT*>(w.skeys[1]);
   {
     prof::Scope ps("k_emit", s);
     k_emit<KeyT><<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n, reinterpret_cast<const ushort4*>(proj->rect),
                                                          batch->views, batch->n_views, w.super_base, w.bsum, cap, k0,
-                                                         w.svals[0]);
+                                                         w.svals[0], w.saux[0]);
   }
   const int cur = tiles::sort_pairs<KeyT>(k0, w.svals[0], k1, w.svals[1], w.counters, cap, bits_for(n_super_max),
                                           w.sweep, s, true,
-                                          {"k_super_sort_hist", "k_super_sort_scan", "k_super_sort"});
+                                          {"k_super_sort_hist", "k_super_sort_scan", "k_super_sort"}, w.saux[0],
+                                          w.saux[1]);
   const KeyT* sk = cur ? k1 : k0;
   prof::Scope ps("k_ranges", s);
   k_ranges<KeyT><<<4 * kNumSMs, 256, 0, s>>>(sk, w.counters, (uint32_t)n_super_max, w.sranges);
-  return cur ? w.svals[1] : w.svals[0];
+  return cur;
 }
 
 }  // namespace rs
@@ -647,7 +799,7 @@ extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* 
     prof::Scope ps("k_super_layout", s);
     k_super_layout<<<1, 32, 0, s>>>(batch->views, batch->n_views, w.super_base, n, w.counters + 6);
   }
-  const uint32_t* svals = w.svals[0];
+  int scur = 0;   // buffer set of the sorted super instances
   if (n > 0) {
     // 1) items by depth (four 8-bit passes; an even count leaves the result in buffer 0)
     {
@@ -668,23 +820,29 @@ extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* 
       prof::Scope ps("k_count_top", s);
       k_count_top<<<1, 1024, 0, s>>>(w.bsum, nblk, cap, w.counters, status);
     }
-    svals = (n_super_max <= 65536) ? super_instances<uint16_t>(w, order, n, proj, batch, cap, nblk, n_super_max, s)
-                                   : super_instances<uint32_t>(w, order, n, proj, batch, cap, nblk, n_super_max, s);
+    scur = (n_super_max <= 65536) ? super_instances<uint16_t>(w, order, n, proj, batch, cap, nblk, n_super_max, s)
+                                  : super_instances<uint32_t>(w, order, n, proj, batch, cap, nblk, n_super_max, s);
   }
+  const uint32_t* svals = w.svals[scur];
+  const uint8_t* saux = w.saux[scur];
   // 3) per tile: count (per super-tile segment), scans (ranges and K), scatter
   // at most 8 resident CTAs per SM; the work items (super-tiles x segments) come from a
   // device counter, so a generous bound on the number of super-tiles costs nothing
-  const int64_t fwork = (int64_t)batch->n_tiles * kSegs;
-  const unsigned fgrid = (unsigned)(fwork < 8 * kNumSMs ? fwork : 8 * kNumSMs);
+  const unsigned fgrid = (unsigned)(w.n_work_max < 8 * kNumSMs ? w.n_work_max : 8 * kNumSMs);
+  {
+    prof::Scope ps("k_fine_layout", s);
+    k_fine_layout<<<1, 1024, 0, s>>>(w.super_base, batch->n_views, w.sranges, w.seg_off, w.work_s, w.n_work_max,
+                                     w.counters);
+  }
   {
     prof::Scope ps("k_fine_count", s);
-    k_fine_count<<<fgrid, kFineThreads, 0, s>>>(svals, rect, batch->views, batch->n_views, w.super_base, w.sranges,
-                                                 w.seg_cnt, w.counters + 4);
+    k_fine_count<<<fgrid, kFineThreads, 0, s>>>(saux, batch->views, batch->n_views, w.super_base, w.sranges,
+                                                 w.seg_off, w.work_s, w.counters + 7, w.seg_cnt, w.counters + 4);
   }
   {
     prof::Scope ps("k_fine_seg_scan", s);
-    k_fine_seg_scan<<<(unsigned)((batch->n_tiles + 255) / 256), 256, 0, s>>>(w.seg_cnt, batch->views, batch->n_views,
-                                                                            w.super_base, batch->n_tiles, w.fine_tot);
+    k_fine_seg_scan<<<(unsigned)((batch->n_tiles + 255) / 256), 256, 0, s>>>(
+        w.seg_cnt, batch->views, batch->n_views, w.super_base, w.seg_off, batch->n_tiles, w.fine_tot);
   }
   {
     prof::Scope ps("k_fine_scan", s);
@@ -692,9 +850,17 @@ extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* 
   }
   {
     prof::Scope ps("k_fine_scatter", s);
-    k_fine_scatter<<<fgrid, kFineThreads, 0, s>>>(svals, rect, rgb_d, batch->views, batch->n_views, w.super_base,
-                                                   w.sranges, w.fine_tot, w.seg_cnt, cap, bins->vals,
-                                                   reinterpret_cast<unsigned long long*>(bins->keys), w.counters + 5);
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(bins->keys);
+    if (keys)
+      k_fine_scatter<true><<<fgrid, kFineThreads, 0, s>>>(svals, saux, rgb_d, batch->views, batch->n_views,
+                                                          w.super_base, w.sranges, w.fine_tot, w.seg_off, w.work_s,
+                                                          w.counters + 7, w.seg_cnt, cap, bins->vals, keys,
+                                                          w.counters + 5);
+    else
+      k_fine_scatter<false><<<fgrid, kFineThreads, 0, s>>>(svals, saux, rgb_d, batch->views, batch->n_views,
+                                                           w.super_base, w.sranges, w.fine_tot, w.seg_off, w.work_s,
+                                                           w.counters + 7, w.seg_cnt, cap, bins->vals, nullptr,
+                                                           w.counters + 5);
   }
   return launch_status();
 }

@@ -116,13 +116,15 @@ __global__ void __launch_bounds__(1024) k_tile_scan(uint32_t* __restrict__ cnt, 
   uint32_t* row = cnt + (int64_t)blockIdx.x * n_tiles_max;
   if (threadIdx.x == 0) s_carry = 0u;
   __syncthreads();
-  for (int64_t b0 = 0; b0 < n_tiles; b0 += 4 * 1024) {
-    // four consecutive entries per thread
-    const int64_t b = b0 + 4 * (int64_t)threadIdx.x;
-    uint32_t v[4];
+  constexpr int PER = 4;   // consecutive entries per thread
+  for (int64_t b0 = 0; b0 < n_tiles; b0 += PER * 1024) {
+    const int64_t b = b0 + PER * (int64_t)threadIdx.x;
+    uint32_t v[PER], sum = 0u;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) v[j] = (b + j < n_tiles) ? row[b + j] : 0u;
-    const uint32_t sum = v[0] + v[1] + v[2] + v[3];
+    for (int j = 0; j < PER; ++j) {
+      v[j] = (b + j < n_tiles) ? row[b + j] : 0u;
+      sum += v[j];
+    }
     uint32_t x = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -143,7 +145,7 @@ __global__ void __launch_bounds__(1024) k_tile_scan(uint32_t* __restrict__ cnt, 
     __syncthreads();
     uint32_t run = s_carry + (warp ? s_w[warp - 1] : 0u) + x - sum;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < PER; ++j) {
       if (b + j < n_tiles) row[b + j] = run;
       run += v[j];
     }
@@ -157,13 +159,16 @@ __global__ void __launch_bounds__(1024) k_tile_scan(uint32_t* __restrict__ cnt, 
 template <typename KeyT, int ITEMS = kItems>
 __global__ void __launch_bounds__(kThreads, ITEMS <= 8 ? 4 : 3) k_tile_sort(const KeyT* __restrict__ keys_in,
                                                            const uint32_t* __restrict__ vals_in,
+                                                           const uint8_t* __restrict__ aux_in,
                                                            KeyT* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
+                                                           uint8_t* __restrict__ aux_out,
                                                            const uint32_t* __restrict__ n_dev, int shift, int rbits,
                                                            const uint32_t* __restrict__ cnt, int64_t n_tiles_max,
                                                            const uint32_t* __restrict__ tot) {
   constexpr int TILE = kThreads * ITEMS;
   __shared__ KeyT s_keys[TILE];
   __shared__ uint32_t s_vals[TILE];
+  __shared__ uint8_t s_aux[TILE];   // optional byte payload (aux_in non-null)
   __shared__ uint16_t s_whist[kWarps][kR];   // per-warp digit counts, then prefixes (< 2^16)
   __shared__ uint32_t s_gpos[kR];            // global position of local position 0 of digit d
   __shared__ uint32_t s_lstart[kR];          // tile-local start of digit d
@@ -189,13 +194,16 @@ __global__ void __launch_bounds__(kThreads, ITEMS <= 8 ? 4 : 3) k_tile_sort(cons
     for (int i = threadIdx.x; i < kWarps * kR; i += kThreads) (&s_whist[0][0])[i] = 0;
 
     uint32_t k[ITEMS], v[ITEMS];
+    uint8_t x[ITEMS];
     uint16_t rank[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
       const int li = warp * (ITEMS * 32) + i * 32 + lane;
+      x[i] = 0;
       if (li < tn) {
         k[i] = (uint32_t)__ldcs(keys_in + t0 + li);
         v[i] = __ldcs(vals_in + t0 + li);
+        if (aux_in) x[i] = __ldcs(aux_in + t0 + li);
       } else {
         k[i] = 0xffffffffu;   // sentinel: digit R, never counted
         v[i] = 0u;
@@ -253,6 +261,7 @@ __global__ void __launch_bounds__(kThreads, ITEMS <= 8 ? 4 : 3) k_tile_sort(cons
         const uint32_t p = s_lstart[dg] + s_whist[warp][dg] + rank[i];
         s_keys[p] = (KeyT)k[i];
         s_vals[p] = v[i];
+        if (aux_in) s_aux[p] = x[i];
       }
     }
     __syncthreads();
@@ -262,6 +271,7 @@ __global__ void __launch_bounds__(kThreads, ITEMS <= 8 ? 4 : 3) k_tile_sort(cons
       const uint32_t g = s_gpos[dd] + (uint32_t)p;
       if (keys_out) keys_out[g] = key;
       vals_out[g] = s_vals[p];
+      if (aux_in) aux_out[g] = s_aux[p];
     }
   }
 }
@@ -275,7 +285,8 @@ inline size_t scratch_words(int64_t n_max, int tile = kTile) {
 }
 
 // Stable sort of the first n (device count) pairs on bits [0, bits).  Buffers ping-pong
-// between (k0, v0) and (k1, v1); returns 0 if the result is in (k0, v0), 1 if in (k1, v1).
+// between (k0, v0[, aux0]) and (k1, v1[, aux1]); returns 0 if the result is in the first
+// set, 1 if in the second.
 // n_max bounds the count (grid sizes and scratch).
 // Names under which the launch tracer records the three kernels of a use of the sort.
 struct SortNames {
@@ -284,9 +295,11 @@ struct SortNames {
   const char* sort;
 };
 
+// aux0 / aux1 (optional, both or neither): a byte payload that travels with each pair.
 template <typename KeyT, int ITEMS = kItems>
 inline int sort_pairs(KeyT* k0, uint32_t* v0, KeyT* k1, uint32_t* v1, const uint32_t* n_dev, int64_t n_max, int bits,
-                      uint32_t* scratch, cudaStream_t s, bool write_last_keys, const SortNames& names) {
+                      uint32_t* scratch, cudaStream_t s, bool write_last_keys, const SortNames& names,
+                      uint8_t* aux0 = nullptr, uint8_t* aux1 = nullptr) {
   constexpr int TILE = kThreads * ITEMS;
   const int passes = sort_passes(bits);
   const int rbits = (bits + passes - 1) / passes;
@@ -305,6 +318,8 @@ inline int sort_pairs(KeyT* k0, uint32_t* v0, KeyT* k1, uint32_t* v1, const uint
     uint32_t* vi = cur ? v1 : v0;
     KeyT* ko = cur ? k0 : k1;
     uint32_t* vo = cur ? v0 : v1;
+    const uint8_t* ai = aux0 ? (cur ? aux1 : aux0) : nullptr;
+    uint8_t* ao = aux0 ? (cur ? aux0 : aux1) : nullptr;
     const bool last = (p == passes - 1);
     {
       prof::Scope ps(names.hist, s);
@@ -316,7 +331,7 @@ inline int sort_pairs(KeyT* k0, uint32_t* v0, KeyT* k1, uint32_t* v1, const uint
     }
     prof::Scope ps(names.sort, s);
     k_tile_sort<KeyT, ITEMS><<<grid_sort, kThreads, 0, s>>>(
-        ki, vi, (last && !write_last_keys) ? nullptr : ko, vo, n_dev, shift, rb, cnt, nt, tot);
+        ki, vi, ai, (last && !write_last_keys) ? nullptr : ko, vo, ao, n_dev, shift, rb, cnt, nt, tot);
     cur ^= 1;
   }
   return cur;
