@@ -215,16 +215,17 @@ def run_ours(args):
     mask = torch.empty(scene.n, dtype=torch.uint8, device=dev)
     idx = torch.empty(scene.n, dtype=torch.int32, device=dev)
     chunks = list(zip(vbs, bins_of, bufs, targets))
+    cfg_w = overwrite_cfg(N, cfg)
 
     def views_part():
         h.zero_()
-        gbuf.zero_()
-        for vb, bins, (img, T, L, dL), target in chunks:
+        for k, (vb, bins, (img, T, L, dL), target) in enumerate(chunks):
             api.project(g, vb, cfg, st, out=proj)
             api.bin_sort(proj, vb, bins, ws_sort, st)
             api.render(proj, bins, vb, cfg, image=img, T_final=T, last=L, importance=h)
             loss_fn(img, target, dL, loss)
-            api.render_backward(g, vb, proj, bins, T, L, dL, grads, ws_bwd, cfg)
+            # the first launch writes the gradients, later ones add theirs
+            api.render_backward(g, vb, proj, bins, T, L, dL, grads, ws_bwd, cfg_w if k == 0 else cfg)
 
     def prune():
         api.filter(h, 0.01, N.RS_PRUNE_BELOW, ws_f, mask=mask, idx=idx)
@@ -380,20 +381,21 @@ def stage_times(api, N, torch, g, chunks, cfg, st, proj, h, gbuf, loss, ws_sort,
     names = ["project", "bin_sort", "render_importance", "loss", "backward", "filter"]
     acc = {k: 0.0 for k in names}
     kern = {}
+    cfg_w = overwrite_cfg(N, cfg)
     for r in range(reps + 1):
         h.zero_()
-        gbuf.zero_()
         if r == 1:
             N.profile_enable(True)
         evs = []
-        for vb, bins, (img, T, L, dL), target in chunks:
+        for k, (vb, bins, (img, T, L, dL), target) in enumerate(chunks):
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
             ev[0].record()
             api.project(g, vb, cfg, st, out=proj); ev[1].record()
             api.bin_sort(proj, vb, bins, ws_sort, st); ev[2].record()
             api.render(proj, bins, vb, cfg, image=img, T_final=T, last=L, importance=h); ev[3].record()
             loss_fn(img, target, dL, loss); ev[4].record()
-            api.render_backward(g, vb, proj, bins, T, L, dL, gbuf.views, ws_bwd, cfg); ev[5].record()
+            api.render_backward(g, vb, proj, bins, T, L, dL, gbuf.views, ws_bwd, cfg_w if k == 0 else cfg)
+            ev[5].record()
             evs.append(ev)
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record()
@@ -600,6 +602,13 @@ def plain_loop(api, N, torch, g, vb1, cfg, target, cams, reps, dev, loss_fn):
     return plain, fps
 
 
+def overwrite_cfg(N, cfg):
+    """A copy of cfg whose render_backward writes the gradients (the first launch of a step)."""
+    c = N.RsConfig.from_buffer_copy(cfg)
+    c.grad_overwrite = 1
+    return c
+
+
 def e2e_run(api, N, torch, scene, vbs, cfg, targets, cap, reps, dev, world=1, loss_fn=None):
     """Same batched step through the public API (an api.StepGraph per input buffer set):
     every step copies its parameters and targets from pinned host memory and reads its loss
@@ -622,6 +631,7 @@ def e2e_run(api, N, torch, scene, vbs, cfg, targets, cap, reps, dev, world=1, lo
     dl_buf = [torch.empty(3 * vb.n_pixels, device=dev) for vb in vbs]
     mask = torch.empty(scene.n, dtype=torch.uint8, device=dev)
     idx = torch.empty(scene.n, dtype=torch.int32, device=dev)
+    cfg_w = overwrite_cfg(N, cfg)
 
     def make_set():
         dev_p = [torch.empty_like(t, device=dev) for t in host]
@@ -635,7 +645,6 @@ def e2e_run(api, N, torch, scene, vbs, cfg, targets, cap, reps, dev, world=1, lo
 
         def views_part():
             h.zero_()
-            gbuf.zero_()
             for i, vb in enumerate(vbs):
                 bins = api.Bins(bins_all.vals, bins_all.ranges[:vb.n_tiles], None, cap)
                 api.project(g, vb, cfg, st, out=proj)
@@ -643,7 +652,7 @@ def e2e_run(api, N, torch, scene, vbs, cfg, targets, cap, reps, dev, world=1, lo
                 img, T, L = api.render(proj, bins, vb, cfg, image=img_buf[i], T_final=T_buf[i], last=L_buf[i],
                                        importance=h)
                 loss, dl = loss_fn(img, tgt_d[i], dL=dl_buf[i], loss=loss_d[i:i + 1])
-                api.render_backward(g, vb, proj, bins, T, L, dl, gbuf.views, ws_bwd, cfg)
+                api.render_backward(g, vb, proj, bins, T, L, dl, gbuf.views, ws_bwd, cfg_w if i == 0 else cfg)
 
         def prune():
             api.filter(h, 0.01, N.RS_PRUNE_BELOW, ws_f, mask=mask, idx=idx)
@@ -761,8 +770,8 @@ def kernel_work(vbs, sres, pairs, n_super):
     the count); the super-tile sort moves 2 x (2 + 4 + 1) B per super instance and pass
     (count: 2 B); the fine partition reads the 1 B cover byte per super instance (count),
     then 4 B item + 1 B cover byte per super instance and writes 4 B per instance (scatter);
-    the projection backward reads 236 B and writes 236 B per Gaussian (read-modify-write)
-    plus 52 B per item; the blend kernels count FP32 operations per evaluated pair."""
+    the projection backward reads 236 B and writes 236 B per Gaussian (the gradients are
+    written, not accumulated) plus 52 B per item; the blend kernels count FP32 operations per evaluated pair."""
     vb = _PerLaunch(vbs)
     c = vb.launches
     M, K, Ks, P = vb.n_items, sres["n_instances"], n_super / c, vb.n_pixels
@@ -785,9 +794,10 @@ def kernel_work(vbs, sres, pairs, n_super):
         "k_l1": P * 3 * 4 * 3,
         "k_ssim_stats": P * 3 * (8 + 12),
         "k_ssim_grad": P * 3 * (12 + 8 + 4),
-        # per Gaussian: parameters read once, gradients read and written once (all views
-        # summed in registers); per item: 36 B of image-space gradients + the 16 B colour row
-        "k_project_bwd": vb.n_gaussians * (236 + 2 * 236) + M * (36 + 16),
+        # per Gaussian: parameters read once, gradients written once (all views summed in
+        # registers, written over the arrays); per item: 36 B of image-space gradients + the
+        # 16 B colour row
+        "k_project_bwd": vb.n_gaussians * (236 + 236) + M * (36 + 16),
         "k_filter_count": vb.n_gaussians * 4,
         "k_filter_scatter": vb.n_gaussians * (4 + 1) + vb.n_gaussians * 4,
     }

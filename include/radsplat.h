@@ -128,7 +128,11 @@ typedef struct rs_config {
                             1, 2 or 4 x 64 for 16x16 and 32x8 tiles (x 32 for 8x8); the forward
                             runs 64 threads per tile (32 for 8x8), the backward one warp per
                             tile; other values give RS_ERR_UNSUPPORTED */
-  int32_t reserved[2];
+  int32_t grad_overwrite;  /* rs_render_backward: 0 (default) adds the call's parameter
+                            gradients into the caller's arrays (which the caller zeroes);
+                            1 writes them over the arrays (zero where the call gives none),
+                            so no zeroing is needed */
+  int32_t reserved[1];
 } rs_config;
 
 /* Projected items (all device, [n_items] rows):
@@ -329,8 +333,10 @@ rs_status rs_kmeans(const float* points, int32_t n, float* centres, int32_t k, i
  * given dL/dimage (device, layout of rs_render's image) and the forward's T_final and
  * last, walks each pixel's list back to front from `last` (T_j recovered as
  * T_{j+1}/(1-alpha_j)), then chains through the projection to the parameters.
- * Gradients are ADDED into `grads` (zero them first); items of all views of the same
- * Gaussian are summed.  ws: rs_workspace_size(RS_STAGE_BACKWARD, batch, 0) bytes.
+ * Gradients are ADDED into `grads` (zero them first), or with cfg->grad_overwrite written
+ * over them (every row; for a visibility-list batch the call zeroes `grads` itself, then
+ * adds); items of all views of the same Gaussian are summed.
+ * ws: rs_workspace_size(RS_STAGE_BACKWARD, batch, 0) bytes.
  * Errors: RS_ERR_INVALID_ARG, RS_ERR_WORKSPACE, RS_ERR_UNSUPPORTED, RS_ERR_CUDA. */
 rs_status rs_render_backward(const rs_gaussians* g, const rs_view_batch* batch,
                              const rs_config* cfg, const rs_projected* proj,

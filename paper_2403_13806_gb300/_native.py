@@ -43,7 +43,7 @@ class RsViewBatch(ctypes.Structure):
 
 class RsConfig(ctypes.Structure):
     _fields_ = [("eps2d", c_float), ("near_plane", c_float), ("bg", c_float * 3), ("batch", c_int32),
-                ("reserved", c_int32 * 2)]
+                ("grad_overwrite", c_int32), ("reserved", c_int32 * 1)]
 
 
 class RsProjected(ctypes.Structure):

@@ -37,12 +37,15 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def config(eps2d: float = 0.3, near_plane: float = 0.2, bg=(0.0, 0.0, 0.0), batch: int = 0) -> N.RsConfig:
-    """rs_config; batch = Gaussian records staged per blend batch (0: default)."""
+def config(eps2d: float = 0.3, near_plane: float = 0.2, bg=(0.0, 0.0, 0.0), batch: int = 0,
+           grad_overwrite: bool = False) -> N.RsConfig:
+    """rs_config; batch = Gaussian records staged per blend batch (0: default);
+    grad_overwrite: render_backward writes the gradients instead of adding into them."""
     c = N.lib().rs_config_default()
     c.eps2d = eps2d
     c.near_plane = near_plane
     c.batch = int(batch)
+    c.grad_overwrite = 1 if grad_overwrite else 0
     for i in range(3):
         c.bg[i] = float(bg[i])
     return c
@@ -311,7 +314,8 @@ def kmeans(points: torch.Tensor, init: torch.Tensor, iterations: int = 50, strea
 
 def render_backward(g: Gaussians, vb: ViewBatch, proj: Projected, bins: Bins, T_final, last, dL_dimage,
                     grads: Sequence[torch.Tensor], ws: Workspace, cfg=None, stream=None):
-    """Adds d(L)/d(params) into grads (means, log_scales, quats, opacity_logit, sh)."""
+    """Adds d(L)/d(params) into grads (means, log_scales, quats, opacity_logit, sh), or
+    writes them over grads when cfg.grad_overwrite is set."""
     cfg = cfg or config()
     gs = N.RsGaussianGrads(*(t.data_ptr() for t in grads))
     nbytes = N.lib().rs_workspace_size(N.RS_STAGE_BACKWARD, N.ref(vb.batch), 0)

@@ -289,6 +289,7 @@ struct BwdProjArgs {
   const float* gc;
   const float4* rgb_d;   // forward colours: a clamped channel (max(0, .) = 0) has no gradient
   rs_gaussian_grads out;
+  int32_t overwrite;     // dense kernel: store the sums instead of adding them
 };
 
 template <int D>
@@ -504,6 +505,17 @@ __global__ void __launch_bounds__(128) k_project_bwd_dense(BwdProjArgs a) {
     touched = true;
     item_backward<D>(a, cam, gid, item, ga, gb, gc, pg, shg);
   }
+  if (a.overwrite) {   // every Gaussian's row is written (zeros where no view touched it)
+    for (int c = 0; c < 3; ++c) {
+      a.out.means[c * N + gid] = pg.m[c];
+      a.out.log_scales[c * N + gid] = pg.ls[c];
+    }
+    for (int c = 0; c < 4; ++c) a.out.quats[c * N + gid] = pg.q[c];
+    a.out.opacity_logit[gid] = pg.lg;
+#pragma unroll
+    for (int k = 0; k < 3 * NC; ++k) a.out.sh[(int64_t)k * N + gid] = s_gsh[k][threadIdx.x];
+    return;
+  }
   if (!touched) return;
   for (int c = 0; c < 3; ++c) {
     a.out.means[c * N + gid] += pg.m[c];
@@ -612,8 +624,20 @@ extern "C" rs_status rs_render_backward(const rs_gaussians* g, const rs_view_bat
   if (!blend_batch_ok(batch->tile_w, batch->tile_h, cfg->batch)) return RS_ERR_UNSUPPORTED;
   const BwdWs w = bwd_ws_layout(ws, batch->n_items);
   if (!ws || ws_bytes < w.bytes || !aligned<float4>(ws, 256)) return RS_ERR_WORKSPACE;
-  if (batch->n_items == 0 || batch->n_tiles == 0) return RS_OK;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const bool overwrite = cfg->grad_overwrite != 0;
+  // overwrite with the atomic (visibility-list) kernel, or with nothing to add: zero first
+  if (overwrite && (batch->subset_idx || batch->n_items == 0 || batch->n_tiles == 0)) {
+    const size_t nb = (size_t)g->n * sizeof(float);
+    const size_t nsh = (size_t)3 * (g->sh_degree + 1) * (g->sh_degree + 1);
+    if (cudaMemsetAsync(grads->means, 0, 3 * nb, s) != cudaSuccess ||
+        cudaMemsetAsync(grads->log_scales, 0, 3 * nb, s) != cudaSuccess ||
+        cudaMemsetAsync(grads->quats, 0, 4 * nb, s) != cudaSuccess ||
+        cudaMemsetAsync(grads->opacity_logit, 0, nb, s) != cudaSuccess ||
+        cudaMemsetAsync(grads->sh, 0, nsh * nb, s) != cudaSuccess)
+      return RS_ERR_CUDA;
+  }
+  if (batch->n_items == 0 || batch->n_tiles == 0) return RS_OK;
   if (cudaMemsetAsync(ws, 0, w.bytes, s) != cudaSuccess) return RS_ERR_CUDA;
 
   BwdBlendArgs b;
@@ -652,6 +676,7 @@ extern "C" rs_status rs_render_backward(const rs_gaussians* g, const rs_view_bat
   p.gc = w.gc;
   p.rgb_d = reinterpret_cast<const float4*>(proj->rgb_d);
   p.out = *grads;
+  p.overwrite = (overwrite && !batch->subset_idx) ? 1 : 0;
   const int threads = 128;
   prof::Scope ps("k_project_bwd", s);
   if (!batch->subset_idx) {

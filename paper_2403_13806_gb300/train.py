@@ -55,6 +55,8 @@ class Trainer:
         self.rng = np.random.default_rng(seed)
         self.tile = tuple(tile)
         self.cfg = cfg or api.config()
+        self.cfg_w = N.RsConfig.from_buffer_copy(self.cfg)   # backward writes the gradients
+        self.cfg_w.grad_overwrite = 1
         self.rast = api.Rasterizer(cfg=self.cfg, device=g.means.device)
         if loss not in ("paper", "l1"):
             raise ValueError("loss is 'paper' ((1 - lam) MSE + lam (1 - SSIM)) or 'l1'")
@@ -97,10 +99,8 @@ class Trainer:
                                      loss=self._loss, ws=self.ws_loss)
         else:
             loss, dl = api.l1_loss(out["image"], self.targets[i], loss=self._loss)
-        for t in self.grads:
-            t.zero_()
         api.render_backward(self.g, vb, out["proj"], out["bins"], out["T_final"], out["last"], dl, self.grads,
-                            self.rast.ws_bwd, self.cfg)
+                            self.rast.ws_bwd, self.cfg_w)
         self.step_no += 1
         api.adam_step(self._groups(), self.step_no, self.betas, self.eps)
         lv = float(loss.item())

@@ -107,6 +107,34 @@ def test_backward_with_visibility_subsets():
     compare_groups(full, ref)
 
 
+@pytest.mark.parametrize("subset", [False, True])
+def test_backward_grad_overwrite(subset):
+    """rs_config.grad_overwrite writes the call's gradients over arrays holding anything:
+    the result equals accumulating into zeroed arrays (to rounding: the per-item image-space
+    gradients are summed over tiles by atomics, in no fixed order)."""
+    from paper_2403_13806_gb300 import api
+    scene, cams = synth.fd_crop()
+    cam = cams[0]
+    w = unambiguous_weights(scene, cam, 6)
+    subs = None
+    if subset:
+        rng = np.random.default_rng(10)
+        sub = np.sort(rng.choice(scene.n, size=150, replace=False)).astype(np.uint32)
+        subs = [sub, sub]
+    out = gpu_forward(scene, [cam, cam], subsets=subs, importance=False)
+    dL = torch.as_tensor(np.concatenate([w.ravel(), 0.5 * w.ravel()]).astype(np.float32), device="cuda")
+    acc = [torch.zeros_like(t) for t in out["g"].tensors()]
+    api.render_backward(out["g"], out["vb"], out["proj"], out["bins"], out["T_final"], out["last"], dL, acc,
+                        out["rast"].ws_bwd)
+    over = [torch.full_like(t, 7.0) for t in out["g"].tensors()]
+    api.render_backward(out["g"], out["vb"], out["proj"], out["bins"], out["T_final"], out["last"], dL, over,
+                        out["rast"].ws_bwd, api.config(grad_overwrite=True))
+    torch.cuda.synchronize()
+    for a, b in zip(acc, over):
+        torch.testing.assert_close(b, a, rtol=1e-5, atol=1e-6)
+    assert any(bool((a != 0).any()) for a in acc)
+
+
 def test_autograd_function_l1_step():
     """Config-2 style step on the crop: L1 against the render of a perturbed copy."""
     from paper_2403_13806_gb300 import api
