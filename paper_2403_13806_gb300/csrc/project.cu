@@ -29,14 +29,59 @@ struct ProjectArgs {
   rs_device_status* status;
 };
 
-// One item: Gaussian gid seen from view cam, written at row `item`.
-template <int D>
-__device__ __forceinline__ void project_item(const ProjectArgs& a, const rs_view& cam, int64_t gid, int64_t item) {
-  constexpr int NC = (D + 1) * (D + 1);
-  const int64_t N = a.g.n;
+// View-independent part of a Gaussian: rotation, scales and opacity (identical operations
+// whichever view uses them).
+struct GaussLocal {
+  float R[3][3];
+  float s[3];
+  float o;
+  bool fin;   // every parameter finite
+  bool ok;    // finite, non-zero quaternion and o >= 1/255 (else the item is culled)
+};
 
+// Parameters of one Gaussian: means (3), log-scales (3), quaternion (4), opacity logit,
+// then the SH coefficients k * 3 + c; P(i) returns parameter row i.
+template <int D, typename P>
+__device__ __forceinline__ GaussLocal gauss_local(const P& prm) {
+  constexpr int NC = (D + 1) * (D + 1);
+  GaussLocal gl;
+  const float px = prm(0), py = prm(1), pz = prm(2);
+  const float l0 = prm(3), l1 = prm(4), l2 = prm(5);
+  const float qw = prm(6), qx = prm(7), qy = prm(8), qz = prm(9);
+  const float lg = prm(10);
+  bool fin = isfinite(px) && isfinite(py) && isfinite(pz) && isfinite(l0) && isfinite(l1) && isfinite(l2) &&
+             isfinite(qw) && isfinite(qx) && isfinite(qy) && isfinite(qz) && isfinite(lg);
+#pragma unroll
+  for (int k = 0; k < 3 * NC; ++k) fin = fin && isfinite(prm(11 + k));
+  gl.fin = fin;
+  const float qn2 = qw * qw + qx * qx + qy * qy + qz * qz;
+  const float qi = rsqrtf(qn2);
+  const float w = qw * qi, x = qx * qi, y = qy * qi, z = qz * qi;
+  gl.R[0][0] = 1.f - 2.f * (y * y + z * z);
+  gl.R[0][1] = 2.f * (x * y - w * z);
+  gl.R[0][2] = 2.f * (x * z + w * y);
+  gl.R[1][0] = 2.f * (x * y + w * z);
+  gl.R[1][1] = 1.f - 2.f * (x * x + z * z);
+  gl.R[1][2] = 2.f * (y * z - w * x);
+  gl.R[2][0] = 2.f * (x * z - w * y);
+  gl.R[2][1] = 2.f * (y * z + w * x);
+  gl.R[2][2] = 1.f - 2.f * (x * x + y * y);
+  gl.s[0] = expf(l0);
+  gl.s[1] = expf(l1);
+  gl.s[2] = expf(l2);
+  gl.o = 1.f / (1.f + expf(-lg));
+  gl.ok = fin && qn2 > 0.f && !(gl.o < kAlphaMin);
+  return gl;
+}
+
+// One item: Gaussian gid (parameters prm, view-independent part gl) seen from view cam,
+// written at row `item`.
+template <int D, typename P>
+__device__ __forceinline__ void project_view(const ProjectArgs& a, const rs_view& cam, const P& prm,
+                                             const GaussLocal& gl, int64_t item) {
+  constexpr int NC = (D + 1) * (D + 1);
   const float* W = cam.viewmat;
-  const float px = __ldg(a.g.means + gid), py = __ldg(a.g.means + N + gid), pz = __ldg(a.g.means + 2 * N + gid);
+  const float px = prm(0), py = prm(1), pz = prm(2);
   // FP32 order key, written with an explicit fma chain so that any IEEE FP32 host
   // reproduces it bit for bit.
   const float depth = __fmaf_rn(W[8], px, __fmaf_rn(W[9], py, __fmaf_rn(W[10], pz, W[11])));
@@ -48,35 +93,12 @@ __device__ __forceinline__ void project_item(const ProjectArgs& a, const rs_view
   uint32_t o_n = 0;
 
   do {
-    const float l0 = __ldg(a.g.log_scales + gid), l1 = __ldg(a.g.log_scales + N + gid),
-                l2 = __ldg(a.g.log_scales + 2 * N + gid);
-    const float qw = __ldg(a.g.quats + gid), qx = __ldg(a.g.quats + N + gid), qy = __ldg(a.g.quats + 2 * N + gid),
-                qz = __ldg(a.g.quats + 3 * N + gid);
-    const float lg = __ldg(a.g.opacity_logit + gid);
-    float shc[NC][3];
-    bool fin = isfinite(px) && isfinite(py) && isfinite(pz) && isfinite(l0) && isfinite(l1) && isfinite(l2) &&
-               isfinite(qw) && isfinite(qx) && isfinite(qy) && isfinite(qz) && isfinite(lg);
-#pragma unroll
-    for (int k = 0; k < NC; ++k)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        shc[k][c] = __ldg(a.g.sh + (int64_t)(k * 3 + c) * N + gid);
-        fin = fin && isfinite(shc[k][c]);
-      }
-    if (!fin) {
+    if (!gl.fin) {
       if (a.status) atomicAdd(&a.status->nonfinite, 1);
       break;
     }
     if (!(depth > a.near_plane)) break;
-
-    const float qn2 = qw * qw + qx * qx + qy * qy + qz * qz;
-    if (!(qn2 > 0.f)) break;
-    const float qi = rsqrtf(qn2);
-    const float w = qw * qi, x = qx * qi, y = qy * qi, z = qz * qi;
-    const float R[3][3] = {{1.f - 2.f * (y * y + z * z), 2.f * (x * y - w * z), 2.f * (x * z + w * y)},
-                           {2.f * (x * y + w * z), 1.f - 2.f * (x * x + z * z), 2.f * (y * z - w * x)},
-                           {2.f * (x * z - w * y), 2.f * (y * z + w * x), 1.f - 2.f * (x * x + y * y)}};
-    const float s[3] = {expf(l0), expf(l1), expf(l2)};
+    if (!gl.ok) break;
 
     const float tz = depth;
     const float tx = __fmaf_rn(W[0], px, __fmaf_rn(W[1], py, __fmaf_rn(W[2], pz, W[3])));
@@ -97,7 +119,8 @@ __device__ __forceinline__ void project_item(const ProjectArgs& a, const rs_view
 #pragma unroll
     for (int r = 0; r < 2; ++r)
 #pragma unroll
-      for (int k = 0; k < 3; ++k) Mm[r][k] = (T[r][0] * R[0][k] + T[r][1] * R[1][k] + T[r][2] * R[2][k]) * s[k];
+      for (int k = 0; k < 3; ++k)
+        Mm[r][k] = (T[r][0] * gl.R[0][k] + T[r][1] * gl.R[1][k] + T[r][2] * gl.R[2][k]) * gl.s[k];
     const float s00 = Mm[0][0] * Mm[0][0] + Mm[0][1] * Mm[0][1] + Mm[0][2] * Mm[0][2];
     const float s01 = Mm[0][0] * Mm[1][0] + Mm[0][1] * Mm[1][1] + Mm[0][2] * Mm[1][2];
     const float s11 = Mm[1][0] * Mm[1][0] + Mm[1][1] * Mm[1][1] + Mm[1][2] * Mm[1][2];
@@ -110,9 +133,7 @@ __device__ __forceinline__ void project_item(const ProjectArgs& a, const rs_view
     const float det = det0 + a.eps2d * (s00 + s11) + a.eps2d * a.eps2d;
     if (!(det > 0.f)) break;
     const float idet = 1.f / det;
-
-    const float o = 1.f / (1.f + expf(-lg));
-    if (o < kAlphaMin) break;
+    const float o = gl.o;
 
     const float mx = __fmaf_rn(cam.fx, ux, cam.cx);
     const float my = __fmaf_rn(cam.fy, uy, cam.cy);
@@ -138,7 +159,7 @@ __device__ __forceinline__ void project_item(const ProjectArgs& a, const rs_view
     for (int c = 0; c < 3; ++c) {
       float acc = 0.5f;
 #pragma unroll
-      for (int k = 0; k < NC; ++k) acc = fmaf(shc[k][c], Y[k], acc);
+      for (int k = 0; k < NC; ++k) acc = fmaf(prm(11 + 3 * k + c), Y[k], acc);
       col[c] = fmaxf(acc, 0.f);
     }
 
@@ -160,6 +181,28 @@ __device__ __forceinline__ void project_item(const ProjectArgs& a, const rs_view
   a.n_tiles[item] = o_n;
 }
 
+// Parameter rows of Gaussian gid straight from the structure-of-arrays inputs.
+struct GlobalParams {
+  const rs_gaussians* g;
+  int64_t gid;
+  __device__ __forceinline__ float operator()(int i) const {
+    const int64_t N = g->n;
+    const float* base = i < 3 ? g->means + (int64_t)i * N
+                      : i < 6 ? g->log_scales + (int64_t)(i - 3) * N
+                      : i < 10 ? g->quats + (int64_t)(i - 6) * N
+                      : i < 11 ? g->opacity_logit
+                               : g->sh + (int64_t)(i - 11) * N;
+    return __ldg(base + gid);
+  }
+};
+
+// Parameter rows staged in shared memory: row i of the thread's column.
+struct SmemParams {
+  const float* col;
+  int stride;
+  __device__ __forceinline__ float operator()(int i) const { return col[i * stride]; }
+};
+
 // Visibility-list batches: one thread per item.
 template <int D>
 __global__ void __launch_bounds__(256) k_project(ProjectArgs a) {
@@ -168,20 +211,47 @@ __global__ void __launch_bounds__(256) k_project(ProjectArgs a) {
   const int v = find_view_by_item(a.views, a.n_views, item);
   const rs_view& cam = a.views[v];
   const int64_t gid = a.subset ? (int64_t)__ldg(a.subset + item) : item - cam.item_base;
-  project_item<D>(a, cam, gid, item);
+  const GlobalParams prm{&a.g, gid};
+  const GaussLocal gl = gauss_local<D>(prm);
+  project_view<D>(a, cam, prm, gl, item);
 }
 
-// Dense batches (every view lists every Gaussian): one thread per Gaussian walks the views,
-// so the 236 bytes of its parameters come from HBM once (later views read them from L1)
-// instead of once per view.
+// Dense batches (every view lists every Gaussian): one thread per Gaussian walks the views.
+// The CTA's parameter block (one column per thread, 11 + 3 (D+1)^2 rows) is copied into
+// shared memory with asynchronous 4-byte copies -- every load of the block in flight at
+// once, no registers held -- so the 236 bytes of a Gaussian come from HBM once; rotation,
+// scales and opacity are computed once for all views.
+constexpr int kProjDenseThreads = 128;
+
 template <int D>
-__global__ void __launch_bounds__(256, 2) k_project_dense(ProjectArgs a) {
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid >= a.g.n) return;
+__global__ void __launch_bounds__(kProjDenseThreads) k_project_dense(ProjectArgs a) {
+  constexpr int NC = (D + 1) * (D + 1);
+  constexpr int ROWS = 11 + 3 * NC;
+  __shared__ float s_p[ROWS][kProjDenseThreads];
+  const int64_t gid = (int64_t)blockIdx.x * kProjDenseThreads + threadIdx.x;
+  if (gid >= a.g.n) return;   // no barrier below: each thread reads only its own column
+  {
+    const int64_t N = a.g.n;
+    const float* rows[5] = {a.g.means, a.g.log_scales, a.g.quats, a.g.opacity_logit, a.g.sh};
+    const int first[5] = {0, 3, 6, 10, 11};
+    const int count[5] = {3, 3, 4, 1, 3 * NC};
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+#pragma unroll
+      for (int k = 0; k < count[r]; ++k) {
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&s_p[first[r] + k][threadIdx.x]);
+        const float* gsrc = rows[r] + (int64_t)k * N + gid;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(gsrc) : "memory");
+      }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  }
+  const SmemParams prm{&s_p[0][threadIdx.x], kProjDenseThreads};
+  const GaussLocal gl = gauss_local<D>(prm);
 #pragma unroll 1
   for (int v = 0; v < a.n_views; ++v) {
     const rs_view& cam = a.views[v];
-    project_item<D>(a, cam, gid, cam.item_base + gid);
+    project_view<D>(a, cam, prm, gl, cam.item_base + gid);
   }
 }
 
@@ -218,9 +288,9 @@ extern "C" rs_status rs_project(const rs_gaussians* g, const rs_view_batch* batc
   a.rect = reinterpret_cast<ushort4*>(out->rect);
   a.n_tiles = out->n_tiles;
   a.status = status;
-  const int threads = 256;
   // one thread per Gaussian pays off once its parameters serve several views
   const bool dense = !batch->subset_idx && batch->n_views > 1;
+  const int threads = dense ? kProjDenseThreads : 256;
   const int64_t blocks = ((dense ? g->n : batch->n_items) + threads - 1) / threads;
   if (blocks > 0x7fffffffLL) return RS_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
