@@ -9,7 +9,7 @@
 // maps a, b, c (the chain rule through mu_x, E[x^2], E[xy]), so
 //   dL/dx(q) = (1 - lambda) 2 (x - y)(q)/n - lambda/n ((w * a)(q) + x(q)(w * b)(q) + y(q)(w * c)(q)).
 //
-// Two kernels, each on 32 x 16-pixel tiles of one plane with a 5-pixel halo in shared memory
+// Two kernels, each on 32 x 32-pixel tiles of one plane with a 5-pixel halo in shared memory
 // and the window applied as two 11-tap passes (rows, then columns; the window is separable:
 // the outer product of the normalised 1D Gaussian):
 //   k_ssim_stats -- the five window moments, SSIM, the maps a, b, c (to the workspace) and the
@@ -26,8 +26,12 @@
 namespace rs {
 
 constexpr int kSR = 5;                 // window radius
-constexpr int kSTX = 32, kSTY = 16;    // output tile
-constexpr int kSHX = kSTX + 2 * kSR, kSHY = kSTY + 2 * kSR;
+constexpr int kTaps = 2 * kSR + 1;
+constexpr int kST = 32;                // output tile: kST x kST
+constexpr int kSH = kST + 2 * kSR;     // tile with the halo: 42 x 42
+constexpr int kSThreads = 256;
+constexpr int kRowOut = 8;             // row pass: adjacent outputs per task
+constexpr int kColOut = 4;             // column pass: adjacent outputs per task
 constexpr float kC1 = 0.01f * 0.01f, kC2 = 0.03f * 0.03f;
 constexpr int kSlots = 64;             // block sums go to 64 addresses (no single hot atomic)
 
@@ -40,136 +44,125 @@ struct SsimArgs {
   double* loss;
   int W, H, planes;
   float lambda;
-  float w[2 * kSR + 1];   // normalised 1D Gaussian, sigma 1.5
+  float w[kTaps];       // normalised 1D Gaussian, sigma 1.5
 };
 
+
+// Halo tile rows are loaded by columns: thread t < 252 takes column t % 42 of rows
+// t / 42 + 6 p (p < 7), so the index arithmetic is done once per thread.
+constexpr int kLoadRows = kSThreads / kSH;   // 6 rows per round
+constexpr int kLoadRounds = kSH / kLoadRows; // 7 rounds
+static_assert(kLoadRows * kLoadRounds == kSH, "halo rows per load round");
+
 // Shared-memory layouts interleave what a tap reads together (x with y; the five moments
-// as a float4 plus a float; the three maps as a float4), and every thread produces four
-// adjacent outputs of the row pass and two of the column pass from values it loaded once,
-// so the load/store unit (the bound of a naive stencil) carries ~5x fewer instructions.
-__global__ void __launch_bounds__(256) k_ssim_stats(SsimArgs a) {
-  __shared__ __align__(16) float2 sxy[kSHY][kSHX];     // (x, y) with the halo
-  __shared__ __align__(16) float4 hq[kSHY][kSTX + 1];  // row-filtered (mu_x, mu_y, E[x^2], E[y^2])
-  __shared__ float hxy[kSHY][kSTX + 1];                // row-filtered E[xy]
-  __shared__ float red[2][8];
-  const int x0 = blockIdx.x * kSTX, y0 = blockIdx.y * kSTY, pl = blockIdx.z;
+// as a float4 plus a float), the row pass produces 8 adjacent outputs and the column pass 4
+// per task from values loaded once, and row pitches keep 8-lane phases of 16-byte accesses
+// on distinct bank groups.
+__global__ void __launch_bounds__(kSThreads) k_ssim_stats(SsimArgs a) {
+  __shared__ __align__(16) float2 sxy[kSH][kSH];         // (x, y) with the halo
+  __shared__ __align__(16) float4 hq[kSH][kST + 1];      // row-filtered (mu_x, mu_y, E[x^2], E[y^2])
+  __shared__ float hxy[kSH][kST + 1];                    // row-filtered E[xy]
+  __shared__ float2 s_w2[kTaps];
+  __shared__ float red[2][kSThreads / 32];
+  const int x0 = blockIdx.x * kST, y0 = blockIdx.y * kST, pl = blockIdx.z;
   const int64_t plane = (int64_t)a.W * a.H;
   const float* X = a.x + pl * plane;
   const float* Y = a.y + pl * plane;
-  {
-    // every load of the halo tile is issued before the first shared-memory store
-    constexpr int NL = (kSHX * kSHY + 255) / 256;
-    float2 v[NL];
+  const int t = threadIdx.x;
+  if (t == 0) {
 #pragma unroll
-    for (int j = 0; j < NL; ++j) {
-      const int i = threadIdx.x + 256 * j;
-      const int r = i / kSHX, c = i % kSHX;
-      const int gy = y0 + r - kSR, gx = x0 + c - kSR;
-      const bool in = i < kSHX * kSHY && gx >= 0 && gx < a.W && gy >= 0 && gy < a.H;
+    for (int k = 0; k < kTaps; ++k) s_w2[k] = make_float2(a.w[k], a.w[k]);   // (static indices)
+  }
+  if (t < kLoadRows * kSH) {
+    const int c = t % kSH, r0 = t / kSH;
+    const int gx = x0 + c - kSR;
+    const bool cin = gx >= 0 && gx < a.W;
+    float2 v[kLoadRounds];
+#pragma unroll
+    for (int p = 0; p < kLoadRounds; ++p) {
+      const int gy = y0 + r0 + kLoadRows * p - kSR;
       const int64_t o = (int64_t)gy * a.W + gx;
-      v[j] = in ? make_float2(__ldg(X + o), __ldg(Y + o)) : make_float2(0.f, 0.f);
+      v[p] = (cin && gy >= 0 && gy < a.H) ? make_float2(__ldg(X + o), __ldg(Y + o)) : make_float2(0.f, 0.f);
     }
 #pragma unroll
-    for (int j = 0; j < NL; ++j) {
-      const int i = threadIdx.x + 256 * j;
-      if (i < kSHX * kSHY) sxy[i / kSHX][i % kSHX] = v[j];
-    }
+    for (int p = 0; p < kLoadRounds; ++p) sxy[r0 + kLoadRows * p][c] = v[p];
   }
   __syncthreads();
-  // rows: 4 adjacent outputs per task, (kSHY rows) x (kSTX / 4 column groups) tasks
-  {
-    // 8 consecutive lanes take 8 rows of one column group: with the odd row pitches their
-    // 16-byte loads and stores fall in 8 distinct bank groups
-    const int t = threadIdx.x;
-    const int r = (t & 7) + 8 * (t >> 6), c0 = 4 * ((t >> 3) & 7);
-    if (r < kSHY) {
-    float2 v[4 + 2 * kSR];
+  // the window weights as (w, w) register pairs for the packed FP32 instructions, read once
+  // per thread from shared memory (so they stay in registers across the unrolled passes)
+  float2 w2[kTaps];
 #pragma unroll
-    for (int k = 0; k < 4 + 2 * kSR; k += 2) {
-      const float4 q = *reinterpret_cast<const float4*>(&sxy[r][c0 + k]);
-      v[k] = make_float2(q.x, q.y);
-      v[k + 1] = make_float2(q.z, q.w);
-    }
+  for (int k = 0; k < kTaps; ++k) w2[k] = s_w2[k];
+  // rows: kRowOut adjacent outputs per task, kSH rows x (kST / kRowOut) groups
+  if (t < kSH * (kST / kRowOut)) {
+    const int r = t % kSH, c0 = kRowOut * (t / kSH);
     // (mu_x, mu_y) and (E[x^2], E[y^2]) advance as packed pairs, E[xy] alone
-    float2 m1[4], m2[4];
-    float m3[4];
+    float2 m1[kRowOut], m2[kRowOut];
+    float m3[kRowOut];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < kRowOut; ++j) {
       m1[j] = m2[j] = make_float2(0.f, 0.f);
       m3[j] = 0.f;
     }
 #pragma unroll
-    for (int k = 0; k < 4 + 2 * kSR; ++k) {
-      const float2 sq = __fmul2_rn(v[k], v[k]);
-      const float xy = v[k].x * v[k].y;
+    for (int k = 0; k < kRowOut + 2 * kSR; k += 2) {
+      const float4 q = *reinterpret_cast<const float4*>(&sxy[r][c0 + k]);
+      const float2 vv[2] = {make_float2(q.x, q.y), make_float2(q.z, q.w)};
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int tap = k - j;
-        if (tap < 0 || tap > 2 * kSR) continue;   // resolved at compile time
-        const float2 w2 = make_float2(a.w[tap], a.w[tap]);
-        m1[j] = __ffma2_rn(w2, v[k], m1[j]);
-        m2[j] = __ffma2_rn(w2, sq, m2[j]);
-        m3[j] = fmaf(a.w[tap], xy, m3[j]);
+      for (int h = 0; h < 2; ++h) {
+        const float2 v = vv[h];
+        const float2 sq = __fmul2_rn(v, v);
+        const float xy = v.x * v.y;
+#pragma unroll
+        for (int j = 0; j < kRowOut; ++j) {
+          const int tap = k + h - j;
+          if (tap < 0 || tap >= kTaps) continue;   // resolved at compile time
+          m1[j] = __ffma2_rn(w2[tap], v, m1[j]);
+          m2[j] = __ffma2_rn(w2[tap], sq, m2[j]);
+          m3[j] = fmaf(w2[tap].x, xy, m3[j]);
+        }
       }
     }
-    float m[4][5];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      m[j][0] = m1[j].x;
-      m[j][1] = m1[j].y;
-      m[j][2] = m2[j].x;
-      m[j][3] = m2[j].y;
-      m[j][4] = m3[j];
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      hq[r][c0 + j] = make_float4(m[j][0], m[j][1], m[j][2], m[j][3]);
-      hxy[r][c0 + j] = m[j][4];
-    }
+    for (int j = 0; j < kRowOut; ++j) {
+      hq[r][c0 + j] = make_float4(m1[j].x, m1[j].y, m2[j].x, m2[j].y);
+      hxy[r][c0 + j] = m3[j];
     }
   }
   __syncthreads();
-  // columns: 2 adjacent rows per task, kSTX x (kSTY / 2) tasks
+  // columns: kColOut adjacent rows per task, kST columns x (kST / kColOut) groups (one warp
+  // per group, a lane per column)
   const int64_t total = plane * a.planes;
   float s_sum = 0.f, e_sum = 0.f;
-  for (int t = threadIdx.x; t < kSTX * (kSTY / 2); t += blockDim.x) {
-    const int c = t % kSTX, r0 = 2 * (t / kSTX);
-    float2 m1[2], m2[2];
-    float m3[2];
+  {
+    const int c = t % kST, r0 = kColOut * (t / kST);
+    float2 m1[kColOut], m2[kColOut];
+    float m3[kColOut];
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < kColOut; ++j) {
       m1[j] = m2[j] = make_float2(0.f, 0.f);
       m3[j] = 0.f;
     }
 #pragma unroll
-    for (int k = 0; k < 2 + 2 * kSR; ++k) {
+    for (int k = 0; k < kColOut + 2 * kSR; ++k) {
       const float4 hv = hq[r0 + k][c];
       const float hz = hxy[r0 + k][c];
+      const float2 h01 = make_float2(hv.x, hv.y), h23 = make_float2(hv.z, hv.w);
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
+      for (int j = 0; j < kColOut; ++j) {
         const int tap = k - j;
-        if (tap < 0 || tap > 2 * kSR) continue;
-        const float2 w2 = make_float2(a.w[tap], a.w[tap]);
-        m1[j] = __ffma2_rn(w2, make_float2(hv.x, hv.y), m1[j]);
-        m2[j] = __ffma2_rn(w2, make_float2(hv.z, hv.w), m2[j]);
-        m3[j] = fmaf(a.w[tap], hz, m3[j]);
+        if (tap < 0 || tap >= kTaps) continue;
+        m1[j] = __ffma2_rn(w2[tap], h01, m1[j]);
+        m2[j] = __ffma2_rn(w2[tap], h23, m2[j]);
+        m3[j] = fmaf(w2[tap].x, hz, m3[j]);
       }
     }
-    float m[2][5];
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      m[j][0] = m1[j].x;
-      m[j][1] = m1[j].y;
-      m[j][2] = m2[j].x;
-      m[j][3] = m2[j].y;
-      m[j][4] = m3[j];
-    }
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < kColOut; ++j) {
       const int r = r0 + j;
       const int gy = y0 + r, gx = x0 + c;
       if (gx >= a.W || gy >= a.H) continue;
-      const float mx = m[j][0], my = m[j][1], exx = m[j][2], eyy = m[j][3], exy = m[j][4];
+      const float mx = m1[j].x, my = m1[j].y, exx = m2[j].x, eyy = m2[j].y, exy = m3[j];
       const float sxx = exx - mx * mx, syy = eyy - my * my, sxy_ = exy - mx * my;
       const float ln = 2.f * mx * my + kC1, ld = mx * mx + my * my + kC1;
       const float cn = 2.f * sxy_ + kC2, cd = sxx + syy + kC2;
@@ -195,131 +188,138 @@ __global__ void __launch_bounds__(256) k_ssim_stats(SsimArgs a) {
     s_sum += __shfl_xor_sync(0xffffffffu, s_sum, o);
     e_sum += __shfl_xor_sync(0xffffffffu, e_sum, o);
   }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = t >> 5, lane = t & 31;
   if (lane == 0) {
     red[0][warp] = s_sum;
     red[1][warp] = e_sum;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0, e = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      s += red[0][w];
+  if (t == 0) {
+    double ss = 0.0, e = 0.0;
+    for (int w = 0; w < kSThreads / 32; ++w) {
+      ss += red[0][w];
       e += red[1][w];
     }
     const int slot = (blockIdx.x + 7 * blockIdx.y + 13 * blockIdx.z) % kSlots;
-    atomicAdd(&a.sums[slot], s);
+    atomicAdd(&a.sums[slot], ss);
     atomicAdd(&a.sums[kSlots + slot], e);
   }
 }
 
-__global__ void __launch_bounds__(256) k_ssim_grad(SsimArgs a) {
-  __shared__ __align__(16) float4 sm[kSHY][kSHX + 1];   // (a, b, c, 0) with the halo (odd row pitch)
-  __shared__ __align__(16) float4 hm[kSHY][kSTX + 1];   // row-filtered maps
-  const int x0 = blockIdx.x * kSTX, y0 = blockIdx.y * kSTY, pl = blockIdx.z;
+__global__ void __launch_bounds__(kSThreads) k_ssim_grad(SsimArgs a) {
+  __shared__ __align__(16) float2 sab[kSH][kSH];     // (a, b) with the halo
+  __shared__ float sc[kSH][kSH + 1];                 // c with the halo (odd row pitch)
+  __shared__ __align__(16) float2 hab[kSH][kST + 1]; // row-filtered (a, b)
+  __shared__ float hc[kSH][kST + 1];                 // row-filtered c
+  __shared__ float2 s_w2[kTaps];
+  const int x0 = blockIdx.x * kST, y0 = blockIdx.y * kST, pl = blockIdx.z;
   const int64_t plane = (int64_t)a.W * a.H;
   const int64_t total = plane * a.planes;
-  {
-    constexpr int NL = (kSHX * kSHY + 255) / 256;
-    float4 v[NL];
+  const int t = threadIdx.x;
+  if (t == 0) {
 #pragma unroll
-    for (int j = 0; j < NL; ++j) {
-      const int i = threadIdx.x + 256 * j;
-      const int r = i / kSHX, c = i % kSHX;
-      const int gy = y0 + r - kSR, gx = x0 + c - kSR;
-      const bool in = i < kSHX * kSHY && gx >= 0 && gx < a.W && gy >= 0 && gy < a.H;
+    for (int k = 0; k < kTaps; ++k) s_w2[k] = make_float2(a.w[k], a.w[k]);   // (static indices)
+  }
+  if (t < kLoadRows * kSH) {
+    const int c = t % kSH, r0 = t / kSH;
+    const int gx = x0 + c - kSR;
+    const bool cin = gx >= 0 && gx < a.W;
+    float2 vab[kLoadRounds];
+    float vc[kLoadRounds];
+#pragma unroll
+    for (int p = 0; p < kLoadRounds; ++p) {
+      const int gy = y0 + r0 + kLoadRows * p - kSR;
       const int64_t o = pl * plane + (int64_t)gy * a.W + gx;
-      v[j] = in ? make_float4(__ldg(a.maps + o), __ldg(a.maps + total + o), __ldg(a.maps + 2 * total + o), 0.f)
-                : make_float4(0.f, 0.f, 0.f, 0.f);
+      const bool in = cin && gy >= 0 && gy < a.H;
+      vab[p] = in ? make_float2(__ldg(a.maps + o), __ldg(a.maps + total + o)) : make_float2(0.f, 0.f);
+      vc[p] = in ? __ldg(a.maps + 2 * total + o) : 0.f;
     }
 #pragma unroll
-    for (int j = 0; j < NL; ++j) {
-      const int i = threadIdx.x + 256 * j;
-      if (i < kSHX * kSHY) sm[i / kSHX][i % kSHX] = v[j];
+    for (int p = 0; p < kLoadRounds; ++p) {
+      sab[r0 + kLoadRows * p][c] = vab[p];
+      sc[r0 + kLoadRows * p][c] = vc[p];
     }
   }
   __syncthreads();
-  {
-    const int t = threadIdx.x;
-    const int r = (t & 7) + 8 * (t >> 6), c0 = 4 * ((t >> 3) & 7);
-    if (r < kSHY) {
-    float2 mab[4];
-    float mc[4];
+  // the window weights as (w, w) register pairs for the packed FP32 instructions, read once
+  // per thread from shared memory (so they stay in registers across the unrolled passes)
+  float2 w2[kTaps];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+  for (int k = 0; k < kTaps; ++k) w2[k] = s_w2[k];
+  if (t < kSH * (kST / kRowOut)) {
+    const int r = t % kSH, c0 = kRowOut * (t / kSH);
+    float2 mab[kRowOut];
+    float mc[kRowOut];
+#pragma unroll
+    for (int j = 0; j < kRowOut; ++j) {
       mab[j] = make_float2(0.f, 0.f);
       mc[j] = 0.f;
     }
 #pragma unroll
-    for (int k = 0; k < 4 + 2 * kSR; ++k) {
-      const float4 v = sm[r][c0 + k];
+    for (int k = 0; k < kRowOut + 2 * kSR; k += 2) {
+      const float4 q = *reinterpret_cast<const float4*>(&sab[r][c0 + k]);
+      const float2 vv[2] = {make_float2(q.x, q.y), make_float2(q.z, q.w)};
+      const float cc[2] = {sc[r][c0 + k], sc[r][c0 + k + 1]};
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int tap = k - j;
-        if (tap < 0 || tap > 2 * kSR) continue;
-        mab[j] = __ffma2_rn(make_float2(a.w[tap], a.w[tap]), make_float2(v.x, v.y), mab[j]);
-        mc[j] = fmaf(a.w[tap], v.z, mc[j]);
+      for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int j = 0; j < kRowOut; ++j) {
+          const int tap = k + h - j;
+          if (tap < 0 || tap >= kTaps) continue;
+          mab[j] = __ffma2_rn(w2[tap], vv[h], mab[j]);
+          mc[j] = fmaf(w2[tap].x, cc[h], mc[j]);
+        }
       }
     }
-    float m[4][3];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      m[j][0] = mab[j].x;
-      m[j][1] = mab[j].y;
-      m[j][2] = mc[j];
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) hm[r][c0 + j] = make_float4(m[j][0], m[j][1], m[j][2], 0.f);
+    for (int j = 0; j < kRowOut; ++j) {
+      hab[r][c0 + j] = mab[j];
+      hc[r][c0 + j] = mc[j];
     }
   }
   __syncthreads();
   const float n = (float)total;
   const float k_mse = (1.f - a.lambda) * 2.f / n, k_ssim = a.lambda / n;
-  for (int t = threadIdx.x; t < kSTX * (kSTY / 2); t += blockDim.x) {
-    const int c = t % kSTX, r0 = 2 * (t / kSTX);
-    float xv[2], yv[2];
+  {
+    const int c = t % kST, r0 = kColOut * (t / kST);
+    const int gx = x0 + c;
+    float xv[kColOut], yv[kColOut];
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int gy = y0 + r0 + j, gx = x0 + c;
+    for (int j = 0; j < kColOut; ++j) {
+      const int gy = y0 + r0 + j;
       const bool in = gx < a.W && gy < a.H;
       const int64_t o = pl * plane + (int64_t)gy * a.W + gx;
       xv[j] = in ? __ldg(a.x + o) : 0.f;
       yv[j] = in ? __ldg(a.y + o) : 0.f;
     }
-    float2 mab[2];
-    float mc[2];
+    float2 mab[kColOut];
+    float mc[kColOut];
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < kColOut; ++j) {
       mab[j] = make_float2(0.f, 0.f);
       mc[j] = 0.f;
     }
 #pragma unroll
-    for (int k = 0; k < 2 + 2 * kSR; ++k) {
-      const float4 v = hm[r0 + k][c];
+    for (int k = 0; k < kColOut + 2 * kSR; ++k) {
+      const float2 v = hab[r0 + k][c];
+      const float vcc = hc[r0 + k][c];
 #pragma unroll
-      for (int j = 0; j < 2; ++j) {
+      for (int j = 0; j < kColOut; ++j) {
         const int tap = k - j;
-        if (tap < 0 || tap > 2 * kSR) continue;
-        mab[j] = __ffma2_rn(make_float2(a.w[tap], a.w[tap]), make_float2(v.x, v.y), mab[j]);
-        mc[j] = fmaf(a.w[tap], v.z, mc[j]);
+        if (tap < 0 || tap >= kTaps) continue;
+        mab[j] = __ffma2_rn(w2[tap], v, mab[j]);
+        mc[j] = fmaf(w2[tap].x, vcc, mc[j]);
       }
     }
-    float m[2][3];
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      m[j][0] = mab[j].x;
-      m[j][1] = mab[j].y;
-      m[j][2] = mc[j];
-    }
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int gy = y0 + r0 + j, gx = x0 + c;
+    for (int j = 0; j < kColOut; ++j) {
+      const int gy = y0 + r0 + j;
       if (gx >= a.W || gy >= a.H) continue;
       const int64_t o = pl * plane + (int64_t)gy * a.W + gx;
-      a.grad[o] = k_mse * (xv[j] - yv[j]) - k_ssim * (m[j][0] + xv[j] * m[j][1] + yv[j] * m[j][2]);
+      a.grad[o] = k_mse * (xv[j] - yv[j]) - k_ssim * (mab[j].x + xv[j] * mab[j].y + yv[j] * mc[j]);
     }
   }
-  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0 && a.loss) {
+  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && t == 0 && a.loss) {
     double ss = 0.0, se = 0.0;
     for (int k = 0; k < kSlots; ++k) {
       ss += a.sums[k];
@@ -344,7 +344,7 @@ extern "C" rs_status rs_ssim_loss(const float* image, const float* target, int32
                                   size_t ws_bytes, void* stream) {
   if (!image || !target || !dL_dimage || width <= 0 || height <= 0 || n_planes <= 0) return RS_ERR_INVALID_ARG;
   if (!(lambda >= 0.f && lambda <= 1.f)) return RS_ERR_INVALID_ARG;
-  if ((int64_t)height > 65535 * (int64_t)kSTY || n_planes > 65535) return RS_ERR_INVALID_ARG;
+  if ((int64_t)height > 65535 * (int64_t)kST || n_planes > 65535) return RS_ERR_INVALID_ARG;
   const size_t need = rs_ssim_workspace_size(width, height, n_planes);
   if (!ws || ws_bytes < need || !aligned<double>(ws, 256)) return RS_ERR_WORKSPACE;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -359,16 +359,16 @@ extern "C" rs_status rs_ssim_loss(const float* image, const float* target, int32
   a.H = height;
   a.planes = n_planes;
   a.lambda = lambda;
-  double g[2 * kSR + 1], tot = 0.0;
+  double g[kTaps], tot = 0.0;
   for (int k = -kSR; k <= kSR; ++k) tot += (g[k + kSR] = exp(-(double)(k * k) / (2.0 * 1.5 * 1.5)));
-  for (int k = 0; k < 2 * kSR + 1; ++k) a.w[k] = (float)(g[k] / tot);
+  for (int k = 0; k < kTaps; ++k) a.w[k] = (float)(g[k] / tot);
   if (cudaMemsetAsync(ws, 0, 2 * kSlots * sizeof(double), s) != cudaSuccess) return RS_ERR_CUDA;
-  const dim3 grid((unsigned)((width + kSTX - 1) / kSTX), (unsigned)((height + kSTY - 1) / kSTY), (unsigned)n_planes);
+  const dim3 grid((unsigned)((width + kST - 1) / kST), (unsigned)((height + kST - 1) / kST), (unsigned)n_planes);
   {
     prof::Scope ps("k_ssim_stats", s);
-    k_ssim_stats<<<grid, 256, 0, s>>>(a);
+    k_ssim_stats<<<grid, kSThreads, 0, s>>>(a);
   }
   prof::Scope ps("k_ssim_grad", s);
-  k_ssim_grad<<<grid, 256, 0, s>>>(a);
+  k_ssim_grad<<<grid, kSThreads, 0, s>>>(a);
   return launch_status();
 }
