@@ -20,6 +20,7 @@ struct ProjectArgs {
   const uint32_t* subset;
   int64_t n_items;
   int32_t n_views, tile_w, tile_h;
+  int32_t tw_shift, th_shift;   // log2 of the tile sides (8, 16 or 32)
   float eps2d, near_plane;
   float2* xy;
   float4* conic_o;
@@ -168,8 +169,8 @@ __device__ __forceinline__ void project_view(const ProjectArgs& a, const rs_view
     o_rgbd = make_float4(col[0], col[1], col[2], depth);
     if (u0 <= u1 && v0 <= v1) {
       const int iu0 = (int)u0, iu1 = (int)u1, iv0 = (int)v0, iv1 = (int)v1;
-      o_rect = make_ushort4((unsigned short)(iu0 / a.tile_w), (unsigned short)(iv0 / a.tile_h),
-                            (unsigned short)(iu1 / a.tile_w + 1), (unsigned short)(iv1 / a.tile_h + 1));
+      o_rect = make_ushort4((unsigned short)(iu0 >> a.tw_shift), (unsigned short)(iv0 >> a.th_shift),
+                            (unsigned short)((iu1 >> a.tw_shift) + 1), (unsigned short)((iv1 >> a.th_shift) + 1));
       o_n = (uint32_t)(o_rect.z - o_rect.x) * (uint32_t)(o_rect.w - o_rect.y);
     }
   } while (false);
@@ -280,6 +281,10 @@ extern "C" rs_status rs_project(const rs_gaussians* g, const rs_view_batch* batc
   a.n_views = batch->n_views;
   a.tile_w = batch->tile_w;
   a.tile_h = batch->tile_h;
+  if (!((a.tile_w == 8 || a.tile_w == 16 || a.tile_w == 32) && (a.tile_h == 8 || a.tile_h == 16)))
+    return RS_ERR_UNSUPPORTED;
+  a.tw_shift = a.tile_w == 8 ? 3 : a.tile_w == 16 ? 4 : 5;
+  a.th_shift = a.tile_h == 8 ? 3 : 4;
   a.eps2d = cfg->eps2d;
   a.near_plane = cfg->near_plane;
   a.xy = reinterpret_cast<float2*>(out->xy);

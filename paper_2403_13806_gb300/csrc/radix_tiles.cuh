@@ -166,12 +166,13 @@ __global__ void __launch_bounds__(kThreads, ITEMS <= 8 ? 4 : 3) k_tile_sort(cons
                                                            const uint32_t* __restrict__ cnt, int64_t n_tiles_max,
                                                            const uint32_t* __restrict__ tot) {
   constexpr int TILE = kThreads * ITEMS;
+  static_assert(kWarps * kR * 2 == kThreads * 16, "one 16-byte store per thread clears the counters");
   __shared__ KeyT s_keys[TILE];
   __shared__ uint32_t s_vals[TILE];
-  __shared__ uint8_t s_aux[TILE];   // optional byte payload (aux_in non-null)
-  __shared__ uint16_t s_whist[kWarps][kR];   // per-warp digit counts, then prefixes (< 2^16)
+  __shared__ uint8_t s_aux[TILE];                      // optional byte payload (aux_in non-null)
+  __shared__ __align__(16) uint16_t s_whist[kWarps][kR];   // per-warp digit counts, then each
+                                                           // (warp, digit)'s tile-local start
   __shared__ uint32_t s_gpos[kR];            // global position of local position 0 of digit d
-  __shared__ uint32_t s_lstart[kR];          // tile-local start of digit d
   __shared__ uint32_t s_scan[kWarps];
   __shared__ uint32_t s_total;
 
@@ -191,11 +192,11 @@ __global__ void __launch_bounds__(kThreads, ITEMS <= 8 ? 4 : 3) k_tile_sort(cons
     const int64_t t0 = tile * TILE;
     const int tn = (int)min((int64_t)TILE, n - t0);
     __syncthreads();   // the previous tile's shared-memory reads are done
-    for (int i = threadIdx.x; i < kWarps * kR; i += kThreads) (&s_whist[0][0])[i] = 0;
+    reinterpret_cast<uint4*>(&s_whist[0][0])[threadIdx.x] = make_uint4(0u, 0u, 0u, 0u);
 
     uint32_t k[ITEMS], v[ITEMS];
     uint8_t x[ITEMS];
-    uint16_t rank[ITEMS];
+    uint32_t rank2[(ITEMS + 1) / 2];   // 16-bit ranks, two per register
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
       const int li = warp * (ITEMS * 32) + i * 32 + lane;
@@ -233,24 +234,30 @@ __global__ void __launch_bounds__(kThreads, ITEMS <= 8 ? 4 : 3) k_tile_sort(cons
       const int leader = __ffs(peers) - 1;
       uint32_t base = 0;
       if (dg < R) base = s_whist[warp][dg];
-      rank[i] = (uint16_t)(base + __popc(peers & lt_mask));
+      const uint32_t rk = base + __popc(peers & lt_mask);
+      rank2[i / 2] = (i & 1) ? (rank2[i / 2] | (rk << 16)) : rk;
       __syncwarp();
       if (lane == leader && dg < R) s_whist[warp][dg] = (uint16_t)(base + __popc(peers));
       __syncwarp();
     }
     __syncthreads();
-    uint32_t c = 0;
+    // per digit: the warps' counts (kept in registers), the digit's tile-local start from a
+    // block scan of the totals, then each (warp, digit)'s start = digit start + the counts of
+    // the earlier warps (positions < TILE fit the 16-bit counters)
+    uint32_t cw[kWarps], c = 0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+      cw[w] = d < R ? s_whist[w][d] : 0u;
+      c += cw[w];
+    }
+    const uint32_t lstart = block_excl_scan(d < R ? c : 0u, s_scan, &s_total);   // (barriers inside)
     if (d < R) {
+      uint32_t run = lstart;
 #pragma unroll
       for (int w = 0; w < kWarps; ++w) {
-        const uint32_t x = s_whist[w][d];
-        s_whist[w][d] = (uint16_t)c;
-        c += x;
+        s_whist[w][d] = (uint16_t)run;
+        run += cw[w];
       }
-    }
-    const uint32_t lstart = block_excl_scan(d < R ? c : 0u, s_scan, &s_total);
-    if (d < R) {
-      s_lstart[d] = lstart;
       s_gpos[d] = gfirst - lstart;
     }
     __syncthreads();
@@ -258,7 +265,7 @@ __global__ void __launch_bounds__(kThreads, ITEMS <= 8 ? 4 : 3) k_tile_sort(cons
     for (int i = 0; i < ITEMS; ++i) {
       if (k[i] != 0xffffffffu) {
         const int dg = (int)((k[i] >> shift) & mask);
-        const uint32_t p = s_lstart[dg] + s_whist[warp][dg] + rank[i];
+        const uint32_t p = s_whist[warp][dg] + ((rank2[i / 2] >> (16 * (i & 1))) & 0xffffu);
         s_keys[p] = (KeyT)k[i];
         s_vals[p] = v[i];
         if (aux_in) s_aux[p] = x[i];
