@@ -47,7 +47,7 @@ struct BinWs {
   unsigned long long* bsum;   // per emission block: super instances, then exclusive prefix
   char* skeys[2];             // super-tile ids (uint16 or uint32)
   uint32_t* svals[2];         // items
-  uint8_t* saux[2];           // covered part of the super-tile (cover_byte)
+  uint8_t* saux[2];           // covered part of the super-tile (cover byte)
   uint32_t* hist;             // per-tile digit counters of the item (depth) sort
   uint32_t* sweep;            // per-tile digit counters of the super-instance sort
   uint32_t* sranges;          // [n_tiles][2]: super-tile ranges (super-tiles never outnumber tiles)
@@ -129,16 +129,10 @@ __device__ __forceinline__ ushort4 super_rect(ushort4 r) {
   return make_ushort4(r.x / kSuper, r.y / kSuper, (r.z - 1) / kSuper + 1, (r.w - 1) / kSuper + 1);
 }
 
-// The tiles of super-tile (sx, sy) that tile rect r covers, as one byte: first and last
-// covered column (bits 0-1, 2-3) and row (bits 4-5, 6-7) inside its 4 x 4 block.  The rect
-// touches the super-tile and lies inside the view's tile grid, so every field is in 0..3.
-__device__ __forceinline__ uint8_t cover_byte(ushort4 r, int sx, int sy) {
-  const int tx0 = kSuper * sx, ty0 = kSuper * sy;
-  const int lx0 = max((int)r.x - tx0, 0), lx1 = min((int)r.z - 1 - tx0, kSuper - 1);
-  const int ly0 = max((int)r.y - ty0, 0), ly1 = min((int)r.w - 1 - ty0, kSuper - 1);
-  return (uint8_t)(lx0 | (lx1 << 2) | (ly0 << 4) | (ly1 << 6));
-}
-
+// Cover byte: the tiles of a super-tile that an item's tile rect covers, as the first and
+// last covered column (bits 0-1, 2-3) and row (bits 4-5, 6-7) inside its 4 x 4 block.  The
+// rect touches the super-tile and lies inside the view's tile grid, so every field is in
+// 0..3; k_emit writes one per super instance.
 // Bit (fy * kSuper + fx) set for every tile of the block that a cover byte covers.
 __device__ __forceinline__ uint32_t cover_mask(uint32_t c) {
   const int x0 = c & 3, x1 = (c >> 2) & 3, y0 = (c >> 4) & 3, y1 = c >> 6;
@@ -230,7 +224,10 @@ __global__ void __launch_bounds__(1024) k_count_top(unsigned long long* __restri
 // Expansion into super instances: each warp takes 32 consecutive depth-sorted items and
 // writes their super-tile ids, items and cover bytes contiguously (row-major inside each
 // super rect); lanes locate the item of their instance by a binary search over the warp's
-// inclusive prefix.
+// inclusive prefix.  The owner's data travels in six shuffles (packed 16-bit fields), the
+// row inside its super rect comes from a float reciprocal with an exact integer correction,
+// and its cover byte from the four edge offsets of its rect (inner super-tiles are covered
+// whole).
 template <typename KeyT>
 __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restrict__ order, int64_t n,
                                                        const ushort4* __restrict__ rect,
@@ -242,18 +239,24 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
   __shared__ uint32_t s_wtot[kEmitThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t i = (int64_t)blockIdx.x * kEmitThreads + threadIdx.x;
-  uint32_t item = 0, cnt = 0;
-  ushort4 sr = make_ushort4(0, 0, 0, 0), tr = sr;
-  int sbase = 0, sw = 0;
+  uint32_t item = 0, cnt = 0, sbase = 0;
+  uint32_t org = 0;    // super rect origin: x | y << 16
+  uint32_t dims = 1;   // super rect width | view's super-tile row length << 16
+  uint32_t edge = 0;   // cover fields of the rect's first/last super column and row
   if (i < n) {
     item = order[i];
-    tr = rect[item];
-    sr = super_rect(tr);
+    const ushort4 tr = rect[item];
+    const ushort4 sr = super_rect(tr);
     cnt = (uint32_t)(sr.z - sr.x) * (uint32_t)(sr.w - sr.y);
     if (cnt) {
       const int v = find_view_by_item(views, n_views, (int64_t)item);
-      sbase = (int)super_base[v];
-      sw = super_w(views[v]);
+      sbase = super_base[v];
+      org = (uint32_t)sr.x | ((uint32_t)sr.y << 16);
+      dims = (uint32_t)(sr.z - sr.x) | ((uint32_t)super_w(views[v]) << 16);
+      // first covered column inside the first super column, last inside the last one, etc.
+      const uint32_t fx0 = tr.x - kSuper * sr.x, fx1 = tr.z - 1 - kSuper * (sr.z - 1);
+      const uint32_t fy0 = tr.y - kSuper * sr.y, fy1 = tr.w - 1 - kSuper * (sr.w - 1);
+      edge = fx0 | (fx1 << 2) | (fy0 << 4) | (fy1 << 6) | ((uint32_t)(sr.w - sr.y) << 8);
     }
   }
   uint32_t incl = cnt;
@@ -268,7 +271,6 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
   unsigned long long wbase = bpre[blockIdx.x];
   for (int w = 0; w < warp; ++w) wbase += s_wtot[w];
   const uint32_t excl = incl - cnt;
-  const int rw = (int)sr.z - (int)sr.x;
   for (uint32_t e0 = 0; e0 < wtot; e0 += 32) {
     const uint32_t e = e0 + lane;
     int lo = 0;
@@ -279,26 +281,30 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
     }
     const int owner = lo < 31 ? lo : 31;
     const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, owner);
-    const int o_rw = __shfl_sync(0xffffffffu, rw, owner);
-    const int o_x0 = __shfl_sync(0xffffffffu, (int)sr.x, owner);
-    const int o_y0 = __shfl_sync(0xffffffffu, (int)sr.y, owner);
-    const int o_sb = __shfl_sync(0xffffffffu, sbase, owner);
-    const int o_sw = __shfl_sync(0xffffffffu, sw, owner);
     const uint32_t o_item = __shfl_sync(0xffffffffu, item, owner);
-    const uint32_t o_r01 = __shfl_sync(0xffffffffu, (uint32_t)tr.x | ((uint32_t)tr.y << 16), owner);
-    const uint32_t o_r23 = __shfl_sync(0xffffffffu, (uint32_t)tr.z | ((uint32_t)tr.w << 16), owner);
+    const uint32_t o_sb = __shfl_sync(0xffffffffu, sbase, owner);
+    const uint32_t o_org = __shfl_sync(0xffffffffu, org, owner);
+    const uint32_t o_dims = __shfl_sync(0xffffffffu, dims, owner);
+    const uint32_t o_edge = __shfl_sync(0xffffffffu, edge, owner);
     if (e < wtot) {
       const uint32_t r = e - o_excl;
-      const uint32_t ty = r / (uint32_t)o_rw;
-      const uint32_t tx = r - ty * (uint32_t)o_rw;
+      const uint32_t rw = o_dims & 0xffffu;
+      // ty = r / rw: the float estimate is within one of the quotient, then corrected
+      float inv;
+      asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"((float)rw));
+      uint32_t ty = (uint32_t)(((float)r + 0.5f) * inv);
+      if (ty * rw > r) --ty;
+      if ((ty + 1u) * rw <= r) ++ty;
+      const uint32_t tx = r - ty * rw;
       const unsigned long long pos = wbase + e;
       if (pos < (unsigned long long)capacity) {
-        const int sx = o_x0 + (int)tx, sy = o_y0 + (int)ty;
-        skeys[pos] = (KeyT)((uint32_t)o_sb + (uint32_t)sy * (uint32_t)o_sw + (uint32_t)sx);
+        const uint32_t sx = (o_org & 0xffffu) + tx, sy = (o_org >> 16) + ty;
+        skeys[pos] = (KeyT)(o_sb + sy * (o_dims >> 16) + sx);
         svals[pos] = o_item;
-        const ushort4 orr = make_ushort4((unsigned short)(o_r01 & 0xffffu), (unsigned short)(o_r01 >> 16),
-                                         (unsigned short)(o_r23 & 0xffffu), (unsigned short)(o_r23 >> 16));
-        saux[pos] = cover_byte(orr, sx, sy);
+        const uint32_t rh = o_edge >> 8;
+        const uint32_t lx0 = tx == 0 ? (o_edge & 3u) : 0u, lx1 = tx == rw - 1 ? ((o_edge >> 2) & 3u) : 3u;
+        const uint32_t ly0 = ty == 0 ? ((o_edge >> 4) & 3u) : 0u, ly1 = ty == rh - 1 ? ((o_edge >> 6) & 3u) : 3u;
+        saux[pos] = (uint8_t)(lx0 | (lx1 << 2) | (ly0 << 4) | (ly1 << 6));
       }
     }
   }

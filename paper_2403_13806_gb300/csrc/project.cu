@@ -7,6 +7,7 @@
 // bandwidth.
 #include <math.h>
 
+#include "params.cuh"
 #include "profile.cuh"
 #include "radsplat.h"
 #include "rs_common.cuh"
@@ -31,7 +32,7 @@ struct ProjectArgs {
 };
 
 // View-independent part of a Gaussian: rotation, scales and opacity (identical operations
-// whichever view uses them).
+// whichever view uses them).  Parameter rows as in params.cuh.
 struct GaussLocal {
   float R[3][3];
   float s[3];
@@ -40,8 +41,6 @@ struct GaussLocal {
   bool ok;    // finite, non-zero quaternion and o >= 1/255 (else the item is culled)
 };
 
-// Parameters of one Gaussian: means (3), log-scales (3), quaternion (4), opacity logit,
-// then the SH coefficients k * 3 + c; P(i) returns parameter row i.
 template <int D, typename P>
 __device__ __forceinline__ GaussLocal gauss_local(const P& prm) {
   constexpr int NC = (D + 1) * (D + 1);
@@ -182,28 +181,6 @@ __device__ __forceinline__ void project_view(const ProjectArgs& a, const rs_view
   a.n_tiles[item] = o_n;
 }
 
-// Parameter rows of Gaussian gid straight from the structure-of-arrays inputs.
-struct GlobalParams {
-  const rs_gaussians* g;
-  int64_t gid;
-  __device__ __forceinline__ float operator()(int i) const {
-    const int64_t N = g->n;
-    const float* base = i < 3 ? g->means + (int64_t)i * N
-                      : i < 6 ? g->log_scales + (int64_t)(i - 3) * N
-                      : i < 10 ? g->quats + (int64_t)(i - 6) * N
-                      : i < 11 ? g->opacity_logit
-                               : g->sh + (int64_t)(i - 11) * N;
-    return __ldg(base + gid);
-  }
-};
-
-// Parameter rows staged in shared memory: row i of the thread's column.
-struct SmemParams {
-  const float* col;
-  int stride;
-  __device__ __forceinline__ float operator()(int i) const { return col[i * stride]; }
-};
-
 // Visibility-list batches: one thread per item.
 template <int D>
 __global__ void __launch_bounds__(256) k_project(ProjectArgs a) {
@@ -226,27 +203,10 @@ constexpr int kProjDenseThreads = 128;
 
 template <int D>
 __global__ void __launch_bounds__(kProjDenseThreads) k_project_dense(ProjectArgs a) {
-  constexpr int NC = (D + 1) * (D + 1);
-  constexpr int ROWS = 11 + 3 * NC;
-  __shared__ float s_p[ROWS][kProjDenseThreads];
+  __shared__ float s_p[ParamRows<D>::value][kProjDenseThreads];
   const int64_t gid = (int64_t)blockIdx.x * kProjDenseThreads + threadIdx.x;
   if (gid >= a.g.n) return;   // no barrier below: each thread reads only its own column
-  {
-    const int64_t N = a.g.n;
-    const float* rows[5] = {a.g.means, a.g.log_scales, a.g.quats, a.g.opacity_logit, a.g.sh};
-    const int first[5] = {0, 3, 6, 10, 11};
-    const int count[5] = {3, 3, 4, 1, 3 * NC};
-#pragma unroll
-    for (int r = 0; r < 5; ++r) {
-#pragma unroll
-      for (int k = 0; k < count[r]; ++k) {
-        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&s_p[first[r] + k][threadIdx.x]);
-        const float* gsrc = rows[r] + (int64_t)k * N + gid;
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(gsrc) : "memory");
-      }
-    }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-  }
+  stage_params<D>(a.g, gid, &s_p[0][threadIdx.x], kProjDenseThreads);
   const SmemParams prm{&s_p[0][threadIdx.x], kProjDenseThreads};
   const GaussLocal gl = gauss_local<D>(prm);
 #pragma unroll 1

@@ -20,6 +20,7 @@
 //   (including the view-direction term of the mean).
 #include <math.h>
 
+#include "params.cuh"
 #include "profile.cuh"
 #include "radsplat.h"
 #include "blend.cuh"
@@ -313,18 +314,15 @@ struct SmemSH {
   __device__ __forceinline__ void add(int k, int c, float v) { col[(3 * k + c) * stride] += v; }
 };
 
-template <int D, typename SH>
-__device__ __forceinline__ void item_backward(const BwdProjArgs& a, const rs_view& cam, int64_t gid, int64_t item,
+template <int D, typename SH, typename P>
+__device__ __forceinline__ void item_backward(const BwdProjArgs& a, const rs_view& cam, const P& prm, int64_t item,
                                               float4 ga, float4 gb, float gcb, ParamGrad<D>& pg, SH& shg) {
   constexpr int NC = (D + 1) * (D + 1);
-  const int64_t N = a.g.n;
   const float* W = cam.viewmat;
-  const float px = __ldg(a.g.means + gid), py = __ldg(a.g.means + N + gid), pz = __ldg(a.g.means + 2 * N + gid);
-  const float l0 = __ldg(a.g.log_scales + gid), l1 = __ldg(a.g.log_scales + N + gid),
-              l2 = __ldg(a.g.log_scales + 2 * N + gid);
-  const float qw = __ldg(a.g.quats + gid), qx = __ldg(a.g.quats + N + gid), qy = __ldg(a.g.quats + 2 * N + gid),
-              qz = __ldg(a.g.quats + 3 * N + gid);
-  const float lg = __ldg(a.g.opacity_logit + gid);
+  const float px = prm(0), py = prm(1), pz = prm(2);
+  const float l0 = prm(3), l1 = prm(4), l2 = prm(5);
+  const float qw = prm(6), qx = prm(7), qy = prm(8), qz = prm(9);
+  const float lg = prm(10);
 
   // ---- forward recomputation (same formulas as the projection kernel)
   const float qn2 = qw * qw + qx * qx + qy * qy + qz * qz;
@@ -454,7 +452,7 @@ __device__ __forceinline__ void item_backward(const BwdProjArgs& a, const rs_vie
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       shg.add(k, c, gcol[c] * Y[k]);
-      t += gcol[c] * __ldg(a.g.sh + (int64_t)(k * 3 + c) * N + gid);
+      t += gcol[c] * prm(11 + 3 * k + c);
     }
     gY[k] = t;
   }
@@ -477,12 +475,14 @@ __device__ __forceinline__ bool any_grad(float4 ga, float4 gb, float gc) {
          gb.w != 0.f || gc != 0.f;
 }
 
+constexpr int kProjBwdThreads = 128;
+
 // Dense batches: item of Gaussian gid in view v is item_base[v] + gid; all views summed in
 // registers, one read-modify-write of the parameter gradients.
 template <int D>
-__global__ void __launch_bounds__(128) k_project_bwd_dense(BwdProjArgs a) {
+__global__ void __launch_bounds__(kProjBwdThreads) k_project_bwd_dense(BwdProjArgs a) {
   constexpr int NC = (D + 1) * (D + 1);
-  __shared__ float s_gsh[3 * NC][128];
+  __shared__ float s_gsh[3 * NC][kProjBwdThreads];
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t N = a.g.n;
   if (gid >= N) return;   // no barrier below: each thread owns its column
@@ -494,7 +494,10 @@ __global__ void __launch_bounds__(128) k_project_bwd_dense(BwdProjArgs a) {
   pg.lg = 0.f;
 #pragma unroll
   for (int k = 0; k < 3 * NC; ++k) s_gsh[k][threadIdx.x] = 0.f;
-  SmemSH shg{&s_gsh[0][threadIdx.x], 128};
+  SmemSH shg{&s_gsh[0][threadIdx.x], kProjBwdThreads};
+  // (parameters straight from HBM: a Gaussian no view has a gradient for reads none, and
+  // later views find them in L1; staging them in shared memory measured slower)
+  const GlobalParams prm{&a.g, gid};
   bool touched = false;
   for (int v = 0; v < a.n_views; ++v) {
     const rs_view& cam = a.views[v];
@@ -503,7 +506,7 @@ __global__ void __launch_bounds__(128) k_project_bwd_dense(BwdProjArgs a) {
     const float gc = a.gc[item];
     if (!any_grad(ga, gb, gc)) continue;
     touched = true;
-    item_backward<D>(a, cam, gid, item, ga, gb, gc, pg, shg);
+    item_backward<D>(a, cam, prm, item, ga, gb, gc, pg, shg);
   }
   if (a.overwrite) {   // every Gaussian's row is written (zeros where no view touched it)
     for (int c = 0; c < 3; ++c) {
@@ -551,7 +554,8 @@ __global__ void __launch_bounds__(128) k_project_bwd_subset(BwdProjArgs a) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) pg.sh[k][c] = 0.f;
   RegSH<D> shg{pg};
-  item_backward<D>(a, a.views[v], gid, item, ga, gb, gc, pg, shg);
+  const GlobalParams prm{&a.g, gid};
+  item_backward<D>(a, a.views[v], prm, item, ga, gb, gc, pg, shg);
   for (int c = 0; c < 3; ++c) {
     atomicAdd(a.out.means + c * N + gid, pg.m[c]);
     atomicAdd(a.out.log_scales + c * N + gid, pg.ls[c]);
@@ -680,12 +684,13 @@ extern "C" rs_status rs_render_backward(const rs_gaussians* g, const rs_view_bat
   const int threads = 128;
   prof::Scope ps("k_project_bwd", s);
   if (!batch->subset_idx) {
-    const unsigned blocks = (unsigned)((g->n + threads - 1) / threads);
+    const int dt = kProjBwdThreads;
+    const unsigned blocks = (unsigned)((g->n + dt - 1) / dt);
     switch (g->sh_degree) {
-      case 0: k_project_bwd_dense<0><<<blocks, threads, 0, s>>>(p); break;
-      case 1: k_project_bwd_dense<1><<<blocks, threads, 0, s>>>(p); break;
-      case 2: k_project_bwd_dense<2><<<blocks, threads, 0, s>>>(p); break;
-      default: k_project_bwd_dense<3><<<blocks, threads, 0, s>>>(p); break;
+      case 0: k_project_bwd_dense<0><<<blocks, dt, 0, s>>>(p); break;
+      case 1: k_project_bwd_dense<1><<<blocks, dt, 0, s>>>(p); break;
+      case 2: k_project_bwd_dense<2><<<blocks, dt, 0, s>>>(p); break;
+      default: k_project_bwd_dense<3><<<blocks, dt, 0, s>>>(p); break;
     }
   } else {
     const unsigned blocks = (unsigned)((batch->n_items + threads - 1) / threads);
