@@ -722,11 +722,11 @@ OPS_PER_PAIR = {"k_render_importance": 22, "k_render": 22, "k_render_bwd": 46}
 NCU_TRAFFIC = {
     "k_render_bwd": {"bytes_per_view": 25184256, "files": ['render_bwd.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "f50bf20b9822d499",
                 "profile": "k_render_bwd_1M_1view.md"},
-    "k_render_importance": {"bytes_per_view": 5254400, "files": ['render.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "ce077fcbd7e1da48",
+    "k_render_importance": {"bytes_per_view": 4444160, "files": ['render.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "6ec018646b87f52c",
                 "profile": "k_render_1M_1view.md"},
-    "k_fine_scatter": {"bytes_per_view": 24176384, "files": ['binsort.cu', 'rs_common.cuh'], "sha": "4c469002ded06892",
+    "k_fine_scatter": {"bytes_per_view": 20175616, "files": ['binsort.cu', 'rs_common.cuh'], "sha": "ee663dabd98a9a53",
                 "profile": "k_fine_scatter_1M_1view.md"},
-    "k_ssim_stats": {"bytes_per_view": 26043648, "files": ['ssim.cu', 'rs_common.cuh'], "sha": "964260dd02b43d8e",
+    "k_ssim_stats": {"bytes_per_view": 26171392, "files": ['ssim.cu', 'rs_common.cuh'], "sha": "965f973c9899546e",
                 "profile": "k_ssim_stats_1view.md"},
 }
 
