@@ -311,7 +311,7 @@ def run_ours(args):
     stage_ms, kernel_ms, work_counts = stage_times(api, N, torch, g, chunks, cfg, st, proj, h, gbuf, loss, ws_sort,
                                                    ws_bwd, ws_f, mask, idx, reps=max(3, min(args.steps, 10)),
                                                    loss_fn=loss_fn)
-    pairs, n_super = work_counts["pairs"], work_counts["super_instances"]
+    pairs, n_super, touched = work_counts["pairs"], work_counts["super_instances"], work_counts["touched"]
 
     # plain: the same views one at a time, no graph
     plain = None
@@ -328,7 +328,7 @@ def run_ours(args):
     hbm, peak_kind, pk = peaks()
     optim = optimizer_bench(api, N, torch, g, gbuf, h, hbm, reps=10)
     uneven = uneven_bench(api, N, torch, dev, args.uneven_views, reps=3) if args.uneven_views > 0 else None
-    work = kernel_work(vbs, sres, pairs, n_super)
+    work = kernel_work(vbs, sres, pairs, n_super, touched)
     roof = roofline(kernel_ms, work, hbm, peak_kind, B)
     per_kernel = {k: kernel_frac(k, kernel_ms[k], work, hbm) for k in kernel_ms if k in work}
     launches = int(round(sum(v["launches_per_step"] for v in kernel_ms.values()))) * args.steps
@@ -348,6 +348,7 @@ def run_ours(args):
             "batched_over_plain_speedup": round(plain / value, 3) if plain else None,
             "fps_forward_single_view": round(fps, 1) if fps else None,
             "instances_per_view": int(sres["n_instances"] / B),
+            "gaussians_with_gradient": touched,
             "super_instances_per_view": int(n_super / V),
             "pairs_per_pixel": round(pairs / sum(vb.n_pixels for vb in vbs), 2),
             "blends_per_s_forward": round(pairs / (kernel_ms["k_render_importance"]["ms_per_step"] / 1e3), 0)
@@ -428,8 +429,12 @@ def stage_times(api, N, torch, g, chunks, cfg, st, proj, h, gbuf, loss, ws_sort,
         sh = torch.where(nonempty, (r[:, 3] - 1) // 4 - r[:, 1] // 4 + 1, zero)
         n_super += int((sw * sh).sum().item())
         del r, nonempty, zero, sw, sh
+    # Gaussians some view gives a gradient (the last timed step's gradients): only their
+    # parameters are read by the projection backward
+    gm = gbuf.views[0].reshape(3, -1)
+    touched = int(((gm != 0).any(dim=0) | (gbuf.views[3].reshape(-1) != 0)).sum().item())
     torch.cuda.synchronize()
-    return acc, kernels, {"pairs": pairs, "super_instances": n_super}
+    return acc, kernels, {"pairs": pairs, "super_instances": n_super, "touched": touched}
 
 
 def uneven_bench(api, N, torch, dev, n_views, reps):
@@ -759,7 +764,7 @@ class _PerLaunch:
         self.launches = c
 
 
-def kernel_work(vbs, sres, pairs, n_super):
+def kernel_work(vbs, sres, pairs, n_super, touched):
     """Algorithmic work per launch of each library kernel: DRAM bytes the method must move
     (bound "hbm") or FP32 lane operations (bound "alu").
 
@@ -770,8 +775,10 @@ def kernel_work(vbs, sres, pairs, n_super):
     the count); the super-tile sort moves 2 x (2 + 4 + 1) B per super instance and pass
     (count: 2 B); the fine partition reads the 1 B cover byte per super instance (count),
     then 4 B item + 1 B cover byte per super instance and writes 4 B per instance (scatter);
-    the projection backward reads 236 B and writes 236 B per Gaussian (the gradients are
-    written, not accumulated) plus 52 B per item; the blend kernels count FP32 operations per evaluated pair."""
+    the projection backward writes 236 B of gradients per Gaussian (written, not
+    accumulated), reads 36 B of image-space gradients per item, and reads the 236 B of
+    parameters and the 16 B colour rows only for the `touched` Gaussians some view gives a
+    gradient (most of a dense scene is hidden behind saturated pixels); the blend kernels count FP32 operations per evaluated pair."""
     vb = _PerLaunch(vbs)
     c = vb.launches
     M, K, Ks, P = vb.n_items, sres["n_instances"], n_super / c, vb.n_pixels
@@ -794,10 +801,9 @@ def kernel_work(vbs, sres, pairs, n_super):
         "k_l1": P * 3 * 4 * 3,
         "k_ssim_stats": P * 3 * (8 + 12),
         "k_ssim_grad": P * 3 * (12 + 8 + 4),
-        # per Gaussian: parameters read once, gradients written once (all views summed in
-        # registers, written over the arrays); per item: 36 B of image-space gradients + the
-        # 16 B colour row
-        "k_project_bwd": vb.n_gaussians * (236 + 236) + M * (36 + 16),
+        # gradients written once per Gaussian (all views summed in registers); 36 B of
+        # image-space gradients read per item; parameters and colour rows of touched ones
+        "k_project_bwd": vb.n_gaussians * 236 + M * 36 + touched * (236 + 16 * M / vb.n_gaussians),
         "k_filter_count": vb.n_gaussians * 4,
         "k_filter_scatter": vb.n_gaussians * (4 + 1) + vb.n_gaussians * 4,
     }

@@ -38,7 +38,7 @@ namespace rs {
 constexpr int kEmitThreads = 256;
 constexpr int kSuper = 4;           // tiles per super-tile side
 constexpr int kFineThreads = 256;   // threads of a fine-binning CTA
-constexpr int kSegLen = 2048;       // super-list entries per fine work item (segment)
+constexpr int kSegLen = 3840;       // super-list entries per fine work item (segment; 15 per thread)
 constexpr int kNF = kSuper * kSuper;
 
 struct BinWs {
@@ -290,9 +290,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
       const uint32_t r = e - o_excl;
       const uint32_t rw = o_dims & 0xffffu;
       // ty = r / rw: the float estimate is within one of the quotient, then corrected
-      float inv;
-      asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"((float)rw));
-      uint32_t ty = (uint32_t)(((float)r + 0.5f) * inv);
+      uint32_t ty = (uint32_t)(((float)r + 0.5f) * rcp_approx((float)rw));
       if (ty * rw > r) --ty;
       if ((ty + 1u) * rw <= r) ++ty;
       const uint32_t tx = r - ty * rw;

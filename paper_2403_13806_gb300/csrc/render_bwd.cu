@@ -206,7 +206,8 @@ __global__ void __launch_bounds__(TW* TH / PX, 16) k_render_bwd(BwdBlendArgs a) 
         // a skipped entry gets alpha 0: its weight is 0 and T_j = T exactly (1/(1 - 0) = 1)
         const float2 a_eff = sel2(al.in0, al.in1, al.alpha);
         const float2 om = one_minus(a_eff);
-        const float2 inv = make_float2(__fdividef(1.f, om.x), __fdividef(1.f, om.y));
+        // 1 / (1 - alpha) with alpha <= 0.99: the hardware reciprocal
+        const float2 inv = make_float2(rcp_approx(om.x), rcp_approx(om.y));
         const float2 Tj = __fmul2_rn(T[q], inv);
         const float2 w = __fmul2_rn(a_eff, Tj);
         const float2 cG = __ffma2_rn(lo2(r.rg), Gr[q], __ffma2_rn(hi2(r.rg), Gg[q], __fmul2_rn(lo2(r.bc), Gb[q])));

@@ -17,6 +17,13 @@ constexpr float kLog2e = 1.4426950408889634f;
 
 constexpr int kNumSMs = 152;   // GB300: 2 dies x 76 SMs (grid sizing only; not a correctness input)
 
+// 1/x by the hardware approximation (rcp.approx.ftz: within 1 ulp for normal x).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // A view found by a binary search on a sorted int64 key (item_base or tile_base).
 __device__ __forceinline__ int find_view_by_item(const rs_view* views, int n_views, int64_t item) {
   int lo = 0, hi = n_views - 1;

@@ -167,7 +167,8 @@ __global__ void __launch_bounds__(kSThreads) k_ssim_stats(SsimArgs a) {
       const float ln = 2.f * mx * my + kC1, ld = mx * mx + my * my + kC1;
       const float cn = 2.f * sxy_ + kC2, cd = sxx + syy + kC2;
       // two reciprocals give all four: 1/ln = ld q1, 1/ld = ln q1, 1/cn = cd q2, 1/cd = cn q2
-      const float q1 = __frcp_rn(ln * ld), q2 = __frcp_rn(cn * cd);
+      // (the hardware approximation: the products are normal, positive numbers)
+      const float q1 = rcp_approx(ln * ld), q2 = rcp_approx(cn * cd);
       const float s = (ln * ln * q1) * (cn * cn * q2);
       const float d_mx = s * (2.f * my * ld - 2.f * mx * ln) * q1;
       const float d_sxx = -s * cn * q2;
