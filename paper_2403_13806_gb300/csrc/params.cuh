@@ -31,6 +31,17 @@ struct GlobalParams {
   }
 };
 
+// All rows of one Gaussian loaded into registers at once (every load in flight together).
+template <int D>
+struct RegParams {
+  float p[ParamRows<D>::value];
+  __device__ __forceinline__ RegParams(const GlobalParams& src) {
+#pragma unroll
+    for (int i = 0; i < ParamRows<D>::value; ++i) p[i] = src(i);
+  }
+  __device__ __forceinline__ float operator()(int i) const { return p[i]; }
+};
+
 struct SmemParams {
   const float* col;   // row i of the thread's column at col[i * stride]
   int stride;

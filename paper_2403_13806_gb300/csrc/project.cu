@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(256) k_project(ProjectArgs a) {
   const int v = find_view_by_item(a.views, a.n_views, item);
   const rs_view& cam = a.views[v];
   const int64_t gid = a.subset ? (int64_t)__ldg(a.subset + item) : item - cam.item_base;
-  const GlobalParams prm{&a.g, gid};
+  const RegParams<D> prm(GlobalParams{&a.g, gid});
   const GaussLocal gl = gauss_local<D>(prm);
   project_view<D>(a, cam, prm, gl, item);
 }
