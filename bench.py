@@ -217,25 +217,37 @@ def run_ours(args):
     chunks = list(zip(vbs, bins_of, bufs, targets))
     cfg_w = overwrite_cfg(N, cfg)
 
-    def views_part():
+    def prune():
+        api.filter(h, 0.01, N.RS_PRUNE_BELOW, ws_f, mask=mask, idx=idx)
+
+    # N = 1: the prune filter needs only the importance, complete after the last chunk's
+    # render, so it runs on a side stream beside that chunk's loss and backward (the graph
+    # captures the fork and the join)
+    side = torch.cuda.Stream(device=dev)
+    imp_done, prune_done = torch.cuda.Event(), torch.cuda.Event()
+
+    def views_part(overlap_prune=False):
         h.zero_()
         for k, (vb, bins, (img, T, L, dL), target) in enumerate(chunks):
             api.project(g, vb, cfg, st, out=proj)
             api.bin_sort(proj, vb, bins, ws_sort, st)
             api.render(proj, bins, vb, cfg, image=img, T_final=T, last=L, importance=h)
+            if overlap_prune and k == len(chunks) - 1:
+                imp_done.record()
+                with torch.cuda.stream(side):
+                    side.wait_event(imp_done)
+                    prune()
+                    prune_done.record(side)
             loss_fn(img, target, dL, loss)
             # the first launch writes the gradients, later ones add theirs
             api.render_backward(g, vb, proj, bins, T, L, dL, grads, ws_bwd, cfg_w if k == 0 else cfg)
-
-    def prune():
-        api.filter(h, 0.01, N.RS_PRUNE_BELOW, ws_f, mask=mask, idx=idx)
+        if overlap_prune:
+            torch.cuda.current_stream().wait_event(prune_done)
 
     # N = 1: the whole step is one graph.  N > 1: the per-view part is the graph, then the
     # reductions over views (NCCL) and the filter on the reduced importance.
     def step_body():
-        views_part()
-        if world == 1:
-            prune()
+        views_part(overlap_prune=(world == 1))
 
     # capture the batched step in a CUDA graph
     torch.cuda.synchronize()
@@ -648,7 +660,13 @@ def e2e_run(api, N, torch, scene, vbs, cfg, targets, cap, reps, dev, world=1, lo
         g = api.Gaussians(*dev_p, scene.sh_degree)
         gbuf = rd.GradBuffer(dev_p)
 
-        def views_part():
+        def prune():
+            api.filter(h, 0.01, N.RS_PRUNE_BELOW, ws_f, mask=mask, idx=idx)
+
+        side = torch.cuda.Stream(device=dev)
+        imp_done, prune_done = torch.cuda.Event(), torch.cuda.Event()
+
+        def views_part(overlap_prune=False):
             h.zero_()
             for i, vb in enumerate(vbs):
                 bins = api.Bins(bins_all.vals, bins_all.ranges[:vb.n_tiles], None, cap)
@@ -656,14 +674,19 @@ def e2e_run(api, N, torch, scene, vbs, cfg, targets, cap, reps, dev, world=1, lo
                 api.bin_sort(proj, vb, bins, ws_sort, st)
                 img, T, L = api.render(proj, bins, vb, cfg, image=img_buf[i], T_final=T_buf[i], last=L_buf[i],
                                        importance=h)
+                if overlap_prune and i == len(vbs) - 1:   # the filter beside the last loss and backward
+                    imp_done.record()
+                    with torch.cuda.stream(side):
+                        side.wait_event(imp_done)
+                        prune()
+                        prune_done.record(side)
                 loss, dl = loss_fn(img, tgt_d[i], dL=dl_buf[i], loss=loss_d[i:i + 1])
                 api.render_backward(g, vb, proj, bins, T, L, dl, gbuf.views, ws_bwd, cfg_w if i == 0 else cfg)
-
-        def prune():
-            api.filter(h, 0.01, N.RS_PRUNE_BELOW, ws_f, mask=mask, idx=idx)
+            if overlap_prune:
+                torch.cuda.current_stream().wait_event(prune_done)
 
         if world == 1:
-            sg = api.StepGraph(lambda: (views_part(), prune()), outputs=[(loss_d, loss_h)], device=dev)
+            sg = api.StepGraph(lambda: views_part(overlap_prune=True), outputs=[(loss_d, loss_h)], device=dev)
         else:
             sg = api.StepGraph(views_part, device=dev)
         return {"p": dev_p, "t": tgt_d, "sg": sg, "gbuf": gbuf, "prune": prune}
