@@ -10,7 +10,7 @@
 //   (S_j: colour composited behind j), and through a = o exp(power) (no gradient where the
 //   0.99 clamp is active) the image-space gradients of the mean, conic and opacity.  The
 //   nine values of a thread's pixels are summed in registers, across the warp by
-//   recursive halving (16 shuffles, only for entries some lane composited), across the
+//   recursive halving (14 shuffles, only for entries some lane composited), across the
 //   CTA through per-warp shared-memory slots, and added to per-item buffers with two
 //   float4 and one float atomic per (tile, entry).
 // k_project_bwd -- one thread per Gaussian (all views of the Gaussian summed in registers)
@@ -50,13 +50,14 @@ struct BwdBlendArgs {
   Grad2D g;
 };
 
-// Sums v[0..15] over the warp by recursive halving: at each step a lane keeps half of its
-// values and trades the other half with its partner, so the 16 sums take 16 shuffles.
-// On return lanes 2c and 2c + 1 hold the warp total of component c.
-__device__ __forceinline__ float warp_transpose_sum16(float (&v)[16]) {
+// Sums v[0..7] and s over the warp: v by recursive halving over lane bits 16, 8, 4 (7
+// shuffles) and then plain butterflies over bits 2, 1; s by a plain butterfly (5 shuffles).
+// On return lanes 4c .. 4c + 3 hold the warp total of v[c] (the return value) and every lane
+// holds the total of s.
+__device__ __forceinline__ float warp_transpose_sum8_plus1(float (&v)[8], float& s) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+  for (int h = 4, o = 16; h >= 1; h >>= 1, o >>= 1) {
     const bool hi = (lane & o) != 0;
 #pragma unroll
     for (int i = 0; i < h; ++i) {
@@ -64,8 +65,15 @@ __device__ __forceinline__ float warp_transpose_sum16(float (&v)[16]) {
       const float keep = hi ? v[i + h] : v[i];
       v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
     }
+    s += __shfl_xor_sync(0xffffffffu, s, o);
   }
-  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+  float t = v[0];
+#pragma unroll
+  for (int o = 2; o >= 1; o >>= 1) {
+    t += __shfl_xor_sync(0xffffffffu, t, o);
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
+  return t;
 }
 
 __device__ __forceinline__ float2 sel2(bool a, bool b, float2 x) {
@@ -232,7 +240,7 @@ __global__ void __launch_bounds__(TW* TH / PX, 16) k_render_bwd(BwdBlendArgs a) 
         const float d = dx.x;
         const float A = r.ab.x, B = r.ab.z, C = r.co.x;
         const float kl = 0.6931471805599453f;
-        float rr[16];
+        float rr[8];
         rr[0] = kl * (2.f * A * d * Q + B * Qy);
         rr[1] = kl * (B * d * Q + 2.f * C * Qy);
         rr[2] = -0.5f * d * d * Q;
@@ -241,11 +249,10 @@ __global__ void __launch_bounds__(TW* TH / PX, 16) k_render_bwd(BwdBlendArgs a) 
         rr[5] = acc_o.x + acc_o.y;
         rr[6] = acc_r.x + acc_r.y;
         rr[7] = acc_g.x + acc_g.y;
-        rr[8] = acc_b.x + acc_b.y;
-#pragma unroll
-        for (int c = 9; c < 16; ++c) rr[c] = 0.f;
-        const float tot = warp_transpose_sum16(rr);
-        if ((lane & 1) == 0 && lane < 18) part[(lane >> 1) * PS + j] = tot;
+        float r8 = acc_b.x + acc_b.y;
+        const float tot = warp_transpose_sum8_plus1(rr, r8);
+        if ((lane & 3) == 0) part[(lane >> 2) * PS + j] = tot;
+        if (lane == 1) part[8 * PS + j] = r8;
       } else if (lane < 9) {
         part[lane * PS + j] = 0.f;
       }
