@@ -748,13 +748,13 @@ OPS_PER_PAIR = {"k_render_importance": 22, "k_render": 22, "k_render_bwd": 46}
 # of the sources the kernel was built from.  A capture stays valid only while those sources
 # are unchanged; otherwise the roofline reports traffic as null.
 NCU_TRAFFIC = {
-    "k_render_bwd": {"bytes_per_view": 25184256, "files": ['render_bwd.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "f50bf20b9822d499",
+    "k_render_bwd": {"bytes_per_view": 25188352, "files": ['render_bwd.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "f030b2ab72f459ba",
                 "profile": "k_render_bwd_1M_1view.md"},
-    "k_render_importance": {"bytes_per_view": 4444160, "files": ['render.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "6ec018646b87f52c",
+    "k_render_importance": {"bytes_per_view": 4451584, "files": ['render.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "2563e143b71aae9f",
                 "profile": "k_render_1M_1view.md"},
-    "k_fine_scatter": {"bytes_per_view": 20175616, "files": ['binsort.cu', 'rs_common.cuh'], "sha": "ee663dabd98a9a53",
+    "k_fine_scatter": {"bytes_per_view": 20113664, "files": ['binsort.cu', 'rs_common.cuh'], "sha": "003261fc213ee33e",
                 "profile": "k_fine_scatter_1M_1view.md"},
-    "k_ssim_stats": {"bytes_per_view": 26171392, "files": ['ssim.cu', 'rs_common.cuh'], "sha": "965f973c9899546e",
+    "k_ssim_stats": {"bytes_per_view": 25871360, "files": ['ssim.cu', 'rs_common.cuh'], "sha": "77368fb65aa91f37",
                 "profile": "k_ssim_stats_1view.md"},
 }
 
@@ -902,7 +902,7 @@ def oracle_sample_time(n_small: int, n_big: int, threads: int, seed: int = 0):
 
 def cpu_baseline(args):
     threads = os.cpu_count() or 1
-    n_small, n_big = 32, 160
+    n_small, n_big = 64, 480
     try:
         dt, ms_view = oracle_sample_time(n_small, n_big, threads)
     except Exception as e:  # the baseline is reported, not required

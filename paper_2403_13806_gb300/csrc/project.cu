@@ -37,6 +37,7 @@ struct GaussLocal {
   float R[3][3];
   float s[3];
   float o;
+  float q;    // 2 ln(255 o) clamped at 0: the support ellipse is d^T Sigma'^-1 d <= q
   bool fin;   // every parameter finite
   bool ok;    // finite, non-zero quaternion and o >= 1/255 (else the item is culled)
 };
@@ -70,6 +71,7 @@ __device__ __forceinline__ GaussLocal gauss_local(const P& prm) {
   gl.s[1] = expf(l1);
   gl.s[2] = expf(l2);
   gl.o = 1.f / (1.f + expf(-lg));
+  gl.q = fmaxf(2.f * logf(255.f * gl.o), 0.f);
   gl.ok = fin && qn2 > 0.f && !(gl.o < kAlphaMin);
   return gl;
 }
@@ -140,7 +142,7 @@ __device__ __forceinline__ void project_view(const ProjectArgs& a, const rs_view
 
     // support: alpha >= 1/255  <=>  d^T Sigma'^-1 d <= 2 ln(255 o); bounding box of that
     // ellipse, widened by a relative 2^-12 and 2^-10 px to stay a superset under rounding
-    const float q = fmaxf(2.f * logf(255.f * o), 0.f);
+    const float q = gl.q;
     const float ex = sqrtf(q * ea) * (1.f + 0x1p-12f) + 0x1p-10f;
     const float ey = sqrtf(q * ec) * (1.f + 0x1p-12f) + 0x1p-10f;
     const float u0 = fmaxf(ceilf(mx - ex), 0.f), u1 = fminf(floorf(mx + ex), (float)(cam.width - 1));
