@@ -59,7 +59,8 @@ struct BinWs {
   int64_t n_work_max;         // segments: at most capacity / kSegLen + one per super-tile
   uint32_t* counters;         // [0] super instances written, [2] instances written,
                               // [4], [5] work counters of the fine count and scatter,
-                              // [6] item count (the depth sort's device count), [7] segments
+                              // [6] item count (the depth sort's device count), [7] segments,
+                              // [8..11] the super-tile sort's digits (shift, bits) per pass
   size_t bytes;
 };
 
@@ -109,10 +110,16 @@ __global__ void k_depth_keys(const float4* __restrict__ rgb_d, int64_t n, uint32
   vals[i] = (uint32_t)i;
 }
 
-// First super-tile id of every view (exclusive prefix of the views' super-tile counts), and
-// the item count as the depth sort's device count.
+// First super-tile id of every view (exclusive prefix of the views' super-tile counts), the
+// item count as the depth sort's device count, and the digits of the super-tile sort.  The
+// host plans its passes for a bound on the ids (host_bits, from the tile count): P passes
+// of tiles::sort_passes' widths.  The ids actually need b <= host_bits bits; the device
+// digits are as even as the host widths allow (each at most ceil(b / P) and at most the
+// host's width for that pass, any shortfall added to the earliest passes with room), so
+// they cover the b bits and the host's launch grids cover every digit value.
 __global__ void k_super_layout(const rs_view* __restrict__ views, int n_views, uint32_t* __restrict__ super_base,
-                               int64_t n_items, uint32_t* __restrict__ n_dev) {
+                               int64_t n_items, uint32_t* __restrict__ n_dev, int host_bits,
+                               int32_t* __restrict__ digits) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   *n_dev = (uint32_t)n_items;
   uint32_t run = 0;
@@ -121,6 +128,26 @@ __global__ void k_super_layout(const rs_view* __restrict__ views, int n_views, u
     run += (uint32_t)(super_w(views[v]) * super_h(views[v]));
   }
   super_base[n_views] = run;
+  int b = 1;
+  while (b < 32 && (1u << b) < run) ++b;
+  const int P = tiles::sort_passes(host_bits);   // at most 4
+  const int rh = (host_bits + P - 1) / P;
+  int width[4], dv[4], used = 0;
+  for (int p = 0; p < P; ++p) {
+    width[p] = (p * rh + rh <= host_bits) ? rh : host_bits - p * rh;
+    dv[p] = min(width[p], (b + P - 1) / P);
+    used += dv[p];
+  }
+  for (int p = 0; p < P && used < b; ++p) {
+    const int add = min(b - used, width[p] - dv[p]);
+    dv[p] += add;
+    used += add;
+  }
+  for (int p = 0, shift = 0; p < P; ++p) {
+    digits[2 * p] = shift;
+    digits[2 * p + 1] = dv[p];
+    shift += dv[p];
+  }
 }
 
 // Super-tile rect of an item's tile rect (both half-open).
@@ -767,7 +794,7 @@ static int super_instances(const BinWs& w, const uint32_t* order, int64_t n, con
   const int cur = tiles::sort_pairs<KeyT>(k0, w.svals[0], k1, w.svals[1], w.counters, cap, bits_for(n_super_max),
                                           w.sweep, s, true,
                                           {"k_super_sort_hist", "k_super_sort_scan", "k_super_sort"}, w.saux[0],
-                                          w.saux[1]);
+                                          w.saux[1], reinterpret_cast<const int32_t*>(w.counters + 8));
   const KeyT* sk = cur ? k1 : k0;
   prof::Scope ps("k_ranges", s);
   k_ranges<KeyT><<<4 * kNumSMs, 256, 0, s>>>(sk, w.counters, (uint32_t)n_super_max, w.sranges);
@@ -801,7 +828,8 @@ extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* 
   if (cudaMemsetAsync(w.sranges, 0, (size_t)n_super_max * 8, s) != cudaSuccess) return RS_ERR_CUDA;
   {
     prof::Scope ps("k_super_layout", s);
-    k_super_layout<<<1, 32, 0, s>>>(batch->views, batch->n_views, w.super_base, n, w.counters + 6);
+    k_super_layout<<<1, 32, 0, s>>>(batch->views, batch->n_views, w.super_base, n, w.counters + 6,
+                                    bits_for(n_super_max), reinterpret_cast<int32_t*>(w.counters + 8));
   }
   int scur = 0;   // buffer set of the sorted super instances
   if (n > 0) {

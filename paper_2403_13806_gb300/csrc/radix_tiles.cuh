@@ -64,12 +64,16 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* s_warp
 }
 
 // Passes of at most 8 bits for a sort on `bits` key bits.
-inline int sort_passes(int bits) { return bits < 1 ? 1 : (bits + 7) / 8; }
+__host__ __device__ inline int sort_passes(int bits) { return bits < 1 ? 1 : (bits + 7) / 8; }
 
 template <typename KeyT, int TILE = kTile>
 __global__ void __launch_bounds__(kThreads) k_tile_hist(const KeyT* __restrict__ keys, const uint32_t* __restrict__ n_dev,
-                                                        int shift, int rbits, int64_t n_tiles_max,
-                                                        uint32_t* __restrict__ cnt) {
+                                                        int shift, int rbits, const int32_t* __restrict__ dig,
+                                                        int64_t n_tiles_max, uint32_t* __restrict__ cnt) {
+  if (dig) {   // the pass's digit from the device (shift, bits)
+    shift = dig[0];
+    rbits = dig[1];
+  }
   __shared__ uint32_t s[kWarps][kR];
   const int warp = threadIdx.x >> 5;
   const int64_t n = *n_dev;
@@ -108,7 +112,9 @@ __global__ void __launch_bounds__(kThreads) k_tile_hist(const KeyT* __restrict__
 // tiles of the device count (rows have stride n_tiles_max); tot[d] = total.
 template <int TILE>
 __global__ void __launch_bounds__(1024) k_tile_scan(uint32_t* __restrict__ cnt, const uint32_t* __restrict__ n_dev,
-                                                    int64_t n_tiles_max, uint32_t* __restrict__ tot) {
+                                                    const int32_t* __restrict__ dig, int64_t n_tiles_max,
+                                                    uint32_t* __restrict__ tot) {
+  if (dig && (int)blockIdx.x >= (1 << dig[1])) return;   // a digit value the device digit cannot take
   __shared__ uint32_t s_w[32];
   __shared__ uint32_t s_carry;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -163,6 +169,7 @@ __global__ void __launch_bounds__(kThreads, ITEMS <= 8 ? 4 : 3) k_tile_sort(cons
                                                            KeyT* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
                                                            uint8_t* __restrict__ aux_out,
                                                            const uint32_t* __restrict__ n_dev, int shift, int rbits,
+                                                           const int32_t* __restrict__ dig,
                                                            const uint32_t* __restrict__ cnt, int64_t n_tiles_max,
                                                            const uint32_t* __restrict__ tot) {
   constexpr int TILE = kThreads * ITEMS;
@@ -176,6 +183,10 @@ __global__ void __launch_bounds__(kThreads, ITEMS <= 8 ? 4 : 3) k_tile_sort(cons
   __shared__ uint32_t s_scan[kWarps];
   __shared__ uint32_t s_total;
 
+  if (dig) {
+    shift = dig[0];
+    rbits = dig[1];
+  }
   const int R = 1 << rbits;
   const uint32_t mask = (uint32_t)R - 1u;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -303,10 +314,13 @@ struct SortNames {
 };
 
 // aux0 / aux1 (optional, both or neither): a byte payload that travels with each pair.
+// dev_digits (optional): a device array of (shift, bits) per pass that replaces the host's
+// digit plan when the kernels run (keys known on the device to need fewer bits); each pass's
+// device bits must not exceed the host plan's bits for that pass.
 template <typename KeyT, int ITEMS = kItems>
 inline int sort_pairs(KeyT* k0, uint32_t* v0, KeyT* k1, uint32_t* v1, const uint32_t* n_dev, int64_t n_max, int bits,
                       uint32_t* scratch, cudaStream_t s, bool write_last_keys, const SortNames& names,
-                      uint8_t* aux0 = nullptr, uint8_t* aux1 = nullptr) {
+                      uint8_t* aux0 = nullptr, uint8_t* aux1 = nullptr, const int32_t* dev_digits = nullptr) {
   constexpr int TILE = kThreads * ITEMS;
   const int passes = sort_passes(bits);
   const int rbits = (bits + passes - 1) / passes;
@@ -328,17 +342,18 @@ inline int sort_pairs(KeyT* k0, uint32_t* v0, KeyT* k1, uint32_t* v1, const uint
     const uint8_t* ai = aux0 ? (cur ? aux1 : aux0) : nullptr;
     uint8_t* ao = aux0 ? (cur ? aux0 : aux1) : nullptr;
     const bool last = (p == passes - 1);
+    const int32_t* dig = dev_digits ? dev_digits + 2 * p : nullptr;
     {
       prof::Scope ps(names.hist, s);
-      k_tile_hist<KeyT, TILE><<<grid_hist, kThreads, 0, s>>>(ki, n_dev, shift, rb, nt, cnt);
+      k_tile_hist<KeyT, TILE><<<grid_hist, kThreads, 0, s>>>(ki, n_dev, shift, rb, dig, nt, cnt);
     }
     {
       prof::Scope ps(names.scan, s);
-      k_tile_scan<TILE><<<1 << rb, 1024, 0, s>>>(cnt, n_dev, nt, tot);
+      k_tile_scan<TILE><<<1 << rb, 1024, 0, s>>>(cnt, n_dev, dig, nt, tot);
     }
     prof::Scope ps(names.sort, s);
     k_tile_sort<KeyT, ITEMS><<<grid_sort, kThreads, 0, s>>>(
-        ki, vi, ai, (last && !write_last_keys) ? nullptr : ko, vo, ao, n_dev, shift, rb, cnt, nt, tot);
+        ki, vi, ai, (last && !write_last_keys) ? nullptr : ko, vo, ao, n_dev, shift, rb, dig, cnt, nt, tot);
     cur ^= 1;
   }
   return cur;
