@@ -151,7 +151,8 @@ typedef struct rs_projected {
 } rs_projected;
 
 /* Tile lists.  After rs_bin_sort, vals[ranges[2t] .. ranges[2t+1]) are the items that
- * touch global tile t, front to back (by the FP32 depth key, ties to the lower item).
+ * touch global tile t, front to back (by the FP32 depth key, ties to the lower item); an
+ * empty tile has ranges[2t] == ranges[2t+1] (the place its list would start).
  * keys (optional, may be NULL) receive the 64-bit sort keys (tile << 32 | depth bits)
  * in the same order.  The instance count is written to the device status block. */
 typedef struct rs_bins {

@@ -74,12 +74,23 @@ def synthetic_projected(rng, views, m_per_view, span=5):
     return np.concatenate(depth), np.concatenate(rect)
 
 
+def check_ranges(ranges, ranges_o, K):
+    """Tile ranges: exact for every tile with instances; an empty tile's range only has to
+    be empty (start == end; where it sits is not unique) and inside the list."""
+    full = ranges_o[:, 1] > ranges_o[:, 0]
+    assert np.array_equal(ranges[full], ranges_o[full])
+    assert np.all(ranges[~full, 0] == ranges[~full, 1]) and np.all(ranges[~full, 1] <= K)
+
+
 @pytest.mark.parametrize("views,m,span", [([(8, 8)], [5000], 5), ([(80, 52)], [60000], 5),
                                          ([(5, 3), (12, 9), (1, 1)], [700, 3000, 5], 5),
-                                         ([(8, 8)], [200003], 5), ([(30, 21), (7, 9)], [90001, 40000], 12)])
+                                         ([(8, 8)], [200003], 5), ([(30, 21), (7, 9)], [90001, 40000], 12),
+                                         ([(80, 52)] * 20, [3000] * 20, 5)])
 def test_bin_sort_bit_exact(views, m, span):
     """Keys, values and ranges equal the oracle's stable sort of the duplicated keys, also
-    where the per-super-tile lists span many 256-entry chunks with a ragged last chunk."""
+    where the per-super-tile lists span many 256-entry chunks with a ragged last chunk, and
+    beyond 65536 tiles (32-bit super-tile keys, three sort passes whose digit widths the
+    device narrows to the super-tiles present)."""
     from paper_2403_13806_gb300 import api, _native as N
     rng = np.random.default_rng(len(m) * 7 + m[0])
     depth, rect = synthetic_projected(rng, views, m, span)
@@ -107,7 +118,7 @@ def test_bin_sort_bit_exact(views, m, span):
         K = len(keys_o)
         assert np.array_equal(bins.keys[:K].cpu().numpy().view(np.uint64), keys_o)
         assert np.array_equal(u32(bins.vals[:K]), vals_o)
-        assert np.array_equal(bins.ranges.cpu().numpy().view(np.uint32), ranges_o)
+        check_ranges(bins.ranges.cpu().numpy().view(np.uint32), ranges_o, K)
     # capacity overflow is reported, nothing is written out of bounds
     bins = api.Bins.empty(len(keys_o) // 2, n_tiles)
     st = api.DeviceStatus()
