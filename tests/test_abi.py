@@ -73,6 +73,7 @@ def test_config_defaults(native):
     c = native.lib().rs_config_default()
     assert c.eps2d == pytest.approx(0.3) and c.near_plane == pytest.approx(0.2)
     assert list(c.bg) == [0.0, 0.0, 0.0]
+    assert c.batch == 0 and c.grad_overwrite == 0   # default staging; gradients are added
 
 
 def make_cams(sizes):
