@@ -764,7 +764,7 @@ NCU_TRAFFIC = {
                 "profile": "k_render_bwd_1M_1view.md"},
     "k_render_importance": {"bytes_per_view": 4451584, "files": ['render.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "2563e143b71aae9f",
                 "profile": "k_render_1M_1view.md"},
-    "k_fine_scatter": {"bytes_per_view": 20114176, "files": ['binsort.cu', 'rs_common.cuh'], "sha": "baf00aec8445c8aa",
+    "k_fine_scatter": {"bytes_per_view": 20113664, "files": ['binsort.cu', 'rs_common.cuh'], "sha": "4bf8f48e228d0be8",
                 "profile": "k_fine_scatter_1M_1view.md"},
     "k_ssim_stats": {"bytes_per_view": 25871360, "files": ['ssim.cu', 'rs_common.cuh'], "sha": "77368fb65aa91f37",
                 "profile": "k_ssim_stats_1view.md"},

@@ -39,12 +39,15 @@ constexpr int kEmitThreads = 256;
 constexpr int kSuper = 4;           // tiles per super-tile side
 constexpr int kFineThreads = 256;   // threads of a fine-binning CTA
 constexpr int kSegLen = 3840;       // super-list entries per fine work item (segment; 15 per thread)
+constexpr int kTileBlock = 256;     // tiles per CTA of the per-tile scans
+constexpr int kCountChunk = 256;    // emission blocks per CTA of the block-count scan
 constexpr int kNF = kSuper * kSuper;
 
 struct BinWs {
   uint32_t* dkeys[2];
   uint32_t* dvals[2];
   unsigned long long* bsum;   // per emission block: super instances, then exclusive prefix
+  unsigned long long* csum;   // per chunk of kCountChunk emission blocks: super instances
   char* skeys[2];             // super-tile ids (uint16 or uint32)
   uint32_t* svals[2];         // items
   uint8_t* saux[2];           // covered part of the super-tile (cover byte)
@@ -53,6 +56,7 @@ struct BinWs {
   uint32_t* sranges;          // [n_tiles][2]: super-tile ranges (super-tiles never outnumber tiles)
   uint32_t* super_base;       // [n_views + 1]
   uint32_t* fine_tot;         // [n_tiles]: instances per tile, then first position
+  unsigned long long* tile_blk;   // [ceil(n_tiles / kTileBlock)]: instances per block of tiles
   uint32_t* seg_off;          // [n_tiles + 1]: first segment of every super-tile, then the total
   uint32_t* work_s;           // [n_work_max]: super-tile of every segment
   uint32_t* seg_cnt;          // [n_work_max][16]: per (segment, tile) counts, then prefixes
@@ -78,6 +82,7 @@ static BinWs bin_ws_layout(void* base, int64_t n_items, int64_t capacity, int n_
   for (int i = 0; i < 2; ++i) w.dkeys[i] = reinterpret_cast<uint32_t*>(take(ni * 4));
   for (int i = 0; i < 2; ++i) w.dvals[i] = reinterpret_cast<uint32_t*>(take(ni * 4));
   w.bsum = reinterpret_cast<unsigned long long*>(take((size_t)(nblk > 0 ? nblk : 1) * 8));
+  w.csum = reinterpret_cast<unsigned long long*>(take((size_t)((nblk > 0 ? nblk : 1) + kCountChunk - 1) / kCountChunk * 8));
   for (int i = 0; i < 2; ++i) w.skeys[i] = take(cap * 4);
   for (int i = 0; i < 2; ++i) w.svals[i] = reinterpret_cast<uint32_t*>(take(cap * 4));
   for (int i = 0; i < 2; ++i) w.saux[i] = reinterpret_cast<uint8_t*>(take(cap));
@@ -86,6 +91,8 @@ static BinWs bin_ws_layout(void* base, int64_t n_items, int64_t capacity, int n_
   w.sranges = reinterpret_cast<uint32_t*>(take((size_t)(n_tiles > 0 ? n_tiles : 1) * 8));
   w.super_base = reinterpret_cast<uint32_t*>(take((size_t)(n_views + 1) * 4));
   w.fine_tot = reinterpret_cast<uint32_t*>(take((size_t)(n_tiles > 0 ? n_tiles : 1) * 4));
+  w.tile_blk = reinterpret_cast<unsigned long long*>(
+      take((size_t)((n_tiles > 0 ? n_tiles : 1) + kTileBlock - 1) / kTileBlock * 8));
   w.n_work_max = (int64_t)(cap / kSegLen) + (n_tiles > 0 ? n_tiles : 1) + 1;
   w.seg_off = reinterpret_cast<uint32_t*>(take((size_t)((n_tiles > 0 ? n_tiles : 1) + 1) * 4));
   w.work_s = reinterpret_cast<uint32_t*>(take((size_t)w.n_work_max * 4));
@@ -168,10 +175,12 @@ __device__ __forceinline__ uint32_t cover_mask(uint32_t c) {
   return (row * rep) << (kSuper * y0);                               // row repeated on rows y0 .. y1
 }
 
-// Super instances per block of kEmitThreads depth-sorted items.
+// Super instances per block of kEmitThreads depth-sorted items, also added into the total
+// of the block's chunk of kCountChunk blocks (csum, zeroed by the caller).
 __global__ void __launch_bounds__(kEmitThreads) k_count_blocks(const uint32_t* __restrict__ order, int64_t n,
                                                                const ushort4* __restrict__ rect,
-                                                               unsigned long long* __restrict__ bsum) {
+                                                               unsigned long long* __restrict__ bsum,
+                                                               unsigned long long* __restrict__ csum) {
   __shared__ unsigned long long s[kEmitThreads / 32];
   const int64_t i = (int64_t)blockIdx.x * kEmitThreads + threadIdx.x;
   unsigned long long c = 0;
@@ -187,62 +196,55 @@ __global__ void __launch_bounds__(kEmitThreads) k_count_blocks(const uint32_t* _
     unsigned long long t = 0;
     for (int w = 0; w < kEmitThreads / 32; ++w) t += s[w];
     bsum[blockIdx.x] = t;
+    if (t) atomicAdd(csum + blockIdx.x / kCountChunk, t);
   }
 }
 
-// Exclusive prefix over the block counts (one block, kScanPer consecutive counts per
-// thread) and the super-instance total.
-constexpr int kScanPer = 4;
-
-__global__ void __launch_bounds__(1024) k_count_top(unsigned long long* __restrict__ bsum, int64_t nblk,
-                                                    int64_t capacity, uint32_t* __restrict__ counters,
-                                                    rs_device_status* st) {
-  __shared__ unsigned long long s_w[32];
-  __shared__ unsigned long long s_carry;
+// Sum of one value per thread over a 256-thread CTA (every thread receives it).
+__device__ __forceinline__ unsigned long long block_sum256_u64(unsigned long long v, unsigned long long* s_w) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) s_carry = 0ull;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) s_w[warp] = v;
   __syncthreads();
-  for (int64_t b0 = 0; b0 < nblk; b0 += 1024 * kScanPer) {
-    const int64_t b = b0 + (int64_t)threadIdx.x * kScanPer;
-    unsigned long long c[kScanPer], v = 0ull;
+  unsigned long long t = 0;
 #pragma unroll
-    for (int j = 0; j < kScanPer; ++j) {
-      c[j] = b + j < nblk ? bsum[b + j] : 0ull;
-      v += c[j];
-    }
-    unsigned long long x = v;
+  for (int w = 0; w < 8; ++w) t += s_w[w];
+  __syncthreads();
+  return t;
+}
+
+// Exclusive prefix over the block counts, one CTA per chunk of kCountChunk blocks: the
+// chunk's base is the sum of the earlier chunks' totals, the blocks' places inside it a
+// CTA scan.  The CTA of the last block writes the super-instance total.
+__global__ void __launch_bounds__(kCountChunk) k_count_top(unsigned long long* __restrict__ bsum,
+                                                           const unsigned long long* __restrict__ csum, int64_t nblk,
+                                                           int64_t capacity, uint32_t* __restrict__ counters,
+                                                           rs_device_status* st) {
+  static_assert(kCountChunk == 256, "one thread per block of the chunk");
+  __shared__ unsigned long long s_w[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long pre = 0;
+  for (int c = threadIdx.x; c < (int)blockIdx.x; c += kCountChunk) pre += csum[c];
+  const unsigned long long base = block_sum256_u64(pre, s_w);
+  const int64_t b = (int64_t)blockIdx.x * kCountChunk + threadIdx.x;
+  const unsigned long long v = b < nblk ? bsum[b] : 0ull;
+  unsigned long long x = v;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) s_w[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      unsigned long long w = s_w[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += y;
-      }
-      s_w[lane] = w;
-    }
-    __syncthreads();
-    const unsigned long long carry = s_carry;
-    unsigned long long run = carry + (warp ? s_w[warp - 1] : 0ull) + x - v;
-#pragma unroll
-    for (int j = 0; j < kScanPer; ++j) {
-      if (b + j < nblk) bsum[b + j] = run;
-      run += c[j];
-    }
-    __syncthreads();
-    if (threadIdx.x == 1023) s_carry = carry + s_w[31];
-    __syncthreads();
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
   }
-  if (threadIdx.x == 0) {
+  if (lane == 31) s_w[warp] = x;
+  __syncthreads();
+  unsigned long long wpre = 0;
+  for (int w = 0; w < warp; ++w) wpre += s_w[w];
+  const unsigned long long run = base + wpre + x - v;
+  if (b < nblk) bsum[b] = run;
+  if (b == nblk - 1) {
     // super instances never outnumber instances: more than the capacity means the instances
     // overflow too (k_fine_scan records the required count)
-    const unsigned long long Ks = s_carry;
+    const unsigned long long Ks = run + v;
     counters[0] = (uint32_t)(Ks < (unsigned long long)capacity ? Ks : (unsigned long long)capacity);
     if (st && Ks > (unsigned long long)capacity) atomicCAS(&st->code, 0, (int)RS_ERR_CAPACITY);
   }
@@ -549,89 +551,80 @@ __global__ void __launch_bounds__(kFineThreads) k_fine_count(const uint8_t* __re
   }
 }
 
+static_assert(kTileBlock == 256, "the per-tile scans use the 256-thread CTA sum");
+
 // One thread per tile: exclusive prefix of its counts over its super-tile's segments (in
-// place, four segments' loads at a time) and the tile's total.
-__global__ void k_fine_seg_scan(uint32_t* __restrict__ seg_cnt, const rs_view* __restrict__ views, int n_views,
-                                const uint32_t* __restrict__ super_base, const uint32_t* __restrict__ seg_off,
-                                int n_tiles, uint32_t* __restrict__ fine_tot) {
-  const int T = blockIdx.x * blockDim.x + threadIdx.x;
-  if (T >= n_tiles) return;
-  const int v = find_view_by_tile(views, n_views, T);
-  const rs_view& cam = views[v];
-  const int local = T - cam.tile_base;
-  const int ty = local / cam.tiles_x, tx = local - ty * cam.tiles_x;
-  const uint32_t S = super_base[v] + (uint32_t)((ty / kSuper) * super_w(cam) + tx / kSuper);
-  const int f = (ty % kSuper) * kSuper + tx % kSuper;
-  const uint32_t w0 = seg_off[S], w1 = seg_off[S + 1];
+// place, four segments' loads at a time), the tile's total, and the total of each block of
+// kTileBlock tiles.
+__global__ void __launch_bounds__(kTileBlock) k_fine_seg_scan(uint32_t* __restrict__ seg_cnt,
+                                                              const rs_view* __restrict__ views, int n_views,
+                                                              const uint32_t* __restrict__ super_base,
+                                                              const uint32_t* __restrict__ seg_off, int n_tiles,
+                                                              uint32_t* __restrict__ fine_tot,
+                                                              unsigned long long* __restrict__ tile_blk) {
+  __shared__ unsigned long long s_w[kTileBlock / 32];
+  const int T = blockIdx.x * kTileBlock + threadIdx.x;
   uint32_t run = 0;
-  for (uint32_t w = w0; w < w1; w += 4) {
-    uint32_t x[4];
+  if (T < n_tiles) {
+    const int v = find_view_by_tile(views, n_views, T);
+    const rs_view& cam = views[v];
+    const int local = T - cam.tile_base;
+    const int ty = local / cam.tiles_x, tx = local - ty * cam.tiles_x;
+    const uint32_t S = super_base[v] + (uint32_t)((ty / kSuper) * super_w(cam) + tx / kSuper);
+    const int f = (ty % kSuper) * kSuper + tx % kSuper;
+    const uint32_t w0 = seg_off[S], w1 = seg_off[S + 1];
+    for (uint32_t w = w0; w < w1; w += 4) {
+      uint32_t x[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) x[k] = w + k < w1 ? seg_cnt[(int64_t)(w + k) * kNF + f] : 0u;
+      for (int k = 0; k < 4; ++k) x[k] = w + k < w1 ? seg_cnt[(int64_t)(w + k) * kNF + f] : 0u;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (w + k < w1) seg_cnt[(int64_t)(w + k) * kNF + f] = run;
-      run += x[k];
+      for (int k = 0; k < 4; ++k) {
+        if (w + k < w1) seg_cnt[(int64_t)(w + k) * kNF + f] = run;
+        run += x[k];
+      }
     }
+    fine_tot[T] = run;
   }
-  fine_tot[T] = run;
+  const unsigned long long b = block_sum256_u64(run, s_w);
+  if (threadIdx.x == 0) tile_blk[blockIdx.x] = b;
 }
 
-// Exclusive scan of the per-tile totals (one CTA): first position of every tile (in place,
-// saturated to 32 bits), ranges clamped to the capacity, K, and the capacity check.
-__global__ void __launch_bounds__(1024) k_fine_scan(uint32_t* __restrict__ tot, int n_tiles, int64_t capacity,
-                                                    uint32_t* __restrict__ ranges, uint32_t* __restrict__ counters,
-                                                    rs_device_status* st) {
-  __shared__ unsigned long long s_w[32];
-  __shared__ unsigned long long s_carry;
+// Exclusive scan of the per-tile totals, one CTA per block of kTileBlock tiles: the block's
+// base is the sum of the earlier blocks' totals (read by the whole CTA), the tiles' places
+// inside it a block scan.  Writes every tile's first position (in place, saturated to 32
+// bits) and its range clamped to the capacity; the CTA of the last tile writes K and
+// checks the capacity.
+__global__ void __launch_bounds__(kTileBlock) k_fine_scan(uint32_t* __restrict__ tot,
+                                                          const unsigned long long* __restrict__ tile_blk,
+                                                          int n_tiles, int64_t capacity, uint32_t* __restrict__ ranges,
+                                                          uint32_t* __restrict__ counters, rs_device_status* st) {
+  __shared__ unsigned long long s_w[kTileBlock / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned long long cap = (unsigned long long)capacity;
-  if (threadIdx.x == 0) s_carry = 0ull;
-  __syncthreads();
-  for (int b0 = 0; b0 < n_tiles; b0 += kScanPer * 1024) {
-    const int b = b0 + kScanPer * (int)threadIdx.x;
-    uint32_t v[kScanPer];
-    unsigned long long sum = 0;
+  unsigned long long pre = 0;
+  for (int b = threadIdx.x; b < (int)blockIdx.x; b += kTileBlock) pre += tile_blk[b];
+  const unsigned long long base = block_sum256_u64(pre, s_w);
+  const int T = blockIdx.x * kTileBlock + threadIdx.x;
+  const unsigned long long v = T < n_tiles ? tot[T] : 0ull;
+  // exclusive scan of v over the CTA
+  unsigned long long x = v;
 #pragma unroll
-    for (int j = 0; j < kScanPer; ++j) {
-      v[j] = (b + j < n_tiles) ? tot[b + j] : 0u;
-      sum += v[j];
-    }
-    unsigned long long x = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) s_w[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      unsigned long long w = s_w[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
-        if (lane >= o) w += y;
-      }
-      s_w[lane] = w;
-    }
-    __syncthreads();
-    unsigned long long run = s_carry + (warp ? s_w[warp - 1] : 0ull) + x - sum;
-#pragma unroll
-    for (int j = 0; j < kScanPer; ++j) {
-      if (b + j < n_tiles) {
-        const unsigned long long e = run + v[j];
-        tot[b + j] = (uint32_t)(run < 0xffffffffull ? run : 0xffffffffull);
-        ranges[2 * (int64_t)(b + j)] = (uint32_t)(run < cap ? run : cap);
-        ranges[2 * (int64_t)(b + j) + 1] = (uint32_t)(e < cap ? e : cap);
-        run = e;
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 1023) s_carry += s_w[31];
-    __syncthreads();
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
   }
-  if (threadIdx.x == 0) {
-    const unsigned long long K = s_carry;
+  if (lane == 31) s_w[warp] = x;
+  __syncthreads();
+  unsigned long long wpre = 0;
+  for (int w = 0; w < warp; ++w) wpre += s_w[w];
+  const unsigned long long run = base + wpre + x - v, e = run + v;
+  if (T < n_tiles) {
+    tot[T] = (uint32_t)(run < 0xffffffffull ? run : 0xffffffffull);
+    ranges[2 * (int64_t)T] = (uint32_t)(run < cap ? run : cap);
+    ranges[2 * (int64_t)T + 1] = (uint32_t)(e < cap ? e : cap);
+  }
+  if (T == n_tiles - 1) {
+    const unsigned long long K = e;
     counters[2] = (uint32_t)(K < cap ? K : cap);
     if (st) {
       atomicMax(reinterpret_cast<unsigned long long*>(&st->required), K);
@@ -844,13 +837,16 @@ extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* 
     const uint32_t* order = w.dvals[dcur];
     // 2) super instances in depth order, sorted stably on the super-tile id
     const int64_t nblk = (n + kEmitThreads - 1) / kEmitThreads;
+    if (cudaMemsetAsync(w.csum, 0, (size_t)((nblk + kCountChunk - 1) / kCountChunk) * 8, s) != cudaSuccess)
+      return RS_ERR_CUDA;
     {
       prof::Scope ps("k_count_blocks", s);
-      k_count_blocks<<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n, rect, w.bsum);
+      k_count_blocks<<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n, rect, w.bsum, w.csum);
     }
     {
       prof::Scope ps("k_count_top", s);
-      k_count_top<<<1, 1024, 0, s>>>(w.bsum, nblk, cap, w.counters, status);
+      k_count_top<<<(unsigned)((nblk + kCountChunk - 1) / kCountChunk), kCountChunk, 0, s>>>(w.bsum, w.csum, nblk, cap,
+                                                                                          w.counters, status);
     }
     scur = (n_super_max <= 65536) ? super_instances<uint16_t>(w, order, n, proj, batch, cap, nblk, n_super_max, s)
                                   : super_instances<uint32_t>(w, order, n, proj, batch, cap, nblk, n_super_max, s);
@@ -873,12 +869,13 @@ extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* 
   }
   {
     prof::Scope ps("k_fine_seg_scan", s);
-    k_fine_seg_scan<<<(unsigned)((batch->n_tiles + 255) / 256), 256, 0, s>>>(
-        w.seg_cnt, batch->views, batch->n_views, w.super_base, w.seg_off, batch->n_tiles, w.fine_tot);
+    k_fine_seg_scan<<<(unsigned)((batch->n_tiles + kTileBlock - 1) / kTileBlock), kTileBlock, 0, s>>>(
+        w.seg_cnt, batch->views, batch->n_views, w.super_base, w.seg_off, batch->n_tiles, w.fine_tot, w.tile_blk);
   }
   {
     prof::Scope ps("k_fine_scan", s);
-    k_fine_scan<<<1, 1024, 0, s>>>(w.fine_tot, batch->n_tiles, cap, bins->ranges, w.counters, status);
+    k_fine_scan<<<(unsigned)((batch->n_tiles + kTileBlock - 1) / kTileBlock), kTileBlock, 0, s>>>(
+        w.fine_tot, w.tile_blk, batch->n_tiles, cap, bins->ranges, w.counters, status);
   }
   {
     prof::Scope ps("k_fine_scatter", s);
