@@ -914,7 +914,7 @@ def oracle_sample_time(n_small: int, n_big: int, threads: int, seed: int = 0):
 
 def cpu_baseline(args):
     threads = os.cpu_count() or 1
-    n_small, n_big = 64, 480
+    n_small, n_big = 64, 960
     try:
         dt, ms_view = oracle_sample_time(n_small, n_big, threads)
     except Exception as e:  # the baseline is reported, not required
