@@ -4,8 +4,10 @@
 //   arrays with their own learning rates, in one launch: m <- b1 m + (1 - b1) g,
 //   v <- b2 v + (1 - b2) g^2, p <- p - lr (m / bc1) / (sqrt(v / bc2) + eps) with
 //   bc = 1 - b^t.  Every element is read once (p, g, m, v) and written once (p, m, v):
-//   28 bytes, HBM-bound.  Threads take four consecutive elements (16-byte loads when all
-//   four arrays of the group are 16-byte aligned) over the concatenation of the groups.
+//   28 bytes, HBM-bound.  Each CTA owns a contiguous run of one group (CTAs are dealt to
+//   the groups in proportion to their sizes on the host, so no thread searches for its
+//   group); threads take four consecutive elements (16-byte loads when all four arrays of
+//   the group are 16-byte aligned), two such units in flight per thread.
 // rs_gather_columns -- the compaction after pruning: for every structure-of-arrays
 //   parameter (and optimiser moment) dst[r][k] = src[r][idx[k]] for k < count, count and
 //   idx being the device outputs of rs_filter (the survivors, ascending).  One thread per
@@ -28,7 +30,7 @@ struct AdamArgs {
   float* m[kMaxAdamGroups];
   float* v[kMaxAdamGroups];
   int64_t n[kMaxAdamGroups];
-  int64_t unit0[kMaxAdamGroups + 1];   // first 4-element unit of each group
+  int32_t cta0[kMaxAdamGroups + 1];    // first CTA of each group
   float lr[kMaxAdamGroups];
   int32_t vec[kMaxAdamGroups];         // 1: 16-byte loads and stores
   int32_t n_groups;
@@ -43,34 +45,67 @@ __device__ __forceinline__ void adam_one(float& p, float g, float& m, float& v, 
   p = __fsub_rn(p, __fdiv_rn(__fmul_rn(lr, mhat), __fadd_rn(__fsqrt_rn(vhat), a.eps)));
 }
 
+// One 4-element unit (16-byte accesses when vec) at element e of group gi.
+__device__ __forceinline__ void adam_unit(const AdamArgs& a, int gi, int64_t e) {
+  const int64_t n = a.n[gi];
+  const float lr = a.lr[gi];
+  if (a.vec[gi] && e + 4 <= n) {
+    float4 p = *reinterpret_cast<const float4*>(a.p[gi] + e);
+    const float4 g = __ldcs(reinterpret_cast<const float4*>(a.g[gi] + e));
+    float4 m = *reinterpret_cast<const float4*>(a.m[gi] + e);
+    float4 v = *reinterpret_cast<const float4*>(a.v[gi] + e);
+    adam_one(p.x, g.x, m.x, v.x, lr, a);
+    adam_one(p.y, g.y, m.y, v.y, lr, a);
+    adam_one(p.z, g.z, m.z, v.z, lr, a);
+    adam_one(p.w, g.w, m.w, v.w, lr, a);
+    *reinterpret_cast<float4*>(a.p[gi] + e) = p;
+    *reinterpret_cast<float4*>(a.m[gi] + e) = m;
+    *reinterpret_cast<float4*>(a.v[gi] + e) = v;
+  } else {
+    for (int64_t k = e; k < e + 4 && k < n; ++k) {
+      float p = a.p[gi][k], m = a.m[gi][k], v = a.v[gi][k];
+      adam_one(p, a.g[gi][k], m, v, lr, a);
+      a.p[gi][k] = p;
+      a.m[gi][k] = m;
+      a.v[gi][k] = v;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) k_adam(AdamArgs a) {
-  const int64_t total = a.unit0[a.n_groups];
-  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < total; u += (int64_t)gridDim.x * blockDim.x) {
-    int gi = 0;
-    while (gi + 1 < a.n_groups && u >= a.unit0[gi + 1]) ++gi;   // at most 8 groups
-    const int64_t e = 4 * (u - a.unit0[gi]);
-    const int64_t n = a.n[gi];
-    const float lr = a.lr[gi];
-    if (a.vec[gi] && e + 4 <= n) {
-      float4 p = *reinterpret_cast<const float4*>(a.p[gi] + e);
-      const float4 g = __ldcs(reinterpret_cast<const float4*>(a.g[gi] + e));
-      float4 m = *reinterpret_cast<const float4*>(a.m[gi] + e);
-      float4 v = *reinterpret_cast<const float4*>(a.v[gi] + e);
-      adam_one(p.x, g.x, m.x, v.x, lr, a);
-      adam_one(p.y, g.y, m.y, v.y, lr, a);
-      adam_one(p.z, g.z, m.z, v.z, lr, a);
-      adam_one(p.w, g.w, m.w, v.w, lr, a);
-      *reinterpret_cast<float4*>(a.p[gi] + e) = p;
-      *reinterpret_cast<float4*>(a.m[gi] + e) = m;
-      *reinterpret_cast<float4*>(a.v[gi] + e) = v;
-    } else {
-      for (int64_t k = e; k < e + 4 && k < n; ++k) {
-        float p = a.p[gi][k], m = a.m[gi][k], v = a.v[gi][k];
-        adam_one(p, a.g[gi][k], m, v, lr, a);
-        a.p[gi][k] = p;
-        a.m[gi][k] = m;
-        a.v[gi][k] = v;
+  int gi = 0;   // the CTA's group (uniform)
+  while (gi + 1 < a.n_groups && (int)blockIdx.x >= a.cta0[gi + 1]) ++gi;
+  const int64_t ctas = a.cta0[gi + 1] - a.cta0[gi];
+  const int64_t units = (a.n[gi] + 3) / 4;
+  const int64_t stride = ctas * 256;
+  const int64_t n = a.n[gi];
+  const float lr = a.lr[gi];
+  // two units per thread and round: all eight 16-byte loads are issued before any store
+  for (int64_t u = (int64_t)(blockIdx.x - a.cta0[gi]) * 256 + threadIdx.x; u < units; u += 2 * stride) {
+    const int64_t e1 = 4 * u, e2 = 4 * (u + stride);
+    if (a.vec[gi] && e2 + 4 <= n) {
+      float4 p[2], m[2], v[2], g[2];
+      const int64_t e[2] = {e1, e2};
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        p[k] = *reinterpret_cast<const float4*>(a.p[gi] + e[k]);
+        g[k] = __ldcs(reinterpret_cast<const float4*>(a.g[gi] + e[k]));
+        m[k] = *reinterpret_cast<const float4*>(a.m[gi] + e[k]);
+        v[k] = *reinterpret_cast<const float4*>(a.v[gi] + e[k]);
       }
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        adam_one(p[k].x, g[k].x, m[k].x, v[k].x, lr, a);
+        adam_one(p[k].y, g[k].y, m[k].y, v[k].y, lr, a);
+        adam_one(p[k].z, g[k].z, m[k].z, v[k].z, lr, a);
+        adam_one(p[k].w, g[k].w, m[k].w, v[k].w, lr, a);
+        *reinterpret_cast<float4*>(a.p[gi] + e[k]) = p[k];
+        *reinterpret_cast<float4*>(a.m[gi] + e[k]) = m[k];
+        *reinterpret_cast<float4*>(a.v[gi] + e[k]) = v[k];
+      }
+    } else {
+      adam_unit(a, gi, e1);
+      if (u + stride < units) adam_unit(a, gi, e2);
     }
   }
 }
@@ -92,7 +127,18 @@ __global__ void __launch_bounds__(256) k_gather_columns(GatherArgs a, const uint
     for (int d = 0; d < a.n_desc; ++d) {
       const float* s = a.src[d] + i;
       float* o = a.dst[d] + k;
-      for (int64_t r = 0; r < a.rows[d]; ++r) o[r * a.dst_stride[d]] = __ldg(s + r * a.src_stride[d]);
+      const int64_t rows = a.rows[d], ss = a.src_stride[d], ds = a.dst_stride[d];
+      // eight rows' loads in flight before their stores (source and destination may not
+      // be told apart by the compiler, so it would not reorder them itself)
+      int64_t r = 0;
+      for (; r + 8 <= rows; r += 8) {
+        float t[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) t[j] = __ldg(s + (r + j) * ss);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) o[(r + j) * ds] = t[j];
+      }
+      for (; r < rows; ++r) o[r * ds] = __ldg(s + r * ss);
     }
   }
 }
@@ -124,16 +170,25 @@ extern "C" rs_status rs_adam_step(const rs_adam_group* groups, int32_t n_groups,
     a.lr[i] = g.lr;
     a.vec[i] = aligned<float4>(g.param, 16) && aligned<float4>(g.grad, 16) && aligned<float4>(g.m, 16) &&
                aligned<float4>(g.v, 16);
-    a.unit0[i] = units;
     units += (g.n + 3) / 4;
   }
-  a.unit0[n_groups] = units;
   if (units == 0) return RS_OK;
+  // CTAs dealt to the groups in proportion to their units (at least one each, at most one
+  // per 256 units), about 16 per SM in total
+  const int64_t budget = 16 * kNumSMs;
+  int32_t total = 0;
+  for (int32_t i = 0; i < n_groups; ++i) {
+    a.cta0[i] = total;
+    const int64_t u = (groups[i].n + 3) / 4;
+    int64_t c = (u * budget + units - 1) / units;
+    const int64_t cmax = (u + 255) / 256;
+    c = c < 1 ? 1 : (c > cmax ? (cmax > 0 ? cmax : 1) : c);
+    total += (int32_t)c;
+  }
+  a.cta0[n_groups] = total;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  const int64_t blocks = (units + 255) / 256;
-  const unsigned grid = (unsigned)(blocks < 16 * kNumSMs ? blocks : 16 * kNumSMs);
   prof::Scope ps("k_adam", s);
-  k_adam<<<grid, 256, 0, s>>>(a);
+  k_adam<<<(unsigned)total, 256, 0, s>>>(a);
   return launch_status();
 }
 
