@@ -34,15 +34,18 @@ struct AdamArgs {
   float lr[kMaxAdamGroups];
   int32_t vec[kMaxAdamGroups];         // 1: 16-byte loads and stores
   int32_t n_groups;
-  float b1, b2, eps, bc1, bc2;
+  float b1, b2, eps, ibc1, ibc2;   // ibc = 1 / (1 - b^t), rounded once on the host
 };
 
+// (the bias corrections multiply by host-rounded reciprocals and the step's ratio uses the
+// fast division: within a few ulps of the correctly rounded operations, far inside what
+// FP32 parameters resolve)
 __device__ __forceinline__ void adam_one(float& p, float g, float& m, float& v, float lr, const AdamArgs& a) {
   m = __fmaf_rn(a.b1, m, __fmul_rn(1.f - a.b1, g));
   v = __fmaf_rn(a.b2, v, __fmul_rn(__fmul_rn(1.f - a.b2, g), g));
-  const float mhat = __fdiv_rn(m, a.bc1);
-  const float vhat = __fdiv_rn(v, a.bc2);
-  p = __fsub_rn(p, __fdiv_rn(__fmul_rn(lr, mhat), __fadd_rn(__fsqrt_rn(vhat), a.eps)));
+  const float mhat = __fmul_rn(m, a.ibc1);
+  const float vhat = __fmul_rn(v, a.ibc2);
+  p = __fsub_rn(p, __fdividef(__fmul_rn(lr, mhat), __fadd_rn(__fsqrt_rn(vhat), a.eps)));
 }
 
 // One 4-element unit (16-byte accesses when vec) at element e of group gi.
@@ -156,8 +159,8 @@ extern "C" rs_status rs_adam_step(const rs_adam_group* groups, int32_t n_groups,
   a.b1 = beta1;
   a.b2 = beta2;
   a.eps = eps;
-  a.bc1 = (float)(1.0 - pow((double)beta1, (double)step));
-  a.bc2 = (float)(1.0 - pow((double)beta2, (double)step));
+  a.ibc1 = (float)(1.0 / (1.0 - pow((double)beta1, (double)step)));
+  a.ibc2 = (float)(1.0 / (1.0 - pow((double)beta2, (double)step)));
   int64_t units = 0;
   for (int32_t i = 0; i < n_groups; ++i) {
     const rs_adam_group& g = groups[i];
