@@ -760,7 +760,7 @@ OPS_PER_PAIR = {"k_render_importance": 22, "k_render": 22, "k_render_bwd": 46}
 # of the sources the kernel was built from.  A capture stays valid only while those sources
 # are unchanged; otherwise the roofline reports traffic as null.
 NCU_TRAFFIC = {
-    "k_render_bwd": {"bytes_per_view": 25188352, "files": ['render_bwd.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "f030b2ab72f459ba",
+    "k_render_bwd": {"bytes_per_view": 25183488, "files": ['render_bwd.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "930e0ad64f2543d8",
                 "profile": "k_render_bwd_1M_1view.md"},
     "k_render_importance": {"bytes_per_view": 4451584, "files": ['render.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "2563e143b71aae9f",
                 "profile": "k_render_1M_1view.md"},

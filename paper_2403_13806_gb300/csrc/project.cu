@@ -31,6 +31,13 @@ struct ProjectArgs {
   rs_device_status* status;
 };
 
+// sqrt(x) by the hardware approximation (sqrt.approx.ftz, within a few ulps).
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // View-independent part of a Gaussian: rotation, scales and opacity (identical operations
 // whichever view uses them).  Parameter rows as in params.cuh.
 struct GaussLocal {
@@ -109,7 +116,10 @@ __device__ __forceinline__ void project_view(const ProjectArgs& a, const rs_view
     const float uxc = fminf(fmaxf(ux, -cam.lim_x), cam.lim_x);
     const float uyc = fminf(fmaxf(uy, -cam.lim_y), cam.lim_y);
     // T = J M: row0 = fx/tz (M0 - uxc M2), row1 = fy/tz (M1 - uyc M2)
-    const float jx = cam.fx / tz, jy = cam.fy / tz;
+    // (the image mean above uses correctly rounded quotients; J and the conic below take the
+    // hardware reciprocal: they feed only the blend, which tolerates their ulps)
+    const float itz = rcp_approx(tz);
+    const float jx = cam.fx * itz, jy = cam.fy * itz;
     float T[2][3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -134,7 +144,7 @@ __device__ __forceinline__ void project_view(const ProjectArgs& a, const rs_view
     const float ea = s00 + a.eps2d, ec = s11 + a.eps2d;
     const float det = det0 + a.eps2d * (s00 + s11) + a.eps2d * a.eps2d;
     if (!(det > 0.f)) break;
-    const float idet = 1.f / det;
+    const float idet = rcp_approx(det);
     const float o = gl.o;
 
     const float mx = __fmaf_rn(cam.fx, ux, cam.cx);
@@ -143,8 +153,8 @@ __device__ __forceinline__ void project_view(const ProjectArgs& a, const rs_view
     // support: alpha >= 1/255  <=>  d^T Sigma'^-1 d <= 2 ln(255 o); bounding box of that
     // ellipse, widened by a relative 2^-12 and 2^-10 px to stay a superset under rounding
     const float q = gl.q;
-    const float ex = sqrtf(q * ea) * (1.f + 0x1p-12f) + 0x1p-10f;
-    const float ey = sqrtf(q * ec) * (1.f + 0x1p-12f) + 0x1p-10f;
+    const float ex = sqrt_approx(q * ea) * (1.f + 0x1p-12f) + 0x1p-10f;   // (margin >> its error)
+    const float ey = sqrt_approx(q * ec) * (1.f + 0x1p-12f) + 0x1p-10f;
     const float u0 = fmaxf(ceilf(mx - ex), 0.f), u1 = fminf(floorf(mx + ex), (float)(cam.width - 1));
     const float v0 = fmaxf(ceilf(my - ey), 0.f), v1 = fminf(floorf(my + ey), (float)(cam.height - 1));
 

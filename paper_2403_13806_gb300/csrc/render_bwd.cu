@@ -347,7 +347,8 @@ __device__ __forceinline__ void item_backward(const BwdProjArgs& a, const rs_vie
   const bool clx = !(ux > -cam.lim_x && ux < cam.lim_x), cly = !(uy > -cam.lim_y && uy < cam.lim_y);
   const float uxc = fminf(fmaxf(ux, -cam.lim_x), cam.lim_x);
   const float uyc = fminf(fmaxf(uy, -cam.lim_y), cam.lim_y);
-  const float jx = cam.fx / tz, jy = cam.fy / tz;
+  const float itz = rcp_approx(tz);   // as the projection: J and the conic from the reciprocal
+  const float jx = cam.fx * itz, jy = cam.fy * itz;
   float T[2][3], Ebase[2][3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -373,7 +374,7 @@ __device__ __forceinline__ void item_backward(const BwdProjArgs& a, const rs_vie
   const float det0 = c0 * c0 + c1 * c1 + c2 * c2;
   const float ea = s00 + a.eps2d, ec = s11 + a.eps2d;
   const float det = det0 + a.eps2d * (s00 + s11) + a.eps2d * a.eps2d;
-  const float idet = 1.f / det;
+  const float idet = rcp_approx(det);
   const float Qa = ec * idet, Qb = -s01 * idet, Qc = ea * idet;   // conic
   const float o = 1.f / (1.f + expf(-lg));
 
@@ -436,8 +437,8 @@ __device__ __forceinline__ void item_backward(const BwdProjArgs& a, const rs_vie
   }
   float gux = ga.x * cam.fx + (clx ? 0.f : guxc);
   float guy = ga.y * cam.fy + (cly ? 0.f : guyc);
-  const float gtx = gux / tz, gty = guy / tz;
-  const float gtz = -(gux * ux + guy * uy) / tz - (gjx * jx + gjy * jy) / tz;
+  const float gtx = gux * itz, gty = guy * itz;
+  const float gtz = -((gux * ux + guy * uy) + (gjx * jx + gjy * jy)) * itz;
   float gp[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) gp[c] = W[c] * gtx + W[4 + c] * gty + W[8 + c] * gtz;
