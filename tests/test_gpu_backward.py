@@ -135,6 +135,29 @@ def test_backward_grad_overwrite(subset):
     assert any(bool((a != 0).any()) for a in acc)
 
 
+def test_backward_overwrite_then_add_over_chunks():
+    """A step split into view chunks: the first chunk's backward writes the gradients
+    (grad_overwrite), the others add theirs; the sum equals one launch over all views."""
+    from paper_2403_13806_gb300 import api
+    scene, cams = synth.fd_crop()
+    cam = cams[0]
+    w = unambiguous_weights(scene, cam, 7)
+    dl = torch.as_tensor(w.astype(np.float32).ravel(), device="cuda")
+    both = gpu_forward(scene, [cam, cam], importance=False)
+    ref = [torch.zeros_like(t) for t in both["g"].tensors()]
+    api.render_backward(both["g"], both["vb"], both["proj"], both["bins"], both["T_final"], both["last"],
+                        torch.cat([dl, 0.25 * dl]), ref, both["rast"].ws_bwd)
+    got = [torch.full_like(t, -3.0) for t in both["g"].tensors()]
+    for k, scale in enumerate((1.0, 0.25)):
+        one = gpu_forward(scene, [cam], importance=False)
+        cfg = api.config(grad_overwrite=(k == 0))
+        api.render_backward(one["g"], one["vb"], one["proj"], one["bins"], one["T_final"], one["last"], scale * dl,
+                            got, one["rast"].ws_bwd, cfg)
+    torch.cuda.synchronize()
+    for a, b in zip(ref, got):
+        torch.testing.assert_close(b, a, rtol=1e-5, atol=1e-6)
+
+
 def test_autograd_function_l1_step():
     """Config-2 style step on the crop: L1 against the render of a perturbed copy."""
     from paper_2403_13806_gb300 import api
