@@ -193,6 +193,26 @@ def test_importance_matches_oracle():
     check_importance(h_gpu, h, h_amb)
 
 
+def test_importance_entry_point_equals_render_importance():
+    """rs_importance (no image, T_final or last outputs) accumulates exactly the maxima the
+    render with importance does, also on top of values already in h (Eq. importance-score
+    over several calls)."""
+    from paper_2403_13806_gb300 import api
+    scene, cams = synth.config1(n=20000, n_views=3, width=320, height=208)
+    out = gpu_forward(scene, cams)
+    h_ref = out["h"]
+    h = torch.zeros_like(h_ref)
+    api.importance(out["proj"], out["bins"], out["vb"], h)
+    torch.cuda.synchronize()
+    assert torch.equal(h, h_ref)
+    # accumulation: a second call over the same views changes nothing; seeded larger values stay
+    seed = torch.where(torch.arange(h.numel(), device="cuda") % 7 == 0, torch.full_like(h, 0x3f700000), h)
+    h2 = seed.clone()
+    api.importance(out["proj"], out["bins"], out["vb"], h2)
+    torch.cuda.synchronize()
+    assert torch.equal(h2, torch.maximum(seed, h_ref))
+
+
 def test_multiview_batch_with_subsets():
     scene, cams = synth.config1(n=20000, n_views=3, width=256, height=160)
     rng = np.random.default_rng(5)
