@@ -240,7 +240,9 @@ rs_status rs_project(const rs_gaussians* g, const rs_view_batch* batch, const rs
  * The sort runs in levels that give exactly that order: the items by depth (radix), their
  * instances per 4 x 4-tile super-tile by super-tile id (stable radix), then each
  * super-tile list partitioned in order into its tile lists.  Writes vals, ranges, and
- * keys if non-NULL.
+ * keys if non-NULL.  Reads proj->rgb_d (depth in .w), proj->rect and proj->n_tiles as
+ * rs_project writes them; rects given by other means must lie inside their view's tile
+ * grid.
  * If the instance count K exceeds bins->capacity, status->code = RS_ERR_CAPACITY,
  * status->required = K, and only the first capacity instances are written (the lists
  * are then incomplete; re-run with capacity >= required).
