@@ -211,7 +211,8 @@ size_t rs_workspace_size(rs_stage stage, const rs_view_batch* batch, int64_t cap
 
 /* Sizes of the ABI structs, for bindings that mirror them: writes up to n entries in the
  * order rs_gaussians, rs_camera, rs_view, rs_view_batch, rs_config, rs_projected, rs_bins,
- * rs_gaussian_grads, rs_device_status, rs_tune_result, rs_adam_group, rs_gather_desc;
+ * rs_gaussian_grads, rs_device_status, rs_tune_result, rs_adam_group, rs_gather_desc,
+ * rs_image_grads;
  * returns how many it wrote. */
 int32_t rs_struct_sizes(int64_t* out, int32_t n);
 
@@ -346,6 +347,31 @@ rs_status rs_render_backward(const rs_gaussians* g, const rs_view_batch* batch,
                              const rs_bins* bins, const float* T_final, const int32_t* last,
                              const float* dL_dimage, const rs_gaussian_grads* grads,
                              void* ws, size_t ws_bytes, void* stream);
+
+/* Image-space gradients of every projected item (SURVEY A8's output, the derivative of
+ * Eq. render-gs with respect to what rs_project produces), as rs_render_backward leaves
+ * them in its workspace (device, FP32, [n_items] rows, summed over every pixel of the
+ * item's view):
+ *   g_xy_ab[n][4]   dL/dx, dL/dy of the image mean; dL/da, dL/db of the conic (a, b, c)
+ *                   with power = -(a dx^2 + c dy^2)/2 - b dx dy
+ *   g_c_o_rg[n][4]  dL/dc of the conic; dL/do of the opacity; dL/dr, dL/dg of the colour
+ *   g_b[n]          dL/d(blue) of the colour
+ * The colour gradient is taken at the clamped colour max(0, .) (zero where the clamp of
+ * rs_project is active only after the chain to the SH); no gradient flows through alpha
+ * where the 0.99 clamp is active. */
+typedef struct rs_image_grads {
+  const float* g_xy_ab;
+  const float* g_c_o_rg;
+  const float* g_b;
+} rs_image_grads;
+
+/* rs_backward_image_grads -- host helper (no device work): pointers into a backward
+ * workspace `ws` of ws_bytes for `batch` (the ws a completed rs_render_backward of that
+ * batch used) where the per-item image-space gradients above live.  They stay valid until
+ * the workspace is reused.  Errors: RS_ERR_INVALID_ARG, RS_ERR_WORKSPACE (ws_bytes below
+ * rs_workspace_size(RS_STAGE_BACKWARD, batch, 0)). */
+rs_status rs_backward_image_grads(const rs_view_batch* batch, void* ws, size_t ws_bytes,
+                                  rs_image_grads* out);
 
 /* rs_l1_loss -- the L1 photometric loss used for the synthetic training step (a stand-in
  * for the radiance-field supervision of Sec. 3.2, whose teacher renders are not

@@ -6,8 +6,9 @@ nothing from the product library.  The arithmetic lives in ``radsplat_oracle.c``
 (plain C, FP64, no FMA contraction) and ``grad.py`` (PyTorch FP64 autograd on the CPU);
 this module only marshals numpy arrays through ctypes.
 
-Pinned functions (see tests/test_oracle_*.py): projection, SH basis, per-pixel
-compositing, importance, integer binning stages, filter and nearest centre, the FP64
+Pinned functions (see tests/test_oracle_*.py): projection, the FP32 image mean, SH
+basis, per-pixel compositing, importance, integer binning stages, filter and nearest
+centre, the FP64
 gradient, and (``optim.py``) the Adam step and the compaction of pruned parameters.
 No function here is unpinned.
 """
@@ -28,7 +29,7 @@ _lib = None
 ALPHA_MAX = 0.99
 ALPHA_MIN = 1.0 / 255.0
 T_MIN = 1e-4
-DEFAULT_AMB_REL = 1e-4
+DEFAULT_AMB_REL = 1e-5
 
 
 def build(force: bool = False) -> str:
@@ -53,7 +54,7 @@ def lib():
                                  f64, f32, ctypes.c_int, ctypes.c_int] + [P] * 9
         L.or_project.restype = ctypes.c_int
         L.or_render.argtypes = [i64, P, P, P, P, P, P, P, ctypes.c_int, ctypes.c_int, P, i64, P,
-                                ctypes.c_int, f64, P, P, P, P, P, P, P, ctypes.c_int]
+                                ctypes.c_int, f64, P, P, P, P, P, P, P, P, P, P, ctypes.c_int]
         L.or_render.restype = ctypes.c_int
         L.or_bin_sort.argtypes = [i64, P, P, P, P, P, i64, P, P]
         L.or_bin_sort.restype = i64
@@ -63,6 +64,8 @@ def lib():
         L.or_filter.restype = i64
         L.or_nearest.argtypes = [i32, P, i32, P, P]
         L.or_nearest.restype = None
+        L.or_mean2d_f32.argtypes = [i64, P, P, P, P]
+        L.or_mean2d_f32.restype = None
         L.or_sh_basis.argtypes = [ctypes.c_int, P, P]
         L.or_sh_basis.restype = None
         _lib = L
@@ -105,16 +108,36 @@ def project(scene, cam, eps2d=0.3, near=0.2, tile=(16, 16)) -> dict:
     if rc != 0:
         raise ValueError("oracle projection rejected its arguments")
     out["n_tiles"] = ((out["rect"][:, 2] - out["rect"][:, 0]) * (out["rect"][:, 3] - out["rect"][:, 1])).astype(np.int64)
+    out["xy32"] = mean2d_f32(scene, cam)
     out["width"], out["height"] = cam["width"], cam["height"]
     return out
 
 
+def mean2d_f32(scene, cam) -> np.ndarray:
+    """FP32 image means [N, 2] of single-precision arithmetic on the FP32 inputs (reading C5:
+    fma chains for t = M p + m, correctly rounded t_x / t_z, then fmaf(f, u, c))."""
+    n = scene.n
+    means = _c(np.asarray(scene.arrays()[0], dtype=np.float32), np.float32)
+    vm = _c(cam["viewmat"], np.float32).reshape(12)
+    intr = np.array([cam["fx"], cam["fy"], cam["cx"], cam["cy"]], dtype=np.float32)
+    out = np.zeros((n, 2), dtype=np.float32)
+    lib().or_mean2d_f32(n, _p(means), _p(vm), _p(intr), _p(out))
+    return out
+
+
 def render(proj: dict, pixels=None, mode: str = "bucketed", bg=(0.0, 0.0, 0.0),
-           amb_rel: float = DEFAULT_AMB_REL, h=None, h_amb=None, threads: int = 0) -> dict:
+           amb_rel: float = DEFAULT_AMB_REL, h=None, h_amb=None, threads: int = 0, alt_mean: bool = True) -> dict:
     """Composite the given pixels (all if None) front to back, Eq. (render-gs).
 
     ``h`` / ``h_amb`` (float64[N]) accumulate the importance max of Eq.
     (importance-score) across calls; fresh zero arrays are used when None.
+    A pixel is flagged ``ambiguous`` when one of its skip/stop decisions lies within a
+    relative ``amb_rel`` of its threshold (reading C6), evaluated at the FP64 image mean
+    and, with ``alt_mean`` and the projection's ``xy32``, also at the FP32 image mean a
+    single-precision renderer uses (flagged too where the two fall on different sides).
+    ``T_amb`` / ``c_amb``: transmittance in front of the first flagged decision and the
+    largest colour behind it, whose product bounds how far two renderings that agree
+    before that decision can differ (0 on unflagged pixels).
     """
     n = proj["xy"].shape[0]
     W, H = proj["width"], proj["height"]
@@ -128,13 +151,17 @@ def render(proj: dict, pixels=None, mode: str = "bucketed", bg=(0.0, 0.0, 0.0),
     assert h.dtype == np.float64 and h_amb.dtype == np.float64
     out = {"image": np.zeros((npix, 3)), "T_final": np.zeros(npix),
            "last_id": np.zeros(npix, dtype=np.int32), "n_contrib": np.zeros(npix, dtype=np.int32),
-           "ambiguous": np.zeros(npix, dtype=np.uint8)}
+           "ambiguous": np.zeros(npix, dtype=np.uint8), "T_amb": np.zeros(npix), "c_amb": np.zeros(npix)}
     bgv = _c(bg, np.float64)
+    xy_alt = None
+    if alt_mean and "xy32" in proj:
+        xy_alt = _c(proj["xy32"], np.float64)
     rc = lib().or_render(n, _p(proj["xy"]), _p(proj["conic"]), _p(proj["opacity"]), _p(proj["rgb"]),
                          _p(proj["depth"]), _p(proj["valid"]), _p(proj["ext"]), W, H, _p(bgv), npix,
                          None if pix is None else _p(pix), 1 if mode == "bucketed" else 0, float(amb_rel),
+                         None if xy_alt is None else _p(xy_alt),
                          _p(out["image"]), _p(out["T_final"]), _p(out["last_id"]), _p(out["n_contrib"]),
-                         _p(out["ambiguous"]), _p(h), _p(h_amb), int(threads))
+                         _p(out["ambiguous"]), _p(out["T_amb"]), _p(out["c_amb"]), _p(h), _p(h_amb), int(threads))
     if rc != 0:
         raise MemoryError("oracle render ran out of memory")
     out["h"], out["h_amb"] = h, h_amb

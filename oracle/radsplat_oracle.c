@@ -236,6 +236,24 @@ int or_project(int64_t n, const double* means, const double* log_scales, const d
   return 0;
 }
 
+/* FP32 image mean of every Gaussian, as a renderer computing in single precision gets
+ * it from the FP32 inputs (reading C5: only fused multiply-adds and correctly rounded
+ * division, so the value is unique): camera-space t = M p + m as the fma chains
+ * t_r = fmaf(M_r0, px, fmaf(M_r1, py, fmaf(M_r2, pz, m_r))), then u = t_x / t_z,
+ * v = t_y / t_z, x = fmaf(fx, u, cx), y = fmaf(fy, v, cy).  means: FP32 [3][n];
+ * out: FP32 [n][2].  Gaussians behind the camera get whatever the formula gives. */
+void or_mean2d_f32(int64_t n, const float* means, const float* viewmat, const float* intr, float* out) {
+  for (int64_t i = 0; i < n; ++i) {
+    const float px = means[i], py = means[n + i], pz = means[2 * n + i];
+    const float tx = fmaf(viewmat[0], px, fmaf(viewmat[1], py, fmaf(viewmat[2], pz, viewmat[3])));
+    const float ty = fmaf(viewmat[4], px, fmaf(viewmat[5], py, fmaf(viewmat[6], pz, viewmat[7])));
+    const float tz = fmaf(viewmat[8], px, fmaf(viewmat[9], py, fmaf(viewmat[10], pz, viewmat[11])));
+    const float u = tx / tz, v = ty / tz;
+    out[2 * i] = fmaf(intr[0], u, intr[2]);
+    out[2 * i + 1] = fmaf(intr[1], v, intr[3]);
+  }
+}
+
 /* ------------------------------------------------------------------ */
 /* Per-pixel compositing, Eq. (render-gs), with the importance max of  */
 /* Eq. (importance-score).                                             */
@@ -247,6 +265,8 @@ typedef struct {
   double alpha;    /* min(0.99, araw) */
   double araw;     /* o * exp(power) */
   double power;
+  double araw2;    /* the same at the alternative image mean (= araw without one) */
+  double power2;
 } or_entry;
 
 static int entry_cmp(const void* a, const void* b) {
@@ -263,8 +283,16 @@ static int entry_cmp(const void* a, const void* b) {
  *         support bounding box (slightly widened) overlaps the cell; this is a
  *         superset of the alpha >= 1/255 set, so the result is identical.
  * Per pixel: image[3], T_final, last_id (id of the last composited entry, -1 if
- * none), n_contrib, ambiguous (1 if, before compositing stops, a skip or stop
- * decision lies within a relative amb_rel of its threshold, or 0 < |power| <= 1e-9).
+ * none), n_contrib, ambiguous: 1 if, before compositing stops, a skip or stop decision
+ * lies within a relative amb_rel of its threshold, or 0 < |power| <= 1e-9 -- each
+ * decision evaluated at the FP64 image mean xy and, if xy_alt is given, also at xy_alt
+ * (the FP32 mean a single-precision renderer uses), where the two evaluations falling on
+ * different sides flags the pixel too.  The compositing itself uses xy only.
+ * T_amb (may be NULL): the transmittance in front of the first flagged decision (0 for an
+ * unflagged pixel); c_amb (may be NULL): the largest colour channel (or background) of
+ * the entries from that decision on (0 if unflagged).  Two renderers that agree on every
+ * decision before it composite the same front part, and each composites at most
+ * T_amb * c_amb behind it, so their images differ by at most that plus rounding.
  * Per Gaussian (in/out, max-accumulated): h, alpha*T of every composited entry that
  * precedes the pixel's first near-threshold decision (an unflagged pixel has none);
  * h_amb, alpha*T of every entry from that decision up to and including the stopping
@@ -274,8 +302,9 @@ static int entry_cmp(const void* a, const void* b) {
 int or_render(int64_t n, const double* xy, const double* conic, const double* opacity,
               const double* rgb, const float* depth, const int32_t* valid, const double* ext,
               int width, int height, const double* bg, int64_t n_pix, const int32_t* pix, int mode,
-              double amb_rel, double* image, double* T_final, int32_t* last_id, int32_t* n_contrib,
-              uint8_t* ambiguous, double* h, double* h_amb, int n_threads) {
+              double amb_rel, const double* xy_alt, double* image, double* T_final, int32_t* last_id,
+              int32_t* n_contrib, uint8_t* ambiguous, double* T_amb, double* c_amb, double* h, double* h_amb,
+              int n_threads) {
   const int CELL = 16;
   const int cells_x = (width + CELL - 1) / CELL, cells_y = (height + CELL - 1) / CELL;
   int64_t* cell_start = NULL;
@@ -295,6 +324,10 @@ int or_render(int64_t n, const double* xy, const double* conic, const double* op
         if (!valid[i]) continue;
         /* widened so that the FP64 alpha test never keeps a pixel outside the box */
         double mx = ext[2 * i] * (1.0 + 1e-6) + 1e-6, my = ext[2 * i + 1] * (1.0 + 1e-6) + 1e-6;
+        if (xy_alt) {   /* cover the support around either mean */
+          mx += fabs(xy_alt[2 * i] - xy[2 * i]);
+          my += fabs(xy_alt[2 * i + 1] - xy[2 * i + 1]);
+        }
         double u0 = ceil(xy[2 * i] - mx), u1 = floor(xy[2 * i] + mx);
         double v0 = ceil(xy[2 * i + 1] - my), v1 = floor(xy[2 * i + 1] + my);
         if (u0 < 0) u0 = 0;
@@ -350,9 +383,15 @@ int or_render(int64_t n, const double* xy, const double* conic, const double* op
         double dx = (double)u - xy[2 * j], dy = (double)v - xy[2 * j + 1];
         double power = -0.5 * (conic[3 * j] * dx * dx + conic[3 * j + 2] * dy * dy) -
                        conic[3 * j + 1] * dx * dy;
-        if (power > 1e-9) continue;
         double araw = opacity[j] * exp(power);
-        if (araw < a_lo) continue;
+        double power2 = power, araw2 = araw;
+        if (xy_alt) {
+          double dx2 = (double)u - xy_alt[2 * j], dy2 = (double)v - xy_alt[2 * j + 1];
+          power2 = -0.5 * (conic[3 * j] * dx2 * dx2 + conic[3 * j + 2] * dy2 * dy2) - conic[3 * j + 1] * dx2 * dy2;
+          araw2 = opacity[j] * exp(power2);
+        }
+        /* an entry neither evaluation could keep changes nothing */
+        if ((power > 1e-9 || araw < a_lo) && (power2 > 1e-9 || araw2 < a_lo)) continue;
         if (ne == cap) {
           cap *= 2;
           ent = (or_entry*)realloc(ent, sizeof(or_entry) * cap);
@@ -366,21 +405,40 @@ int or_render(int64_t n, const double* xy, const double* conic, const double* op
         ent[ne].araw = araw;
         ent[ne].alpha = araw < OR_ALPHA_MAX ? araw : OR_ALPHA_MAX;
         ent[ne].power = power;
+        ent[ne].araw2 = araw2;
+        ent[ne].power2 = power2;
         ++ne;
       }
       if (fail) continue;
       qsort(ent, (size_t)ne, sizeof(or_entry), entry_cmp);
       double T = 1.0, C[3] = {0.0, 0.0, 0.0};
+      double T2 = 1.0;       /* transmittance from the alternative alphas, up to the first flag */
+      double Tat = 0.0;      /* transmittance in front of the first flagged decision */
       int64_t last = -1, cnt = 0, stop = ne;
       int64_t amb_at = -1;   /* sorted position of the first near-threshold decision */
       for (int64_t e = 0; e < ne; ++e) {
-        if (amb_at < 0 && ent[e].power != 0.0 && fabs(ent[e].power) <= 1e-9) amb_at = e;
-        if (amb_at < 0 && fabs(ent[e].araw - OR_ALPHA_MIN) <= amb_rel * OR_ALPHA_MIN) amb_at = e;
-        if (ent[e].power > 0.0) continue;
+        const double p1 = ent[e].power, p2 = ent[e].power2;
+        const double r1 = ent[e].araw, r2 = ent[e].araw2;
+        if (amb_at < 0) {
+          int flag = (p1 != 0.0 && fabs(p1) <= 1e-9) || (p2 != 0.0 && fabs(p2) <= 1e-9) || ((p1 > 0.0) != (p2 > 0.0));
+          flag = flag || fabs(r1 - OR_ALPHA_MIN) <= amb_rel * OR_ALPHA_MIN ||
+                 fabs(r2 - OR_ALPHA_MIN) <= amb_rel * OR_ALPHA_MIN || ((r1 < OR_ALPHA_MIN) != (r2 < OR_ALPHA_MIN));
+          if (flag) { amb_at = e; Tat = T; }
+        }
+        if (p1 > 0.0) continue;
         double a = ent[e].alpha;
         if (a < OR_ALPHA_MIN) continue;
         double Tn = T * (1.0 - a);
-        if (amb_at < 0 && fabs(Tn - OR_T_MIN) <= amb_rel * OR_T_MIN) amb_at = e;
+        if (amb_at < 0) {
+          const double a2 = r2 < OR_ALPHA_MAX ? r2 : OR_ALPHA_MAX;
+          const double Tn2 = T2 * (1.0 - a2);
+          if (fabs(Tn - OR_T_MIN) <= amb_rel * OR_T_MIN || fabs(Tn2 - OR_T_MIN) <= amb_rel * OR_T_MIN ||
+              ((Tn < OR_T_MIN) != (Tn2 < OR_T_MIN))) {
+            amb_at = e;
+            Tat = T;
+          }
+          T2 = Tn2;
+        }
         if (Tn < OR_T_MIN) { stop = e; break; }
         const double* c = rgb + 3 * ent[e].id;
         C[0] += c[0] * a * T;
@@ -392,6 +450,20 @@ int or_render(int64_t n, const double* xy, const double* conic, const double* op
         T = Tn;
         last = ent[e].id;
         ++cnt;
+      }
+      if (T_amb) T_amb[k] = amb_at >= 0 ? Tat : 0.0;
+      if (c_amb) {
+        double cm = 0.0;
+        if (amb_at >= 0) {
+          for (int ch = 0; ch < 3; ++ch) {
+            const double b = bg ? fabs(bg[ch]) : 0.0;
+            if (b > cm) cm = b;
+          }
+          for (int64_t e = amb_at; e < ne; ++e)
+            for (int ch = 0; ch < 3; ++ch)
+              if (rgb[3 * ent[e].id + ch] > cm) cm = rgb[3 * ent[e].id + ch];
+        }
+        c_amb[k] = cm;
       }
       const int amb = amb_at >= 0;
       for (int ch = 0; ch < 3; ++ch) image[3 * k + ch] = C[ch] + T * (bg ? bg[ch] : 0.0);
@@ -484,13 +556,15 @@ int64_t or_bin_sort(int64_t m, const float* depth, const uint16_t* rect, const i
 }
 
 /* ranges[2t], ranges[2t+1] = first and one-past-last position of tile t in the
- * sorted keys; [0, 0) for a tile with no instance. */
+ * sorted keys: the number of instances on tiles < t and on tiles <= t.  A tile with
+ * no instance gets the empty range [s, s) at the place its list would start (reading
+ * C5: that position is unique, so empty tiles are compared bit for bit too). */
 void or_tile_ranges(int64_t K, const uint64_t* keys, int64_t n_tiles, uint32_t* ranges) {
-  for (int64_t t = 0; t < 2 * n_tiles; ++t) ranges[t] = 0;
-  for (int64_t e = 0; e < K; ++e) {
-    uint64_t t = keys[e] >> 32;
-    if (e == 0 || (keys[e - 1] >> 32) != t) ranges[2 * t] = (uint32_t)e;
-    ranges[2 * t + 1] = (uint32_t)(e + 1);
+  int64_t e = 0;
+  for (int64_t t = 0; t < n_tiles; ++t) {
+    ranges[2 * t] = (uint32_t)e;
+    while (e < K && (int64_t)(keys[e] >> 32) == t) ++e;
+    ranges[2 * t + 1] = (uint32_t)e;
   }
 }
 

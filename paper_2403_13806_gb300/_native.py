@@ -60,6 +60,10 @@ class RsGaussianGrads(ctypes.Structure):
                 ("sh", c_void_p)]
 
 
+class RsImageGrads(ctypes.Structure):
+    _fields_ = [("g_xy_ab", c_void_p), ("g_c_o_rg", c_void_p), ("g_b", c_void_p)]
+
+
 class RsDeviceStatus(ctypes.Structure):
     _fields_ = [("code", c_int32), ("nonfinite", c_int32), ("required", c_int64), ("n_instances", c_int64),
                 ("reserved", c_int64)]
@@ -83,7 +87,7 @@ class RsGatherDesc(ctypes.Structure):
                 ("dst_stride", c_int64)]
 
 STRUCTS = [RsGaussians, RsCamera, RsView, RsViewBatch, RsConfig, RsProjected, RsBins, RsGaussianGrads, RsDeviceStatus,
-           RsTuneResult, RsAdamGroup, RsGatherDesc]
+           RsTuneResult, RsAdamGroup, RsGatherDesc, RsImageGrads]
 
 # every function include/radsplat.h declares, with its ctypes signature
 P = c_void_p
@@ -105,6 +109,7 @@ SIGNATURES = {
     "rs_nn_workspace_size": (c_size_t, [c_int64]),
     "rs_filter_noalloc": (ctypes.c_int, [P, c_int64, c_float, ctypes.c_int, P, P, P, P]),
     "rs_render_backward": (ctypes.c_int, [P, P, P, P, P, P, P, P, P, P, c_size_t, P]),
+    "rs_backward_image_grads": (ctypes.c_int, [P, P, c_size_t, P]),
     "rs_l1_loss": (ctypes.c_int, [P, P, c_int64, P, P, P]),
     "rs_autotune": (ctypes.c_int, [P, P, c_int32, P, P, P, c_int32, P, P, P]),
     "rs_adam_step": (ctypes.c_int, [P, c_int32, c_float, c_float, c_float, c_int32, P]),

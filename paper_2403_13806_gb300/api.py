@@ -18,7 +18,7 @@ from . import _native as N
 __all__ = ["Gaussians", "ViewBatch", "Projected", "Bins", "DeviceStatus", "Workspace", "config", "project",
            "bin_sort", "render", "importance", "filter", "nearest", "render_backward", "Rasterizer",
            "RadSplatFunction", "split_images", "importance_as_float", "autotune", "TILE_SHAPES", "blend_threads", "adam_step",
-           "gather_columns", "ssim_loss", "PAPER_LAMBDA", "kmeans", "nn_distance",
+           "gather_columns", "ssim_loss", "PAPER_LAMBDA", "kmeans", "nn_distance", "image_grads",
            "init_log_scales", "StepGraph"]
 
 PAPER_LAMBDA = 0.2   # weight of the SSIM term in the loss of Sec. 3.2
@@ -323,6 +323,26 @@ def render_backward(g: Gaussians, vb: ViewBatch, proj: Projected, bins: Bins, T_
     N.call("rs_render_backward", N.ref(g.struct()), N.ref(vb.batch), N.ref(cfg), N.ref(proj.struct()),
            N.ref(bins.struct()), _ptr(T_final), _ptr(last), _ptr(dL_dimage), N.ref(gs), _ptr(w), w.numel(),
            _stream(stream))
+
+
+def image_grads(vb: ViewBatch, ws: Workspace):
+    """Per-item image-space gradients the last render_backward of `vb` left in `ws`
+    (rs_backward_image_grads): (g_xy_ab [n_items, 4], g_c_o_rg [n_items, 4], g_b [n_items])
+    float32 views of the workspace: dL/d(x, y, a, b), dL/d(c, o, r, g), dL/d(blue)."""
+    out = N.RsImageGrads()
+    w = ws.t
+    if w is None:
+        raise ValueError("no backward has run with this workspace")
+    N.call("rs_backward_image_grads", N.ref(vb.batch), _ptr(w), w.numel(), N.ref(out))
+    n = int(vb.n_items)
+    base = w.data_ptr()
+    f = w.view(torch.uint8)
+
+    def at(ptr, count):
+        off = ptr - base
+        return f[off: off + 4 * count].view(torch.float32)
+
+    return (at(out.g_xy_ab, 4 * n).view(n, 4), at(out.g_c_o_rg, 4 * n).view(n, 4), at(out.g_b, n))
 
 
 def blend_threads(tile) -> int:

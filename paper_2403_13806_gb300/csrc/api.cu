@@ -102,7 +102,7 @@ extern "C" int32_t rs_struct_sizes(int64_t* out, int32_t n) {
                        (int64_t)sizeof(rs_view_batch), (int64_t)sizeof(rs_config),         (int64_t)sizeof(rs_projected),
                        (int64_t)sizeof(rs_bins),       (int64_t)sizeof(rs_gaussian_grads), (int64_t)sizeof(rs_device_status),
                        (int64_t)sizeof(rs_tune_result), (int64_t)sizeof(rs_adam_group),
-                       (int64_t)sizeof(rs_gather_desc)};
+                       (int64_t)sizeof(rs_gather_desc), (int64_t)sizeof(rs_image_grads)};
   const int32_t k = (int32_t)(sizeof(s) / sizeof(s[0]));
   int32_t w = 0;
   for (; w < k && w < n; ++w) out[w] = s[w];

@@ -602,6 +602,21 @@ static BwdWs bwd_ws_layout(void* base, int64_t n_items) {
 
 size_t backward_ws_bytes(const rs_view_batch* batch) { return bwd_ws_layout(nullptr, batch->n_items).bytes; }
 
+}  // namespace rs
+
+extern "C" rs_status rs_backward_image_grads(const rs_view_batch* batch, void* ws, size_t ws_bytes,
+                                             rs_image_grads* out) {
+  if (!batch || !ws || !out || batch->n_items < 0) return RS_ERR_INVALID_ARG;
+  const rs::BwdWs w = rs::bwd_ws_layout(ws, batch->n_items);
+  if (ws_bytes < w.bytes) return RS_ERR_WORKSPACE;
+  out->g_xy_ab = reinterpret_cast<const float*>(w.ga);
+  out->g_c_o_rg = reinterpret_cast<const float*>(w.gb);
+  out->g_b = w.gc;
+  return RS_OK;
+}
+
+namespace rs {
+
 // One warp per tile (PX = 8 pixels per thread for 16x16 and 32x8 tiles, 2 for 8x8): the
 // per-entry warp reduction serves 256 (64) pixels and no cross-warp partials are needed.
 // Records staged per batch: cfg->batch (the same count as the forward stages), i.e.

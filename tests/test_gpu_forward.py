@@ -37,6 +37,8 @@ def test_projection_matches_oracle():
             xy = p.xy.cpu().numpy()
             co = p.conic_o.cpu().numpy()
             rgb = p.rgb_d[:, :3].cpu().numpy()
+            # the image mean is the FP32 mirror's bit for bit (reading C5), close to the FP64 one
+            assert np.array_equal(xy[vis], o["xy32"][vis])
             np.testing.assert_allclose(xy[vis], o["xy"][vis], rtol=1e-5, atol=2e-3)
             np.testing.assert_allclose(co[vis, 3], o["opacity"][vis], rtol=1e-5)
             np.testing.assert_allclose(rgb[vis], o["rgb"][vis], atol=2e-5)
@@ -75,11 +77,10 @@ def synthetic_projected(rng, views, m_per_view, span=5):
 
 
 def check_ranges(ranges, ranges_o, K):
-    """Tile ranges: exact for every tile with instances; an empty tile's range only has to
-    be empty (start == end; where it sits is not unique) and inside the list."""
-    full = ranges_o[:, 1] > ranges_o[:, 0]
-    assert np.array_equal(ranges[full], ranges_o[full])
-    assert np.all(ranges[~full, 0] == ranges[~full, 1]) and np.all(ranges[~full, 1] <= K)
+    """Tile ranges bit for bit, empty tiles included (reading C5: an empty tile's range is
+    the empty one at the place its list would start)."""
+    assert np.array_equal(ranges, ranges_o)
+    assert ranges_o[-1, 1] == K
 
 
 @pytest.mark.parametrize("views,m,span", [([(8, 8)], [5000], 5), ([(80, 52)], [60000], 5),
@@ -133,7 +134,7 @@ def test_render_config0_matches_brute_oracle(tile):
     scene, cams = synth.config0()
     out = gpu_forward(scene, cams, tile=tile)
     err, namb, ro = check_view_against_oracle(out, scene, cams[0], 0, mode="brute")
-    assert namb < 0.005 * 128 * 128
+    assert namb < 1e-4 * 128 * 128          # reading C6: flagged pixels below 1e-4 of the image
 
 
 def test_images_identical_across_tile_shapes():
@@ -168,7 +169,7 @@ def test_staging_batch_changes_nothing(tile):
     assert e.value.code == N.RS_ERR_UNSUPPORTED
 
 
-def check_importance(h_gpu, h, h_amb, min_strict=0.8):
+def check_importance(h_gpu, h, h_amb, min_strict=0.999):
     """h: max alpha*T over entries no near-threshold decision precedes; h_amb: over the
     others.  Flipping an alpha decision rescales later T by at most 1/(1 - 1/255), and a
     stop flip adds or removes the stopping entry (included in h_amb), so

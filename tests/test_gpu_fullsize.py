@@ -61,7 +61,9 @@ def test_config2_full_view_sampled():
     rng = np.random.default_rng(20)
     pix = sample_pixels(rng, cams[0], 2048)
     err, namb, _ = check_view_against_oracle(out, scene, cams[0], 0, pixels=pix)
-    assert namb < 0.02 * len(pix)
+    # reading C6 at this depth: ~10^2 decisions per pixel, so a few pixels per thousand carry one
+    # within the 1e-5 band (0.5-1 per thousand seen)
+    assert namb <= 2e-3 * len(pix)
     check_bins_properties(out)
 
 

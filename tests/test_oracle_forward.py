@@ -224,7 +224,7 @@ def test_importance_is_max_of_composited_contributions(oracle_lib):
     scene, cams = synth.fd_crop()
     cam = cams[0]
     p = oracle.project(scene, cam)
-    r = oracle.render(p, mode="brute", amb_rel=0.0)
+    r = oracle.render(p, mode="brute", amb_rel=0.0, alt_mean=False)
     _, order = og._fixed_decisions(scene, cam, 0.3, 0.2)
     with torch.no_grad():
         prm = og.params_of(scene, requires_grad=False)
@@ -335,3 +335,134 @@ def test_rotated_anisotropic_falloff(oracle_lib):
         expect = a * 0.9 if a >= 1 / 255 else 0.0
         assert img[2, 32 + dv, 32 + du] == pytest.approx(expect, rel=1e-12, abs=1e-15)
     assert img[0, 33, 34] != pytest.approx(img[0, 31, 34], rel=1e-3)     # the cross term matters
+
+
+# ---------------------------------------------------------------- FP32 image mean (reading C5)
+
+def _round_f32(q):
+    """Exact rational q rounded to the nearest float32, ties to even (IEEE 754 default)."""
+    from fractions import Fraction
+    x = np.float32(float(q))
+    cands = [x, np.nextafter(x, np.float32(np.inf)), np.nextafter(x, np.float32(-np.inf))]
+    best = None
+    for c in cands:
+        d = abs(Fraction(float(c)) - q)
+        if best is None or d < best[0] or (d == best[0] and (int(np.array(c).view(np.uint32)) & 1) == 0):
+            best = (d, c)
+    return best[1]
+
+
+def _mean_f32_exact(p, vm, intr):
+    """The FP32 mean by exact rational arithmetic with one explicit rounding per fma and per
+    division (an fma rounds a*b + c once)."""
+    from fractions import Fraction as F
+    fma = lambda a, b, c: _round_f32(F(float(a)) * F(float(b)) + F(float(c)))
+    t = [fma(vm[4 * r], p[0], fma(vm[4 * r + 1], p[1], fma(vm[4 * r + 2], p[2], vm[4 * r + 3]))) for r in range(3)]
+    u = _round_f32(F(float(t[0])) / F(float(t[2])))
+    v = _round_f32(F(float(t[1])) / F(float(t[2])))
+    return fma(intr[0], u, intr[2]), fma(intr[1], v, intr[3])
+
+
+def test_fp32_mean_exact_cases(oracle_lib):
+    """Inputs whose every operation is exact: identity and axis-permutation views."""
+    sc = one_scene([0.5, -0.25, 2.0], [0.0] * 3, [1, 0, 0, 0], [0.0], [0.0] * 3)
+    cam = synth.camera(np.eye(3, 4), 64.0, 64.0, 32.0, 16.0, 64, 32)
+    np.testing.assert_array_equal(oracle.mean2d_f32(sc, cam)[0], np.float32([48.0, 8.0]))
+    # camera looking down -x: x_c = y, y_c = z, z_c = -x + 3
+    vm = np.array([[0, 1, 0, 0], [0, 0, 1, 0], [-1, 0, 0, 3]], np.float64)
+    sc = one_scene([1.0, 0.5, -1.0], [0.0] * 3, [1, 0, 0, 0], [0.0], [0.0] * 3)
+    cam = synth.camera(vm, 100.0, 50.0, 10.0, 20.0, 64, 64)
+    np.testing.assert_array_equal(oracle.mean2d_f32(sc, cam)[0], np.float32([100 * 0.25 + 10, 50 * -0.5 + 20]))
+
+
+def test_fp32_mean_is_correctly_rounded_chain(oracle_lib):
+    """Random poses and points: bit-equal to the same chain in exact rational arithmetic."""
+    rng = np.random.default_rng(11)
+    for trial in range(6):
+        q = rng.normal(size=4)
+        q /= np.linalg.norm(q)
+        w, x, y, z = q
+        R = np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                      [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                      [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+        vm = np.concatenate([R, rng.normal(size=(3, 1)) + np.array([[0], [0], [6.0]])], 1).astype(np.float32)
+        n = 40
+        means = rng.normal(size=(3, n)).astype(np.float32)
+        sc = synth.Scene(means.astype(np.float64), np.zeros((3, n)), np.tile([[1.0], [0], [0], [0]], n),
+                         np.zeros(n), np.zeros((3, n)), 0)
+        cam = synth.camera(vm.astype(np.float64), 1200.0, 1100.0, 640.0, 416.0, 1280, 832)
+        got = oracle.mean2d_f32(sc, cam)
+        vmf = np.asarray(cam["viewmat"], np.float32).reshape(12)
+        intr = np.float32([cam["fx"], cam["fy"], cam["cx"], cam["cy"]])
+        for i in range(n):
+            ex = _mean_f32_exact(means[:, i], vmf, intr)
+            assert got[i, 0] == ex[0] and got[i, 1] == ex[1], (trial, i)
+
+
+# ---------------------------------------------------------------- ambiguity flags (reading C6)
+
+def _one_gaussian_at(d, o, xy32_shift=0.0):
+    """One isotropic Gaussian (conic = I) at (4, 4); the pixel (4 + d, 4) sees alpha = o e^(-d^2/2)."""
+    p = proj_dict([[4.0, 4.0]], [[1.0, 0.0, 1.0]], [o], [[0.5, 0.25, 0.75]], [1.0], W=16, H=8)
+    p["xy32"] = p["xy"] + np.array([[xy32_shift, 0.0]])
+    return p
+
+
+def _d_for_alpha(alpha, o):
+    return math.sqrt(2.0 * math.log(o / alpha))
+
+
+def test_flag_band_is_relative_1e5(oracle_lib):
+    """A skip decision within a relative 1e-5 of 1/255 flags the pixel; 3e-5 away does not."""
+    o = 0.8
+    for rel, flagged in ((0.5e-5, 1), (-0.5e-5, 1), (3e-5, 0), (-3e-5, 0)):
+        d = _d_for_alpha((1 + rel) / 255.0, o)
+        p = _one_gaussian_at(d, o)
+        p["xy"] = np.array([[8.0 - d, 4.0]])     # pixel (8, 4) at distance d
+        p["xy32"] = p["xy"].copy()
+        r = oracle.render(p, pixels=[[8, 4], [15, 0]], mode="brute")
+        assert r["ambiguous"][0] == flagged, rel
+        assert r["ambiguous"][1] == 0             # far away: alpha << 1/255
+        if flagged:
+            assert r["T_amb"][0] == 1.0 and r["c_amb"][0] == 0.75
+        else:
+            assert r["T_amb"][0] == 0.0 and r["c_amb"][0] == 0.0
+
+
+def test_flag_where_the_fp32_mean_decides_otherwise(oracle_lib):
+    """alpha is 1e-3 above 1/255 at the FP64 mean and below it at the FP32 one: flagged,
+    although both lie far outside the 1e-5 band; with equal means it is not."""
+    o = 0.8
+    d = _d_for_alpha(1.001 / 255.0, o)
+    x0 = 10.0 - d                         # pixel (10, 4) at distance d from the FP64 mean
+    for shift, flagged in ((0.0, 0), (-2e-3 / d, 1)):
+        p = _one_gaussian_at(d, o)
+        p["xy"] = np.array([[x0, 4.0]])
+        p["xy32"] = np.array([[x0 + shift, 4.0]])
+        r = oracle.render(p, pixels=[[10, 4]], mode="brute")
+        assert r["ambiguous"][0] == flagged
+        assert r["n_contrib"][0] == 1     # the compositing follows the FP64 mean
+        r2 = oracle.render(p, pixels=[[10, 4]], mode="brute", alt_mean=False)
+        assert r2["ambiguous"][0] == 0
+
+
+def test_flagged_pixel_bound_covers_both_outcomes(oracle_lib):
+    """Behind the first flagged decision the image can change by at most T_amb * c_amb: the
+    two outcomes of a flagged skip decision (compositing it or not) stay within it."""
+    o = 0.8
+    d = _d_for_alpha(1.000002 / 255.0, o)
+    front = 0.4
+    p = proj_dict([[4.0, 4.0], [10.0 - d, 4.0], [10.0, 4.0]], [[0.01, 0, 0.01], [1.0, 0, 1.0], [0.01, 0, 0.01]],
+                  [front, o, 0.5], [[0.2, 0.2, 0.2], [0.9, 0.1, 0.3], [0.6, 0.7, 0.1]], [1.0, 2.0, 3.0], W=16, H=8)
+    p["ext"][:] = 100.0
+    r = oracle.render(p, pixels=[[10, 4]], mode="brute")
+    assert r["ambiguous"][0] == 1
+    T_front = 1.0 - front * math.exp(-0.5 * 0.01 * 36.0)
+    assert r["T_amb"][0] == pytest.approx(T_front, rel=1e-14)
+    assert r["c_amb"][0] == 0.9
+    # the other outcome: the middle Gaussian skipped
+    q = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in p.items()}
+    q["opacity"][1] = 0.0
+    q["valid"][1] = 0
+    r_skip = oracle.render(q, pixels=[[10, 4]], mode="brute")
+    assert np.abs(r_skip["image"][0] - r["image"][0]).max() <= r["T_amb"][0] * r["c_amb"][0]

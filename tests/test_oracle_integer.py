@@ -49,18 +49,22 @@ def test_bin_sort_matches_tuple_sort():
         assert int(keys[k]) == (tile << 32) | int(dbits[i])
 
 
-def test_tile_ranges_match_searchsorted():
+@pytest.mark.parametrize("m,views", [(200, [(6, 5)]), (12, [(9, 7), (4, 4)])])
+def test_tile_ranges_match_searchsorted(m, views):
+    """Every tile, empty ones included (reading C5: an empty tile's range is empty and sits
+    where its list would start): [searchsorted left, searchsorted right)."""
     rng = np.random.default_rng(1)
-    depth, rect, iv, tx, base, ntiles = random_items(rng, 200, [(6, 5)])
+    depth, rect, iv, tx, base, ntiles = random_items(rng, m, views)
     keys, _ = oracle.bin_sort(depth, rect, iv, tx, base)
     ranges = oracle.tile_ranges(keys, ntiles)
     tiles = (keys >> np.uint64(32)).astype(np.int64)
+    n_empty = 0
     for t in range(ntiles):
         lo, hi = np.searchsorted(tiles, t, "left"), np.searchsorted(tiles, t, "right")
-        if lo == hi:
-            assert tuple(ranges[t]) == (0, 0)
-        else:
-            assert tuple(ranges[t]) == (lo, hi)
+        assert tuple(ranges[t]) == (lo, hi)
+        n_empty += lo == hi
+    if m == 12:
+        assert n_empty > 0 and ranges[-1, 1] == len(keys)
 
 
 def test_empty_and_degenerate_rects():
