@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--tile", default="auto", help="tile shape WxH with all views in one launch, or 'auto' "
                                                    "(autotuner: tile shape, staging batch, views per launch)")
     ap.add_argument("--sample-pixels", type=int, default=0, help="reference arm: pixels per step (0: auto)")
+    ap.add_argument("--probes", action="store_true", help="only run the peak probe kernels and print their rates")
     return ap.parse_args()
 
 
@@ -341,8 +342,9 @@ def run_ours(args):
     optim = optimizer_bench(api, N, torch, g, gbuf, h, hbm, reps=10)
     uneven = uneven_bench(api, N, torch, dev, args.uneven_views, reps=3) if args.uneven_views > 0 else None
     work = kernel_work(vbs, sres, pairs, n_super, touched)
-    roof = roofline(kernel_ms, work, hbm, peak_kind, B)
-    per_kernel = {k: kernel_frac(k, kernel_ms[k], work, hbm) for k in kernel_ms if k in work}
+    probes = probe_peaks(N, torch, dev)
+    roof = roofline(kernel_ms, work, hbm, peak_kind, B, probes)
+    per_kernel = {k: kernel_frac(k, kernel_ms[k], work, hbm, probes) for k in kernel_ms if k in work}
     launches = int(round(sum(v["launches_per_step"] for v in kernel_ms.values()))) * args.steps
 
     if rank == 0:
@@ -373,7 +375,7 @@ def run_ours(args):
             "stage_ms_per_step": {k: round(v, 5) for k, v in stage_ms.items()},
             "kernel_ms_per_step": {k: round(v["ms_per_step"], 5) for k, v in
                                    sorted(kernel_ms.items(), key=lambda kv: -kv[1]["ms_per_step"])},
-            "e2e": e2e, "roofline": roof, "roofline_per_kernel": per_kernel, "optimizer": optim,
+            "e2e": e2e, "roofline": roof, "roofline_per_kernel": per_kernel, "probes": probes, "optimizer": optim,
             "uneven_batch": uneven, "cpu_baseline": cpu,
             "clocks": clk.summary(),
             "gpu_launches": launches,
@@ -748,12 +750,65 @@ def e2e_run(api, N, torch, scene, vbs, cfg, targets, cap, reps, dev, world=1, lo
                               "step k's loss is read on the host once step k+1 is queued"}
 
 
-# FP32 lane-operations per second of the GB300: 152 SMs x 128 FP32 lanes x 2070 MHz.
-ALU_PEAK_OPS = 152 * 128 * 2070e6
-# FP32 operations per (pixel, Gaussian) pair of the blend kernels, counted from their source:
-# forward 22 (offset 2, quadratic form 5, tests 3, exp2 and scale 2, clamp and test 2,
-# transmittance 3, weight 1, colour 3, bookkeeping 1); backward 46.
-OPS_PER_PAIR = {"k_render_importance": 22, "k_render": 22, "k_render_bwd": 46}
+# Algorithmic work per evaluated (pixel, Gaussian) pair of the blend kernels, as the
+# method's arithmetic counts it (an FMA is one operation): the forward blend (A5) needs about
+# 15 FP32 operations and one ex2, the importance maximum (A6) one more operation; the
+# backward blend (A8) about 40 FP32 operations and one ex2.
+FP32_OPS_PER_PAIR = {"k_render_importance": 16, "k_render": 15, "k_render_bwd": 40}
+EX2_PER_PAIR = 1
+# The FP32 operations the kernels as written execute per pair (counted from their source:
+# forward 22 = offsets 2, quadratic form 5, tests 3, exp2 and scale 2, clamp and test 2,
+# transmittance 3, weight 1, colour 3, bookkeeping 1; backward 46), reported beside the
+# algorithmic figure.
+INSTR_OPS_PER_PAIR = {"k_render_importance": 22, "k_render": 22, "k_render_bwd": 46}
+L2_BYTES = 126 * 2 ** 20     # the working set below which a kernel's bytes stay in L2
+
+# Probe kernels (rs_peak_probe): name, kind, iterations per launch (about 1-3 ms each).
+PROBES = (("ffma", 0, 20000), ("ffma2", 1, 10000), ("alu", 2, 12000), ("ex2", 3, 2500), ("smem", 4, 3000),
+          ("l2", 5, 300))
+
+
+def probe_peaks(N, torch, dev, reps=5):
+    """Measured peaks (rates per second) of the probe kernels on this GPU: best of `reps`
+    launches after two untimed ones, CUDA events on the launching stream, SM clocks sampled
+    meanwhile.  FP32/ALU/ex2 in lane operations per second, smem and L2 in bytes per second."""
+    import ctypes
+    L = N.lib()
+    sink = torch.zeros(int(L.rs_peak_probe_sink_floats()), device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    rates = {}
+    with ClockSampler(dev.index or 0) as clk:
+        for name, kind, iters in PROBES:
+            work = ctypes.c_double()
+            best = 0.0
+            for r in range(2 + reps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                N.call("rs_peak_probe", kind, iters, ctypes.c_void_p(sink.data_ptr()), sink.numel(),
+                       ctypes.byref(work), sp)
+                e1.record(stream)
+                e1.synchronize()
+                if r >= 2:
+                    best = max(best, work.value / (e0.elapsed_time(e1) / 1e3))
+            rates[name] = best
+    c = clk.summary()
+    mhz = c["sm_mhz"] or 2070.0
+    per = 152 * mhz * 1e6
+    return {
+        "ffma_tops": round(rates["ffma"] / 1e12, 2), "ffma2_tops": round(rates["ffma2"] / 1e12, 2),
+        "alu_tops": round(rates["alu"] / 1e12, 2), "ex2_tops": round(rates["ex2"] / 1e12, 3),
+        "smem_tbs": round(rates["smem"] / 1e12, 2), "l2_tbs": round(rates["l2"] / 1e12, 2),
+        "per_sm_per_clock": {"ffma": round(rates["ffma"] / per, 1), "ffma2": round(rates["ffma2"] / per, 1),
+                             "alu": round(rates["alu"] / per, 1), "ex2": round(rates["ex2"] / per, 1),
+                             "smem_bytes": round(rates["smem"] / per, 1), "l2_bytes": round(rates["l2"] / per, 1)},
+        "fp32_peak_tops": round(max(rates["ffma"], rates["ffma2"]) / 1e12, 2),
+        "clocks": c,
+        "how": "rs_peak_probe kernels (8 CTAs x 256 threads per SM, 8 independent chains per thread), best of "
+               f"{reps} launches, CUDA events; FP32 peak = the larger of the FFMA and packed-FFMA2 lane-op rates",
+    }
+
 
 # DRAM bytes (read + write) per launch of a kernel, per view of the benchmark workload, from
 # one ncu capture of a one-view run (command and figures under profiles/), with the hashes
@@ -813,7 +868,8 @@ def kernel_work(vbs, sres, pairs, n_super, touched):
     the projection backward writes 236 B of gradients per Gaussian (written, not
     accumulated), reads 36 B of image-space gradients per item, and reads the 236 B of
     parameters and the 16 B colour rows only for the `touched` Gaussians some view gives a
-    gradient (most of a dense scene is hidden behind saturated pixels); the blend kernels count FP32 operations per evaluated pair."""
+    gradient (most of a dense scene is hidden behind saturated pixels); for the blend kernels
+    the work is the (pixel, Gaussian) pairs evaluated per launch."""
     vb = _PerLaunch(vbs)
     c = vb.launches
     M, K, Ks, P = vb.n_items, sres["n_instances"], n_super / c, vb.n_pixels
@@ -843,38 +899,57 @@ def kernel_work(vbs, sres, pairs, n_super, touched):
         "k_filter_scatter": vb.n_gaussians * (4 + 1) + vb.n_gaussians * 4,
     }
     out = {k: ("hbm", v) for k, v in hbm.items()}
-    for k, ops in OPS_PER_PAIR.items():
-        out[k] = ("alu", pairs * ops)
+    for k in FP32_OPS_PER_PAIR:
+        out[k] = ("alu", pairs)     # pairs evaluated per launch
     return out
 
 
-def kernel_frac(name, rec, work, hbm_peak):
-    bound, w = work[name]
+def kernel_frac(name, rec, work, hbm_peak, probes):
+    """Achieved rate of one kernel against its bound.  Byte-bound kernels: GB/s of their
+    algorithmic bytes against the measured HBM copy bandwidth, and against the probed L2
+    bandwidth; the bound is "l2" when the bytes of one launch fit in L2 (they are then
+    served from it), else "hbm".  Blend kernels: FP32 lane operations per second of the
+    method's count per pair against the probed FP32 peak, with the ex2 rate against MUFU."""
+    kind, w = work[name]
     t = rec["ms_per_launch"] / 1000.0
-    if bound == "hbm":
+    if kind == "hbm":
         a = w / t / 1e9
-        return {"bound": "hbm", "achieved_gbs": round(a, 1), "frac": round(a / hbm_peak, 4)}
-    a = w / t / 1e12
-    return {"bound": "alu", "achieved_tops": round(a, 2), "frac": round(a / (ALU_PEAK_OPS / 1e12), 4)}
+        l2 = probes["l2_tbs"] * 1e3
+        bound = "l2" if w <= L2_BYTES else "hbm"
+        out = {"bound": bound, "achieved_gbs": round(a, 1), "frac_hbm": round(a / hbm_peak, 4),
+               "frac_l2": round(a / l2, 4)}
+        out["frac"] = out["frac_l2"] if bound == "l2" else out["frac_hbm"]
+        return out
+    pairs = w
+    a = pairs * FP32_OPS_PER_PAIR[name] / t / 1e12
+    ex2 = pairs * EX2_PER_PAIR / t / 1e12
+    return {"bound": "alu", "achieved_tops": round(a, 2), "frac": round(a / probes["fp32_peak_tops"], 4),
+            "ex2_frac": round(ex2 / probes["ex2_tops"], 4),
+            "instr_tops": round(pairs * INSTR_OPS_PER_PAIR[name] / t / 1e12, 2),
+            "instr_frac": round(pairs * INSTR_OPS_PER_PAIR[name] / t / 1e12 / probes["fp32_peak_tops"], 4)}
 
 
-def roofline(kernel_ms, work, hbm, peak_kind, views):
+def roofline(kernel_ms, work, hbm, peak_kind, views, probes):
     """Roofline of the kernel with the largest share of the step (library launch events)."""
     name, rec = max(kernel_ms.items(), key=lambda kv: kv[1]["ms_per_step"])
     t = rec["ms_per_launch"] / 1000.0
-    bound, w = work.get(name, ("hbm", 0))
+    kind, w = work.get(name, ("hbm", 0))
     traffic = ncu_traffic(name, views)
-    if bound == "hbm":
+    if kind == "hbm":
         a = w / t / 1e9
         return {"kernel": name, "bound": "hbm", "achieved": round(a, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(a / hbm, 4), "traffic": traffic,
                 "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                 "work_per_launch": int(w), "ms_per_launch": round(rec["ms_per_launch"], 5)}
-    a = w / t / 1e12
-    peak = ALU_PEAK_OPS / 1e12
-    return {"kernel": name, "bound": "alu", "achieved": round(a, 2), "peak": round(peak, 2),
-            "unit": "TOP/s (FP32 lane ops)", "frac": round(a / peak, 4), "traffic": traffic,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2070 MHz", "work_per_launch": int(w),
+    f = kernel_frac(name, rec, work, hbm, probes)
+    ops = w * FP32_OPS_PER_PAIR[name]
+    return {"kernel": name, "bound": "alu", "achieved": f["achieved_tops"], "peak": probes["fp32_peak_tops"],
+            "unit": "TOP/s (FP32 lane ops)", "frac": f["frac"], "traffic": traffic,
+            "peak_source": "measured: rs_peak_probe FFMA / FFMA2 probe kernels on this GPU during this run "
+                           f"(SM clock {probes['clocks']['sm_mhz']} MHz)",
+            "work_per_launch": int(ops),
+            "work": f"{int(w)} (pixel, Gaussian) pairs x {FP32_OPS_PER_PAIR[name]} FP32 ops (+{EX2_PER_PAIR} ex2)",
+            "ex2_frac": f["ex2_frac"], "instr_frac": f["instr_frac"],
             "ms_per_launch": round(rec["ms_per_launch"], 5)}
 
 
@@ -952,9 +1027,19 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_probes():
+    import torch
+    from paper_2403_13806_gb300 import _native as N
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    print(json.dumps({"probes": probe_peaks(N, torch, dev)}))
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.probes:
+        run_probes()
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

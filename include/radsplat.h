@@ -293,8 +293,9 @@ rs_status rs_filter(const float* h, int64_t n, float t, rs_filter_mode mode, uin
  * library, RS_FILTER_NOALLOC_MAX_N / 4096 words (64 KB) that every GPU loading the library
  * holds until the process exits.  Nothing is allocated: no cudaMalloc, no cudaFree, no
  * allocating library call.  The caller still passes h, mask, idx and count.
- * The first call on a device looks up that array's device address (with the device
- * current) and caches it; make that first call before capturing a stream into a CUDA
+ * Every call looks up that array's device address on the current device (a lookup that
+ * allocates nothing and stays valid across a device reset); the first call on a device may
+ * load the library's device code there, so make it before capturing a stream into a CUDA
  * graph.  Every call shares the one array, and each call overwrites all of the scratch it
  * reads before reading it (the per-block counts), so nothing from an earlier call leaks
  * into a later one; but calls that overlap on the GPU (other streams, other threads) race
@@ -490,6 +491,31 @@ int32_t rs_autotune_candidates(int32_t n_views);
 
 /* Empties the autotuner's cache (host state, guarded by a mutex). */
 void rs_autotune_clear(void);
+
+/* ---- peak probes -------------------------------------------------------------------- */
+
+/* Kinds of rs_peak_probe. */
+typedef enum rs_probe_kind {
+  RS_PROBE_FFMA = 0,     /* FP32 fused multiply-add; work = FMA lane operations */
+  RS_PROBE_FFMA2 = 1,    /* packed two-lane FP32 FMA (__ffma2_rn); work = FP32 lane operations */
+  RS_PROBE_ALU = 2,      /* FP32 minimum / maximum (ALU pipe); work = lane operations */
+  RS_PROBE_EX2 = 3,      /* ex2.approx (MUFU); work = lane operations */
+  RS_PROBE_SMEM = 4,     /* conflict-free 16-byte shared-memory loads; work = bytes */
+  RS_PROBE_L2 = 5        /* 16-byte loads of a 24 MB buffer held in L2 (the first 24 MB of
+                            sink, read only); work = bytes */
+} rs_probe_kind;
+
+/* rs_peak_probe -- measures a peak the library's rooflines divide by (the paper has no
+ * counterpart).  Launches one kernel of independent operations of the given kind on every
+ * SM (8 CTAs of 256 threads per SM, `iters` iterations of 8 independent chains per thread,
+ * or of passes over the L2 buffer) on `stream` and writes to *work (HOST) how many
+ * operations (bytes for RS_PROBE_SMEM and RS_PROBE_L2) it performs; the caller times the
+ * launch (CUDA events) and divides.  sink: device float
+ * [sink_floats >= rs_peak_probe_sink_floats()], overwritten with meaningless values.
+ * Errors: RS_ERR_INVALID_ARG, RS_ERR_CUDA. */
+rs_status rs_peak_probe(int32_t kind, int32_t iters, float* sink, int64_t sink_floats, double* work,
+                        void* stream);
+int64_t rs_peak_probe_sink_floats(void);
 
 /* ---- tracing ------------------------------------------------------------------------ */
 

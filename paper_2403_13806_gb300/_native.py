@@ -17,6 +17,7 @@ RS_OK, RS_ERR_INVALID_ARG, RS_ERR_WORKSPACE, RS_ERR_UNSUPPORTED, RS_ERR_CUDA, RS
 RS_PRUNE_BELOW, RS_KEEP_ABOVE, RS_PRUNE_KEEP = 0, 1, 2
 RS_FILTER_NOALLOC_MAX_N = 1 << 26
 RS_STAGE_PROJECT, RS_STAGE_BIN_SORT, RS_STAGE_RENDER, RS_STAGE_BACKWARD, RS_STAGE_FILTER = range(5)
+RS_PROBE_FFMA, RS_PROBE_FFMA2, RS_PROBE_ALU, RS_PROBE_EX2, RS_PROBE_SMEM, RS_PROBE_L2 = range(6)
 
 
 class RsGaussians(ctypes.Structure):
@@ -118,6 +119,8 @@ SIGNATURES = {
     "rs_gather_columns": (ctypes.c_int, [P, c_int32, P, P, c_int64, P]),
     "rs_autotune_candidates": (c_int32, [c_int32]),
     "rs_autotune_clear": (None, []),
+    "rs_peak_probe": (ctypes.c_int, [c_int32, c_int32, P, c_int64, P, P]),
+    "rs_peak_probe_sink_floats": (c_int64, []),
     "rs_profile_enable": (ctypes.c_int, [c_int32]),
     "rs_profile_count": (c_int32, []),
     "rs_profile_read": (ctypes.c_int, [c_int32, P, P]),

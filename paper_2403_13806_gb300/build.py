@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "libradsplat.so")
-SOURCES = ["api.cu", "project.cu", "binsort.cu", "render.cu", "render_bwd.cu", "filter.cu", "loss.cu", "profile.cu", "autotune.cu", "optim.cu", "ssim.cu", "cluster.cu", "knn.cu"]
+SOURCES = ["api.cu", "project.cu", "binsort.cu", "render.cu", "render_bwd.cu", "filter.cu", "loss.cu", "profile.cu", "autotune.cu", "optim.cu", "ssim.cu", "cluster.cu", "knn.cu", "probes.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + INCLUDE, "-I" + CSRC]

@@ -6,7 +6,6 @@
 // byte mask), one exclusive scan of the block counts, and an order-preserving scatter of
 // the indices (block-local scan with warp ballots).  The block counts are the only
 // scratch memory (4 bytes per 4096 elements).
-#include <mutex>
 
 #include "profile.cuh"
 #include "radsplat.h"
@@ -158,8 +157,10 @@ rs_status filter_launch(const float* h, int64_t n, float t, int mode, uint8_t* m
   k_filter_count<<<(unsigned)nblk, kFiltThreads, 0, s>>>(h, n, t, mode, mask, bcount); }
   { prof::Scope ps("k_filter_scan", s);
   k_filter_scan<<<1, 1024, 0, s>>>(bcount, nblk, count); }
-  prof::Scope ps("k_filter_scatter", s);
-  if (idx) k_filter_scatter<<<(unsigned)nblk, kFiltThreads, 0, s>>>(h, n, t, mode, bcount, idx);
+  if (idx) {
+    prof::Scope ps("k_filter_scatter", s);
+    k_filter_scatter<<<(unsigned)nblk, kFiltThreads, 0, s>>>(h, n, t, mode, bcount, idx);
+  }
   return launch_status();
 }
 
@@ -195,22 +196,13 @@ namespace rs {
 constexpr int64_t kNoallocMaxBlocks = (RS_FILTER_NOALLOC_MAX_N + kFiltTile - 1) / kFiltTile;   // 16384 words
 static __device__ __align__(256) uint32_t g_filter_scratch[kNoallocMaxBlocks];
 
-constexpr int kNoallocMaxDevices = 64;
-static std::mutex g_noalloc_mu;
-static uint32_t* g_noalloc_ptr[kNoallocMaxDevices] = {};
-
-// Device address of g_filter_scratch on the current device, looked up once per device.
-// (In host code the array's name is only a host-side stand-in, never a device address.)
+// Device address of g_filter_scratch on the current device.  (In host code the array's name
+// is only a host-side stand-in, never a device address.)  Looked up on every call: the
+// lookup allocates nothing and stays right after a device reset reloads the module.
 static rs_status noalloc_scratch(uint32_t** out) {
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return RS_ERR_CUDA;
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_filter_scratch) != cudaSuccess || !p) return RS_ERR_CUDA;
-    g_noalloc_ptr[dev] = static_cast<uint32_t*>(p);
-  }
-  *out = g_noalloc_ptr[dev];
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_filter_scratch) != cudaSuccess || !p) return RS_ERR_CUDA;
+  *out = static_cast<uint32_t*>(p);
   return RS_OK;
 }
 
