@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--smem-batch", type=int, default=0,
                     help="with a fixed --tile: Gaussian records staged per blend batch (rs_config.batch, 0: default)")
-    ap.add_argument("--uneven-views", type=int, default=32,
+    ap.add_argument("--no-legs", action="store_true", help="skip the filtered-rendering and importance legs")
+    ap.add_argument("--uneven-views", type=int, default=256,
                     help="views of the uneven-batch leg (house-scale 3M scene, random resolutions, per-view "
                          "visibility lists); 0 skips it")
     ap.add_argument("--step-only", action="store_true",
@@ -58,6 +59,8 @@ def parse():
                                                    "(autotuner: tile shape, staging batch, views per launch)")
     ap.add_argument("--sample-pixels", type=int, default=0, help="reference arm: pixels per step (0: auto)")
     ap.add_argument("--probes", action="store_true", help="only run the peak probe kernels and print their rates")
+    ap.add_argument("--cpu-report", action="store_true",
+                    help="only time the FP64 C oracle on the host cores (config 0 full image, config 2 full view)")
     return ap.parse_args()
 
 
@@ -264,11 +267,13 @@ def run_ours(args):
         step_body()
     torch.cuda.synchronize()
 
+    exchange = rd.SparseGradExchange(gbuf, scene.n)
+
     def run_step():
         graph.replay()
         if world > 1:
             rd.allreduce_importance(h)
-            rd.allreduce_grads(gbuf)
+            exchange.allreduce()
             prune()
 
     def barrier():
@@ -326,12 +331,33 @@ def run_ours(args):
                                                    loss_fn=loss_fn)
     pairs, n_super, touched = work_counts["pairs"], work_counts["super_instances"], work_counts["touched"]
 
-    # plain: the same views one at a time, no graph
+    # plain: the same views one at a time, no graph, the library's default configuration;
+    # then the gain split: the autotuned configuration one view at a time, the autotuned
+    # views per launch without the graph, and the graph (the value)
     plain = None
     fps = None
+    gain = None
     if not args.no_plain:
-        plain, fps = plain_loop(api, N, torch, g, vb1, cfg, torch.cat(targets), cams, reps=max(3, min(args.steps, 10)),
-                                dev=dev, loss_fn=loss_fn)
+        rp = max(3, min(args.steps, 10))
+        plain, fps = plain_loop(api, N, torch, g, vb1, api.config(), torch.cat(targets), cams, reps=rp, dev=dev,
+                                loss_fn=loss_fn)
+        vb1t = [api.ViewBatch([c], scene.n, tile=tile, device=dev) for c in cams]
+        plain_t, _ = plain_loop(api, N, torch, g, vb1t, cfg, torch.cat(targets), cams, reps=rp, dev=dev,
+                                loss_fn=loss_fn)
+        step_body()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(rp):
+            step_body()
+        e1.record()
+        torch.cuda.synchronize()
+        nograph = e0.elapsed_time(e1) / (rp * V)
+        gain = {"plain_default_ms_per_view": round(plain, 5), "plain_autotuned_ms_per_view": round(plain_t, 5),
+                "batched_no_graph_ms_per_view": round(nograph, 5), "batched_graph_ms_per_view": round(value, 5),
+                "note": "every variant does the same work per step: project, bin/sort, blend with importance, loss "
+                        "and backward per view, one prune filter per step"}
 
     # end to end through the public API: host parameters and targets in pinned memory
     e2e = e2e_run(api, N, torch, scene, vbs, cfg, targets, cap, reps=max(3, min(args.steps, 5)), dev=dev, world=world,
@@ -340,7 +366,9 @@ def run_ours(args):
     # roofline of the dominant kernel
     hbm, peak_kind, pk = peaks()
     optim = optimizer_bench(api, N, torch, g, gbuf, h, hbm, reps=10)
-    uneven = uneven_bench(api, N, torch, dev, args.uneven_views, reps=3) if args.uneven_views > 0 else None
+    uneven = uneven_bench(api, N, torch, dev, args.uneven_views, reps=2) if args.uneven_views > 0 else None
+    filtered = filtered_bench(api, N, torch, dev, reps=5) if not args.no_legs else None
+    imp_leg = importance_bench(api, N, torch, dev, reps=5) if not args.no_legs else None
     work = kernel_work(vbs, sres, pairs, n_super, touched)
     probes = probe_peaks(N, torch, dev)
     roof = roofline(kernel_ms, work, hbm, peak_kind, B, probes)
@@ -356,10 +384,13 @@ def run_ours(args):
             "data": "synthetic (seeded 360-capture scene; target = render of a perturbed copy)",
             "config": dict(workload_config(V, world, tile, B, args.loss),
                            parallelism=(f"views sharded over {world} GPUs; all-reduce MAX of importance and SUM "
-                                        f"of gradients per step" if world > 1 else "1 GPU, no collective")),
+                                        f"of the gradient columns some rank touched per step" if world > 1
+                                        else "1 GPU, no collective")),
+            "gradient_exchange": exchange.last if world > 1 else None,
             "batched_ms_per_view": round(value, 5),
             "plain_ms_per_view": round(plain, 5) if plain else None,
             "batched_over_plain_speedup": round(plain / value, 3) if plain else None,
+            "gain_split": gain,
             "fps_forward_single_view": round(fps, 1) if fps else None,
             "instances_per_view": int(sres["n_instances"] / B),
             "gaussians_with_gradient": touched,
@@ -376,7 +407,8 @@ def run_ours(args):
             "kernel_ms_per_step": {k: round(v["ms_per_step"], 5) for k, v in
                                    sorted(kernel_ms.items(), key=lambda kv: -kv[1]["ms_per_step"])},
             "e2e": e2e, "roofline": roof, "roofline_per_kernel": per_kernel, "probes": probes, "optimizer": optim,
-            "uneven_batch": uneven, "cpu_baseline": cpu,
+            "uneven_batch": uneven, "visibility_filtered_64_views": filtered, "importance_32_views": imp_leg,
+            "cpu_baseline": cpu,
             "clocks": clk.summary(),
             "gpu_launches": launches,
         }
@@ -452,32 +484,34 @@ def stage_times(api, N, torch, g, chunks, cfg, st, proj, h, gbuf, loss, ws_sort,
 
 
 def uneven_bench(api, N, torch, dev, n_views, reps):
-    """Uneven batch: views of random resolution (320-1920 x 240-1080) of the 3M-Gaussian
-    house-scale scene, each with its own ascending visibility list of 0.2M-2M Gaussians
-    (the first n_views of the 256-view set).  fwd+bwd ms/view (L1 loss per view, gradients
-    summed over views) with the autotuner's tile shape, staging batch and views per launch,
-    against a loop of plain single-view launches.  Includes every stage of the step but
-    the pruning filter."""
+    """Uneven batch (config 4): views of random resolution (320-1920 x 240-1080) of the
+    3M-Gaussian house-scale scene, each with its own ascending visibility list of 0.2M-2M
+    Gaussians (the first n_views of the 256-view set).  fwd+bwd ms/view (L1 loss per view,
+    gradients summed over views) with the autotuner's tile shape, staging batch and views per
+    launch, processed in chunks of that many views, against a loop of plain single-view
+    launches.  Each side reuses one Rasterizer (instance capacity grown to the largest
+    chunk), so device memory stays bounded by one chunk.  Includes every stage of the step
+    but the pruning filter."""
     from paper_2403_13806_gb300 import synth
     scene, _, _ = synth.config3()
     cams, subsets = synth.config4(scene, n_views=n_views)   # the first n_views of the 256-view set
     g = api.Gaussians.from_scene(scene, device=dev)
     grads = [torch.zeros_like(t) for t in g.tensors()]
-    tune = api.autotune(g, cams, subsets=subsets, backward=True)
+    tune = api.autotune(g, cams[:32], subsets=subsets[:32], backward=True)
     B = tune["views_per_launch"]
     cfg = api.config(batch=tune["smem_batch"])
 
     def make(chunks, tile, cfg_):
-        out = []
-        for i in range(0, len(cams), chunks):
-            vb = api.ViewBatch(cams[i:i + chunks], scene.n, subsets=subsets[i:i + chunks], tile=tile, device=dev)
-            r = api.Rasterizer(cfg=cfg_, device=dev)
-            r.forward(g, vb)   # sizes the capacity
-            out.append((vb, r))
-        return out
+        r = api.Rasterizer(cfg=cfg_, device=dev)
+        vbs = [api.ViewBatch(cams[i:i + chunks], scene.n, subsets=subsets[i:i + chunks], tile=tile, device=dev)
+               for i in range(0, len(cams), chunks)]
+        for vb in vbs:
+            r.forward(g, vb)   # grows the capacity to the largest chunk
+        return r, vbs
 
     def run(plan):
-        for vb, r in plan:
+        r, vbs = plan
+        for vb in vbs:
             o = r.forward(g, vb)
             loss, dl = api.l1_loss(o["image"], torch.zeros_like(o["image"]))
             api.render_backward(g, vb, o["proj"], o["bins"], o["T_final"], o["last"], dl, grads, r.ws_bwd, r.cfg)
@@ -493,14 +527,140 @@ def uneven_bench(api, N, torch, dev, n_views, reps):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / (reps * len(cams))
 
-    batched = timed(make(B, tune["tile"], cfg))
-    plain = timed(make(1, (16, 16), api.config()))
+    plan = make(B, tune["tile"], cfg)
+    batched = timed(plan)
+    del plan
+    plan = make(1, (16, 16), api.config())
+    plain = timed(plan)
+    del plan
+    torch.cuda.empty_cache()
     return {"views": len(cams), "pixels": int(sum(c["width"] * c["height"] for c in cams)),
             "items": int(sum(len(s) for s in subsets)), "tile": f"{tune['tile'][0]}x{tune['tile'][1]}",
             "smem_batch": tune["smem_batch"], "views_per_launch": B,
             "batched_ms_per_view": round(batched, 4), "plain_ms_per_view": round(plain, 4),
             "batched_over_plain_speedup": round(plain / batched, 3),
-            "note": "Rasterizer calls (one host read of the instance count per launch) on both sides"}
+            "note": "autotuned on the first 32 views; Rasterizer calls (one host read of the instance count per "
+                    "launch) on both sides"}
+
+
+def _graph_of(torch, body):
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        body()
+        body()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    gr = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gr):
+        body()
+    torch.cuda.synchronize()
+    return gr
+
+
+def _replay_ms(torch, gr, reps):
+    gr.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        gr.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _forward_plan(api, torch, g, vb, cfg, dev, importance=None, image=True):
+    """Buffers and a body for one forward (project -> bin_sort -> render) of a batch with the
+    instance capacity sized by a first render."""
+    r = api.Rasterizer(cfg=cfg, device=dev)
+    r.forward(g, vb)
+    cap = int(r.status.read()["required"] * 1.02) + 4096
+    st = api.DeviceStatus(dev)
+    proj = api.Projected.empty(vb.n_items, dev)
+    bins = api.Bins.empty(cap, vb.n_tiles, device=dev)
+    ws = api.Workspace(dev)
+    img = torch.empty(3 * vb.n_pixels, device=dev) if image else False
+    T = torch.empty(vb.n_pixels, device=dev) if image else False
+    L = torch.empty(vb.n_pixels, dtype=torch.int32, device=dev) if image else False
+    del r
+
+    def body():
+        api.project(g, vb, cfg, st, out=proj)
+        api.bin_sort(proj, vb, bins, ws, st)
+        api.render(proj, bins, vb, cfg, image=img, T_final=T, last=L, importance=importance)
+
+    return body, st, cap
+
+
+def filtered_bench(api, N, torch, dev, reps):
+    """Visibility-filtered rendering (config 3, Sec. 3.4): the 3M-Gaussian house-scale scene,
+    64 views of 960x544 at 8 camera clusters.  Setup (untimed): per cluster, the importance of
+    Eq. importance-score-vis over the cluster's views and its list h > 0.005.  Timed: the
+    forward of all 64 views in one launch per stage, replayed as a CUDA graph, once with every
+    view on its cluster's list and once on all 3M Gaussians; FPS = views / time."""
+    from paper_2403_13806_gb300 import synth
+    scene, cams, site = synth.config3()
+    g = api.Gaussians.from_scene(scene, device=dev)
+    cfg = api.config()
+    lists = {}
+    rast = api.Rasterizer(device=dev)
+    for s in range(int(site.max()) + 1):
+        vb = api.ViewBatch([c for c, k in zip(cams, site) if k == s], scene.n, device=dev)
+        h = torch.zeros(scene.n, dtype=torch.int32, device=dev)
+        rast.forward(g, vb, importance=h, image=False)
+        m, idx, cnt = api.filter(h, 0.005, N.RS_KEEP_ABOVE)
+        lists[s] = idx[:int(cnt.item())].clone()
+    del rast
+    out = {"views": len(cams), "width": 960, "height": 544, "gaussians": scene.n, "t_cluster": 0.005,
+           "mean_list_fraction": round(float(np.mean([lists[int(k)].numel() for k in site])) / scene.n, 4)}
+    for name, subsets in (("filtered", [lists[int(k)] for k in site]), ("unfiltered", None)):
+        vb = api.ViewBatch(cams, scene.n, subsets=subsets, device=dev)
+        body, st, cap = _forward_plan(api, torch, g, vb, cfg, dev)
+        gr = _graph_of(torch, body)
+        ms = _replay_ms(torch, gr, reps)
+        if st.read()["code"] != 0:
+            raise RuntimeError(f"device status {st.read()}")
+        out[name] = {"ms_per_batch": round(ms, 3), "fps": round(len(cams) / (ms / 1e3), 1),
+                     "items": int(vb.n_items), "instances": int(st.read()["n_instances"])}
+        del gr, body, vb
+        torch.cuda.empty_cache()
+    out["fps_gain"] = round(out["filtered"]["fps"] / out["unfiltered"]["fps"], 3)
+    return out
+
+
+def importance_bench(api, N, torch, dev, reps):
+    """Importance scoring (config 1, Sec. 3.3): 500k Gaussians, 32 views of 1280x832 in one
+    launch per stage (project -> bin_sort -> rs_importance, no image outputs), replayed as a
+    CUDA graph, then the prune filter h < 0.01 with its index list."""
+    from paper_2403_13806_gb300 import synth
+    scene, cams = synth.config1()
+    g = api.Gaussians.from_scene(scene, device=dev)
+    cfg = api.config()
+    vb = api.ViewBatch(cams, scene.n, device=dev)
+    h = torch.zeros(scene.n, dtype=torch.int32, device=dev)
+    body, st, cap = _forward_plan(api, torch, g, vb, cfg, dev, importance=h, image=False)
+
+    def imp():
+        h.zero_()
+        body()
+
+    gr = _graph_of(torch, imp)
+    ms = _replay_ms(torch, gr, reps)
+    ws = api.Workspace(dev)
+    mask = torch.empty(scene.n, dtype=torch.uint8, device=dev)
+    idx = torch.empty(scene.n, dtype=torch.int32, device=dev)
+    cnt_holder = {}
+
+    def filt():
+        cnt_holder["c"] = api.filter(h, 0.01, N.RS_PRUNE_BELOW, ws, mask=mask, idx=idx)[2]
+
+    grf = _graph_of(torch, filt)
+    ms_f = _replay_ms(torch, grf, max(reps, 10))
+    pruned = int(cnt_holder["c"].item())
+    return {"views": len(cams), "gaussians": scene.n, "ms_importance_32_views": round(ms, 3),
+            "ms_per_view": round(ms / len(cams), 4), "ms_filter": round(ms_f, 4),
+            "pruned_at_t_0.01": pruned, "kept": scene.n - pruned, "instances": int(st.read()["n_instances"])}
 
 
 def optimizer_bench(api, N, torch, g, gbuf, h, hbm, reps):
@@ -562,11 +722,13 @@ def optimizer_bench(api, N, torch, g, gbuf, h, hbm, reps):
 
 
 def plain_loop(api, N, torch, g, vb1, cfg, target, cams, reps, dev, loss_fn):
-    """The same views one at a time with plain launches (no graph): fwd+bwd ms/view, and
-    forward-only FPS of one view (project + bin/sort + blend)."""
+    """The same views one at a time with plain launches (no graph), the step's work per view
+    (project, bin/sort, blend with importance, loss, backward) and its one prune filter per
+    step: fwd+bwd ms/view, and forward-only FPS of one view (project + bin/sort + blend).
+    cfg and the views' tile shape are the caller's (defaults, or the autotuned ones)."""
     rasts = []
     for vb in vb1:
-        r = api.Rasterizer(device=dev)
+        r = api.Rasterizer(cfg=cfg, device=dev)
         r.forward(g, vb)
         cap = int(r.status.read()["required"] * 1.05) + 4096
         rasts.append((r, api.Bins.empty(cap, vb.n_tiles, device=dev)))
@@ -586,7 +748,8 @@ def plain_loop(api, N, torch, g, vb1, cfg, target, cams, reps, dev, loss_fn):
         img, T, L = api.render(proj, bins, vb, r.cfg, importance=h)
         l, dl = loss_fn(img, tg[i])
         api.render_backward(g, vb, proj, bins, T, L, dl, grads, r.ws_bwd, r.cfg)
-        api.filter(h, 0.01, N.RS_PRUNE_BELOW, ws_f)
+        if i == V - 1:
+            api.filter(h, 0.01, N.RS_PRUNE_BELOW, ws_f)
 
     for i in range(V):
         one(i)
@@ -1027,6 +1190,76 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_report(full_view: bool = True):
+    """The FP64 C oracle timed alone on the host cores (wall clock): config 0 forward in
+    brute mode over its full 128x128 image, single thread and all cores, best of 3; config 2
+    (1M Gaussians, one 1280x832 view) forward in bucketed mode over the full view on all cores
+    (once), and single-thread on 4096 seeded pixels (best of 3, scaled to the view); the FP64
+    autograd gradient on 512 seeded pixels (scaled to the view, labelled as autograd)."""
+    import oracle
+    import oracle.grad as og
+    import torch
+    from paper_2403_13806_gb300 import synth
+    oracle.build()
+    cores = os.cpu_count() or 1
+    torch.set_num_threads(cores)
+    rep = {"nproc": cores, "cpu_model": _cpu_model(), "how": "wall clock (time.perf_counter), best of 3 unless noted"}
+
+    def best(f, k=3):
+        return min(f() for _ in range(k))
+
+    def timed(f):
+        t = time.perf_counter()
+        f()
+        return time.perf_counter() - t
+
+    scene0, cams0 = synth.config0()
+    p0 = oracle.project(scene0, cams0[0])
+    rep["config0_forward_brute_full_image_s"] = {
+        "threads_1": round(best(lambda: timed(lambda: oracle.render(p0, mode="brute", threads=1))), 4),
+        f"threads_{cores}": round(best(lambda: timed(lambda: oracle.render(p0, mode="brute", threads=cores))), 4)}
+    scene, cams = synth.config2(n=N_GAUSSIANS, n_views=1)
+    cam = cams[0]
+    tproj = best(lambda: timed(lambda: oracle.project(scene, cam)))
+    p = oracle.project(scene, cam)
+    P = WIDTH * HEIGHT
+    rng = np.random.default_rng(7)
+    pix = np.stack([rng.integers(0, WIDTH, 4096), rng.integers(0, HEIGHT, 4096)], 1).astype(np.int32)
+    t1 = best(lambda: timed(lambda: oracle.render(p, pixels=pix, mode="bucketed", threads=1)))
+    c2 = {"projection_1M_s": round(tproj, 3), "threads_1_per_view_s_scaled_from_4096_pixels": round(tproj + t1 / 4096 * P, 1)}
+    if full_view:
+        tf = timed(lambda: oracle.render(p, mode="bucketed", threads=cores))
+        c2[f"threads_{cores}_full_view_s"] = round(tproj + tf, 1)
+    rep["config2_forward_bucketed"] = c2
+    pg = pix[:512]
+    w = rng.normal(size=(512, 3))
+    tg = timed(lambda: og.gradients(scene, cam, w, pixels=pg))
+    rep["config2_gradient_autograd"] = {"pixels": 512, "s": round(tg, 2),
+                                        "per_view_s_scaled": round(tg / 512 * P, 1),
+                                        "note": "FP64 PyTorch autograd restatement, one pixel at a time"}
+    fwd = c2.get(f"threads_{cores}_full_view_s")
+    if fwd is not None:
+        rep["fwd_plus_bwd_ms_per_view"] = round((fwd + tg / 512 * P) * 1000.0, 0)
+    return rep
+
+
 def run_probes():
     import torch
     from paper_2403_13806_gb300 import _native as N
@@ -1039,6 +1272,8 @@ def main():
     args = parse()
     if args.probes:
         run_probes()
+    elif args.cpu_report:
+        print(json.dumps({"cpu_report": cpu_report()}))
     elif args.impl == "reference":
         run_reference(args)
     else:

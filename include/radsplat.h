@@ -442,6 +442,26 @@ typedef struct rs_gather_desc {
 rs_status rs_gather_columns(const rs_gather_desc* descs, int32_t n_desc, const uint32_t* idx,
                             const uint32_t* count, int64_t max_count, void* stream);
 
+/* ---- view-sharded training over several GPUs ---------------------------------------- */
+
+/* rs_touched_columns -- for a gradient matrix src (device float [rows][n], e.g. every
+ * parameter gradient of n Gaussians stacked row by row), out[i] (device float [n]) = 1 if
+ * some row of column i is non-zero, else 0: the Gaussians this rank's views gave a gradient.
+ * Ranks that share views (the training loss of Sec. 3.2 is a sum over images) exchange only
+ * the union of these columns (max over ranks of out, then rs_filter RS_KEEP_ABOVE 0.5, then
+ * rs_gather_columns, a sum over ranks, and rs_scatter_columns), not all n.
+ * Errors: RS_ERR_INVALID_ARG, RS_ERR_CUDA. */
+rs_status rs_touched_columns(const float* src, int64_t rows, int64_t n, float* out, void* stream);
+
+/* rs_scatter_columns -- the inverse placement of rs_gather_columns: dst[r][idx[k]] =
+ * src[r][k] for k < min(*count, max_count) and every row r of each of the n_desc (1..16)
+ * descriptors, here read as src = the packed rows x src_stride array (src_stride >=
+ * max_count) and dst = the rows x dst_stride array it came from; columns not listed in idx
+ * are left as they are.  idx (ascending, distinct) and count (device) as rs_filter writes
+ * them.  descs: HOST array.  Errors: RS_ERR_INVALID_ARG, RS_ERR_CUDA. */
+rs_status rs_scatter_columns(const rs_gather_desc* descs, int32_t n_desc, const uint32_t* idx,
+                             const uint32_t* count, int64_t max_count, void* stream);
+
 /* ---- batched execution: autotuner --------------------------------------------------- */
 
 /* Choice of rs_autotune. */

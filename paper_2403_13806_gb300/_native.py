@@ -117,6 +117,8 @@ SIGNATURES = {
     "rs_ssim_loss": (ctypes.c_int, [P, P, c_int32, c_int32, c_int32, c_float, P, P, P, c_size_t, P]),
     "rs_ssim_workspace_size": (c_size_t, [c_int32, c_int32, c_int32]),
     "rs_gather_columns": (ctypes.c_int, [P, c_int32, P, P, c_int64, P]),
+    "rs_scatter_columns": (ctypes.c_int, [P, c_int32, P, P, c_int64, P]),
+    "rs_touched_columns": (ctypes.c_int, [P, c_int64, c_int64, P, P]),
     "rs_autotune_candidates": (c_int32, [c_int32]),
     "rs_autotune_clear": (None, []),
     "rs_peak_probe": (ctypes.c_int, [c_int32, c_int32, P, c_int64, P, P]),

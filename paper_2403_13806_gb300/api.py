@@ -18,7 +18,7 @@ from . import _native as N
 __all__ = ["Gaussians", "ViewBatch", "Projected", "Bins", "DeviceStatus", "Workspace", "config", "project",
            "bin_sort", "render", "importance", "filter", "nearest", "render_backward", "Rasterizer",
            "RadSplatFunction", "split_images", "importance_as_float", "autotune", "TILE_SHAPES", "blend_threads", "adam_step",
-           "gather_columns", "ssim_loss", "PAPER_LAMBDA", "kmeans", "nn_distance", "image_grads",
+           "gather_columns", "scatter_columns", "touched_columns", "ssim_loss", "PAPER_LAMBDA", "kmeans", "nn_distance", "image_grads",
            "init_log_scales", "StepGraph"]
 
 PAPER_LAMBDA = 0.2   # weight of the SSIM term in the loss of Sec. 3.2
@@ -435,6 +435,29 @@ def gather_columns(pairs: Sequence[tuple], idx: torch.Tensor, count: torch.Tenso
         rows = src.shape[0] if src.dim() == 2 else 1
         arr[i] = N.RsGatherDesc(src.data_ptr(), dst.data_ptr(), rows, src.shape[-1], dst.shape[-1])
     N.call("rs_gather_columns", arr, len(pairs), _ptr(idx), _ptr(count), int(max_count), _stream(stream))
+
+
+def scatter_columns(pairs: Sequence[tuple], idx: torch.Tensor, count: torch.Tensor, max_count: int, stream=None):
+    """rs_scatter_columns: for each (src [rows, >= max_count] packed, dst [rows, n]) float32
+    pair, dst[:, idx[k]] = src[:, k] for k < count (device)."""
+    arr = (N.RsGatherDesc * len(pairs))()
+    for i, (src, dst) in enumerate(pairs):
+        if src.dtype != torch.float32 or dst.dtype != torch.float32 or not src.is_contiguous() \
+                or not dst.is_contiguous():
+            raise ValueError("scatter arrays must be contiguous float32 tensors")
+        rows = dst.shape[0] if dst.dim() == 2 else 1
+        arr[i] = N.RsGatherDesc(src.data_ptr(), dst.data_ptr(), rows, src.shape[-1], dst.shape[-1])
+    N.call("rs_scatter_columns", arr, len(pairs), _ptr(idx), _ptr(count), int(max_count), _stream(stream))
+
+
+def touched_columns(src: torch.Tensor, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """rs_touched_columns: float32 [n], 1 where a column of src [rows, n] has a non-zero entry."""
+    if src.dtype != torch.float32 or not src.is_contiguous() or src.dim() != 2:
+        raise ValueError("src must be a contiguous float32 [rows, n] tensor")
+    rows, n = src.shape
+    out = torch.empty(n, dtype=torch.float32, device=src.device) if out is None else out
+    N.call("rs_touched_columns", _ptr(src), rows, n, _ptr(out), _stream(stream))
+    return out
 
 
 class StepGraph:

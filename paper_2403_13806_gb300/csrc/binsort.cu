@@ -42,6 +42,7 @@ constexpr int kSegLen = 3840;       // super-list entries per fine work item (se
 constexpr int kTileBlock = 256;     // tiles per CTA of the per-tile scans
 constexpr int kCountChunk = 256;    // emission blocks per CTA of the block-count scan
 constexpr int kNF = kSuper * kSuper;
+constexpr int kCounterWords = 32;   // the device counters block (see BinWs::counters)
 
 struct BinWs {
   uint32_t* dkeys[2];
@@ -64,7 +65,9 @@ struct BinWs {
   uint32_t* counters;         // [0] super instances written, [2] instances written,
                               // [4], [5] work counters of the fine count and scatter,
                               // [6] item count (the depth sort's device count), [7] segments,
-                              // [8..11] the super-tile sort's digits (shift, bits) per pass
+                              // [8..15] the super-tile sort's digits (shift, bits) of up to
+                              // four passes, [16] items the depth sort kept (those with
+                              // instances); kCounterWords words in all
   size_t bytes;
 };
 
@@ -97,7 +100,7 @@ static BinWs bin_ws_layout(void* base, int64_t n_items, int64_t capacity, int n_
   w.seg_off = reinterpret_cast<uint32_t*>(take((size_t)((n_tiles > 0 ? n_tiles : 1) + 1) * 4));
   w.work_s = reinterpret_cast<uint32_t*>(take((size_t)w.n_work_max * 4));
   w.seg_cnt = reinterpret_cast<uint32_t*>(take((size_t)w.n_work_max * kNF * 4));
-  w.counters = reinterpret_cast<uint32_t*>(take(64));
+  w.counters = reinterpret_cast<uint32_t*>(take(kCounterWords * 4));
   w.bytes = off;
   return w;
 }
@@ -106,14 +109,15 @@ __device__ __forceinline__ int super_w(const rs_view& v) { return (v.tiles_x + k
 __device__ __forceinline__ int super_h(const rs_view& v) { return (v.tiles_y + kSuper - 1) / kSuper; }
 
 // Depth sort keys: the FP32 depth bits with the sign bit cleared.  Every item that emits
-// instances has depth > near_plane > 0, whose bits order like the value and are unchanged;
-// culled items (any depth, possibly negative or NaN) emit nothing, so their place in the
-// order is irrelevant, and no key can equal the sort's all-ones padding sentinel.
-__global__ void k_depth_keys(const float4* __restrict__ rgb_d, int64_t n, uint32_t* __restrict__ keys,
-                             uint32_t* __restrict__ vals) {
+// instances has depth > near_plane > 0, whose bits order like the value and are unchanged,
+// and no such key equals the sort's all-ones sentinel.  Items that emit nothing (culled, or
+// off the image: n_tiles = 0) get the sentinel, which the first sort pass drops, so the
+// later passes and the emission order only the items that have instances.
+__global__ void k_depth_keys(const float4* __restrict__ rgb_d, const uint32_t* __restrict__ n_tiles, int64_t n,
+                             uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  keys[i] = __float_as_uint(rgb_d[i].w) & 0x7fffffffu;
+  keys[i] = n_tiles[i] ? (__float_as_uint(rgb_d[i].w) & 0x7fffffffu) : 0xffffffffu;
   vals[i] = (uint32_t)i;
 }
 
@@ -177,11 +181,13 @@ __device__ __forceinline__ uint32_t cover_mask(uint32_t c) {
 
 // Super instances per block of kEmitThreads depth-sorted items, also added into the total
 // of the block's chunk of kCountChunk blocks (csum, zeroed by the caller).
-__global__ void __launch_bounds__(kEmitThreads) k_count_blocks(const uint32_t* __restrict__ order, int64_t n,
+__global__ void __launch_bounds__(kEmitThreads) k_count_blocks(const uint32_t* __restrict__ order,
+                                                               const uint32_t* __restrict__ n_dev,
                                                                const ushort4* __restrict__ rect,
                                                                unsigned long long* __restrict__ bsum,
                                                                unsigned long long* __restrict__ csum) {
   __shared__ unsigned long long s[kEmitThreads / 32];
+  const int64_t n = *n_dev;   // the items the depth sort kept (those with instances)
   const int64_t i = (int64_t)blockIdx.x * kEmitThreads + threadIdx.x;
   unsigned long long c = 0;
   if (i < n) {
@@ -258,7 +264,8 @@ __global__ void __launch_bounds__(kCountChunk) k_count_top(unsigned long long* _
 // and its cover byte from the four edge offsets of its rect (inner super-tiles are covered
 // whole).
 template <typename KeyT>
-__global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restrict__ order, int64_t n,
+__global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restrict__ order,
+                                                       const uint32_t* __restrict__ n_dev,
                                                        const ushort4* __restrict__ rect,
                                                        const rs_view* __restrict__ views, int n_views,
                                                        const uint32_t* __restrict__ super_base,
@@ -267,6 +274,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
                                                        uint8_t* __restrict__ saux) {
   __shared__ uint32_t s_wtot[kEmitThreads / 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t n = *n_dev;   // the items the depth sort kept (those with instances)
   const int64_t i = (int64_t)blockIdx.x * kEmitThreads + threadIdx.x;
   uint32_t item = 0, cnt = 0, sbase = 0;
   uint32_t org = 0;    // super rect origin: x | y << 16
@@ -774,13 +782,13 @@ size_t bin_sort_ws_bytes(const rs_view_batch* b, int64_t capacity) {
 // Super instances: expansion, stable sort on the super-tile id (KeyT-wide), ranges.
 // Returns which buffer set (0 or 1) holds the sorted items and cover bytes.
 template <typename KeyT>
-static int super_instances(const BinWs& w, const uint32_t* order, int64_t n, const rs_projected* proj,
+static int super_instances(const BinWs& w, const uint32_t* order, const uint32_t* n_kept, const rs_projected* proj,
                            const rs_view_batch* batch, int64_t cap, int64_t nblk, int n_super_max, cudaStream_t s) {
   KeyT* k0 = reinterpret_cast<KeyT*>(w.skeys[0]);
   KeyT* k1 = reinterpret_cast<KeyT*>(w.skeys[1]);
   {
     prof::Scope ps("k_emit", s);
-    k_emit<KeyT><<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n, reinterpret_cast<const ushort4*>(proj->rect),
+    k_emit<KeyT><<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n_kept, reinterpret_cast<const ushort4*>(proj->rect),
                                                          batch->views, batch->n_views, w.super_base, w.bsum, cap, k0,
                                                          w.svals[0], w.saux[0]);
   }
@@ -817,7 +825,7 @@ extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* 
   // super-tiles never outnumber tiles: a bound for the super-tile key width and ranges
   const int n_super_max = batch->n_tiles;
 
-  if (cudaMemsetAsync(w.counters, 0, 64, s) != cudaSuccess) return RS_ERR_CUDA;
+  if (cudaMemsetAsync(w.counters, 0, kCounterWords * 4, s) != cudaSuccess) return RS_ERR_CUDA;
   if (cudaMemsetAsync(w.sranges, 0, (size_t)n_super_max * 8, s) != cudaSuccess) return RS_ERR_CUDA;
   {
     prof::Scope ps("k_super_layout", s);
@@ -829,11 +837,14 @@ extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* 
     // 1) items by depth (four 8-bit passes; an even count leaves the result in buffer 0)
     {
       prof::Scope ps("k_depth_keys", s);
-      k_depth_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rgb_d, n, w.dkeys[0], w.dvals[0]);
+      k_depth_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rgb_d, proj->n_tiles, n, w.dkeys[0], w.dvals[0]);
     }
+    // the first pass drops the items without instances; counters[16] = the items kept
+    uint32_t* n_kept = w.counters + 16;
     const int dcur = tiles::sort_pairs<uint32_t>(w.dkeys[0], w.dvals[0], w.dkeys[1], w.dvals[1], w.counters + 6, n, 31,
                                                  w.hist, s, false,
-                                                 {"k_depth_sort_hist", "k_depth_sort_scan", "k_depth_sort"});
+                                                 {"k_depth_sort_hist", "k_depth_sort_scan", "k_depth_sort"}, nullptr,
+                                                 nullptr, nullptr, n_kept);
     const uint32_t* order = w.dvals[dcur];
     // 2) super instances in depth order, sorted stably on the super-tile id
     const int64_t nblk = (n + kEmitThreads - 1) / kEmitThreads;
@@ -841,15 +852,15 @@ extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* 
       return RS_ERR_CUDA;
     {
       prof::Scope ps("k_count_blocks", s);
-      k_count_blocks<<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n, rect, w.bsum, w.csum);
+      k_count_blocks<<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n_kept, rect, w.bsum, w.csum);
     }
     {
       prof::Scope ps("k_count_top", s);
       k_count_top<<<(unsigned)((nblk + kCountChunk - 1) / kCountChunk), kCountChunk, 0, s>>>(w.bsum, w.csum, nblk, cap,
                                                                                           w.counters, status);
     }
-    scur = (n_super_max <= 65536) ? super_instances<uint16_t>(w, order, n, proj, batch, cap, nblk, n_super_max, s)
-                                  : super_instances<uint32_t>(w, order, n, proj, batch, cap, nblk, n_super_max, s);
+    scur = (n_super_max <= 65536) ? super_instances<uint16_t>(w, order, n_kept, proj, batch, cap, nblk, n_super_max, s)
+                                  : super_instances<uint32_t>(w, order, n_kept, proj, batch, cap, nblk, n_super_max, s);
   }
   const uint32_t* svals = w.svals[scur];
   const uint8_t* saux = w.saux[scur];

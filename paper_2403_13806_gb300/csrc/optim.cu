@@ -146,6 +146,39 @@ __global__ void __launch_bounds__(256) k_gather_columns(GatherArgs a, const uint
   }
 }
 
+// The inverse placement: dst column idx[k] of every row receives src column k.
+__global__ void __launch_bounds__(256) k_scatter_columns(GatherArgs a, const uint32_t* __restrict__ idx,
+                                                         const uint32_t* __restrict__ count, int64_t max_count) {
+  const int64_t cnt = min((int64_t)*count, max_count);
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx[k];
+    for (int d = 0; d < a.n_desc; ++d) {
+      const float* s = a.src[d] + k;
+      float* o = a.dst[d] + i;
+      const int64_t rows = a.rows[d], ss = a.src_stride[d], ds = a.dst_stride[d];
+      int64_t r = 0;
+      for (; r + 8 <= rows; r += 8) {
+        float t[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) t[j] = __ldg(s + (r + j) * ss);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) o[(r + j) * ds] = t[j];
+      }
+      for (; r < rows; ++r) o[r * ds] = __ldg(s + r * ss);
+    }
+  }
+}
+
+// out[i] = 1 where some row of column i is non-zero (the Gaussians a gradient reaches).
+__global__ void __launch_bounds__(256) k_touched_columns(const float* __restrict__ src, int64_t rows, int64_t n,
+                                                         float* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    bool any = false;
+    for (int64_t r = 0; r < rows && !any; ++r) any = __ldcs(src + r * n + i) != 0.f;
+    out[i] = any ? 1.f : 0.f;
+  }
+}
+
 }  // namespace rs
 
 using namespace rs;
@@ -215,5 +248,39 @@ extern "C" rs_status rs_gather_columns(const rs_gather_desc* descs, int32_t n_de
   const unsigned grid = (unsigned)(blocks < 8 * kNumSMs ? blocks : 8 * kNumSMs);
   prof::Scope ps("k_gather_columns", s);
   k_gather_columns<<<grid, 256, 0, s>>>(a, idx, count, max_count);
+  return launch_status();
+}
+
+extern "C" rs_status rs_scatter_columns(const rs_gather_desc* descs, int32_t n_desc, const uint32_t* idx,
+                                        const uint32_t* count, int64_t max_count, void* stream) {
+  if (!descs || n_desc < 1 || n_desc > kMaxGather || !idx || !count || max_count < 0) return RS_ERR_INVALID_ARG;
+  GatherArgs a{};
+  a.n_desc = n_desc;
+  for (int32_t d = 0; d < n_desc; ++d) {
+    const rs_gather_desc& g = descs[d];
+    if (!g.src || !g.dst || g.rows < 0 || g.src_stride < max_count || g.dst_stride < 0) return RS_ERR_INVALID_ARG;
+    a.src[d] = g.src;
+    a.dst[d] = g.dst;
+    a.rows[d] = g.rows;
+    a.src_stride[d] = g.src_stride;
+    a.dst_stride[d] = g.dst_stride;
+  }
+  if (max_count == 0) return RS_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t blocks = (max_count + 255) / 256;
+  const unsigned grid = (unsigned)(blocks < 8 * kNumSMs ? blocks : 8 * kNumSMs);
+  prof::Scope ps("k_scatter_columns", s);
+  k_scatter_columns<<<grid, 256, 0, s>>>(a, idx, count, max_count);
+  return launch_status();
+}
+
+extern "C" rs_status rs_touched_columns(const float* src, int64_t rows, int64_t n, float* out, void* stream) {
+  if ((!src && rows > 0 && n > 0) || !out || rows < 0 || n < 0) return RS_ERR_INVALID_ARG;
+  if (n == 0) return RS_OK;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t blocks = (n + 255) / 256;
+  const unsigned grid = (unsigned)(blocks < 8 * kNumSMs ? blocks : 8 * kNumSMs);
+  prof::Scope ps("k_touched_columns", s);
+  k_touched_columns<<<grid, 256, 0, s>>>(src, rows, n, out);
   return launch_status();
 }

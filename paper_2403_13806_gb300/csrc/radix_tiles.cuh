@@ -1,7 +1,8 @@
 // Stable LSD radix sort of (key, uint32 value) pairs -- the items by depth and the
 // super-tile instances by super-tile id: CTAs work on tiles of 2048 keys in every kernel,
 // with no waits between CTAs.  Keys are 16-bit when every key fits (fewer bytes per pass),
-// else 32-bit (all-ones is reserved as the padding sentinel).
+// else 32-bit (all-ones is reserved as the padding sentinel; a 32-bit key equal to it is
+// never counted nor written, so a caller can drop pairs by giving them that key).
 //
 // A pass over one digit (<= 8 bits) is three kernels:
 //   k_tile_hist  -- per tile: its digit histogram, stored digit-major cnt[d][tile];
@@ -92,11 +93,14 @@ __global__ void __launch_bounds__(kThreads) k_tile_hist(const KeyT* __restrict__
         const uint4 w = __ldcs(kv + i);
         const KeyT* k = reinterpret_cast<const KeyT*>(&w);
 #pragma unroll
-        for (int j = 0; j < kVec; ++j) atomicAdd(&s[warp][((uint32_t)k[j] >> shift) & mask], 1u);
+        for (int j = 0; j < kVec; ++j)
+          if ((uint32_t)k[j] != 0xffffffffu) atomicAdd(&s[warp][((uint32_t)k[j] >> shift) & mask], 1u);
       }
     } else {
-      for (int i = threadIdx.x; i < tn; i += kThreads)
-        atomicAdd(&s[warp][((uint32_t)keys[t0 + i] >> shift) & mask], 1u);
+      for (int i = threadIdx.x; i < tn; i += kThreads) {
+        const uint32_t kk = (uint32_t)keys[t0 + i];
+        if (kk != 0xffffffffu) atomicAdd(&s[warp][(kk >> shift) & mask], 1u);
+      }
     }
     __syncthreads();
     const int d = threadIdx.x;
@@ -171,7 +175,8 @@ __global__ void __launch_bounds__(kThreads, ITEMS <= 8 ? 4 : 3) k_tile_sort(cons
                                                            const uint32_t* __restrict__ n_dev, int shift, int rbits,
                                                            const int32_t* __restrict__ dig,
                                                            const uint32_t* __restrict__ cnt, int64_t n_tiles_max,
-                                                           const uint32_t* __restrict__ tot) {
+                                                           const uint32_t* __restrict__ tot,
+                                                           uint32_t* __restrict__ n_out) {
   constexpr int TILE = kThreads * ITEMS;
   static_assert(kWarps * kR * 2 == kThreads * 16, "one 16-byte store per thread clears the counters");
   __shared__ KeyT s_keys[TILE];
@@ -192,10 +197,12 @@ __global__ void __launch_bounds__(kThreads, ITEMS <= 8 ? 4 : 3) k_tile_sort(cons
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t n = *n_dev;
   const int64_t n_tiles = (n + TILE - 1) / TILE;
-  if ((int64_t)blockIdx.x >= n_tiles) return;   // uniform per CTA
-  // global position of the first key of digit d over all tiles (exclusive prefix of totals)
+  // global position of the first key of digit d over all tiles (exclusive prefix of totals);
+  // their sum is the number of keys that are not the padding sentinel, which CTA 0 reports
   const int d = threadIdx.x;
   const uint32_t dbase = block_excl_scan(d < R ? tot[d] : 0u, s_scan, &s_total);
+  if (n_out && blockIdx.x == 0 && threadIdx.x == 0) *n_out = s_total;
+  if ((int64_t)blockIdx.x >= n_tiles) return;   // uniform per CTA
   const unsigned lt_mask = (1u << lane) - 1u;
 
   // grid-stride over the tiles the device count needs (the grid is sized for the bound)
@@ -262,6 +269,7 @@ __global__ void __launch_bounds__(kThreads, ITEMS <= 8 ? 4 : 3) k_tile_sort(cons
       c += cw[w];
     }
     const uint32_t lstart = block_excl_scan(d < R ? c : 0u, s_scan, &s_total);   // (barriers inside)
+    const int tv = (int)s_total;   // the tile's keys that are not the sentinel (all of them but padding)
     if (d < R) {
       uint32_t run = lstart;
 #pragma unroll
@@ -283,7 +291,7 @@ __global__ void __launch_bounds__(kThreads, ITEMS <= 8 ? 4 : 3) k_tile_sort(cons
       }
     }
     __syncthreads();
-    for (int p = threadIdx.x; p < tn; p += kThreads) {
+    for (int p = threadIdx.x; p < tv; p += kThreads) {
       const KeyT key = s_keys[p];
       const int dd = (int)(((uint32_t)key >> shift) & mask);
       const uint32_t g = s_gpos[dd] + (uint32_t)p;
@@ -317,10 +325,13 @@ struct SortNames {
 // dev_digits (optional): a device array of (shift, bits) per pass that replaces the host's
 // digit plan when the kernels run (keys known on the device to need fewer bits); each pass's
 // device bits must not exceed the host plan's bits for that pass.
+// n_kept (optional): keys equal to the all-ones sentinel (32-bit keys) are dropped by the
+// first pass, which writes the count of the others here; the later passes sort that many.
 template <typename KeyT, int ITEMS = kItems>
 inline int sort_pairs(KeyT* k0, uint32_t* v0, KeyT* k1, uint32_t* v1, const uint32_t* n_dev, int64_t n_max, int bits,
                       uint32_t* scratch, cudaStream_t s, bool write_last_keys, const SortNames& names,
-                      uint8_t* aux0 = nullptr, uint8_t* aux1 = nullptr, const int32_t* dev_digits = nullptr) {
+                      uint8_t* aux0 = nullptr, uint8_t* aux1 = nullptr, const int32_t* dev_digits = nullptr,
+                      uint32_t* n_kept = nullptr) {
   constexpr int TILE = kThreads * ITEMS;
   const int passes = sort_passes(bits);
   const int rbits = (bits + passes - 1) / passes;
@@ -343,17 +354,19 @@ inline int sort_pairs(KeyT* k0, uint32_t* v0, KeyT* k1, uint32_t* v1, const uint
     uint8_t* ao = aux0 ? (cur ? aux0 : aux1) : nullptr;
     const bool last = (p == passes - 1);
     const int32_t* dig = dev_digits ? dev_digits + 2 * p : nullptr;
+    const uint32_t* np = (n_kept && p > 0) ? n_kept : n_dev;
     {
       prof::Scope ps(names.hist, s);
-      k_tile_hist<KeyT, TILE><<<grid_hist, kThreads, 0, s>>>(ki, n_dev, shift, rb, dig, nt, cnt);
+      k_tile_hist<KeyT, TILE><<<grid_hist, kThreads, 0, s>>>(ki, np, shift, rb, dig, nt, cnt);
     }
     {
       prof::Scope ps(names.scan, s);
-      k_tile_scan<TILE><<<1 << rb, 1024, 0, s>>>(cnt, n_dev, dig, nt, tot);
+      k_tile_scan<TILE><<<1 << rb, 1024, 0, s>>>(cnt, np, dig, nt, tot);
     }
     prof::Scope ps(names.sort, s);
     k_tile_sort<KeyT, ITEMS><<<grid_sort, kThreads, 0, s>>>(
-        ki, vi, ai, (last && !write_last_keys) ? nullptr : ko, vo, ao, n_dev, shift, rb, dig, cnt, nt, tot);
+        ki, vi, ai, (last && !write_last_keys) ? nullptr : ko, vo, ao, np, shift, rb, dig, cnt, nt, tot,
+        p == 0 ? n_kept : nullptr);
     cur ^= 1;
   }
   return cur;

@@ -22,6 +22,13 @@
 
 namespace rs {
 
+// max(a, b, c) in one instruction (the importance maximum over a pixel pair and the running value).
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
 struct RenderArgs {
   const float2* xy;
   const float4* conic_o;
@@ -133,7 +140,7 @@ __global__ void __launch_bounds__(TW* TH / PX) k_render(RenderArgs a) {
         cb[q] = __ffma2_rn(w, lo2(r.bc), cb[q]);
         last[2 * q] = ok0 ? base + j + 1 : last[2 * q];
         last[2 * q + 1] = ok1 ? base + j + 1 : last[2 * q + 1];
-        if (IMPORTANCE) m = fmaxf(m, fmaxf(w.x, w.y));
+        if (IMPORTANCE) m = max3f(m, w.x, w.y);
       }
       if (stop) {   // rare: retire the stopped pixels
 #pragma unroll

@@ -9,8 +9,14 @@ collective each per step:
 * the importance score (Eq. importance-score) is a max over all images: an all-reduce MAX of
   h, held as the int32 bits of non-negative float32 values (their integer order is the float
   order, so the max of the bits is the bits of the max);
-* the parameter gradient is a sum over images: an all-reduce SUM of one flat buffer that
-  holds all parameter gradients, so the exchange is a single call.
+* the parameter gradient is a sum over images.  In a deep scene only a small part of the
+  Gaussians get a gradient from a step's views (the rest lie behind saturated pixels), so
+  the sum is exchanged over the union of the columns (Gaussians) some rank touched: an
+  all-reduce MAX of a per-Gaussian touched flag (4 B per Gaussian), its ascending index
+  list, a gather of those columns of every gradient row into one packed buffer, an
+  all-reduce SUM of that buffer, and a scatter back.  Columns outside the union are zero on
+  every rank, so the result equals the dense sum element for element.  (The dense
+  all-reduce of one flat buffer of all gradients is kept as allreduce_grads.)
 
 Pruning (Sec. 3.3) then thresholds the reduced h identically on every rank.
 """
@@ -21,7 +27,7 @@ from typing import List, Sequence, Tuple
 import torch
 import torch.distributed as dist
 
-__all__ = ["shard", "GradBuffer", "allreduce_importance", "allreduce_grads"]
+__all__ = ["shard", "GradBuffer", "allreduce_importance", "allreduce_grads", "SparseGradExchange", "LibraryOps"]
 
 
 def shard(n_total: int, world: int, rank: int) -> Tuple[int, int]:
@@ -66,3 +72,59 @@ def allreduce_grads(grads: GradBuffer, group=None) -> GradBuffer:
     if dist.is_initialized() and dist.get_world_size(group) > 1:
         dist.all_reduce(grads.flat, op=dist.ReduceOp.SUM, group=group)
     return grads
+
+
+class LibraryOps:
+    """The device steps of SparseGradExchange, all in the library's kernels."""
+
+    def touched(self, mat: torch.Tensor) -> torch.Tensor:
+        from . import api
+        return api.touched_columns(mat)
+
+    def compact(self, flag: torch.Tensor):
+        from . import _native as N
+        from . import api
+        _, idx, cnt = api.filter(flag, 0.5, N.RS_KEEP_ABOVE, mask=False)
+        return idx, cnt
+
+    def gather(self, mat: torch.Tensor, idx: torch.Tensor, cnt: torch.Tensor, k: int) -> torch.Tensor:
+        from . import api
+        packed = torch.empty((mat.shape[0], max(k, 1)), dtype=mat.dtype, device=mat.device)
+        api.gather_columns([(mat, packed)], idx, cnt, k)
+        return packed
+
+    def scatter(self, packed: torch.Tensor, mat: torch.Tensor, idx: torch.Tensor, cnt: torch.Tensor, k: int):
+        from . import api
+        api.scatter_columns([(packed, mat)], idx, cnt, k)
+
+
+class SparseGradExchange:
+    """Sum over ranks of the parameter gradients, exchanging only the columns some rank has
+    a gradient for (see the module notes).  grads: the GradBuffer whose flat storage is the
+    [rows, n] matrix of every gradient row of n Gaussians (means 3, log-scales 3,
+    quaternions 4, opacity logit 1, SH (D+1)^2 * 3 rows).  One host read per step: the size
+    of the union, which the packed all-reduce needs."""
+
+    def __init__(self, grads: GradBuffer, n: int, ops=None):
+        if grads.flat.numel() % n:
+            raise ValueError("the gradient buffer is not a whole number of rows of n")
+        self.grads = grads
+        self.n = int(n)
+        self.mat = grads.flat.view(-1, self.n)
+        self.ops = ops if ops is not None else LibraryOps()
+        self.last = {}
+
+    def allreduce(self, group=None) -> GradBuffer:
+        if not (dist.is_initialized() and dist.get_world_size(group) > 1):
+            return self.grads
+        flag = self.ops.touched(self.mat)
+        dist.all_reduce(flag, op=dist.ReduceOp.MAX, group=group)
+        idx, cnt = self.ops.compact(flag)
+        k = int(cnt.item())
+        if k:
+            packed = self.ops.gather(self.mat, idx, cnt, k)
+            dist.all_reduce(packed, op=dist.ReduceOp.SUM, group=group)
+            self.ops.scatter(packed, self.mat, idx, cnt, k)
+        self.last = {"columns": k, "bytes_exchanged": 4 * self.n + 4 * k * self.mat.shape[0],
+                     "dense_bytes": 4 * self.mat.numel()}
+        return self.grads

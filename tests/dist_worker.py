@@ -59,3 +59,50 @@ def run(rank, world, port, out_dir):
                  local_h=h32, local_flat=np.concatenate([x.ravel() for x in g32]))
     finally:
         dist.destroy_process_group()
+
+
+class TorchCpuOps:
+    """The device steps of the sparse exchange restated with plain tensor indexing on the CPU
+    (the library's kernels need a GPU; their own parity is tested there)."""
+
+    def touched(self, mat):
+        return (mat != 0).any(0).to(torch.float32)
+
+    def compact(self, flag):
+        idx = torch.nonzero(flag > 0.5).flatten().to(torch.int32)
+        return idx, torch.tensor([idx.numel()], dtype=torch.int32)
+
+    def gather(self, mat, idx, cnt, k):
+        return mat[:, idx[:k].long()].contiguous()
+
+    def scatter(self, packed, mat, idx, cnt, k):
+        mat[:, idx[:k].long()] = packed
+
+
+def sparse_grads(rank, n=1000, rows=59):
+    """Seeded gradient rows with a few hundred touched columns per rank, overlapping."""
+    rng = np.random.default_rng(500 + rank)
+    g = np.zeros((rows, n), np.float32)
+    cols = rng.choice(n, size=150, replace=False)
+    g[:, cols] = rng.normal(size=(rows, len(cols))).astype(np.float32)
+    g[rng.integers(0, rows, 40), cols[:40]] = 0.0    # touched columns with some zero rows
+    return g
+
+
+def run_sparse(rank, world, port, out_dir):
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        g = sparse_grads(rank)
+        params = [torch.zeros(3, 1000), torch.zeros(3, 1000), torch.zeros(4, 1000), torch.zeros(1000),
+                  torch.zeros(48, 1000)]
+        dense = rd.GradBuffer(params)
+        sparse = rd.GradBuffer(params)
+        dense.flat.copy_(torch.from_numpy(g.ravel()))
+        sparse.flat.copy_(torch.from_numpy(g.ravel()))
+        rd.allreduce_grads(dense)
+        ex = rd.SparseGradExchange(sparse, 1000, ops=TorchCpuOps())
+        ex.allreduce()
+        np.savez(os.path.join(out_dir, f"sparse{rank}.npz"), dense=dense.flat.numpy(), sparse=sparse.flat.numpy(),
+                 columns=ex.last["columns"], sent=ex.last["bytes_exchanged"], full=ex.last["dense_bytes"])
+    finally:
+        dist.destroy_process_group()

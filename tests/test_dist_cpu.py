@@ -78,3 +78,25 @@ def test_two_rank_reductions_match_single_process(tmp_path):
         flat = np.concatenate([gk[n].ravel() for n in ("means", "log_scales", "quats", "opacity_logit", "sh")])
         tot = flat if tot is None else tot + flat
     assert np.max(np.abs(res[0]["flat"] - tot)) <= 1e-6 * max(1.0, np.abs(tot).max())
+
+
+def test_two_rank_sparse_gradient_exchange_equals_dense_sum(tmp_path):
+    """The exchange over the union of touched columns gives the dense all-reduce SUM bit for
+    bit, and moves the union's columns only."""
+    import dist_worker as w
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    procs = [ctx.Process(target=w.run_sparse, args=(r, 2, port, str(tmp_path))) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=300)
+        assert p.exitcode == 0
+    res = [np.load(tmp_path / f"sparse{r}.npz") for r in range(2)]
+    for r in res:
+        assert np.array_equal(r["dense"], r["sparse"])
+    expect = w.sparse_grads(0).ravel() + w.sparse_grads(1).ravel()
+    assert np.array_equal(res[0]["sparse"], expect)
+    union = ((w.sparse_grads(0) != 0).any(0) | (w.sparse_grads(1) != 0).any(0)).sum()
+    assert int(res[0]["columns"]) == int(union) and 150 < union < 300
+    assert int(res[0]["sent"]) == 4 * 1000 + 4 * 59 * int(union) < int(res[0]["full"])
