@@ -57,7 +57,9 @@ typedef enum rs_status {
 /* Device-side status block (device memory, caller-owned, zeroed by the caller before
  * the first call of a sequence).  Fields only ever grow; `code` keeps the first error. */
 typedef struct rs_device_status {
-  int32_t code;          /* RS_OK, RS_ERR_CAPACITY or RS_ERR_TIMEOUT */
+  int32_t code;          /* RS_OK, RS_ERR_CAPACITY, RS_ERR_TIMEOUT, or RS_ERR_INVALID_ARG
+                            (rs_bin_sort: the batch's n_tiles is below its views' tile count;
+                            the tile lists are then left empty) */
   int32_t nonfinite;     /* projected items culled for non-finite parameters */
   int64_t required;      /* largest instance count any rs_bin_sort needed */
   int64_t n_instances;   /* instances the last rs_bin_sort produced (<= capacity) */

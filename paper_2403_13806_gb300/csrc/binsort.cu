@@ -128,17 +128,28 @@ __global__ void k_depth_keys(const float4* __restrict__ rgb_d, const uint32_t* _
 // digits are as even as the host widths allow (each at most ceil(b / P) and at most the
 // host's width for that pass, any shortfall added to the earliest passes with room), so
 // they cover the b bits and the host's launch grids cover every digit value.
+// A batch whose n_tiles is below its views' tile count (only a hand-built rs_view_batch can
+// be) would need more tiles and super-tiles than the per-tile arrays, ranges and segment
+// tables hold: it is reported as RS_ERR_INVALID_ARG in the device status and binned as if no
+// view had a super-tile (no fine work items, every tile list empty), with every access in
+// bounds.
 __global__ void k_super_layout(const rs_view* __restrict__ views, int n_views, uint32_t* __restrict__ super_base,
                                int64_t n_items, uint32_t* __restrict__ n_dev, int host_bits,
-                               int32_t* __restrict__ digits) {
+                               int32_t* __restrict__ digits, int64_t n_tiles, rs_device_status* st) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   *n_dev = (uint32_t)n_items;
-  uint32_t run = 0;
+  uint64_t run = 0, tiles = 0;
   for (int v = 0; v < n_views; ++v) {
-    super_base[v] = run;
-    run += (uint32_t)(super_w(views[v]) * super_h(views[v]));
+    super_base[v] = (uint32_t)run;
+    run += (uint64_t)super_w(views[v]) * (uint64_t)super_h(views[v]);
+    tiles += (uint64_t)views[v].tiles_x * (uint64_t)views[v].tiles_y;
   }
-  super_base[n_views] = run;
+  if (tiles > (uint64_t)n_tiles) {   // (super-tiles never outnumber tiles)
+    if (st) atomicCAS(&st->code, 0, (int)RS_ERR_INVALID_ARG);
+    for (int v = 0; v < n_views; ++v) super_base[v] = 0;
+    run = 0;
+  }
+  super_base[n_views] = (uint32_t)run;
   int b = 1;
   while (b < 32 && (1u << b) < run) ++b;
   const int P = tiles::sort_passes(host_bits);   // at most 4
@@ -580,7 +591,9 @@ __global__ void __launch_bounds__(kTileBlock) k_fine_seg_scan(uint32_t* __restri
     const int ty = local / cam.tiles_x, tx = local - ty * cam.tiles_x;
     const uint32_t S = super_base[v] + (uint32_t)((ty / kSuper) * super_w(cam) + tx / kSuper);
     const int f = (ty % kSuper) * kSuper + tx % kSuper;
-    const uint32_t w0 = seg_off[S], w1 = seg_off[S + 1];
+    // (S is below the super-tile count unless k_super_layout rejected the batch)
+    const bool ok = S < super_base[n_views];
+    const uint32_t w0 = ok ? seg_off[S] : 0u, w1 = ok ? seg_off[S + 1] : 0u;
     for (uint32_t w = w0; w < w1; w += 4) {
       uint32_t x[4];
 #pragma unroll
@@ -830,7 +843,8 @@ extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* 
   {
     prof::Scope ps("k_super_layout", s);
     k_super_layout<<<1, 32, 0, s>>>(batch->views, batch->n_views, w.super_base, n, w.counters + 6,
-                                    bits_for(n_super_max), reinterpret_cast<int32_t*>(w.counters + 8));
+                                    bits_for(n_super_max), reinterpret_cast<int32_t*>(w.counters + 8), batch->n_tiles,
+                                    status);
   }
   int scur = 0;   // buffer set of the sorted super instances
   if (n > 0) {

@@ -252,3 +252,27 @@ def test_empty_and_degenerate_inputs():
     torch.cuda.synchronize()
     assert st.read()["nonfinite"] == 10
     assert np.all(u32(p.n_tiles)[:10] == 0)
+
+
+def test_bin_sort_rejects_a_batch_with_too_few_tiles():
+    """A hand-built batch whose n_tiles is below its views' tile count is reported through the
+    device status (RS_ERR_INVALID_ARG) and binned to empty lists, not out of bounds."""
+    from paper_2403_13806_gb300 import api, _native as N
+    scene, cams = synth.config1(n=4000, n_views=2, width=320, height=208)
+    g = api.Gaussians.from_scene(scene)
+    vb = api.ViewBatch(cams, scene.n)
+    proj = api.project(g, vb)
+    real = vb.batch.n_tiles               # 2 views x 20 x 13 tiles (2 x 20 super-tiles)
+    vb.batch.n_tiles = real // 4          # 130 tiles declared: enough for the super-tiles, not the tiles
+    bins = api.Bins.empty(4 * vb.n_items + 65536, vb.batch.n_tiles)
+    st = api.DeviceStatus()
+    api.bin_sort(proj, vb, bins, api.Workspace(), st)
+    torch.cuda.synchronize()
+    s = st.read()
+    assert s["code"] == N.RS_ERR_INVALID_ARG and s["n_instances"] == 0
+    r = bins.ranges.cpu().numpy()
+    assert np.all(r[:, 0] == r[:, 1])
+    # the same projection with the true tile count bins normally
+    vb.batch.n_tiles = real
+    out = gpu_forward(scene, cams)
+    assert out["n_instances"] > 0
