@@ -980,9 +980,9 @@ def probe_peaks(N, torch, dev, reps=5):
 NCU_TRAFFIC = {
     "k_render_bwd": {"bytes_per_view": 25183488, "files": ['render_bwd.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "930e0ad64f2543d8",
                 "profile": "k_render_bwd_1M_1view.md"},
-    "k_render_importance": {"bytes_per_view": 4451584, "files": ['render.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "2563e143b71aae9f",
+    "k_render_importance": {"bytes_per_view": 4441600, "files": ['render.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "d09583f05603764e",
                 "profile": "k_render_1M_1view.md"},
-    "k_fine_scatter": {"bytes_per_view": 20113664, "files": ['binsort.cu', 'rs_common.cuh'], "sha": "4bf8f48e228d0be8",
+    "k_fine_scatter": {"bytes_per_view": 20112128, "files": ['binsort.cu', 'rs_common.cuh'], "sha": "4cffedcde21798e1",
                 "profile": "k_fine_scatter_1M_1view.md"},
     "k_ssim_stats": {"bytes_per_view": 25871360, "files": ['ssim.cu', 'rs_common.cuh'], "sha": "77368fb65aa91f37",
                 "profile": "k_ssim_stats_1view.md"},
