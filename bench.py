@@ -369,6 +369,7 @@ def run_ours(args):
     uneven = uneven_bench(api, N, torch, dev, args.uneven_views, reps=2) if args.uneven_views > 0 else None
     filtered = filtered_bench(api, N, torch, dev, reps=5) if not args.no_legs else None
     imp_leg = importance_bench(api, N, torch, dev, reps=5) if not args.no_legs else None
+    small = small_scene_bench(api, N, torch, dev, reps=50) if not args.no_legs else None
     work = kernel_work(vbs, sres, pairs, n_super, touched)
     probes = probe_peaks(N, torch, dev)
     roof = roofline(kernel_ms, work, hbm, peak_kind, B, probes)
@@ -408,6 +409,7 @@ def run_ours(args):
                                    sorted(kernel_ms.items(), key=lambda kv: -kv[1]["ms_per_step"])},
             "e2e": e2e, "roofline": roof, "roofline_per_kernel": per_kernel, "probes": probes, "optimizer": optim,
             "uneven_batch": uneven, "visibility_filtered_64_views": filtered, "importance_32_views": imp_leg,
+            "config0_forward": small,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
             "gpu_launches": launches,
@@ -627,6 +629,20 @@ def filtered_bench(api, N, torch, dev, reps):
         torch.cuda.empty_cache()
     out["fps_gain"] = round(out["filtered"]["fps"] / out["unfiltered"]["fps"], 3)
     return out
+
+
+def small_scene_bench(api, N, torch, dev, reps):
+    """Config 0 (2000 Gaussians, one 128x128 view, SH degree 0): the plain forward (project ->
+    bin_sort -> render) replayed as a CUDA graph; launch-bound at this size."""
+    from paper_2403_13806_gb300 import synth
+    scene, cams = synth.config0()
+    g = api.Gaussians.from_scene(scene, device=dev)
+    vb = api.ViewBatch(cams, scene.n, device=dev)
+    body, st, cap = _forward_plan(api, torch, g, vb, api.config(), dev)
+    gr = _graph_of(torch, body)
+    ms = _replay_ms(torch, gr, reps)
+    return {"gaussians": scene.n, "width": 128, "height": 128, "ms_forward": round(ms, 4),
+            "fps": round(1000.0 / ms, 1), "instances": int(st.read()["n_instances"])}
 
 
 def importance_bench(api, N, torch, dev, reps):
