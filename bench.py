@@ -397,6 +397,7 @@ def run_ours(args):
             "gaussians_with_gradient": touched,
             "super_instances_per_view": int(n_super / V),
             "pairs_per_pixel": round(pairs / sum(vb.n_pixels for vb in vbs), 2),
+            "tile_list_fraction_walked": round(work_counts["walked"] / max(1, sres["n_instances"] * len(vbs)), 4),
             "blends_per_s_forward": round(pairs / (kernel_ms["k_render_importance"]["ms_per_step"] / 1e3), 0)
             if "k_render_importance" in kernel_ms else None,
             "autotune": None if tune is None else {
@@ -464,12 +465,19 @@ def stage_times(api, N, torch, g, chunks, cfg, st, proj, h, gbuf, loss, ws_sort,
     N.profile_enable(False)
     kernels = {k: {"launches_per_step": v[0] / reps, "ms_per_step": v[1] / reps, "ms_per_launch": v[1] / v[0]}
                for k, v in kern.items()}
-    pairs, n_super = 0, 0
+    pairs, n_super, walked = 0, 0, 0
     for vb, bins, (img, T, L, dL), target in chunks:
         api.project(g, vb, cfg, st, out=proj)
         api.bin_sort(proj, vb, bins, ws_sort, st)
         api.render(proj, bins, vb, cfg, image=img, T_final=T, last=L)
         pairs += int(L.to(torch.int64).sum().item())
+        # entries a tile's blend reads: up to the largest `last` of its pixels
+        tw, th = vb.tile
+        for v in range(vb.n_views):
+            hv = vb.views_host[v]
+            Lv = L[hv.pixel_base: hv.pixel_base + hv.width * hv.height].view(hv.height, hv.width)
+            Lp = torch.nn.functional.pad(Lv, (0, hv.tiles_x * tw - hv.width, 0, hv.tiles_y * th - hv.height))
+            walked += int(Lp.view(hv.tiles_y, th, hv.tiles_x, tw).amax(dim=(1, 3)).to(torch.int64).sum().item())
         r = proj.rect[:vb.n_items].to(torch.int64) & 0xffff
         nonempty = (r[:, 2] > r[:, 0]) & (r[:, 3] > r[:, 1])
         zero = torch.zeros_like(r[:, 0])
@@ -482,7 +490,7 @@ def stage_times(api, N, torch, g, chunks, cfg, st, proj, h, gbuf, loss, ws_sort,
     gm = gbuf.views[0].reshape(3, -1)
     touched = int(((gm != 0).any(dim=0) | (gbuf.views[3].reshape(-1) != 0)).sum().item())
     torch.cuda.synchronize()
-    return acc, kernels, {"pairs": pairs, "super_instances": n_super, "touched": touched}
+    return acc, kernels, {"pairs": pairs, "super_instances": n_super, "touched": touched, "walked": walked}
 
 
 def uneven_bench(api, N, torch, dev, n_views, reps):
@@ -994,7 +1002,7 @@ def probe_peaks(N, torch, dev, reps=5):
 # of the sources the kernel was built from.  A capture stays valid only while those sources
 # are unchanged; otherwise the roofline reports traffic as null.
 NCU_TRAFFIC = {
-    "k_render_bwd": {"bytes_per_view": 25183488, "files": ['render_bwd.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "930e0ad64f2543d8",
+    "k_render_bwd": {"bytes_per_view": 25182976, "files": ['render_bwd.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "ce5f65528d017c7f",
                 "profile": "k_render_bwd_1M_1view.md"},
     "k_render_importance": {"bytes_per_view": 4441600, "files": ['render.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "d09583f05603764e",
                 "profile": "k_render_1M_1view.md"},

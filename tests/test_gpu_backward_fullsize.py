@@ -74,10 +74,20 @@ def run_batch(scene, cams, subsets, n_pix, seed, tile=None, batch=None):
         L_max = max(L_max, int(last[hv.pixel_base + pix[:, 1] * W + pix[:, 0]].max()))
         sel.append((pix, w))
     grads = [torch.zeros_like(t) for t in g.tensors()]
-    api.render_backward(g, vb, fo["proj"], fo["bins"], fo["T_final"], fo["last"], torch.as_tensor(dL, device="cuda"),
-                        grads, rast.ws_bwd, cfg)
+    dLt = torch.as_tensor(dL, device="cuda")
+    api.render_backward(g, vb, fo["proj"], fo["bins"], fo["T_final"], fo["last"], dLt, grads, rast.ws_bwd, cfg)
     torch.cuda.synchronize()
     img = [t.cpu().numpy().astype(np.float64) for t in api.image_grads(vb, rast.ws_bwd)]
+    # the benchmark's first launch of a step writes the gradients (grad_overwrite) over arrays
+    # holding anything: the same gradients as accumulating into zeros, up to the order in which
+    # the per-item atomics add
+    over = [torch.full_like(t, 3.0) for t in g.tensors()]
+    api.render_backward(g, vb, fo["proj"], fo["bins"], fo["T_final"], fo["last"], dLt, over, rast.ws_bwd,
+                        api.config(batch=batch, grad_overwrite=True))
+    torch.cuda.synchronize()
+    for a, b in zip(grads, over):
+        a, b = a.cpu().numpy().astype(np.float64), b.cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(a - b) <= 1e-4 * np.abs(a) + 1e-6 * np.abs(a).max())
     return vb, sel, grads, img, L_max
 
 
