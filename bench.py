@@ -945,9 +945,9 @@ FP32_OPS_PER_PAIR = {"k_render_importance": 16, "k_render": 15, "k_render_bwd": 
 EX2_PER_PAIR = 1
 # The FP32 operations the kernels as written execute per pair (counted from their source:
 # forward 22 = offsets 2, quadratic form 5, tests 3, exp2 and scale 2, clamp and test 2,
-# transmittance 3, weight 1, colour 3, bookkeeping 1; backward 46), reported beside the
+# transmittance 3, weight 1, colour 3, bookkeeping 1; backward 45), reported beside the
 # algorithmic figure.
-INSTR_OPS_PER_PAIR = {"k_render_importance": 22, "k_render": 22, "k_render_bwd": 46}
+INSTR_OPS_PER_PAIR = {"k_render_importance": 22, "k_render": 22, "k_render_bwd": 45}
 L2_BYTES = 126 * 2 ** 20     # the working set below which a kernel's bytes stay in L2
 
 # Probe kernels (rs_peak_probe): name, kind, iterations per launch (about 1-3 ms each).

@@ -82,10 +82,11 @@ __device__ __forceinline__ float2 sel2(bool a, bool b, float2 x) {
 
 // Back-to-front walk of one tile.  Per pixel pair q (lanes = the two pixels): T[q] is the
 // transmittance after the current entry (T_final at the start), G*[q] = dL/dC per channel,
-// bgG[q] = T_final (bg . dL/dC), SG[q] = (colour composited behind the current entry) .
-// dL/dC; entries at positions >= last[k] were not composited for pixel k.  Per entry e the
-// thread's pixels add up, with a = alpha_e and T_e = T/(1 - a):
-//   d/dcolour = a T_e dL/dC,  dL/da = T_e (c . dL/dC) - (SG + bgG)/(1 - a),
+// SG[q] = (everything composited behind the current entry, the background's T_final bg
+// included) . dL/dC -- it starts at T_final (bg . dL/dC); entries at positions >= last[k]
+// were not composited for pixel k.  Per entry e the thread's pixels add up, with
+// a = alpha_e and T_e = T/(1 - a):
+//   d/dcolour = a T_e dL/dC,  dL/da = T_e (c . dL/dC) - SG/(1 - a),
 // and, unless the 0.99 clamp was active, d/do = dL/da 2^p2 and with q = dL/da * a (the
 // derivative with respect to the power) the moments sum(q), sum(q dy), sum(q dy^2); the
 // column's common dx turns them into the mean and conic gradients.
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(TW* TH / PX, 16) k_render_bwd(BwdBlendArgs a) 
   const uint2 rg = a.ranges[tile];
   const uint32_t start = rg.x;
 
-  float2 nv[NP], T[NP], Gr[NP], Gg[NP], Gb[NP], bgG[NP], SG[NP];
+  float2 nv[NP], T[NP], Gr[NP], Gg[NP], Gb[NP], SG[NP];
   int last[PX];
   const int64_t HW = (int64_t)cam.width * cam.height;
   const float* gi = a.dL_dimage + 3 * cam.pixel_base;
@@ -139,9 +140,8 @@ __global__ void __launch_bounds__(TW* TH / PX, 16) k_render_bwd(BwdBlendArgs a) 
     Gr[q] = make_float2(g0[0], g0[1]);
     Gg[q] = make_float2(g1[0], g1[1]);
     Gb[q] = make_float2(g2[0], g2[1]);
-    bgG[q] = make_float2(t[0] * (a.bg0 * g0[0] + a.bg1 * g1[0] + a.bg2 * g2[0]),
-                         t[1] * (a.bg0 * g0[1] + a.bg1 * g1[1] + a.bg2 * g2[1]));
-    SG[q] = make_float2(0.f, 0.f);
+    SG[q] = make_float2(t[0] * (a.bg0 * g0[0] + a.bg1 * g1[0] + a.bg2 * g2[0]),
+                        t[1] * (a.bg0 * g0[1] + a.bg1 * g1[1] + a.bg2 * g2[1]));
   }
   int my_last = 0;
 #pragma unroll
@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(TW* TH / PX, 16) k_render_bwd(BwdBlendArgs a) 
         const float2 Tj = __fmul2_rn(T[q], inv);
         const float2 w = __fmul2_rn(a_eff, Tj);
         const float2 cG = __ffma2_rn(lo2(r.rg), Gr[q], __ffma2_rn(hi2(r.rg), Gg[q], __fmul2_rn(lo2(r.bc), Gb[q])));
-        const float2 X = __fmul2_rn(__fadd2_rn(SG[q], bgG[q]), inv);
+        const float2 X = __fmul2_rn(SG[q], inv);
         const float2 dLda = __ffma2_rn(Tj, cG, make_float2(-X.x, -X.y));
         const float2 dl = sel2(al.in0 && al.raw.x < kAlphaMax, al.in1 && al.raw.y < kAlphaMax, dLda);
         acc_r = __ffma2_rn(w, Gr[q], acc_r);
