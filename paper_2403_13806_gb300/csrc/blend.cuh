@@ -58,10 +58,23 @@ __device__ __forceinline__ float2 pair_dx(const BlendRec& r, float2 nu) { return
 // (y - v0, y - v1) for a pixel pair in rows v0, v1 (nv = (-v0, -v1)).
 __device__ __forceinline__ float2 pair_dy(const BlendRec& r, float2 nv) { return __fadd2_rn(hi2(r.xy), nv); }
 
-// p2 = log2(e) * power for both pixels of a pair: dx (A dx + B dy) + (C dy) dy.
-__device__ __forceinline__ float2 pair_power(const BlendRec& r, float2 dx, float2 dy) {
-  return __ffma2_rn(dx, __ffma2_rn(lo2(r.ab), dx, __fmul2_rn(hi2(r.ab), dy)),
-                    __fmul2_rn(__fmul2_rn(lo2(r.co), dy), dy));
+// A thread's pixels share one column, hence one dx per record: the terms A dx^2 and B dx of
+// p2 = A dx^2 + dy (B dx + C dy) are computed once per record for all its pixel pairs.
+struct ColTerms {
+  float2 adx2;   // (A dx^2, A dx^2)
+  float2 bdx;    // (B dx, B dx)
+};
+
+__device__ __forceinline__ ColTerms col_terms(const BlendRec& r, float2 dx) {
+  ColTerms c;
+  c.adx2 = __fmul2_rn(__fmul2_rn(lo2(r.ab), dx), dx);
+  c.bdx = __fmul2_rn(hi2(r.ab), dx);
+  return c;
+}
+
+// p2 = log2(e) * power for both pixels of a pair: A dx^2 + dy (B dx + C dy).
+__device__ __forceinline__ float2 pair_power(const BlendRec& r, const ColTerms& c, float2 dy) {
+  return __ffma2_rn(dy, __ffma2_rn(lo2(r.co), dy, c.bdx), c.adx2);
 }
 
 // Per-pixel outcome of the blend rule's tests on one record.

@@ -110,12 +110,12 @@ __global__ void __launch_bounds__(TW* TH / PX) k_render(RenderArgs a) {
     const int base = (int)(b0 - start);
     for (int j = 0; j < nb; ++j) {
       const BlendRec r = s_rec[j];
-      const float2 dx = pair_dx(r, nu);
+      const ColTerms ct = col_terms(r, pair_dx(r, nu));
       float2 p2[NP];
       bool any = false;
 #pragma unroll
       for (int q = 0; q < NP; ++q) {
-        p2[q] = pair_power(r, dx, pair_dy(r, nv[q]));
+        p2[q] = pair_power(r, ct, pair_dy(r, nv[q]));
         any |= p2[q].x >= r.bc.z || p2[q].y >= r.bc.z;   // NaN (done) compares false
       }
       if (!__any_sync(0xffffffffu, any)) continue;   // no pixel of the warp is in this record's support
