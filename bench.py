@@ -32,6 +32,7 @@ if ROOT not in sys.path:
 
 METRIC = "FPS and fwd+bwd ms/view at 1M Gaussians, 1280×832; batched vs plain on one GB300"
 N_GAUSSIANS = 1_000_000
+FRONT = True   # tile lists binned by rs_bin_sort_front (--lists whole: rs_bin_sort)
 WIDTH, HEIGHT = 1280, 832
 
 
@@ -58,6 +59,9 @@ def parse():
     ap.add_argument("--tile", default="auto", help="tile shape WxH with all views in one launch, or 'auto' "
                                                    "(autotuner: tile shape, staging batch, views per launch)")
     ap.add_argument("--sample-pixels", type=int, default=0, help="reference arm: pixels per step (0: auto)")
+    ap.add_argument("--lists", default="front", choices=["front", "whole"],
+                    help="tile lists: the part in front of each tile's provable saturation depth "
+                         "(rs_bin_sort_front) or whole (rs_bin_sort); the rendered results are the same")
     ap.add_argument("--probes", action="store_true", help="only run the peak probe kernels and print their rates")
     ap.add_argument("--cpu-report", action="store_true",
                     help="only time the FP64 C oracle on the host cores (config 0 full image, config 2 full view)")
@@ -174,7 +178,7 @@ def run_ours(args):
 
     # tile shape and views per launch from the autotuner (setup, untimed; cached per workload)
     if args.tile == "auto":
-        tune = api.autotune(g, cams, cfg=cfg, backward=True)
+        tune = api.autotune(g, cams, cfg=cfg, backward=True, front=FRONT)
         tile, B = tune["tile"], tune["views_per_launch"]
         cfg = api.config(batch=tune["smem_batch"])
     else:
@@ -186,12 +190,12 @@ def run_ours(args):
     # synthetic targets: renders of a perturbed copy (setup, untimed)
     tscene = synth.perturbed_copy(scene, 12)
     tg = api.Gaussians.from_scene(tscene, device=dev)
-    trast = api.Rasterizer(device=dev)
+    trast = api.Rasterizer(device=dev, front=FRONT)
     targets = [trast.forward(tg, vb)["image"].clone() for vb in vbs]
     del trast, tg
 
     # capacity from a first (plain) forward of every chunk
-    rast = api.Rasterizer(device=dev)
+    rast = api.Rasterizer(device=dev, front=FRONT)
     K_max = 0
     for vb in vbs:
         rast.forward(g, vb)
@@ -234,7 +238,7 @@ def run_ours(args):
         h.zero_()
         for k, (vb, bins, (img, T, L, dL), target) in enumerate(chunks):
             api.project(g, vb, cfg, st, out=proj)
-            api.bin_sort(proj, vb, bins, ws_sort, st)
+            api.bin_sort(proj, vb, bins, ws_sort, st, front=FRONT)
             api.render(proj, bins, vb, cfg, image=img, T_final=T, last=L, importance=h)
             if overlap_prune and k == len(chunks) - 1:
                 imp_done.record()
@@ -388,6 +392,8 @@ def run_ours(args):
                                         f"of the gradient columns some rank touched per step" if world > 1
                                         else "1 GPU, no collective")),
             "gradient_exchange": exchange.last if world > 1 else None,
+            "tile_lists": ("front: each tile's list up to the depth where its pixels provably stop "
+                           "(rs_bin_sort_front; same results)" if FRONT else "whole (rs_bin_sort)"),
             "batched_ms_per_view": round(value, 5),
             "plain_ms_per_view": round(plain, 5) if plain else None,
             "batched_over_plain_speedup": round(plain / value, 3) if plain else None,
@@ -441,7 +447,7 @@ def stage_times(api, N, torch, g, chunks, cfg, st, proj, h, gbuf, loss, ws_sort,
             ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
             ev[0].record()
             api.project(g, vb, cfg, st, out=proj); ev[1].record()
-            api.bin_sort(proj, vb, bins, ws_sort, st); ev[2].record()
+            api.bin_sort(proj, vb, bins, ws_sort, st, front=FRONT); ev[2].record()
             api.render(proj, bins, vb, cfg, image=img, T_final=T, last=L, importance=h); ev[3].record()
             loss_fn(img, target, dL, loss); ev[4].record()
             api.render_backward(g, vb, proj, bins, T, L, dL, gbuf.views, ws_bwd, cfg_w if k == 0 else cfg)
@@ -468,7 +474,7 @@ def stage_times(api, N, torch, g, chunks, cfg, st, proj, h, gbuf, loss, ws_sort,
     pairs, n_super, walked = 0, 0, 0
     for vb, bins, (img, T, L, dL), target in chunks:
         api.project(g, vb, cfg, st, out=proj)
-        api.bin_sort(proj, vb, bins, ws_sort, st)
+        api.bin_sort(proj, vb, bins, ws_sort, st, front=FRONT)
         api.render(proj, bins, vb, cfg, image=img, T_final=T, last=L)
         pairs += int(L.to(torch.int64).sum().item())
         # entries a tile's blend reads: up to the largest `last` of its pixels
@@ -507,12 +513,12 @@ def uneven_bench(api, N, torch, dev, n_views, reps):
     cams, subsets = synth.config4(scene, n_views=n_views)   # the first n_views of the 256-view set
     g = api.Gaussians.from_scene(scene, device=dev)
     grads = [torch.zeros_like(t) for t in g.tensors()]
-    tune = api.autotune(g, cams[:32], subsets=subsets[:32], backward=True)
+    tune = api.autotune(g, cams[:32], subsets=subsets[:32], backward=True, front=FRONT)
     B = tune["views_per_launch"]
     cfg = api.config(batch=tune["smem_batch"])
 
     def make(chunks, tile, cfg_):
-        r = api.Rasterizer(cfg=cfg_, device=dev)
+        r = api.Rasterizer(cfg=cfg_, device=dev, front=FRONT)
         vbs = [api.ViewBatch(cams[i:i + chunks], scene.n, subsets=subsets[i:i + chunks], tile=tile, device=dev)
                for i in range(0, len(cams), chunks)]
         for vb in vbs:
@@ -583,7 +589,7 @@ def _replay_ms(torch, gr, reps):
 def _forward_plan(api, torch, g, vb, cfg, dev, importance=None, image=True):
     """Buffers and a body for one forward (project -> bin_sort -> render) of a batch with the
     instance capacity sized by a first render."""
-    r = api.Rasterizer(cfg=cfg, device=dev)
+    r = api.Rasterizer(cfg=cfg, device=dev, front=FRONT)
     r.forward(g, vb)
     cap = int(r.status.read()["required"] * 1.02) + 4096
     st = api.DeviceStatus(dev)
@@ -597,7 +603,7 @@ def _forward_plan(api, torch, g, vb, cfg, dev, importance=None, image=True):
 
     def body():
         api.project(g, vb, cfg, st, out=proj)
-        api.bin_sort(proj, vb, bins, ws, st)
+        api.bin_sort(proj, vb, bins, ws, st, front=FRONT)
         api.render(proj, bins, vb, cfg, image=img, T_final=T, last=L, importance=importance)
 
     return body, st, cap
@@ -614,7 +620,7 @@ def filtered_bench(api, N, torch, dev, reps):
     g = api.Gaussians.from_scene(scene, device=dev)
     cfg = api.config()
     lists = {}
-    rast = api.Rasterizer(device=dev)
+    rast = api.Rasterizer(device=dev, front=FRONT)
     for s in range(int(site.max()) + 1):
         vb = api.ViewBatch([c for c, k in zip(cams, site) if k == s], scene.n, device=dev)
         h = torch.zeros(scene.n, dtype=torch.int32, device=dev)
@@ -752,7 +758,7 @@ def plain_loop(api, N, torch, g, vb1, cfg, target, cams, reps, dev, loss_fn):
     cfg and the views' tile shape are the caller's (defaults, or the autotuned ones)."""
     rasts = []
     for vb in vb1:
-        r = api.Rasterizer(cfg=cfg, device=dev)
+        r = api.Rasterizer(cfg=cfg, device=dev, front=FRONT)
         r.forward(g, vb)
         cap = int(r.status.read()["required"] * 1.05) + 4096
         rasts.append((r, api.Bins.empty(cap, vb.n_tiles, device=dev)))
@@ -768,7 +774,7 @@ def plain_loop(api, N, torch, g, vb1, cfg, target, cams, reps, dev, loss_fn):
         vb = vb1[i]
         r, bins = rasts[i]
         proj = api.project(g, vb, r.cfg, st)
-        api.bin_sort(proj, vb, bins, r.ws_sort, st)
+        api.bin_sort(proj, vb, bins, r.ws_sort, st, front=FRONT)
         img, T, L = api.render(proj, bins, vb, r.cfg, importance=h)
         l, dl = loss_fn(img, tg[i])
         api.render_backward(g, vb, proj, bins, T, L, dl, grads, r.ws_bwd, r.cfg)
@@ -794,13 +800,13 @@ def plain_loop(api, N, torch, g, vb1, cfg, target, cams, reps, dev, loss_fn):
     fr = max(reps, 10)
     for _ in range(3):
         api.project(g, vb, r.cfg, st, out=proj)
-        api.bin_sort(proj, vb, bins, r.ws_sort, st)
+        api.bin_sort(proj, vb, bins, r.ws_sort, st, front=FRONT)
         api.render(proj, bins, vb, r.cfg, image=img, T_final=False, last=False)
     torch.cuda.synchronize()
     e0.record()
     for _ in range(fr):
         api.project(g, vb, r.cfg, st, out=proj)
-        api.bin_sort(proj, vb, bins, r.ws_sort, st)
+        api.bin_sort(proj, vb, bins, r.ws_sort, st, front=FRONT)
         api.render(proj, bins, vb, r.cfg, image=img, T_final=False, last=False)
     e1.record()
     torch.cuda.synchronize()
@@ -862,7 +868,7 @@ def e2e_run(api, N, torch, scene, vbs, cfg, targets, cap, reps, dev, world=1, lo
             for i, vb in enumerate(vbs):
                 bins = api.Bins(bins_all.vals, bins_all.ranges[:vb.n_tiles], None, cap)
                 api.project(g, vb, cfg, st, out=proj)
-                api.bin_sort(proj, vb, bins, ws_sort, st)
+                api.bin_sort(proj, vb, bins, ws_sort, st, front=FRONT)
                 img, T, L = api.render(proj, bins, vb, cfg, image=img_buf[i], T_final=T_buf[i], last=L_buf[i],
                                        importance=h)
                 if overlap_prune and i == len(vbs) - 1:   # the filter beside the last loss and backward
@@ -1047,7 +1053,8 @@ def kernel_work(vbs, sres, pairs, n_super, touched):
 
     Items M (view, Gaussian) pairs, instances K, super-tile instances Ks, pixels P:
     projection reads 236 B of parameters per Gaussian (per item for visibility lists) and
-    writes 52 B per item; the depth sort moves
+    writes 52 B per item; the occlusion cut of front lists reads 36 B per item of the
+    nearest sixteenth and 256 B of bound sums per tile; the depth sort moves
     8 B per item and pass (read key+value, write key+value = 16 B in the scatter, 4 B read in
     the count); the super-tile sort moves 2 x (2 + 4 + 1) B per super instance and pass
     (count: 2 B); the fine partition reads the 1 B cover byte per super instance (count),
@@ -1071,6 +1078,10 @@ def kernel_work(vbs, sres, pairs, n_super, touched):
         "k_emit": M * (4 + 8) + Ks * (kb + 4 + 1),
         "k_depth_sort_hist": M * 4,
         "k_depth_sort": M * 16,
+        # occlusion cut (front lists): the nearest sixteenth of the items, their order entry,
+        # mean, conic and rect; then 64 bound sums per tile
+        "k_cut_accumulate": -(-M // 16) * (4 + 8 + 16 + 8),
+        "k_cut_tiles": vb.n_tiles * 64 * 4,
         "k_super_sort_hist": Ks * kb,
         "k_super_sort": Ks * 2 * (kb + 4 + 1),
         "k_ranges": Ks * kb,
@@ -1293,7 +1304,9 @@ def run_probes():
 
 
 def main():
+    global FRONT
     args = parse()
+    FRONT = args.lists == "front"
     if args.probes:
         run_probes()
     elif args.cpu_report:

@@ -255,6 +255,29 @@ rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* batch,
                       const rs_bins* bins, void* ws, size_t ws_bytes,
                       rs_device_status* status, void* stream);
 
+/* rs_bin_sort_front -- rs_bin_sort restricted to the front of every tile list that the
+ * blend of Eq. render-gs can reach (the paper has no counterpart; rs_render,
+ * rs_importance and rs_render_backward give the same results on either lists).
+ * Blending stops a pixel before the first entry whose T(1 - alpha) falls below 1e-4.  For
+ * every tile, the items among the nearest ceil(n / 32) in depth order whose alpha is at
+ * least some alpha_lb >= 1/255 at every pixel centre of the tile (the smallest over the
+ * tile's four corner pixels, the power being concave; with margins for FP32 rounding)
+ * bound T from above by the product of their (1 - alpha_lb); the depth rank by which that
+ * product provably falls below 5e-5 (rounded up to the end of one of 64 rank buckets,
+ * narrower at the front) is the tile's cut, and every super-tile of 4 x 4 tiles takes its
+ * tiles' largest cut (a tile without one keeps its whole list, and so does its
+ * super-tile).  vals[ranges[2t] .. ranges[2t+1]) is then the first part of rs_bin_sort's
+ * list for tile t: the items ranked before the cut, in the same order; every entry the
+ * blend composites or tests lies in it.  keys, capacity and status as in rs_bin_sort (the
+ * instance count is that of the shortened lists).
+ * Reads proj->xy and proj->conic_o besides what rs_bin_sort reads, and batch->tile_w /
+ * tile_h (the pixel rectangle of every tile).
+ * ws: rs_workspace_size(RS_STAGE_BIN_SORT, batch, capacity) bytes (the same workspace).
+ * Errors: RS_ERR_INVALID_ARG (also for NULL xy or conic_o), RS_ERR_WORKSPACE, RS_ERR_CUDA. */
+rs_status rs_bin_sort_front(const rs_projected* proj, const rs_view_batch* batch,
+                            const rs_bins* bins, void* ws, size_t ws_bytes,
+                            rs_device_status* status, void* stream);
+
 /* rs_render -- Eq. (render-gs): per pixel, walk its tile's list front to back with
  * alpha = min(0.99, o exp(power)), power = -(a dx^2 + c dy^2)/2 - b dx dy; skip entries
  * with power > 0 or alpha < 1/255; stop before the first entry whose T(1-alpha) < 1e-4;
@@ -479,20 +502,22 @@ typedef struct rs_tune_result {
 
 #define RS_TUNE_BACKWARD 1  /* time render_backward too (training), else the forward only */
 #define RS_TUNE_FORCE 2     /* measure even when the workload is cached */
+#define RS_TUNE_FRONT 4     /* bin with rs_bin_sort_front (else rs_bin_sort) */
 
 /* rs_autotune -- chooses the tile shape, the Gaussians staged per shared-memory batch of
  * the blend kernels and the views per launch for rendering the given views (the paper has
  * no counterpart: it serves the batched execution of many views, the training views of
  * Sec. 3.2 and the per-cluster view sets of Sec. 3.4).  It times the library's own
- * project -> bin_sort -> render (with importance) [-> render_backward] in two stages:
+ * project -> bin_sort (rs_bin_sort_front with RS_TUNE_FRONT) -> render (with importance)
+ * [-> render_backward] in two stages:
  * (1) every tile shape (16x16, 32x8, 8x8) x staging batch (1, 2, 4 records per thread),
  * all of the first min(n_views, 16) views in one launch per stage; (2) with the winner of
  * (1), views per launch 1, 2, 4, ... and n_views over the first min(n_views,
  * max(views per launch, 16)) views.  Each candidate gets one untimed pass and three timed
  * passes (CUDA events on `stream`); the score is device milliseconds per view.  The choice
  * is cached under the workload (view sizes, n_items, g->n, sh_degree, subset use,
- * RS_TUNE_BACKWARD, cfg apart from batch); a later call with the same workload returns it
- * without device work unless RS_TUNE_FORCE.
+ * RS_TUNE_BACKWARD, RS_TUNE_FRONT, cfg apart from batch); a later call with the same
+ * workload returns it without device work unless RS_TUNE_FORCE.
  * g, subset_idx (device, may be NULL) and n_items (host [n_views]) as in a batch of all the
  * views; cams: host [n_views]; cfg: its batch field is ignored; cand_ms (host, may be
  * NULL): rs_autotune_candidates(n_views) floats, device ms per view of each candidate in

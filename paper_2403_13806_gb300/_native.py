@@ -75,7 +75,7 @@ class RsTuneResult(ctypes.Structure):
                 ("ms_per_view", c_float), ("cached", c_int32), ("n_candidates", c_int32), ("reserved", c_int32)]
 
 
-RS_TUNE_BACKWARD, RS_TUNE_FORCE = 1, 2
+RS_TUNE_BACKWARD, RS_TUNE_FORCE, RS_TUNE_FRONT = 1, 2, 4
 
 
 class RsAdamGroup(ctypes.Structure):
@@ -101,6 +101,7 @@ SIGNATURES = {
     "rs_struct_sizes": (c_int32, [P, c_int32]),
     "rs_project": (ctypes.c_int, [P, P, P, P, P, P]),
     "rs_bin_sort": (ctypes.c_int, [P, P, P, P, c_size_t, P, P]),
+    "rs_bin_sort_front": (ctypes.c_int, [P, P, P, P, c_size_t, P, P]),
     "rs_render": (ctypes.c_int, [P, P, P, P, P, P, P, P, c_int64, P]),
     "rs_importance": (ctypes.c_int, [P, P, P, P, P, c_int64, P]),
     "rs_filter": (ctypes.c_int, [P, c_int64, c_float, ctypes.c_int, P, P, P, P, c_size_t, P]),

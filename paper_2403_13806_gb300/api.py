@@ -222,11 +222,15 @@ def project(g: Gaussians, vb: ViewBatch, cfg: Optional[N.RsConfig] = None, statu
     return out
 
 
-def bin_sort(proj: Projected, vb: ViewBatch, bins: Bins, ws: Workspace, status: DeviceStatus, stream=None) -> Bins:
+def bin_sort(proj: Projected, vb: ViewBatch, bins: Bins, ws: Workspace, status: DeviceStatus, stream=None,
+             front: bool = False) -> Bins:
+    """rs_bin_sort (every tile's whole list), or with ``front`` rs_bin_sort_front (the part of
+    every list in front of the depth where the tile's pixels provably saturate: the blend,
+    importance and backward results are the same)."""
     nbytes = N.lib().rs_workspace_size(N.RS_STAGE_BIN_SORT, N.ref(vb.batch), bins.capacity)
     w = ws.get(nbytes)
-    N.call("rs_bin_sort", N.ref(proj.struct()), N.ref(vb.batch), N.ref(bins.struct()), _ptr(w), w.numel(),
-           status.ptr(), _stream(stream))
+    N.call("rs_bin_sort_front" if front else "rs_bin_sort", N.ref(proj.struct()), N.ref(vb.batch),
+           N.ref(bins.struct()), _ptr(w), w.numel(), status.ptr(), _stream(stream))
     return bins
 
 
@@ -351,9 +355,10 @@ def blend_threads(tile) -> int:
 
 
 def autotune(g: Gaussians, cams: Sequence[dict], subsets: Optional[Sequence] = None, cfg=None,
-             backward: bool = True, force: bool = False, stream=None) -> dict:
+             backward: bool = True, force: bool = False, stream=None, front: bool = True) -> dict:
     """rs_autotune: tile shape, records staged per blend batch and views per launch for
-    rendering `cams` (cached per workload).
+    rendering `cams` (cached per workload); ``front`` times binning by rs_bin_sort_front
+    (the Rasterizer's default), else by rs_bin_sort.
 
     Returns {"tile": (w, h), "smem_batch": rs_config.batch, "views_per_launch", "cached",
     "ms_per_view", "n_candidates", "stage1": {(w, h, records per thread): ms per view},
@@ -371,7 +376,8 @@ def autotune(g: Gaussians, cams: Sequence[dict], subsets: Optional[Sequence] = N
     res = N.RsTuneResult()
     nc = N.lib().rs_autotune_candidates(V)
     cand = (ctypes.c_float * nc)()
-    flags = (N.RS_TUNE_BACKWARD if backward else 0) | (N.RS_TUNE_FORCE if force else 0)
+    flags = ((N.RS_TUNE_BACKWARD if backward else 0) | (N.RS_TUNE_FORCE if force else 0) |
+             (N.RS_TUNE_FRONT if front else 0))
     N.call("rs_autotune", N.ref(g.struct()), cam_arr, V, n_items.ctypes.data_as(ctypes.c_void_p), _ptr(sub),
            N.ref(cfg), flags, N.ref(res), cand, _stream(stream))
     batches = []
@@ -524,13 +530,17 @@ class Rasterizer:
 
     The capacity grows on demand: rs_bin_sort reports the instance count it needed, and a
     render whose count exceeded the capacity is redone with a larger one (one host
-    synchronisation per call on this path; fixed-capacity graph replay avoids it)."""
+    synchronisation per call on this path; fixed-capacity graph replay avoids it).
+    ``front`` (default): bin with rs_bin_sort_front, which leaves out the entries behind the
+    depth where every pixel of a tile has provably stopped; False keeps every list whole."""
 
-    def __init__(self, cfg: Optional[N.RsConfig] = None, device="cuda", capacity: int = 0, keys: bool = False):
+    def __init__(self, cfg: Optional[N.RsConfig] = None, device="cuda", capacity: int = 0, keys: bool = False,
+                 front: bool = True):
         self.cfg = cfg or config()
         self.device = device
         self.capacity = int(capacity)
         self.keys = keys
+        self.front = front
         self.ws_sort = Workspace(device)
         self.ws_bwd = Workspace(device)
         self.status = DeviceStatus(device)
@@ -550,7 +560,7 @@ class Rasterizer:
         proj = project(g, vb, self.cfg, self.status)
         while True:
             bins = self.bins_for(vb)
-            bin_sort(proj, vb, bins, self.ws_sort, self.status)
+            bin_sort(proj, vb, bins, self.ws_sort, self.status, front=self.front)
             st = self.status.read()
             if st["required"] <= bins.capacity:
                 break

@@ -6,8 +6,8 @@
 // thread, all of the first min(n_views, 16) views in one launch; stage 2 keeps the winner
 // and tries 1, 2, 4, ... and n_views views per launch (the views taken in order in
 // consecutive chunks) over the first min(n_views, max(views per launch, 16)) views.  Each
-// candidate runs project -> bin_sort -> render (image, T_final, last, importance) and,
-// with RS_TUNE_BACKWARD, render_backward: one untimed pass (which also sizes the instance
+// candidate runs project -> bin_sort (front lists with RS_TUNE_FRONT) -> render (image,
+// T_final, last, importance) and, with RS_TUNE_BACKWARD, render_backward: one untimed pass (which also sizes the instance
 // capacity), then three timed passes bracketed by CUDA events on the caller's stream.
 // The score is milliseconds per view.  A candidate whose chunks would need 2^32 or more
 // instances, or whose buffers cannot be allocated, is skipped.
@@ -83,11 +83,12 @@ extern "C" rs_status rs_autotune(const rs_gaussians* g, const rs_camera* cams, i
                                  int32_t flags, rs_tune_result* out, float* cand_ms, void* stream) {
   if (!g || !cams || !n_items || !cfg || !out || n_views <= 0 || g->n <= 0) return RS_ERR_INVALID_ARG;
   if (g->sh_degree < 0 || g->sh_degree > 3) return RS_ERR_UNSUPPORTED;
-  if (flags & ~(RS_TUNE_BACKWARD | RS_TUNE_FORCE)) return RS_ERR_INVALID_ARG;
+  if (flags & ~(RS_TUNE_BACKWARD | RS_TUNE_FORCE | RS_TUNE_FRONT)) return RS_ERR_INVALID_ARG;
   const bool bwd = (flags & RS_TUNE_BACKWARD) != 0;
+  const bool front = (flags & RS_TUNE_FRONT) != 0;
   int32_t cfg_bits[5];
   memcpy(cfg_bits, cfg, sizeof(cfg_bits));   // eps2d, near_plane, bg (batch excluded)
-  std::vector<int64_t> key = {n_views, g->n, g->sh_degree, bwd ? 1 : 0, subset_idx ? 1 : 0};
+  std::vector<int64_t> key = {n_views, g->n, g->sh_degree, bwd ? 1 : 0, subset_idx ? 1 : 0, front ? 1 : 0};
   for (int i = 0; i < 5; ++i) key.push_back(cfg_bits[i]);
   std::vector<int64_t> item_off(n_views + 1, 0);
   for (int32_t v = 0; v < n_views; ++v) {
@@ -197,7 +198,9 @@ extern "C" rs_status rs_autotune(const rs_gaussians* g, const rs_camera* cams, i
           if (bwd && !grow(bwd_ws, bwb)) return RS_ERR_CUDA;
           rs_bins bins{nullptr, vals.as<uint32_t>(), ranges.as<uint32_t>(), capacity};
           rs_status r = rs_project(g, &c.batch, &c_cfg, &proj, st, s);
-          if (r == RS_OK) r = rs_bin_sort(&proj, &c.batch, &bins, sort_ws.p, sort_ws.n, st, s);
+          if (r == RS_OK)
+            r = front ? rs_bin_sort_front(&proj, &c.batch, &bins, sort_ws.p, sort_ws.n, st, s)
+                      : rs_bin_sort(&proj, &c.batch, &bins, sort_ws.p, sort_ws.n, st, s);
           if (r == RS_OK)
             r = rs_render(&proj, &bins, &c.batch, &c_cfg, img.as<float>(), T.as<float>(), last.as<int32_t>(),
                           imp.as<uint32_t>(), g->n, s);

@@ -28,6 +28,7 @@
 //   (radix_tiles); k_ranges (super ranges); k_fine_layout (segments); k_fine_count;
 //   k_fine_seg_scan; k_fine_scan (ranges, K, capacity check); k_fine_scatter (vals,
 //   optional keys).
+#include "front_cut.cuh"
 #include "profile.cuh"
 #include "radix_tiles.cuh"
 #include "radsplat.h"
@@ -62,12 +63,16 @@ struct BinWs {
   uint32_t* work_s;           // [n_work_max]: super-tile of every segment
   uint32_t* seg_cnt;          // [n_work_max][16]: per (segment, tile) counts, then prefixes
   int64_t n_work_max;         // segments: at most capacity / kSegLen + one per super-tile
+  uint32_t* cut_acc;          // [kCutBuckets][n_tiles]: occlusion bound sums (rs_bin_sort_front)
+  uint32_t* cut_s;            // [n_tiles]: rank cut of every super-tile (rs_bin_sort_front)
+  uint32_t* wsum;             // [blocks][kEmitThreads / 32]: kept super instances per warp (front)
   uint32_t* counters;         // [0] super instances written, [2] instances written,
                               // [4], [5] work counters of the fine count and scatter,
                               // [6] item count (the depth sort's device count), [7] segments,
                               // [8..15] the super-tile sort's digits (shift, bits) of up to
                               // four passes, [16] items the depth sort kept (those with
-                              // instances); kCounterWords words in all
+                              // instances), [17] the largest tile cut (rs_bin_sort_front);
+                              // kCounterWords words in all
   size_t bytes;
 };
 
@@ -101,6 +106,9 @@ static BinWs bin_ws_layout(void* base, int64_t n_items, int64_t capacity, int n_
   w.work_s = reinterpret_cast<uint32_t*>(take((size_t)w.n_work_max * 4));
   w.seg_cnt = reinterpret_cast<uint32_t*>(take((size_t)w.n_work_max * kNF * 4));
   w.counters = reinterpret_cast<uint32_t*>(take(kCounterWords * 4));
+  w.cut_acc = reinterpret_cast<uint32_t*>(take((size_t)(n_tiles > 0 ? n_tiles : 1) * kCutBuckets * 4));
+  w.cut_s = reinterpret_cast<uint32_t*>(take((size_t)(n_tiles > 0 ? n_tiles : 1) * 4));
+  w.wsum = reinterpret_cast<uint32_t*>(take((size_t)(nblk > 0 ? nblk : 1) * (kEmitThreads / 32) * 4));
   w.bytes = off;
   return w;
 }
@@ -190,24 +198,149 @@ __device__ __forceinline__ uint32_t cover_mask(uint32_t c) {
   return (row * rep) << (kSuper * y0);                               // row repeated on rows y0 .. y1
 }
 
+// Per-lane data of one depth-ranked item for its expansion into super instances.
+struct SuperItem {
+  uint32_t item = 0;
+  uint32_t cnt = 0;     // cells of its super rect (0: no item)
+  uint32_t sbase = 0;   // the view's first super-tile id
+  uint32_t org = 0;     // super rect origin: x | y << 16
+  uint32_t dims = 1;    // super rect width | view's super-tile row length << 16
+  uint32_t edge = 0;    // cover fields of the rect's first/last super column and row | rows << 8
+};
+
+__device__ __forceinline__ SuperItem super_item(const uint32_t* __restrict__ order, const ushort4* __restrict__ rect,
+                                                const rs_view* __restrict__ views, int n_views,
+                                                const uint32_t* __restrict__ super_base, int64_t i, bool live) {
+  SuperItem s;
+  if (!live) return s;
+  s.item = order[i];
+  const ushort4 tr = rect[s.item];
+  const ushort4 sr = super_rect(tr);
+  s.cnt = (uint32_t)(sr.z - sr.x) * (uint32_t)(sr.w - sr.y);
+  if (s.cnt) {
+    const int v = find_view_by_item(views, n_views, (int64_t)s.item);
+    s.sbase = super_base[v];
+    s.org = (uint32_t)sr.x | ((uint32_t)sr.y << 16);
+    s.dims = (uint32_t)(sr.z - sr.x) | ((uint32_t)super_w(views[v]) << 16);
+    // first covered column inside the first super column, last inside the last one, etc.
+    const uint32_t fx0 = tr.x - kSuper * sr.x, fx1 = tr.z - 1 - kSuper * (sr.z - 1);
+    const uint32_t fy0 = tr.y - kSuper * sr.y, fy1 = tr.w - 1 - kSuper * (sr.w - 1);
+    s.edge = fx0 | (fx1 << 2) | (fy0 << 4) | (fy1 << 6) | ((uint32_t)(sr.w - sr.y) << 8);
+  }
+  return s;
+}
+
+// Cell e of a warp's expansion: the lane whose item owns it (a binary search over the
+// warp's inclusive prefix of cell counts), and its super-tile id and place in the owner's
+// super rect.  The owner's data travels in shuffles (packed 16-bit fields); the row inside
+// the rect comes from a float reciprocal with an exact integer correction.  Every lane of
+// the warp must call it; the result is meaningful for e < the warp's total only.
+struct SuperCell {
+  int owner;
+  uint32_t item, sid, tx, ty, rw, edge;
+};
+
+__device__ __forceinline__ SuperCell super_cell(const SuperItem& s, uint32_t incl, uint32_t excl, uint32_t e) {
+  SuperCell c;
+  int lo = 0;
+#pragma unroll
+  for (int sh = 16; sh > 0; sh >>= 1) {
+    const uint32_t v = __shfl_sync(0xffffffffu, incl, lo + sh - 1);
+    if (v <= e) lo += sh;
+  }
+  c.owner = lo < 31 ? lo : 31;
+  const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, c.owner);
+  c.item = __shfl_sync(0xffffffffu, s.item, c.owner);
+  const uint32_t o_sb = __shfl_sync(0xffffffffu, s.sbase, c.owner);
+  const uint32_t o_org = __shfl_sync(0xffffffffu, s.org, c.owner);
+  const uint32_t o_dims = __shfl_sync(0xffffffffu, s.dims, c.owner);
+  c.edge = __shfl_sync(0xffffffffu, s.edge, c.owner);
+  const uint32_t r = e - o_excl;
+  c.rw = o_dims & 0xffffu;   // >= 1
+  // ty = r / rw: the float estimate is within one of the quotient, then corrected
+  uint32_t ty = (uint32_t)(((float)r + 0.5f) * rcp_approx((float)c.rw));
+  if (ty * c.rw > r) --ty;
+  if ((ty + 1u) * c.rw <= r) ++ty;
+  c.ty = ty;
+  c.tx = r - ty * c.rw;
+  c.sid = o_sb + ((o_org >> 16) + ty) * (o_dims >> 16) + (o_org & 0xffffu) + c.tx;
+  return c;
+}
+
+// With the occlusion cut: whether super instance (item of depth rank `rank`, super-tile
+// sid) is kept, i.e. the super-tile's rank cut lies beyond the item.
+__device__ __forceinline__ bool super_kept(uint32_t sid, uint32_t rank, uint32_t n_super, const uint32_t* cut_s) {
+  return sid < n_super && rank < cut_s[sid];   // n_super is 0 for a rejected batch
+}
+
+// The super-tiles' rank cuts as the keep tests read them: a copy in shared memory (s) when
+// they fit, else the global array.  Contains a barrier: every thread of the CTA calls it.
+constexpr uint32_t kCutSmem = 8192;
+__device__ __forceinline__ const uint32_t* stage_cuts(const uint32_t* __restrict__ cut_s, uint32_t n_super,
+                                                      uint32_t* s) {
+  if (n_super > kCutSmem) return cut_s;
+  for (uint32_t k = threadIdx.x; k < n_super; k += blockDim.x) s[k] = cut_s[k];
+  __syncthreads();
+  return s;
+}
+
 // Super instances per block of kEmitThreads depth-sorted items, also added into the total
-// of the block's chunk of kCountChunk blocks (csum, zeroed by the caller).
+// of the block's chunk of kCountChunk blocks (csum, zeroed by the caller).  CUT: only the
+// instances that k_emit keeps (super_kept), counted by a warp-wide walk over the cells of
+// the warp's items, per warp into wsum as well; blocks whose items all lie beyond the
+// largest cut count 0 at once.
+template <bool CUT>
 __global__ void __launch_bounds__(kEmitThreads) k_count_blocks(const uint32_t* __restrict__ order,
                                                                const uint32_t* __restrict__ n_dev,
                                                                const ushort4* __restrict__ rect,
+                                                               const rs_view* __restrict__ views, int n_views,
+                                                               const uint32_t* __restrict__ super_base,
+                                                               const uint32_t* __restrict__ cut_s,
+                                                               const uint32_t* __restrict__ cut_max,
                                                                unsigned long long* __restrict__ bsum,
-                                                               unsigned long long* __restrict__ csum) {
+                                                               unsigned long long* __restrict__ csum,
+                                                               uint32_t* __restrict__ wsum) {
   __shared__ unsigned long long s[kEmitThreads / 32];
+  __shared__ uint32_t s_cut[CUT ? kCutSmem : 1];
+  const int lane = threadIdx.x & 31;
   const int64_t n = *n_dev;   // the items the depth sort kept (those with instances)
+  const int64_t lim = CUT ? min(n, (int64_t)*cut_max) : n;
   const int64_t i = (int64_t)blockIdx.x * kEmitThreads + threadIdx.x;
+  if (CUT && (int64_t)blockIdx.x * kEmitThreads >= lim) {   // uniform per CTA
+    if (threadIdx.x == 0) bsum[blockIdx.x] = 0ull;
+    return;
+  }
   unsigned long long c = 0;
-  if (i < n) {
-    const ushort4 sr = super_rect(rect[order[i]]);
-    c = (unsigned long long)(sr.z - sr.x) * (unsigned long long)(sr.w - sr.y);
+  if (!CUT) {
+    if (i < n) {
+      const ushort4 sr = super_rect(rect[order[i]]);
+      c = (unsigned long long)(sr.z - sr.x) * (unsigned long long)(sr.w - sr.y);
+    }
+  } else {
+    const SuperItem si = super_item(order, rect, views, n_views, super_base, i, i < lim);
+    uint32_t incl = si.cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t excl = incl - si.cnt;
+    const uint32_t ns = super_base[n_views];
+    const uint32_t* cuts = stage_cuts(cut_s, ns, s_cut);
+    const uint32_t first_rank = (uint32_t)(i - lane);
+    uint32_t kept = 0;
+    for (uint32_t e0 = 0; e0 < wtot; e0 += 32) {   // uniform per warp
+      const SuperCell sc = super_cell(si, incl, excl, e0 + lane);
+      kept += (uint32_t)__popc(
+          __ballot_sync(0xffffffffu, e0 + lane < wtot && super_kept(sc.sid, first_rank + (uint32_t)sc.owner, ns, cuts)));
+    }
+    if (lane == 0) wsum[blockIdx.x * (kEmitThreads / 32) + (threadIdx.x >> 5)] = kept;
+    c = lane == 0 ? kept : 0u;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = c;
+  if (lane == 0) s[threadIdx.x >> 5] = c;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long t = 0;
@@ -269,89 +402,63 @@ __global__ void __launch_bounds__(kCountChunk) k_count_top(unsigned long long* _
 
 // Expansion into super instances: each warp takes 32 consecutive depth-sorted items and
 // writes their super-tile ids, items and cover bytes contiguously (row-major inside each
-// super rect); lanes locate the item of their instance by a binary search over the warp's
-// inclusive prefix.  The owner's data travels in six shuffles (packed 16-bit fields), the
-// row inside its super rect comes from a float reciprocal with an exact integer correction,
-// and its cover byte from the four edge offsets of its rect (inner super-tiles are covered
-// whole).
-template <typename KeyT>
+// super rect), 32 cells per round (super_cell); the cover byte comes from the four edge
+// offsets of the rect (inner super-tiles are covered whole).  CUT: only the kept instances
+// (super_kept) are written, packed in the same order by a warp ballot per round, from the
+// warp's base given by k_count_blocks' per-warp counts.
+template <typename KeyT, bool CUT>
 __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restrict__ order,
                                                        const uint32_t* __restrict__ n_dev,
                                                        const ushort4* __restrict__ rect,
                                                        const rs_view* __restrict__ views, int n_views,
                                                        const uint32_t* __restrict__ super_base,
+                                                       const uint32_t* __restrict__ cut_s,
+                                                       const uint32_t* __restrict__ cut_max,
                                                        const unsigned long long* __restrict__ bpre, int64_t capacity,
+                                                       const uint32_t* __restrict__ wsum,
                                                        KeyT* __restrict__ skeys, uint32_t* __restrict__ svals,
                                                        uint8_t* __restrict__ saux) {
   __shared__ uint32_t s_wtot[kEmitThreads / 32];
+  __shared__ uint32_t s_cut[CUT ? kCutSmem : 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t n = *n_dev;   // the items the depth sort kept (those with instances)
+  const int64_t lim = CUT ? min(n, (int64_t)*cut_max) : n;
+  if (CUT && (int64_t)blockIdx.x * kEmitThreads >= lim) return;   // uniform per CTA: nothing kept
   const int64_t i = (int64_t)blockIdx.x * kEmitThreads + threadIdx.x;
-  uint32_t item = 0, cnt = 0, sbase = 0;
-  uint32_t org = 0;    // super rect origin: x | y << 16
-  uint32_t dims = 1;   // super rect width | view's super-tile row length << 16
-  uint32_t edge = 0;   // cover fields of the rect's first/last super column and row
-  if (i < n) {
-    item = order[i];
-    const ushort4 tr = rect[item];
-    const ushort4 sr = super_rect(tr);
-    cnt = (uint32_t)(sr.z - sr.x) * (uint32_t)(sr.w - sr.y);
-    if (cnt) {
-      const int v = find_view_by_item(views, n_views, (int64_t)item);
-      sbase = super_base[v];
-      org = (uint32_t)sr.x | ((uint32_t)sr.y << 16);
-      dims = (uint32_t)(sr.z - sr.x) | ((uint32_t)super_w(views[v]) << 16);
-      // first covered column inside the first super column, last inside the last one, etc.
-      const uint32_t fx0 = tr.x - kSuper * sr.x, fx1 = tr.z - 1 - kSuper * (sr.z - 1);
-      const uint32_t fy0 = tr.y - kSuper * sr.y, fy1 = tr.w - 1 - kSuper * (sr.w - 1);
-      edge = fx0 | (fx1 << 2) | (fy0 << 4) | (fy1 << 6) | ((uint32_t)(sr.w - sr.y) << 8);
-    }
-  }
-  uint32_t incl = cnt;
+  const SuperItem si = super_item(order, rect, views, n_views, super_base, i, i < lim);
+  uint32_t incl = si.cnt;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += y;
   }
   const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
-  if (lane == 0) s_wtot[warp] = wtot;
+  const uint32_t excl = incl - si.cnt;
+  const uint32_t ns = CUT ? super_base[n_views] : 0u;
+  const uint32_t* cuts = CUT ? stage_cuts(cut_s, ns, s_cut) : nullptr;
+  const uint32_t first_rank = (uint32_t)(i - lane);
+  if (lane == 0) s_wtot[warp] = CUT ? wsum[blockIdx.x * (kEmitThreads / 32) + warp] : wtot;
   __syncthreads();
   unsigned long long wbase = bpre[blockIdx.x];
   for (int w = 0; w < warp; ++w) wbase += s_wtot[w];
-  const uint32_t excl = incl - cnt;
+  uint32_t run = 0;   // CUT: instances the warp wrote in earlier rounds
   for (uint32_t e0 = 0; e0 < wtot; e0 += 32) {
     const uint32_t e = e0 + lane;
-    int lo = 0;
-#pragma unroll
-    for (int s = 16; s > 0; s >>= 1) {
-      const uint32_t v = __shfl_sync(0xffffffffu, incl, lo + s - 1);
-      if (v <= e) lo += s;
+    const SuperCell sc = super_cell(si, incl, excl, e);
+    const bool keep = e < wtot && (!CUT || super_kept(sc.sid, first_rank + (uint32_t)sc.owner, ns, cuts));
+    unsigned long long pos = wbase + e;
+    if (CUT) {
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      pos = wbase + run + (uint32_t)__popc(bal & ((1u << lane) - 1u));
+      run += (uint32_t)__popc(bal);
     }
-    const int owner = lo < 31 ? lo : 31;
-    const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, owner);
-    const uint32_t o_item = __shfl_sync(0xffffffffu, item, owner);
-    const uint32_t o_sb = __shfl_sync(0xffffffffu, sbase, owner);
-    const uint32_t o_org = __shfl_sync(0xffffffffu, org, owner);
-    const uint32_t o_dims = __shfl_sync(0xffffffffu, dims, owner);
-    const uint32_t o_edge = __shfl_sync(0xffffffffu, edge, owner);
-    if (e < wtot) {
-      const uint32_t r = e - o_excl;
-      const uint32_t rw = o_dims & 0xffffu;
-      // ty = r / rw: the float estimate is within one of the quotient, then corrected
-      uint32_t ty = (uint32_t)(((float)r + 0.5f) * rcp_approx((float)rw));
-      if (ty * rw > r) --ty;
-      if ((ty + 1u) * rw <= r) ++ty;
-      const uint32_t tx = r - ty * rw;
-      const unsigned long long pos = wbase + e;
-      if (pos < (unsigned long long)capacity) {
-        const uint32_t sx = (o_org & 0xffffu) + tx, sy = (o_org >> 16) + ty;
-        skeys[pos] = (KeyT)(o_sb + sy * (o_dims >> 16) + sx);
-        svals[pos] = o_item;
-        const uint32_t rh = o_edge >> 8;
-        const uint32_t lx0 = tx == 0 ? (o_edge & 3u) : 0u, lx1 = tx == rw - 1 ? ((o_edge >> 2) & 3u) : 3u;
-        const uint32_t ly0 = ty == 0 ? ((o_edge >> 4) & 3u) : 0u, ly1 = ty == rh - 1 ? ((o_edge >> 6) & 3u) : 3u;
-        saux[pos] = (uint8_t)(lx0 | (lx1 << 2) | (ly0 << 4) | (ly1 << 6));
-      }
+    if (keep && pos < (unsigned long long)capacity) {
+      skeys[pos] = (KeyT)sc.sid;
+      svals[pos] = sc.item;
+      const uint32_t rh = sc.edge >> 8;
+      const uint32_t lx0 = sc.tx == 0 ? (sc.edge & 3u) : 0u, lx1 = sc.tx == sc.rw - 1 ? ((sc.edge >> 2) & 3u) : 3u;
+      const uint32_t ly0 = sc.ty == 0 ? ((sc.edge >> 4) & 3u) : 0u, ly1 = sc.ty == rh - 1 ? ((sc.edge >> 6) & 3u) : 3u;
+      saux[pos] = (uint8_t)(lx0 | (lx1 << 2) | (ly0 << 4) | (ly1 << 6));
     }
   }
 }
@@ -794,16 +901,16 @@ size_t bin_sort_ws_bytes(const rs_view_batch* b, int64_t capacity) {
 
 // Super instances: expansion, stable sort on the super-tile id (KeyT-wide), ranges.
 // Returns which buffer set (0 or 1) holds the sorted items and cover bytes.
-template <typename KeyT>
+template <typename KeyT, bool CUT>
 static int super_instances(const BinWs& w, const uint32_t* order, const uint32_t* n_kept, const rs_projected* proj,
                            const rs_view_batch* batch, int64_t cap, int64_t nblk, int n_super_max, cudaStream_t s) {
   KeyT* k0 = reinterpret_cast<KeyT*>(w.skeys[0]);
   KeyT* k1 = reinterpret_cast<KeyT*>(w.skeys[1]);
   {
     prof::Scope ps("k_emit", s);
-    k_emit<KeyT><<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n_kept, reinterpret_cast<const ushort4*>(proj->rect),
-                                                         batch->views, batch->n_views, w.super_base, w.bsum, cap, k0,
-                                                         w.svals[0], w.saux[0]);
+    k_emit<KeyT, CUT><<<(unsigned)nblk, kEmitThreads, 0, s>>>(
+        order, n_kept, reinterpret_cast<const ushort4*>(proj->rect), batch->views, batch->n_views, w.super_base,
+        w.cut_s, w.counters + 17, w.bsum, cap, w.wsum, k0, w.svals[0], w.saux[0]);
   }
   const int cur = tiles::sort_pairs<KeyT>(k0, w.svals[0], k1, w.svals[1], w.counters, cap, bits_for(n_super_max),
                                           w.sweep, s, true,
@@ -815,12 +922,15 @@ static int super_instances(const BinWs& w, const uint32_t* order, const uint32_t
   return cur;
 }
 
-}  // namespace rs
+template <bool CUT>
+static int super_stage(const BinWs& w, const uint32_t* order, const uint32_t* n_kept, const rs_projected* proj,
+                       const rs_view_batch* batch, int64_t cap, int64_t nblk, int n_super_max, cudaStream_t s) {
+  return (n_super_max <= 65536) ? super_instances<uint16_t, CUT>(w, order, n_kept, proj, batch, cap, nblk, n_super_max, s)
+                                : super_instances<uint32_t, CUT>(w, order, n_kept, proj, batch, cap, nblk, n_super_max, s);
+}
 
-using namespace rs;
-
-extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* batch, const rs_bins* bins,
-                                 void* ws, size_t ws_bytes, rs_device_status* status, void* stream) {
+static rs_status bin_sort_impl(const rs_projected* proj, const rs_view_batch* batch, const rs_bins* bins, void* ws,
+                               size_t ws_bytes, rs_device_status* status, cudaStream_t s, bool front) {
   if (!proj || !batch || !bins) return RS_ERR_INVALID_ARG;
   if (!bins->vals || !bins->ranges || bins->capacity <= 0 || bins->capacity >= ((int64_t)1 << 32))
     return RS_ERR_INVALID_ARG;
@@ -828,9 +938,9 @@ extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* 
       batch->n_views <= 0)
     return RS_ERR_INVALID_ARG;
   if (!proj->rgb_d || !proj->rect || !proj->n_tiles) return RS_ERR_INVALID_ARG;
+  if (front && (!proj->xy || !proj->conic_o || batch->tile_w <= 0 || batch->tile_h <= 0)) return RS_ERR_INVALID_ARG;
   const BinWs w = bin_ws_layout(ws, batch->n_items, bins->capacity, batch->n_tiles, batch->n_views);
   if (!ws || ws_bytes < w.bytes || !aligned<uint4>(ws, 256)) return RS_ERR_WORKSPACE;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int64_t n = batch->n_items;
   const int64_t cap = bins->capacity;
   const float4* rgb_d = reinterpret_cast<const float4*>(proj->rgb_d);
@@ -860,21 +970,48 @@ extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* 
                                                  {"k_depth_sort_hist", "k_depth_sort_scan", "k_depth_sort"}, nullptr,
                                                  nullptr, nullptr, n_kept);
     const uint32_t* order = w.dvals[dcur];
+    if (front) {
+      // occlusion cut: bound sums over the nearest items, then a rank cut per super-tile
+      if (cudaMemsetAsync(w.cut_acc, 0, (size_t)batch->n_tiles * kCutBuckets * 4, s) != cudaSuccess) return RS_ERR_CUDA;
+      if (cudaMemsetAsync(w.cut_s, 0, (size_t)n_super_max * 4, s) != cudaSuccess) return RS_ERR_CUDA;
+      const int64_t wmax = (n + kCutWindowDiv - 1) / kCutWindowDiv;   // window bound (ranks)
+      {
+        prof::Scope ps("k_cut_accumulate", s);
+        // one warp per group of kCutGroup window items, striding: at most 8 CTAs of 8 warps per SM
+        const int64_t groups = (wmax + kCutGroup - 1) / kCutGroup;
+        const int64_t cgrid = (groups + 7) / 8 < 8 * kNumSMs ? (groups + 7) / 8 : 8 * kNumSMs;
+        k_cut_accumulate<<<(unsigned)cgrid, 256, 0, s>>>(
+            order, n_kept, reinterpret_cast<const float2*>(proj->xy), reinterpret_cast<const float4*>(proj->conic_o),
+            rect, batch->views, batch->n_views, batch->tile_w, batch->tile_h, batch->n_tiles, w.cut_acc);
+      }
+      {
+        prof::Scope ps("k_cut_tiles", s);
+        k_cut_tiles<<<(unsigned)((batch->n_tiles + 127) / 128), 128, 0, s>>>(
+            w.cut_acc, n_kept, batch->views, batch->n_views, w.super_base, batch->n_tiles, w.cut_s, w.counters + 17);
+      }
+    }
     // 2) super instances in depth order, sorted stably on the super-tile id
     const int64_t nblk = (n + kEmitThreads - 1) / kEmitThreads;
     if (cudaMemsetAsync(w.csum, 0, (size_t)((nblk + kCountChunk - 1) / kCountChunk) * 8, s) != cudaSuccess)
       return RS_ERR_CUDA;
     {
       prof::Scope ps("k_count_blocks", s);
-      k_count_blocks<<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n_kept, rect, w.bsum, w.csum);
+      if (front)
+        k_count_blocks<true><<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n_kept, rect, batch->views, batch->n_views,
+                                                                     w.super_base, w.cut_s, w.counters + 17, w.bsum,
+                                                                     w.csum, w.wsum);
+      else
+        k_count_blocks<false><<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n_kept, rect, batch->views,
+                                                                      batch->n_views, w.super_base, nullptr, nullptr,
+                                                                      w.bsum, w.csum, nullptr);
     }
     {
       prof::Scope ps("k_count_top", s);
       k_count_top<<<(unsigned)((nblk + kCountChunk - 1) / kCountChunk), kCountChunk, 0, s>>>(w.bsum, w.csum, nblk, cap,
                                                                                           w.counters, status);
     }
-    scur = (n_super_max <= 65536) ? super_instances<uint16_t>(w, order, n_kept, proj, batch, cap, nblk, n_super_max, s)
-                                  : super_instances<uint32_t>(w, order, n_kept, proj, batch, cap, nblk, n_super_max, s);
+    scur = front ? super_stage<true>(w, order, n_kept, proj, batch, cap, nblk, n_super_max, s)
+                 : super_stage<false>(w, order, n_kept, proj, batch, cap, nblk, n_super_max, s);
   }
   const uint32_t* svals = w.svals[scur];
   const uint8_t* saux = w.saux[scur];
@@ -917,4 +1054,18 @@ extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* 
                                                            w.counters + 5);
   }
   return launch_status();
+}
+
+}  // namespace rs
+
+using namespace rs;
+
+extern "C" rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* batch, const rs_bins* bins,
+                                 void* ws, size_t ws_bytes, rs_device_status* status, void* stream) {
+  return bin_sort_impl(proj, batch, bins, ws, ws_bytes, status, reinterpret_cast<cudaStream_t>(stream), false);
+}
+
+extern "C" rs_status rs_bin_sort_front(const rs_projected* proj, const rs_view_batch* batch, const rs_bins* bins,
+                                       void* ws, size_t ws_bytes, rs_device_status* status, void* stream) {
+  return bin_sort_impl(proj, batch, bins, ws, ws_bytes, status, reinterpret_cast<cudaStream_t>(stream), true);
 }

@@ -52,6 +52,24 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// max(a, b, c) in one instruction; a NaN operand is ignored unless all three are NaN.
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// The largest p2 of a thread's pixels, NaN (a done or not-yet-live pixel) ignored: it is at
+// least the cut exactly when some pixel's p2 is, so the warp-level support pre-test takes one
+// comparison per thread instead of one per pixel.
+template <int NP>
+__device__ __forceinline__ float max_p2(const float2 (&p2)[NP]) {
+  float m = fmaxf(p2[0].x, p2[0].y);
+#pragma unroll
+  for (int q = 1; q < NP; ++q) m = max3f(m, p2[q].x, p2[q].y);
+  return m;
+}
+
 // (x - u, x - u) for the thread's column u (nu = (-u, -u)).
 __device__ __forceinline__ float2 pair_dx(const BlendRec& r, float2 nu) { return __fadd2_rn(lo2(r.xy), nu); }
 

@@ -22,13 +22,6 @@
 
 namespace rs {
 
-// max(a, b, c) in one instruction (the importance maximum over a pixel pair and the running value).
-__device__ __forceinline__ float max3f(float a, float b, float c) {
-  float r;
-  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-  return r;
-}
-
 struct RenderArgs {
   const float2* xy;
   const float4* conic_o;
@@ -112,13 +105,11 @@ __global__ void __launch_bounds__(TW* TH / PX) k_render(RenderArgs a) {
       const BlendRec r = s_rec[j];
       const ColTerms ct = col_terms(r, pair_dx(r, nu));
       float2 p2[NP];
-      bool any = false;
 #pragma unroll
-      for (int q = 0; q < NP; ++q) {
-        p2[q] = pair_power(r, ct, pair_dy(r, nv[q]));
-        any |= p2[q].x >= r.bc.z || p2[q].y >= r.bc.z;   // NaN (done) compares false
-      }
-      if (!__any_sync(0xffffffffu, any)) continue;   // no pixel of the warp is in this record's support
+      for (int q = 0; q < NP; ++q) p2[q] = pair_power(r, ct, pair_dy(r, nv[q]));
+      // skip the record when no pixel of the warp is in its support; NaN (done) pixels drop
+      // out of the maximum, and all done gives NaN, which compares false
+      if (!__any_sync(0xffffffffu, max_p2(p2) >= r.bc.z)) continue;
       float m = 0.f;
       bool stop = false;
       bool st[PX];

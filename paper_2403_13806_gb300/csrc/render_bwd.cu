@@ -194,14 +194,13 @@ __global__ void __launch_bounds__(TW* TH / PX, 16) k_render_bwd(BwdBlendArgs a) 
       const float2 dx = pair_dx(r, nu);
       const ColTerms ct = col_terms(r, dx);
       float2 dy[NP], p2[NP];
-      bool any = false;
 #pragma unroll
       for (int q = 0; q < NP; ++q) {
         dy[q] = pair_dy(r, nv[q]);
         p2[q] = __fadd2_rn(pair_power(r, ct, dy[q]), gate[q]);
-        any |= p2[q].x >= r.bc.z || p2[q].y >= r.bc.z;   // NaN (not live) compares false
       }
-      if (!__any_sync(0xffffffffu, any)) {
+      // NaN (not live) pixels drop out of the maximum; none live gives NaN, which compares false
+      if (!__any_sync(0xffffffffu, max_p2(p2) >= r.bc.z)) {
         if (lane < 9) part[lane * PS + j] = 0.f;
         continue;
       }

@@ -12,11 +12,11 @@ def u32(t: torch.Tensor) -> np.ndarray:
     return t.detach().cpu().numpy().view(np.uint32)
 
 
-def gpu_forward(scene, cams, tile=(16, 16), subsets=None, importance=True, keys=False, capacity=0):
+def gpu_forward(scene, cams, tile=(16, 16), subsets=None, importance=True, keys=False, capacity=0, front=True):
     from paper_2403_13806_gb300 import api
     g = api.Gaussians.from_scene(scene)
     vb = api.ViewBatch(cams, scene.n, subsets=subsets, tile=tile)
-    rast = api.Rasterizer(capacity=capacity, keys=keys)
+    rast = api.Rasterizer(capacity=capacity, keys=keys, front=front)
     h = torch.zeros(scene.n, dtype=torch.int32, device="cuda") if importance else None
     out = rast.forward(g, vb, importance=h)
     torch.cuda.synchronize()
