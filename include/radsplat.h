@@ -260,16 +260,18 @@ rs_status rs_bin_sort(const rs_projected* proj, const rs_view_batch* batch,
  * rs_importance and rs_render_backward give the same results on either lists).
  * Blending stops a pixel before the first entry whose T(1 - alpha) falls below 1e-4.  For
  * every tile, the items among the nearest ceil(n / 32) in depth order whose alpha is at
- * least some alpha_lb >= 1/255 at every pixel centre of the tile (the smallest over the
+ * least some alpha_lb >= 0.05 at every pixel centre of the tile (the smallest over the
  * tile's four corner pixels, the power being concave; with margins for FP32 rounding)
  * bound T from above by the product of their (1 - alpha_lb); the depth rank by which that
- * product provably falls below 5e-5 (rounded up to the end of one of 64 rank buckets,
+ * product provably falls below 5e-5 (rounded up to the end of one of 16 rank buckets,
  * narrower at the front) is the tile's cut, and every super-tile of 4 x 4 tiles takes its
  * tiles' largest cut (a tile without one keeps its whole list, and so does its
  * super-tile).  vals[ranges[2t] .. ranges[2t+1]) is then the first part of rs_bin_sort's
  * list for tile t: the items ranked before the cut, in the same order; every entry the
  * blend composites or tests lies in it.  keys, capacity and status as in rs_bin_sort (the
  * instance count is that of the shortened lists).
+ * A batch with fewer than 32 items per tile on average (n_items < 32 n_tiles) gets whole
+ * lists, as from rs_bin_sort: its lists are too short for the cut to pay for its passes.
  * Reads proj->xy and proj->conic_o besides what rs_bin_sort reads, and batch->tile_w /
  * tile_h (the pixel rectangle of every tile).
  * ws: rs_workspace_size(RS_STAGE_BIN_SORT, batch, capacity) bytes (the same workspace).

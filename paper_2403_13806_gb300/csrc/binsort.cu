@@ -43,6 +43,7 @@ constexpr int kSegLen = 3840;       // super-list entries per fine work item (se
 constexpr int kTileBlock = 256;     // tiles per CTA of the per-tile scans
 constexpr int kCountChunk = 256;    // emission blocks per CTA of the block-count scan
 constexpr int kNF = kSuper * kSuper;
+constexpr int64_t kFrontItemsPerTile = 32;   // rs_bin_sort_front: below this, whole lists
 constexpr int kCounterWords = 32;   // the device counters block (see BinWs::counters)
 
 struct BinWs {
@@ -63,7 +64,8 @@ struct BinWs {
   uint32_t* work_s;           // [n_work_max]: super-tile of every segment
   uint32_t* seg_cnt;          // [n_work_max][16]: per (segment, tile) counts, then prefixes
   int64_t n_work_max;         // segments: at most capacity / kSegLen + one per super-tile
-  uint32_t* cut_acc;          // [kCutBuckets][n_tiles]: occlusion bound sums (rs_bin_sort_front)
+  uint32_t* cut_acc;          // [kCutBuckets][n_tiles]: occlusion bound sums (rs_bin_sort_front);
+                              // cut_s follows it directly (zeroed together)
   uint32_t* cut_s;            // [n_tiles]: rank cut of every super-tile (rs_bin_sort_front)
   uint32_t* wsum;             // [blocks][kEmitThreads / 32]: kept super instances per warp (front)
   uint32_t* counters;         // [0] super instances written, [2] instances written,
@@ -121,9 +123,13 @@ __device__ __forceinline__ int super_h(const rs_view& v) { return (v.tiles_y + k
 // and no such key equals the sort's all-ones sentinel.  Items that emit nothing (culled, or
 // off the image: n_tiles = 0) get the sentinel, which the first sort pass drops, so the
 // later passes and the emission order only the items that have instances.
+// For rs_bin_sort_front the grid also zeroes the occlusion cut's bound sums and super-tile
+// cuts (z, nz 16-byte words; nullptr / 0 otherwise), which the cut kernels use next.
 __global__ void k_depth_keys(const float4* __restrict__ rgb_d, const uint32_t* __restrict__ n_tiles, int64_t n,
-                             uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+                             uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, uint4* __restrict__ z,
+                             int64_t nz) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int64_t k = i; k < nz; k += (int64_t)gridDim.x * blockDim.x) z[k] = make_uint4(0u, 0u, 0u, 0u);
   if (i >= n) return;
   keys[i] = n_tiles[i] ? (__float_as_uint(rgb_d[i].w) & 0x7fffffffu) : 0xffffffffu;
   vals[i] = (uint32_t)i;
@@ -939,6 +945,9 @@ static rs_status bin_sort_impl(const rs_projected* proj, const rs_view_batch* ba
     return RS_ERR_INVALID_ARG;
   if (!proj->rgb_d || !proj->rect || !proj->n_tiles) return RS_ERR_INVALID_ARG;
   if (front && (!proj->xy || !proj->conic_o || batch->tile_w <= 0 || batch->tile_h <= 0)) return RS_ERR_INVALID_ARG;
+  // with fewer than kFrontItemsPerTile items per tile on average the lists are too short for
+  // the occlusion cut to pay for its passes: whole lists (the same results)
+  if (front && batch->n_items < kFrontItemsPerTile * (int64_t)batch->n_tiles) front = false;
   const BinWs w = bin_ws_layout(ws, batch->n_items, bins->capacity, batch->n_tiles, batch->n_views);
   if (!ws || ws_bytes < w.bytes || !aligned<uint4>(ws, 256)) return RS_ERR_WORKSPACE;
   const int64_t n = batch->n_items;
@@ -961,7 +970,13 @@ static rs_status bin_sort_impl(const rs_projected* proj, const rs_view_batch* ba
     // 1) items by depth (four 8-bit passes; an even count leaves the result in buffer 0)
     {
       prof::Scope ps("k_depth_keys", s);
-      k_depth_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rgb_d, proj->n_tiles, n, w.dkeys[0], w.dvals[0]);
+      // front: the bound sums and the super-tile cuts, adjacent in the workspace, are zeroed
+      // here (their reserved bytes are whole multiples of 256)
+      const int64_t nz = front ? (int64_t)((reinterpret_cast<char*>(w.cut_s) - reinterpret_cast<char*>(w.cut_acc)) +
+                                           align_up((size_t)n_super_max * 4, 256)) / 16
+                               : 0;
+      k_depth_keys<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rgb_d, proj->n_tiles, n, w.dkeys[0], w.dvals[0],
+                                                             front ? reinterpret_cast<uint4*>(w.cut_acc) : nullptr, nz);
     }
     // the first pass drops the items without instances; counters[16] = the items kept
     uint32_t* n_kept = w.counters + 16;
@@ -972,8 +987,6 @@ static rs_status bin_sort_impl(const rs_projected* proj, const rs_view_batch* ba
     const uint32_t* order = w.dvals[dcur];
     if (front) {
       // occlusion cut: bound sums over the nearest items, then a rank cut per super-tile
-      if (cudaMemsetAsync(w.cut_acc, 0, (size_t)batch->n_tiles * kCutBuckets * 4, s) != cudaSuccess) return RS_ERR_CUDA;
-      if (cudaMemsetAsync(w.cut_s, 0, (size_t)n_super_max * 4, s) != cudaSuccess) return RS_ERR_CUDA;
       const int64_t wmax = (n + kCutWindowDiv - 1) / kCutWindowDiv;   // window bound (ranks)
       {
         prof::Scope ps("k_cut_accumulate", s);

@@ -3,8 +3,9 @@
 // produces the front of each list that the blend of Eq. render-gs can reach.
 //
 // The bound.  Blending stops a pixel before the first entry whose T (1 - alpha) falls below
-// 1e-4, and T only decreases.  Take an item whose alpha stays at or above some alpha_lb at
-// every pixel centre of a tile: at each such entry the pixel either composites it, which
+// 1e-4, and T only decreases.  Take an item whose alpha stays at or above some alpha_lb
+// >= kCutAlphaMin > 1/255 at every pixel centre of a tile (so the blend's skip test never
+// drops it there): at each such entry the pixel either composites it, which
 // multiplies T by at most 1 - alpha_lb, or has already stopped.  Once the product of
 // (1 - alpha_lb) over the items ranked before some point is below 1e-4 (with a factor 2 to
 // spare for the kernels' rounding of T), every pixel of the tile has stopped by then.
@@ -24,7 +25,7 @@
 //
 // Where.  The accumulation looks at the nearest items only (a window of the first
 // ceil(n / 32) depth ranks), in kCutBuckets rank buckets that widen with the rank (bucket b
-// ends at rank ceil(W (b + 1)^2 / 64^2)): a tile's cut is the end of the first bucket at
+// ends at rank ceil(W (b + 1)^2 / 16^2)): a tile's cut is the end of the first bucket at
 // which its prefix sum passes the threshold.  A tile that is not saturated within the
 // window gets no cut (its list stays whole), and a super-tile's cut is the largest of its
 // tiles' cuts, so every tile list is a prefix of the full list that holds every entry the
@@ -34,9 +35,9 @@
 // lg2.approx): their documented errors (a few units in the last place of 2^x; for log2 an
 // absolute 2^-22 on [0.5, 2) and two ulps elsewhere) are far inside the relative margins
 // 2^-12 on alpha_lb and 2^-10 on -log2(1 - alpha_lb), whose smallest value here is
-// -log2(1 - 1/255) ~ 0.0057.  The per-item filters (opacity above 1/255, region wide
-// enough for a tile, the column spans) only choose which pairs are evaluated: a pair they
-// leave out gives no bound, which can only delay a cut.
+// -log2(1 - kCutAlphaMin) ~ 0.074.  The per-item filters (opacity above kCutAlphaMin,
+// region wide enough for a tile, the column spans) only choose which pairs are evaluated:
+// a pair they leave out gives no bound, which can only delay a cut.
 #pragma once
 
 #include "blend.cuh"
@@ -44,16 +45,20 @@
 
 namespace rs {
 
-constexpr int kCutBuckets = 64;         // rank buckets of the window
+constexpr int kCutBuckets = 16;         // rank buckets of the window
 constexpr uint32_t kCutWindowDiv = 32;  // window: the nearest ceil(n_kept / 32) items
 constexpr float kCutScale = 4096.f;     // fixed point of -log2(1 - alpha_lb)
 // prefix sums at or above this give a product of (1 - alpha_lb) <= 2^-14.307 < 5e-5
 constexpr uint32_t kCutThreshold = 58600u;
 constexpr uint32_t kNoCut = 0xffffffffu;
 constexpr int kCutGroup = 8;            // window items per warp and group in k_cut_accumulate
+// Only pairs with alpha_lb >= kCutAlphaMin add to the sums (a pair left out only delays a
+// cut): in the dense headline scene this evaluates 2.4x fewer pairs than alpha_lb >= 1/255
+// for 12% more listed instances.
+constexpr float kCutAlphaMin = 0.05f;
 
 // The window's ranks [0, W); bucket b holds the ranks [E(b), E(b + 1)) with
-// E(b) = ceil(W b^2 / 64^2): narrow buckets at the front, where the tiles of a dense scene
+// E(b) = ceil(W b^2 / 16^2): narrow buckets at the front, where the tiles of a dense scene
 // saturate, so that the cut (the end of a bucket) lies close to the saturating rank.
 __device__ __forceinline__ uint32_t cut_window(uint32_t n_kept) { return (n_kept + kCutWindowDiv - 1) / kCutWindowDiv; }
 
@@ -89,15 +94,15 @@ __device__ __forceinline__ uint32_t cut_contribution(const CutItem& it, float u0
   const float mag = fabsf(it.A) * ax * ax + fabsf(it.B) * ax * ay + fabsf(it.C) * ay * ay;
   const float L = pmin - fmaf(mag, 0x1p-19f, 0x1p-40f);
   const float a_lb = fminf(kAlphaMax, it.o * ex2_approx(fmaxf(L, -126.f))) * (1.f - 0x1p-12f);
-  if (!(a_lb >= kAlphaMin)) return 0u;
+  if (!(a_lb >= kCutAlphaMin)) return 0u;
   const float l = -__log2f(1.f - a_lb) * (kCutScale * (1.f - 0x1p-10f));
   return (uint32_t)l;   // truncation: rounded down
 }
 
 // Per-item part of the bound: the form's coefficients as the blend rounds them and whether
 // the item can give a bound at all (positive definite and well conditioned, opacity above
-// 1/255, and an alpha >= 1/255 region wide enough to hold a whole tile: its semi-minor
-// axis^2 must reach (min(tile_w, tile_h) - 1)^2 / 4).
+// kCutAlphaMin, and an alpha >= kCutAlphaMin region wide enough to hold a whole tile: its
+// semi-minor axis^2 must reach (min(tile_w, tile_h) - 1)^2 / 4).
 __device__ __forceinline__ bool cut_item(const float4 co, const ushort4 tr, int tile_w, int tile_h, CutItem& it) {
   const float A = __fmul_rn(-0.5f * kLog2e, co.x), B = __fmul_rn(-kLog2e, co.y), C = __fmul_rn(-0.5f * kLog2e, co.z);
   // eigenvalues of -[[A, B/2], [B/2, C]] (A, C < 0 for a positive definite conic)
@@ -105,7 +110,7 @@ __device__ __forceinline__ bool cut_item(const float4 co, const ushort4 tr, int 
   const float rt = sqrtf(h * h + 0.25f * B * B);
   const float lam = -0.5f * (A + C) - rt, lam_max = -0.5f * (A + C) + rt;
   const float size = fabsf(A) + fabsf(B) + fabsf(C);
-  const float lvl = __log2f(255.f * co.w);   // > 0 iff o > 1/255 (a filter: rounding only moves it)
+  const float lvl = __log2f(co.w * (1.f / kCutAlphaMin));   // > 0 iff o > kCutAlphaMin (a filter)
   const float s = 0.5f * (float)(min(tile_w, tile_h) - 1);
   it.A = A;
   it.B = B;
@@ -154,7 +159,7 @@ __device__ __forceinline__ void cut_row_span(const CutItem& it, float lv, float 
 // What the pairs of one window item read, staged in shared memory by its lane.
 struct CutSlot {
   CutItem it;
-  float lv;                   // p2 >= lv  <=>  o 2^p2 >= 1/255
+  float lv;                   // p2 >= lv  <=>  o 2^p2 >= kCutAlphaMin
   int gx0, gx1, gy0;          // tile rect: columns gx0..gx1, first row gy0
   int width, height, tiles_x;
   uint32_t tile_base;
@@ -194,7 +199,7 @@ __global__ void __launch_bounds__(256) k_cut_accumulate(const uint32_t* __restri
         const float2 p = xy[item];
         sl.it.x = p.x;
         sl.it.y = p.y;
-        sl.lv = -__log2f(255.f * co.w);
+        sl.lv = -__log2f(co.w * (1.f / kCutAlphaMin));
         const rs_view& cam = views[find_view_by_item(views, n_views, (int64_t)item)];
         sl.gx0 = tr.x;
         sl.gx1 = (int)tr.z - 1;

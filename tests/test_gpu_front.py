@@ -116,18 +116,29 @@ def test_over_65536_tiles_32_bit_super_keys():
 
 @pytest.mark.parametrize("tile", [(16, 16), (32, 8), (8, 8)])
 def test_config0_tile_shapes(tile):
-    """2k Gaussians in front of a 128x128 camera: few tiles saturate, and the rest keep their
-    whole lists."""
-    scene, cams = synth.config0()
+    """20k Gaussians of the config-0 distribution in front of a 128x128 camera (at least 32
+    items per tile for every shape, so the cut runs): some tiles saturate, the rest keep
+    their whole lists."""
+    scene, cams = synth.config0(n=20_000)
     vb, res = both(scene, cams, tile=tile)
     check_same(vb, res)
 
 
-def test_occluders_cut_every_list_short():
-    """config 0 behind five large, nearly opaque Gaussians covering the image (alpha > 0.9 at
-    every pixel): every tile saturates within the first few depth ranks, so each front list
-    holds the occluders and at most a couple of other entries."""
+def test_sparse_batch_bins_whole_lists():
+    """config 0 itself: 2k Gaussians over 64 tiles of 16x16, 31 items per tile, fewer than
+    32: the call bins whole lists, as rs_bin_sort does."""
     scene, cams = synth.config0()
+    vb, res = both(scene, cams)
+    Kw, Kf = check_same(vb, res)
+    assert Kf == Kw
+
+
+def test_occluders_cut_every_list_short():
+    """8k Gaussians of the config-0 distribution behind five large, nearly opaque Gaussians
+    covering the image (alpha > 0.9 at every pixel): every tile saturates within the first
+    few depth ranks, so each front list holds the occluders and at most a couple of other
+    entries."""
+    scene, cams = synth.config0(n=8000)
     scene.means[:, :5] = np.array([[0.0, 0.3, -0.3, 0.0, 0.0], [0.0, 0.0, 0.0, 0.3, -0.3], [1.0] * 5], np.float32)
     scene.log_scales[:, :5] = 1.0
     scene.opacity_logit[:5] = 6.0
@@ -138,8 +149,8 @@ def test_occluders_cut_every_list_short():
 
 
 def test_transparent_scene_keeps_whole_lists():
-    """Opacities just above 1/255: no tile can saturate, so nothing is cut."""
-    scene, cams = synth.config0()
+    """Opacities just above 1/255 (8k Gaussians): no tile can saturate, so nothing is cut."""
+    scene, cams = synth.config0(n=8000)
     scene.opacity_logit[:] = -5.0
     vb, res = both(scene, cams)
     Kw, Kf = check_same(vb, res)
