@@ -1008,7 +1008,7 @@ def probe_peaks(N, torch, dev, reps=5):
 # of the sources the kernel was built from.  A capture stays valid only while those sources
 # are unchanged; otherwise the roofline reports traffic as null.
 NCU_TRAFFIC = {
-    "k_render_bwd": {"bytes_per_view": 25182976, "files": ['render_bwd.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "ce5f65528d017c7f",
+    "k_render_bwd": {"bytes_per_view": 25196544, "files": ['render_bwd.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "f221ffcc78ae3042",
                 "profile": "k_render_bwd_1M_1view.md"},
     "k_render_importance": {"bytes_per_view": 4441600, "files": ['render.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "d09583f05603764e",
                 "profile": "k_render_1M_1view.md"},
