@@ -32,7 +32,8 @@ if ROOT not in sys.path:
 
 METRIC = "FPS and fwd+bwd ms/view at 1M Gaussians, 1280×832; batched vs plain on one GB300"
 N_GAUSSIANS = 1_000_000
-FRONT = True   # tile lists binned by rs_bin_sort_front (--lists whole: rs_bin_sort)
+FRONT_ALLOWED = True   # --lists front: the autotuner may choose front lists (rs_bin_sort_front)
+FRONT = True           # the lists the step bins: the autotuner's choice, else FRONT_ALLOWED
 WIDTH, HEIGHT = 1280, 832
 
 
@@ -155,6 +156,7 @@ def peaks():
 # ------------------------------------------------------------------ our arm
 
 def run_ours(args):
+    global FRONT
     import torch
     import torch.distributed as dist
     from paper_2403_13806_gb300 import api, synth, _native as N
@@ -178,7 +180,8 @@ def run_ours(args):
 
     # tile shape and views per launch from the autotuner (setup, untimed; cached per workload)
     if args.tile == "auto":
-        tune = api.autotune(g, cams, cfg=cfg, backward=True, front=FRONT)
+        tune = api.autotune(g, cams, cfg=cfg, backward=True, front=FRONT_ALLOWED)
+        FRONT = tune["front"]
         tile, B = tune["tile"], tune["views_per_launch"]
         cfg = api.config(batch=tune["smem_batch"])
     else:
@@ -408,7 +411,7 @@ def run_ours(args):
             if "k_render_importance" in kernel_ms else None,
             "autotune": None if tune is None else {
                 "tile": f"{tile[0]}x{tile[1]}", "smem_batch": tune["smem_batch"], "views_per_launch": B,
-                "ms_per_view": round(tune["ms_per_view"], 5),
+                "ms_per_view": round(tune["ms_per_view"], 5), "front_lists": tune["front"],
                 "stage1_ms_per_view": {f"{a}x{b}/{m}": round(v, 5) for (a, b, m), v in tune["stage1"].items()},
                 "stage2_ms_per_view": {str(k): round(v, 5) for k, v in tune["stage2"].items()}},
             "stage_ms_per_step": {k: round(v, 5) for k, v in stage_ms.items()},
@@ -513,12 +516,12 @@ def uneven_bench(api, N, torch, dev, n_views, reps):
     cams, subsets = synth.config4(scene, n_views=n_views)   # the first n_views of the 256-view set
     g = api.Gaussians.from_scene(scene, device=dev)
     grads = [torch.zeros_like(t) for t in g.tensors()]
-    tune = api.autotune(g, cams[:32], subsets=subsets[:32], backward=True, front=FRONT)
+    tune = api.autotune(g, cams[:32], subsets=subsets[:32], backward=True, front=FRONT_ALLOWED)
     B = tune["views_per_launch"]
     cfg = api.config(batch=tune["smem_batch"])
 
-    def make(chunks, tile, cfg_):
-        r = api.Rasterizer(cfg=cfg_, device=dev, front=FRONT)
+    def make(chunks, tile, cfg_, front):
+        r = api.Rasterizer(cfg=cfg_, device=dev, front=front)
         vbs = [api.ViewBatch(cams[i:i + chunks], scene.n, subsets=subsets[i:i + chunks], tile=tile, device=dev)
                for i in range(0, len(cams), chunks)]
         for vb in vbs:
@@ -543,16 +546,16 @@ def uneven_bench(api, N, torch, dev, n_views, reps):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / (reps * len(cams))
 
-    plan = make(B, tune["tile"], cfg)
+    plan = make(B, tune["tile"], cfg, tune["front"])
     batched = timed(plan)
     del plan
-    plan = make(1, (16, 16), api.config())
+    plan = make(1, (16, 16), api.config(), FRONT_ALLOWED)
     plain = timed(plan)
     del plan
     torch.cuda.empty_cache()
     return {"views": len(cams), "pixels": int(sum(c["width"] * c["height"] for c in cams)),
             "items": int(sum(len(s) for s in subsets)), "tile": f"{tune['tile'][0]}x{tune['tile'][1]}",
-            "smem_batch": tune["smem_batch"], "views_per_launch": B,
+            "smem_batch": tune["smem_batch"], "views_per_launch": B, "front_lists": tune["front"],
             "batched_ms_per_view": round(batched, 4), "plain_ms_per_view": round(plain, 4),
             "batched_over_plain_speedup": round(plain / batched, 3),
             "note": "autotuned on the first 32 views; Rasterizer calls (one host read of the instance count per "
@@ -1304,9 +1307,9 @@ def run_probes():
 
 
 def main():
-    global FRONT
+    global FRONT, FRONT_ALLOWED
     args = parse()
-    FRONT = args.lists == "front"
+    FRONT = FRONT_ALLOWED = args.lists == "front"
     if args.probes:
         run_probes()
     elif args.cpu_report:

@@ -499,12 +499,13 @@ typedef struct rs_tune_result {
   float ms_per_view;          /* measured device time per view of the choice */
   int32_t cached;             /* 1: taken from the cache without measuring */
   int32_t n_candidates;       /* candidates measured by this call (0 if cached) */
-  int32_t reserved;
+  int32_t front_lists;        /* 1: bin with rs_bin_sort_front (RS_TUNE_FRONT and faster), 0: rs_bin_sort */
 } rs_tune_result;
 
 #define RS_TUNE_BACKWARD 1  /* time render_backward too (training), else the forward only */
 #define RS_TUNE_FORCE 2     /* measure even when the workload is cached */
-#define RS_TUNE_FRONT 4     /* bin with rs_bin_sort_front (else rs_bin_sort) */
+#define RS_TUNE_FRONT 4     /* bin with rs_bin_sort_front (else rs_bin_sort); the choice is
+                               timed on whole lists too and the faster kept (front_lists) */
 
 /* rs_autotune -- chooses the tile shape, the Gaussians staged per shared-memory batch of
  * the blend kernels and the views per launch for rendering the given views (the paper has
@@ -515,7 +516,9 @@ typedef struct rs_tune_result {
  * (1) every tile shape (16x16, 32x8, 8x8) x staging batch (1, 2, 4 records per thread),
  * all of the first min(n_views, 16) views in one launch per stage; (2) with the winner of
  * (1), views per launch 1, 2, 4, ... and n_views over the first min(n_views,
- * max(views per launch, 16)) views.  Each candidate gets one untimed pass and three timed
+ * max(views per launch, 16)) views; (3) with RS_TUNE_FRONT, the choice of (2) once more on
+ * whole lists (rs_bin_sort), keeping the faster binning (front_lists, also counted in
+ * n_candidates).  Each candidate gets one untimed pass and three timed
  * passes (CUDA events on `stream`); the score is device milliseconds per view.  The choice
  * is cached under the workload (view sizes, n_items, g->n, sh_degree, subset use,
  * RS_TUNE_BACKWARD, RS_TUNE_FRONT, cfg apart from batch); a later call with the same

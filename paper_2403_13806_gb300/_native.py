@@ -72,7 +72,7 @@ class RsDeviceStatus(ctypes.Structure):
 
 class RsTuneResult(ctypes.Structure):
     _fields_ = [("tile_w", c_int32), ("tile_h", c_int32), ("smem_batch", c_int32), ("views_per_launch", c_int32),
-                ("ms_per_view", c_float), ("cached", c_int32), ("n_candidates", c_int32), ("reserved", c_int32)]
+                ("ms_per_view", c_float), ("cached", c_int32), ("n_candidates", c_int32), ("front_lists", c_int32)]
 
 
 RS_TUNE_BACKWARD, RS_TUNE_FORCE, RS_TUNE_FRONT = 1, 2, 4

@@ -361,7 +361,8 @@ def autotune(g: Gaussians, cams: Sequence[dict], subsets: Optional[Sequence] = N
     (the Rasterizer's default), else by rs_bin_sort.
 
     Returns {"tile": (w, h), "smem_batch": rs_config.batch, "views_per_launch", "cached",
-    "ms_per_view", "n_candidates", "stage1": {(w, h, records per thread): ms per view},
+    "ms_per_view", "n_candidates", "front" (bin with front lists: ``front`` given and faster
+    than whole lists for the choice), "stage1": {(w, h, records per thread): ms per view},
     "stage2": {views per launch: ms per view}}."""
     cfg = cfg or config()
     V = len(cams)
@@ -398,7 +399,7 @@ def autotune(g: Gaussians, cams: Sequence[dict], subsets: Optional[Sequence] = N
             stage2[bb] = float(ms)
     return {"tile": (res.tile_w, res.tile_h), "smem_batch": res.smem_batch, "views_per_launch": res.views_per_launch,
             "cached": bool(res.cached), "ms_per_view": float(res.ms_per_view), "n_candidates": res.n_candidates,
-            "stage1": stage1, "stage2": stage2}
+            "front": bool(res.front_lists), "stage1": stage1, "stage2": stage2}
 
 
 def ssim_loss(image: torch.Tensor, target: torch.Tensor, width: int, height: int, lam: float = 0.2,

@@ -5,7 +5,8 @@
 // Stage 1 crosses the tile shapes 16x16, 32x8 and 8x8 with 1, 2 and 4 staged records per
 // thread, all of the first min(n_views, 16) views in one launch; stage 2 keeps the winner
 // and tries 1, 2, 4, ... and n_views views per launch (the views taken in order in
-// consecutive chunks) over the first min(n_views, max(views per launch, 16)) views.  Each
+// consecutive chunks) over the first min(n_views, max(views per launch, 16)) views; with
+// RS_TUNE_FRONT stage 3 times that choice on whole lists as well and keeps the faster.  Each
 // candidate runs project -> bin_sort (front lists with RS_TUNE_FRONT) -> render (image,
 // T_final, last, importance) and, with RS_TUNE_BACKWARD, render_backward: one untimed pass (which also sizes the instance
 // capacity), then three timed passes bracketed by CUDA events on the caller's stream.
@@ -86,6 +87,7 @@ extern "C" rs_status rs_autotune(const rs_gaussians* g, const rs_camera* cams, i
   if (flags & ~(RS_TUNE_BACKWARD | RS_TUNE_FORCE | RS_TUNE_FRONT)) return RS_ERR_INVALID_ARG;
   const bool bwd = (flags & RS_TUNE_BACKWARD) != 0;
   const bool front = (flags & RS_TUNE_FRONT) != 0;
+  bool use_front = front;   // the binning the candidates run (stage 3 tries whole lists too)
   int32_t cfg_bits[5];
   memcpy(cfg_bits, cfg, sizeof(cfg_bits));   // eps2d, near_plane, bg (batch excluded)
   std::vector<int64_t> key = {n_views, g->n, g->sh_degree, bwd ? 1 : 0, subset_idx ? 1 : 0, front ? 1 : 0};
@@ -199,7 +201,7 @@ extern "C" rs_status rs_autotune(const rs_gaussians* g, const rs_camera* cams, i
           rs_bins bins{nullptr, vals.as<uint32_t>(), ranges.as<uint32_t>(), capacity};
           rs_status r = rs_project(g, &c.batch, &c_cfg, &proj, st, s);
           if (r == RS_OK)
-            r = front ? rs_bin_sort_front(&proj, &c.batch, &bins, sort_ws.p, sort_ws.n, st, s)
+            r = use_front ? rs_bin_sort_front(&proj, &c.batch, &bins, sort_ws.p, sort_ws.n, st, s)
                       : rs_bin_sort(&proj, &c.batch, &bins, sort_ws.p, sort_ws.n, st, s);
           if (r == RS_OK)
             r = rs_render(&proj, &bins, &c.batch, &c_cfg, img.as<float>(), T.as<float>(), last.as<int32_t>(),
@@ -269,13 +271,23 @@ extern "C" rs_status rs_autotune(const rs_gaussians* g, const rs_camera* cams, i
     }
     if (best.ms_per_view < 0.f) best = s1;
   }
+  // stage 3 (RS_TUNE_FRONT): the choice again on whole lists; the faster binning is kept
+  best.front_lists = front ? 1 : 0;
+  if (err == RS_OK && front && best.ms_per_view >= 0.f) {
+    use_front = false;
+    float ms = -1.f;
+    err = measure(best.tile_w, best.tile_h, best.smem_batch, best.views_per_launch, ms);
+    if (err == RS_OK && ms >= 0.f && ms < best.ms_per_view) {
+      best.ms_per_view = ms;
+      best.front_lists = 0;
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (err != RS_OK) return err;
   if (timed == 0) return RS_ERR_CAPACITY;
   best.cached = 0;
   best.n_candidates = timed;
-  best.reserved = 0;
   {
     std::lock_guard<std::mutex> lk(g_mu);
     g_cache[key] = best;

@@ -38,15 +38,20 @@ def render_chunks(g, cams, tile, batch, subsets=None, smem_batch=0):
     return imgs
 
 
-def check_choice(r, n_views):
+def check_choice(r, n_views, front=True):
     n_batches = len(r["stage2"])
     assert len(r["stage1"]) == 9 and all(ms > 0 for ms in r["stage1"].values())
-    assert r["n_candidates"] == 9 + n_batches
+    # stage 3 (front lists offered) times the choice once more on whole lists
+    assert r["n_candidates"] == 9 + n_batches + (1 if front else 0)
     # stage 1 picks the fastest tile shape and staging batch, stage 2 the fastest views per launch
     tw, th, m = min(r["stage1"], key=r["stage1"].get)
     assert r["tile"] == (tw, th) and r["smem_batch"] == m * api.blend_threads((tw, th))
     assert r["views_per_launch"] == min(r["stage2"], key=r["stage2"].get)
-    assert r["ms_per_view"] == pytest.approx(min(r["stage2"].values()), rel=1e-6)
+    best2 = min(r["stage2"].values())
+    if r["front"]:   # front lists kept: stage 2's time
+        assert front and r["ms_per_view"] == pytest.approx(best2, rel=1e-6)
+    else:            # whole lists: not offered, or faster than stage 2's front-list time
+        assert r["ms_per_view"] == pytest.approx(best2, rel=1e-6) if not front else r["ms_per_view"] < best2
     assert set(r["stage2"]) <= set([1, 2, 4, 8, 16, 32, 64, 128, n_views])
 
 
@@ -66,7 +71,11 @@ def test_autotune_measures_chooses_and_caches():
     fwd = api.autotune(g, cams, backward=False)
     assert not fwd["cached"]
     forced = api.autotune(g, cams, backward=True, force=True)
-    assert not forced["cached"] and forced["n_candidates"] == 12
+    assert not forced["cached"] and forced["n_candidates"] == 13
+    # whole lists only: no third stage, and a cache entry of its own
+    whole = api.autotune(g, cams, backward=True, front=False)
+    assert not whole["cached"] and not whole["front"]
+    check_choice(whole, 3, front=False)
     # the choice renders the same images as one 16x16 batch of all views
     ref = render_chunks(g, cams, (16, 16), 3)
     got = render_chunks(g, cams, r["tile"], r["views_per_launch"], smem_batch=r["smem_batch"])
