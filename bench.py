@@ -377,7 +377,7 @@ def run_ours(args):
     filtered = filtered_bench(api, N, torch, dev, reps=5) if not args.no_legs else None
     imp_leg = importance_bench(api, N, torch, dev, reps=5) if not args.no_legs else None
     small = small_scene_bench(api, N, torch, dev, reps=50) if not args.no_legs else None
-    work = kernel_work(vbs, sres, pairs, n_super, touched)
+    work = kernel_work(vbs, sres, pairs, n_super, touched, work_counts["kept_items"])
     probes = probe_peaks(N, torch, dev)
     roof = roofline(kernel_ms, work, hbm, peak_kind, B, probes)
     per_kernel = {k: kernel_frac(k, kernel_ms[k], work, hbm, probes) for k in kernel_ms if k in work}
@@ -474,7 +474,7 @@ def stage_times(api, N, torch, g, chunks, cfg, st, proj, h, gbuf, loss, ws_sort,
     N.profile_enable(False)
     kernels = {k: {"launches_per_step": v[0] / reps, "ms_per_step": v[1] / reps, "ms_per_launch": v[1] / v[0]}
                for k, v in kern.items()}
-    pairs, n_super, walked = 0, 0, 0
+    pairs, n_super, walked, kept_items = 0, 0, 0, 0
     for vb, bins, (img, T, L, dL), target in chunks:
         api.project(g, vb, cfg, st, out=proj)
         api.bin_sort(proj, vb, bins, ws_sort, st, front=FRONT)
@@ -487,19 +487,36 @@ def stage_times(api, N, torch, g, chunks, cfg, st, proj, h, gbuf, loss, ws_sort,
             Lv = L[hv.pixel_base: hv.pixel_base + hv.width * hv.height].view(hv.height, hv.width)
             Lp = torch.nn.functional.pad(Lv, (0, hv.tiles_x * tw - hv.width, 0, hv.tiles_y * th - hv.height))
             walked += int(Lp.view(hv.tiles_y, th, hv.tiles_x, tw).amax(dim=(1, 3)).to(torch.int64).sum().item())
-        r = proj.rect[:vb.n_items].to(torch.int64) & 0xffff
-        nonempty = (r[:, 2] > r[:, 0]) & (r[:, 3] > r[:, 1])
-        zero = torch.zeros_like(r[:, 0])
-        sw = torch.where(nonempty, (r[:, 2] - 1) // 4 - r[:, 0] // 4 + 1, zero)
-        sh = torch.where(nonempty, (r[:, 3] - 1) // 4 - r[:, 1] // 4 + 1, zero)
-        n_super += int((sw * sh).sum().item())
-        del r, nonempty, zero, sw, sh
+        kept_items += int((proj.n_tiles[:vb.n_items] != 0).sum().item())
+        if FRONT:
+            # super instances the emission wrote: distinct (super-tile, item) pairs of the lists
+            K = int(st.read()["n_instances"])
+            rg = bins.ranges[:vb.n_tiles].to(torch.int64).view(-1, 2)
+            t_of = torch.repeat_interleave(torch.arange(vb.n_tiles, device=rg.device), rg[:, 1] - rg[:, 0])
+            sid = torch.zeros(vb.n_tiles, dtype=torch.int64, device=rg.device)
+            for v in range(vb.n_views):
+                hv = vb.views_host[v]
+                loc = torch.arange(hv.tiles_x * hv.tiles_y, device=rg.device)
+                sid[hv.tile_base: hv.tile_base + loc.numel()] = \
+                    ((v * 4096 + (loc // hv.tiles_x) // 4) * 4096 + (loc % hv.tiles_x) // 4)
+            items = bins.vals[:K].to(torch.int64) & 0xffffffff
+            n_super += int(torch.unique(sid[t_of] * (1 << 32) + items).numel())
+            del rg, t_of, sid, items
+        else:
+            r = proj.rect[:vb.n_items].to(torch.int64) & 0xffff
+            nonempty = (r[:, 2] > r[:, 0]) & (r[:, 3] > r[:, 1])
+            zero = torch.zeros_like(r[:, 0])
+            sw = torch.where(nonempty, (r[:, 2] - 1) // 4 - r[:, 0] // 4 + 1, zero)
+            sh = torch.where(nonempty, (r[:, 3] - 1) // 4 - r[:, 1] // 4 + 1, zero)
+            n_super += int((sw * sh).sum().item())
+            del r, nonempty, zero, sw, sh
     # Gaussians some view gives a gradient (the last timed step's gradients): only their
     # parameters are read by the projection backward
     gm = gbuf.views[0].reshape(3, -1)
     touched = int(((gm != 0).any(dim=0) | (gbuf.views[3].reshape(-1) != 0)).sum().item())
     torch.cuda.synchronize()
-    return acc, kernels, {"pairs": pairs, "super_instances": n_super, "touched": touched, "walked": walked}
+    return acc, kernels, {"pairs": pairs, "super_instances": n_super, "touched": touched, "walked": walked,
+                          "kept_items": kept_items}
 
 
 def uneven_bench(api, N, torch, dev, n_views, reps):
@@ -1050,14 +1067,15 @@ class _PerLaunch:
         self.launches = c
 
 
-def kernel_work(vbs, sres, pairs, n_super, touched):
+def kernel_work(vbs, sres, pairs, n_super, touched, kept_items):
     """Algorithmic work per launch of each library kernel: DRAM bytes the method must move
     (bound "hbm") or FP32 lane operations (bound "alu").
 
     Items M (view, Gaussian) pairs, instances K, super-tile instances Ks, pixels P:
     projection reads 236 B of parameters per Gaussian (per item for visibility lists) and
     writes 52 B per item; the occlusion cut of front lists reads 36 B per item of the
-    nearest sixteenth and 256 B of bound sums per tile; the depth sort moves
+    nearest 1/32 and 64 B of bound sums per tile, and the emission then reads only the items
+    ranked before the largest cut (counted as the window); the depth sort moves
     8 B per item and pass (read key+value, write key+value = 16 B in the scatter, 4 B read in
     the count); the super-tile sort moves 2 x (2 + 4 + 1) B per super instance and pass
     (count: 2 B); the fine partition reads the 1 B cover byte per super instance (count),
@@ -1070,6 +1088,8 @@ def kernel_work(vbs, sres, pairs, n_super, touched):
     vb = _PerLaunch(vbs)
     c = vb.launches
     M, K, Ks, P = vb.n_items, sres["n_instances"], n_super / c, vb.n_pixels
+    Wc = -(-(kept_items / c) // 32)    # the occlusion cut's window (ranks) per launch
+    Mr = Wc if FRONT else M            # items the super-instance emission reads
     pairs = pairs / c
     kb = 2 if vb.n_tiles <= 65536 else 4
     hbm = {
@@ -1077,14 +1097,15 @@ def kernel_work(vbs, sres, pairs, n_super, touched):
         "k_project": (vb.n_gaussians * 236 + M * 52) if (vbs[0].subset is None and vbs[0].n_views > 1)
         else M * (236 + 52),
         "k_depth_keys": M * (4 + 8),
-        "k_count_blocks": M * (4 + 8),
-        "k_emit": M * (4 + 8) + Ks * (kb + 4 + 1),
+        # front lists: only the items ranked before the largest cut (at most the window) are read
+        "k_count_blocks": Mr * (4 + 8),
+        "k_emit": Mr * (4 + 8) + Ks * (kb + 4 + 1),
         "k_depth_sort_hist": M * 4,
         "k_depth_sort": M * 16,
-        # occlusion cut (front lists): the nearest sixteenth of the items, their order entry,
-        # mean, conic and rect; then 64 bound sums per tile
-        "k_cut_accumulate": -(-M // 16) * (4 + 8 + 16 + 8),
-        "k_cut_tiles": vb.n_tiles * 64 * 4,
+        # occlusion cut (front lists): the nearest 1/32 of the items with instances, their order
+        # entry, mean, conic and rect; then 16 bound sums per tile
+        "k_cut_accumulate": Wc * (4 + 8 + 16 + 8),
+        "k_cut_tiles": vb.n_tiles * 16 * 4,
         "k_super_sort_hist": Ks * kb,
         "k_super_sort": Ks * 2 * (kb + 4 + 1),
         "k_ranges": Ks * kb,
