@@ -377,7 +377,7 @@ def run_ours(args):
     filtered = filtered_bench(api, N, torch, dev, reps=5) if not args.no_legs else None
     imp_leg = importance_bench(api, N, torch, dev, reps=5) if not args.no_legs else None
     small = small_scene_bench(api, N, torch, dev, reps=50) if not args.no_legs else None
-    work = kernel_work(vbs, sres, pairs, n_super, touched, work_counts["kept_items"])
+    work = kernel_work(vbs, sres, pairs, n_super, touched, work_counts["kept_items"], work_counts["touched_items"])
     probes = probe_peaks(N, torch, dev)
     roof = roofline(kernel_ms, work, hbm, peak_kind, B, probes)
     per_kernel = {k: kernel_frac(k, kernel_ms[k], work, hbm, probes) for k in kernel_ms if k in work}
@@ -404,6 +404,7 @@ def run_ours(args):
             "fps_forward_single_view": round(fps, 1) if fps else None,
             "instances_per_view": int(sres["n_instances"] / B),
             "gaussians_with_gradient": touched,
+            "items_with_gradient_per_launch": work_counts["touched_items"],
             "super_instances_per_view": int(n_super / V),
             "pairs_per_pixel": round(pairs / sum(vb.n_pixels for vb in vbs), 2),
             "tile_list_fraction_walked": round(work_counts["walked"] / max(1, sres["n_instances"] * len(vbs)), 4),
@@ -514,9 +515,12 @@ def stage_times(api, N, torch, g, chunks, cfg, st, proj, h, gbuf, loss, ws_sort,
     # parameters are read by the projection backward
     gm = gbuf.views[0].reshape(3, -1)
     touched = int(((gm != 0).any(dim=0) | (gbuf.views[3].reshape(-1) != 0)).sum().item())
+    # items the last launch's backward gave an image-space gradient (per launch: chunks alike)
+    ga, gb, gc = api.image_grads(chunks[-1][0], ws_bwd)
+    touched_items = int(((ga != 0).any(dim=1) | (gb != 0).any(dim=1) | (gc != 0)).sum().item())
     torch.cuda.synchronize()
     return acc, kernels, {"pairs": pairs, "super_instances": n_super, "touched": touched, "walked": walked,
-                          "kept_items": kept_items}
+                          "kept_items": kept_items, "touched_items": touched_items}
 
 
 def uneven_bench(api, N, torch, dev, n_views, reps):
@@ -1067,7 +1071,7 @@ class _PerLaunch:
         self.launches = c
 
 
-def kernel_work(vbs, sres, pairs, n_super, touched, kept_items):
+def kernel_work(vbs, sres, pairs, n_super, touched, kept_items, touched_items):
     """Algorithmic work per launch of each library kernel: DRAM bytes the method must move
     (bound "hbm") or FP32 lane operations (bound "alu").
 
@@ -1081,7 +1085,8 @@ def kernel_work(vbs, sres, pairs, n_super, touched, kept_items):
     (count: 2 B); the fine partition reads the 1 B cover byte per super instance (count),
     then 4 B item + 1 B cover byte per super instance and writes 4 B per instance (scatter);
     the projection backward writes 236 B of gradients per Gaussian (written, not
-    accumulated), reads 36 B of image-space gradients per item, and reads the 236 B of
+    accumulated), reads a 1 B flag per item and 36 B of image-space gradients per flagged
+    item, and reads the 236 B of
     parameters and the 16 B colour rows only for the `touched` Gaussians some view gives a
     gradient (most of a dense scene is hidden behind saturated pixels); for the blend kernels
     the work is the (pixel, Gaussian) pairs evaluated per launch."""
@@ -1114,9 +1119,12 @@ def kernel_work(vbs, sres, pairs, n_super, touched, kept_items):
         "k_l1": P * 3 * 4 * 3,
         "k_ssim_stats": P * 3 * (8 + 12),
         "k_ssim_grad": P * 3 * (12 + 8 + 4),
-        # gradients written once per Gaussian (all views summed in registers); 36 B of
-        # image-space gradients read per item; parameters and colour rows of touched ones
-        "k_project_bwd": vb.n_gaussians * 236 + M * 36 + touched * (236 + 16 * M / vb.n_gaussians),
+        # gradients written once per Gaussian (all views summed in registers); a 1 B flag read
+        # per item, 36 B of image-space gradients per flagged item; parameters and colour rows
+        # of the Gaussians with a gradient
+        "k_project_bwd": vb.n_gaussians * 236 + M * 1 + touched_items * 36 + touched * (236 + 16 * M / vb.n_gaussians),
+        # the previous call's flagged items: flags read, their gradients and flags zeroed
+        "k_bwd_prepare": M * 1 + touched_items * (36 + 1),
         "k_filter_count": vb.n_gaussians * 4,
         "k_filter_scatter": vb.n_gaussians * (4 + 1) + vb.n_gaussians * 4,
     }

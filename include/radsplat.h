@@ -368,7 +368,11 @@ rs_status rs_kmeans(const float* points, int32_t n, float* centres, int32_t k, i
  * Gradients are ADDED into `grads` (zero them first), or with cfg->grad_overwrite written
  * over them (every row; for a visibility-list batch the call zeroes `grads` itself, then
  * adds); items of all views of the same Gaussian are summed.
- * ws: rs_workspace_size(RS_STAGE_BACKWARD, batch, 0) bytes.
+ * ws: rs_workspace_size(RS_STAGE_BACKWARD, batch, 0) bytes.  It carries state from one call
+ * to the next: a completed call marks it clean (the items it left no gradient for hold
+ * zeros) and flags the items it did, so the next call with the same item count zeroes only
+ * those; any other contents are zeroed whole.  Calls that share a workspace must not
+ * overlap on the GPU.
  * Errors: RS_ERR_INVALID_ARG, RS_ERR_WORKSPACE, RS_ERR_UNSUPPORTED, RS_ERR_CUDA. */
 rs_status rs_render_backward(const rs_gaussians* g, const rs_view_batch* batch,
                              const rs_config* cfg, const rs_projected* proj,

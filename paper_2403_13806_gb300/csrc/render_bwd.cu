@@ -30,10 +30,29 @@
 namespace rs {
 
 struct Grad2D {
-  float4* ga;   // (d/dx, d/dy, d/da, d/db) of mean2d and conic (a, b, c)
-  float4* gb;   // (d/dc, d/do, d/dr, d/dg)
-  float* gc;    // d/db(lue)
+  float4* ga;         // (d/dx, d/dy, d/da, d/db) of mean2d and conic (a, b, c)
+  float4* gb;         // (d/dc, d/do, d/dr, d/dg)
+  float* gc;          // d/db(lue)
+  uint8_t* touched;   // 1 for every item the blend added to
 };
+
+// The backward workspace's state word after a completed call (xor the item count).
+constexpr unsigned long long kBwdClean = 0x52534277734c6e21ull;
+
+// Before the blend: zero the image-space gradients and flags of the items the previous call
+// on this workspace touched, or of every item if the workspace is not in that call's clean
+// state (first use, another item count, an interrupted call).
+__global__ void k_bwd_prepare(Grad2D g, const unsigned long long* __restrict__ state, int64_t n) {
+  const bool clean = *state == (kBwdClean ^ (unsigned long long)n);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (!clean || g.touched[i]) {
+      g.ga[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      g.gb[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      g.gc[i] = 0.f;
+      g.touched[i] = 0;
+    }
+  }
+}
 
 struct BwdBlendArgs {
   const float2* xy;
@@ -275,6 +294,7 @@ __global__ void __launch_bounds__(TW* TH / PX, 16) k_render_bwd(BwdBlendArgs a) 
         for (int q = 0; q < 9; ++q) nz |= (c[q] != 0.f);
         if (nz) {
           const uint32_t item = s_item[slot];
+          a.g.touched[item] = 1;
           atomicAdd(a.g.ga + item, make_float4(c[0], c[1], c[2], c[3]));
           atomicAdd(a.g.gb + item, make_float4(c[4], c[5], c[6], c[7]));
           atomicAdd(a.g.gc + item, c[8]);
@@ -296,6 +316,8 @@ struct BwdProjArgs {
   const float4* ga;
   const float4* gb;
   const float* gc;
+  const uint8_t* touched;         // items the blend gave a gradient (the others' are zero)
+  unsigned long long* state;      // set to the clean state by the first thread
   const float4* rgb_d;   // forward colours: a clamped channel (max(0, .) = 0) has no gradient
   rs_gaussian_grads out;
   int32_t overwrite;     // dense kernel: store the sums instead of adding them
@@ -495,6 +517,8 @@ __global__ void __launch_bounds__(kProjBwdThreads) k_project_bwd_dense(BwdProjAr
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t N = a.g.n;
   if (gid >= N) return;   // no barrier below: each thread owns its column
+  // the workspace is clean once this call completes (read only by the next call's prepare)
+  if (gid == 0) *a.state = kBwdClean ^ (unsigned long long)a.n_items;
   ParamGrad<D> pg;
 #pragma unroll
   for (int c = 0; c < 3; ++c) pg.m[c] = pg.ls[c] = 0.f;
@@ -511,6 +535,7 @@ __global__ void __launch_bounds__(kProjBwdThreads) k_project_bwd_dense(BwdProjAr
   for (int v = 0; v < a.n_views; ++v) {
     const rs_view& cam = a.views[v];
     const int64_t item = cam.item_base + gid;
+    if (!a.touched[item]) continue;   // 1 byte instead of the 36 of a zero gradient
     const float4 ga = a.ga[item], gb = a.gb[item];
     const float gc = a.gc[item];
     if (!any_grad(ga, gb, gc)) continue;
@@ -546,6 +571,8 @@ __global__ void __launch_bounds__(128) k_project_bwd_subset(BwdProjArgs a) {
   constexpr int NC = (D + 1) * (D + 1);
   const int64_t item = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (item >= a.n_items) return;
+  if (item == 0) *a.state = kBwdClean ^ (unsigned long long)a.n_items;
+  if (!a.touched[item]) return;
   const float4 ga = a.ga[item], gb = a.gb[item];
   const float gc = a.gc[item];
   if (!any_grad(ga, gb, gc)) return;
@@ -577,10 +604,16 @@ __global__ void __launch_bounds__(128) k_project_bwd_subset(BwdProjArgs a) {
     for (int c = 0; c < 3; ++c) atomicAdd(a.out.sh + (int64_t)(k * 3 + c) * N + gid, pg.sh[k][c]);
 }
 
+// Workspace: a state word, then the per-item image-space gradients and touched flags.  A
+// completed call leaves state = kBwdClean ^ n_items and every gradient of an item without
+// its flag zero, so the next call on the same workspace zeroes only the flagged items; any
+// other state (first use, another item count, an interrupted call) zeroes everything.
 struct BwdWs {
+  unsigned long long* state;
   float4* ga;
   float4* gb;
   float* gc;
+  uint8_t* touched;
   size_t bytes;
 };
 
@@ -593,9 +626,11 @@ static BwdWs bwd_ws_layout(void* base, int64_t n_items) {
     return p;
   };
   const size_t ni = (size_t)(n_items > 0 ? n_items : 1);
+  w.state = reinterpret_cast<unsigned long long*>(take(8));
   w.ga = reinterpret_cast<float4*>(take(ni * 16));
   w.gb = reinterpret_cast<float4*>(take(ni * 16));
   w.gc = reinterpret_cast<float*>(take(ni * 4));
+  w.touched = reinterpret_cast<uint8_t*>(take(ni));
   w.bytes = off;
   return w;
 }
@@ -666,7 +701,12 @@ extern "C" rs_status rs_render_backward(const rs_gaussians* g, const rs_view_bat
       return RS_ERR_CUDA;
   }
   if (batch->n_items == 0 || batch->n_tiles == 0) return RS_OK;
-  if (cudaMemsetAsync(ws, 0, w.bytes, s) != cudaSuccess) return RS_ERR_CUDA;
+  const Grad2D g2{w.ga, w.gb, w.gc, w.touched};
+  {
+    prof::Scope ps("k_bwd_prepare", s);
+    const int64_t pg = (batch->n_items + 255) / 256;
+    k_bwd_prepare<<<(unsigned)(pg < 8 * kNumSMs ? pg : 8 * kNumSMs), 256, 0, s>>>(g2, w.state, batch->n_items);
+  }
 
   BwdBlendArgs b;
   b.xy = reinterpret_cast<const float2*>(proj->xy);
@@ -682,9 +722,7 @@ extern "C" rs_status rs_render_backward(const rs_gaussians* g, const rs_view_bat
   b.T_final = T_final;
   b.last = last;
   b.dL_dimage = dL_dimage;
-  b.g.ga = w.ga;
-  b.g.gb = w.gb;
-  b.g.gc = w.gc;
+  b.g = g2;
   rs_status bst = RS_ERR_UNSUPPORTED;
   if (batch->tile_w == 16 && batch->tile_h == 16) bst = launch_bwd_blend<16, 16, 8>(b, batch->n_tiles, cfg->batch, s);
   else if (batch->tile_w == 32 && batch->tile_h == 8) bst = launch_bwd_blend<32, 8, 8>(b, batch->n_tiles, cfg->batch, s);
@@ -702,6 +740,8 @@ extern "C" rs_status rs_render_backward(const rs_gaussians* g, const rs_view_bat
   p.ga = w.ga;
   p.gb = w.gb;
   p.gc = w.gc;
+  p.touched = w.touched;
+  p.state = w.state;
   p.rgb_d = reinterpret_cast<const float4*>(proj->rgb_d);
   p.out = *grads;
   p.overwrite = (overwrite && !batch->subset_idx) ? 1 : 0;

@@ -209,3 +209,53 @@ def test_backward_staging_batches_agree_with_oracle(tile):
                             out["rast"].ws_bwd, api.config(batch=m * nt))
         torch.cuda.synchronize()
         compare_groups({k: t.cpu().numpy() for k, t in zip(KEYS, grads)}, ref)
+
+
+def test_backward_workspace_reuse_clears_the_previous_call():
+    """A backward workspace carries state between calls: the second call on it zeroes only what
+    the first one touched.  Call 1 has a gradient on the whole image, call 2 only on its left
+    half; call 2's per-item image-space gradients and parameter gradients must equal those of
+    the same call on a fresh workspace (the items only call 1 reached hold exact zeros), up to
+    the order of the float atomics.  A third call with another item count (two views) and then
+    call 2 again exercise the full zeroing of a workspace left by a different batch."""
+    from paper_2403_13806_gb300 import api
+    scene, cams = synth.config0(n=8000)
+    cam = cams[0]
+    out = gpu_forward(scene, [cam], importance=False)
+    g, vb, rast = out["g"], out["vb"], out["rast"]
+    H = W = 128
+    rng = np.random.default_rng(31)
+    d1 = rng.normal(size=(3, H, W)).astype(np.float32)
+    d2 = d1.copy()
+    d2[:, :, W // 2:] = 0.0
+    dl1, dl2 = (torch.as_tensor(d.ravel(), device="cuda") for d in (d1, d2))
+
+    def backward(dl, ws, vb_=vb, out_=out):
+        grads = [torch.zeros_like(t) for t in g.tensors()]
+        api.render_backward(g, vb_, out_["proj"], out_["bins"], out_["T_final"], out_["last"], dl, grads, ws)
+        torch.cuda.synchronize()
+        img = [t.clone() for t in api.image_grads(vb_, ws)]
+        return grads, img
+
+    def close(a, b):
+        for x, y in zip(a, b):
+            x, y = x.cpu().numpy().astype(np.float64), y.cpu().numpy().astype(np.float64)
+            assert np.all(np.abs(x - y) <= 1e-5 * np.abs(y) + 1e-6 * np.abs(y).max(initial=0)), \
+                np.abs(x - y).max()
+
+    ws = api.Workspace()
+    backward(dl1, ws)
+    g_re, i_re = backward(dl2, ws)
+    g_fresh, i_fresh = backward(dl2, api.Workspace())
+    close(g_re, g_fresh)
+    close(i_re, i_fresh)
+    # the items call 2 does not reach are exact zeros on the reused workspace
+    untouched = (i_fresh[0] == 0).all(dim=1) & (i_fresh[1] == 0).all(dim=1) & (i_fresh[2] == 0)
+    assert untouched.any() and bool((i_re[0][untouched] == 0).all() and (i_re[1][untouched] == 0).all()
+                                    and (i_re[2][untouched] == 0).all())
+    # another item count on the same workspace, then call 2 again
+    out2 = gpu_forward(scene, [cam, cam], importance=False)
+    backward(torch.cat([dl1, dl1]), ws, out2["vb"], out2)
+    g_back, i_back = backward(dl2, ws)
+    close(g_back, g_fresh)
+    close(i_back, i_fresh)
