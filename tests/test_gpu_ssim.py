@@ -23,7 +23,7 @@ def images(rng, planes, H, W):
 
 
 @pytest.mark.parametrize("planes,H,W,lam", [(3, 45, 67, 0.2), (2, 16, 32, 0.2), (1, 7, 5, 0.2), (3, 45, 67, 0.0),
-                                            (1, 40, 40, 1.0)])
+                                            (1, 40, 40, 1.0), (2, 48, 100, 0.2)])
 def test_ssim_loss_matches_oracle(planes, H, W, lam):
     rng = np.random.default_rng(planes * 1000 + H + W)
     x, y = images(rng, planes, H, W)
