@@ -1034,7 +1034,7 @@ def probe_peaks(N, torch, dev, reps=5):
 NCU_TRAFFIC = {
     "k_render_bwd": {"bytes_per_view": 25196544, "files": ['render_bwd.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "f221ffcc78ae3042",
                 "profile": "k_render_bwd_1M_1view.md"},
-    "k_render_importance": {"bytes_per_view": 4441600, "files": ['render.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "d09583f05603764e",
+    "k_render_importance": {"bytes_per_view": 4423936, "files": ['render.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "19c71abac4109a86",
                 "profile": "k_render_1M_1view.md"},
     "k_fine_scatter": {"bytes_per_view": 20112128, "files": ['binsort.cu', 'rs_common.cuh'], "sha": "4cffedcde21798e1",
                 "profile": "k_fine_scatter_1M_1view.md"},
