@@ -37,6 +37,19 @@
 namespace rs {
 
 constexpr int kEmitThreads = 256;
+// Blocks of the super-instance counting and emission: the first nb8 hold 64 depth-ranked
+// items (8 per warp), the rest 256 (32 per warp).  With the occlusion cut nb8 covers the
+// cut's window, so that the nearest items -- the largest, ranked first -- spread over four
+// times as many warps (a warp walks all the super cells of its items); whole lists use
+// nb8 = 0.
+__host__ __device__ inline int64_t block_start(int64_t blk, int64_t nb8) {
+  return blk < nb8 ? blk * 64 : nb8 * 64 + (blk - nb8) * 256;
+}
+__host__ __device__ inline int block_ipw(int64_t blk, int64_t nb8) { return blk < nb8 ? 8 : 32; }
+// Blocks for n items with nb8 small blocks.
+inline int64_t block_count(int64_t n, int64_t nb8) {
+  return nb8 + (n > nb8 * 64 ? (n - nb8 * 64 + 255) / 256 : 0);
+}
 constexpr int kSuper = 4;           // tiles per super-tile side
 constexpr int kFineThreads = 256;   // threads of a fine-binning CTA
 constexpr int kSegLen = 3840;       // super-list entries per fine work item (segment; 15 per thread)
@@ -88,7 +101,7 @@ static BinWs bin_ws_layout(void* base, int64_t n_items, int64_t capacity, int n_
   };
   const size_t ni = (size_t)(n_items > 0 ? n_items : 1);
   const size_t cap = (size_t)(capacity > 0 ? capacity : 1);   // super instances <= instances
-  const int64_t nblk = (n_items + kEmitThreads - 1) / kEmitThreads;
+  const int64_t nblk = (n_items + 63) / 64 + 2;   // at least block_count for any nb8
   for (int i = 0; i < 2; ++i) w.dkeys[i] = reinterpret_cast<uint32_t*>(take(ni * 4));
   for (int i = 0; i < 2; ++i) w.dvals[i] = reinterpret_cast<uint32_t*>(take(ni * 4));
   w.bsum = reinterpret_cast<unsigned long long*>(take((size_t)(nblk > 0 ? nblk : 1) * 8));
@@ -290,11 +303,11 @@ __device__ __forceinline__ const uint32_t* stage_cuts(const uint32_t* __restrict
   return s;
 }
 
-// Super instances per block of kEmitThreads depth-sorted items, also added into the total
-// of the block's chunk of kCountChunk blocks (csum, zeroed by the caller).  CUT: only the
-// instances that k_emit keeps (super_kept), counted by a warp-wide walk over the cells of
-// the warp's items, per warp into wsum as well; blocks whose items all lie beyond the
-// largest cut count 0 at once.
+// Super instances per block of depth-sorted items (block_start, block_ipw), also added into
+// the total of the block's chunk of kCountChunk blocks (csum, zeroed by the caller).  CUT:
+// only the instances that k_emit keeps (super_kept), counted by a warp-wide walk over the
+// cells of the warp's items, per warp into wsum as well; blocks whose items all lie beyond
+// the largest cut end at once.
 template <bool CUT>
 __global__ void __launch_bounds__(kEmitThreads) k_count_blocks(const uint32_t* __restrict__ order,
                                                                const uint32_t* __restrict__ n_dev,
@@ -302,57 +315,60 @@ __global__ void __launch_bounds__(kEmitThreads) k_count_blocks(const uint32_t* _
                                                                const rs_view* __restrict__ views, int n_views,
                                                                const uint32_t* __restrict__ super_base,
                                                                const uint32_t* __restrict__ cut_s,
-                                                               const uint32_t* __restrict__ cut_max,
+                                                               const uint32_t* __restrict__ cut_max, int64_t nb8,
                                                                unsigned long long* __restrict__ bsum,
                                                                unsigned long long* __restrict__ csum,
                                                                uint32_t* __restrict__ wsum) {
   __shared__ unsigned long long s[kEmitThreads / 32];
   __shared__ uint32_t s_cut[CUT ? kCutSmem : 1];
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t n = *n_dev;   // the items the depth sort kept (those with instances)
   const int64_t lim = CUT ? min(n, (int64_t)*cut_max) : n;
-  const int64_t i = (int64_t)blockIdx.x * kEmitThreads + threadIdx.x;
-  if (CUT && (int64_t)blockIdx.x * kEmitThreads >= lim) {   // uniform per CTA
-    if (threadIdx.x == 0) bsum[blockIdx.x] = 0ull;
-    return;
-  }
-  unsigned long long c = 0;
-  if (!CUT) {
-    if (i < n) {
-      const ushort4 sr = super_rect(rect[order[i]]);
-      c = (unsigned long long)(sr.z - sr.x) * (unsigned long long)(sr.w - sr.y);
-    }
-  } else {
-    const SuperItem si = super_item(order, rect, views, n_views, super_base, i, i < lim);
-    uint32_t incl = si.cnt;
+  const int64_t blk = blockIdx.x;
+  // CUT: a block at or beyond the largest cut keeps nothing (k_count_top reads its count as 0)
+  if (CUT && block_start(blk, nb8) >= lim) return;   // uniform per CTA
+  const uint32_t ns = CUT ? super_base[n_views] : 0u;
+  const uint32_t* cuts = CUT ? stage_cuts(cut_s, ns, s_cut) : cut_s;
+  const int ipw = block_ipw(blk, nb8);
+  {
+    const int64_t first = block_start(blk, nb8) + warp * ipw;   // the warp's first item (rank)
+    const int64_t i = first + lane;                             // this lane's item, for lane < ipw
+    unsigned long long c = 0;
+    if (!CUT) {
+      if (i < n) {   // (nb8 = 0: 32 items per warp, i = block start + threadIdx.x)
+        const ushort4 sr = super_rect(rect[order[i]]);
+        c = (unsigned long long)(sr.z - sr.x) * (unsigned long long)(sr.w - sr.y);
+      }
+    } else {
+      const SuperItem si = super_item(order, rect, views, n_views, super_base, i, lane < ipw && i < lim);
+      uint32_t incl = si.cnt;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
+      const uint32_t excl = incl - si.cnt;
+      const uint32_t first_rank = (uint32_t)first;
+      uint32_t kept = 0;
+      for (uint32_t e0 = 0; e0 < wtot; e0 += 32) {   // uniform per warp
+        const SuperCell sc = super_cell(si, incl, excl, e0 + lane);
+        const bool keep = e0 + lane < wtot && super_kept(sc.sid, first_rank + (uint32_t)sc.owner, ns, cuts);
+        kept += (uint32_t)__popc(__ballot_sync(0xffffffffu, keep));
+      }
+      if (lane == 0) wsum[blk * (kEmitThreads / 32) + warp] = kept;
+      c = lane == 0 ? kept : 0u;
     }
-    const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
-    const uint32_t excl = incl - si.cnt;
-    const uint32_t ns = super_base[n_views];
-    const uint32_t* cuts = stage_cuts(cut_s, ns, s_cut);
-    const uint32_t first_rank = (uint32_t)(i - lane);
-    uint32_t kept = 0;
-    for (uint32_t e0 = 0; e0 < wtot; e0 += 32) {   // uniform per warp
-      const SuperCell sc = super_cell(si, incl, excl, e0 + lane);
-      kept += (uint32_t)__popc(
-          __ballot_sync(0xffffffffu, e0 + lane < wtot && super_kept(sc.sid, first_rank + (uint32_t)sc.owner, ns, cuts)));
-    }
-    if (lane == 0) wsum[blockIdx.x * (kEmitThreads / 32) + (threadIdx.x >> 5)] = kept;
-    c = lane == 0 ? kept : 0u;
-  }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-  if (lane == 0) s[threadIdx.x >> 5] = c;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long t = 0;
-    for (int w = 0; w < kEmitThreads / 32; ++w) t += s[w];
-    bsum[blockIdx.x] = t;
-    if (t) atomicAdd(csum + blockIdx.x / kCountChunk, t);
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if (lane == 0) s[warp] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long t = 0;
+      for (int w = 0; w < kEmitThreads / 32; ++w) t += s[w];
+      bsum[blk] = t;
+      if (t) atomicAdd(csum + blk / kCountChunk, t);
+    }
   }
 }
 
@@ -370,21 +386,70 @@ __device__ __forceinline__ unsigned long long block_sum256_u64(unsigned long lon
   return t;
 }
 
+// Exclusive prefix of the chunk totals csum[0 .. n_chunks) in place (one CTA, 4 entries
+// per thread per round, a carry between rounds).
+__global__ void __launch_bounds__(1024) k_count_chunks(unsigned long long* __restrict__ csum, int64_t n_chunks) {
+  __shared__ unsigned long long s_w[32];
+  __shared__ unsigned long long s_carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_carry = 0ull;
+  __syncthreads();
+  for (int64_t c0 = 0; c0 < n_chunks; c0 += 4 * 1024) {
+    const int64_t c = c0 + 4 * (int64_t)threadIdx.x;
+    unsigned long long v[4], sum = 0ull;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      v[j] = c + j < n_chunks ? csum[c + j] : 0ull;
+      sum += v[j];
+    }
+    unsigned long long x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      unsigned long long w = s_w[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      s_w[lane] = w;
+    }
+    __syncthreads();
+    unsigned long long run = s_carry + (warp ? s_w[warp - 1] : 0ull) + x - sum;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (c + j < n_chunks) csum[c + j] = run;
+      run += v[j];
+    }
+    __syncthreads();
+    if (threadIdx.x == 1023) s_carry += s_w[31];
+    __syncthreads();
+  }
+}
+
 // Exclusive prefix over the block counts, one CTA per chunk of kCountChunk blocks: the
-// chunk's base is the sum of the earlier chunks' totals, the blocks' places inside it a
+// chunk's base is the scanned total of the earlier chunks, the blocks' places inside it a
 // CTA scan.  The CTA of the last block writes the super-instance total.
+// (With the occlusion cut, blocks starting at or beyond the device limit min(*n_dev,
+// *cut_max) count 0 -- k_count_blocks leaves them; csum holds the chunks' exclusive
+// prefix, from k_count_chunks.)
 __global__ void __launch_bounds__(kCountChunk) k_count_top(unsigned long long* __restrict__ bsum,
                                                            const unsigned long long* __restrict__ csum, int64_t nblk,
                                                            int64_t capacity, uint32_t* __restrict__ counters,
-                                                           rs_device_status* st) {
+                                                           rs_device_status* st, const uint32_t* __restrict__ n_dev,
+                                                           const uint32_t* __restrict__ cut_max, int64_t nb8) {
   static_assert(kCountChunk == 256, "one thread per block of the chunk");
   __shared__ unsigned long long s_w[8];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned long long pre = 0;
-  for (int c = threadIdx.x; c < (int)blockIdx.x; c += kCountChunk) pre += csum[c];
-  const unsigned long long base = block_sum256_u64(pre, s_w);
+  const unsigned long long base = csum[blockIdx.x];
+  const int64_t lim = cut_max ? min((int64_t)*n_dev, (int64_t)*cut_max) : INT64_MAX;
   const int64_t b = (int64_t)blockIdx.x * kCountChunk + threadIdx.x;
-  const unsigned long long v = b < nblk ? bsum[b] : 0ull;
+  const unsigned long long v = (b < nblk && block_start(b, nb8) < lim) ? bsum[b] : 0ull;
   unsigned long long x = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -406,7 +471,8 @@ __global__ void __launch_bounds__(kCountChunk) k_count_top(unsigned long long* _
   }
 }
 
-// Expansion into super instances: each warp takes 32 consecutive depth-sorted items and
+// Expansion into super instances: each warp takes 8 or 32 consecutive depth-sorted items
+// (block_start, block_ipw) and
 // writes their super-tile ids, items and cover bytes contiguously (row-major inside each
 // super rect), 32 cells per round (super_cell); the cover byte comes from the four edge
 // offsets of the rect (inner super-tiles are covered whole).  CUT: only the kept instances
@@ -419,7 +485,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
                                                        const rs_view* __restrict__ views, int n_views,
                                                        const uint32_t* __restrict__ super_base,
                                                        const uint32_t* __restrict__ cut_s,
-                                                       const uint32_t* __restrict__ cut_max,
+                                                       const uint32_t* __restrict__ cut_max, int64_t nb8,
                                                        const unsigned long long* __restrict__ bpre, int64_t capacity,
                                                        const uint32_t* __restrict__ wsum,
                                                        KeyT* __restrict__ skeys, uint32_t* __restrict__ svals,
@@ -429,42 +495,49 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t n = *n_dev;   // the items the depth sort kept (those with instances)
   const int64_t lim = CUT ? min(n, (int64_t)*cut_max) : n;
-  if (CUT && (int64_t)blockIdx.x * kEmitThreads >= lim) return;   // uniform per CTA: nothing kept
-  const int64_t i = (int64_t)blockIdx.x * kEmitThreads + threadIdx.x;
-  const SuperItem si = super_item(order, rect, views, n_views, super_base, i, i < lim);
-  uint32_t incl = si.cnt;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += y;
-  }
-  const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
-  const uint32_t excl = incl - si.cnt;
+  const int64_t blk = blockIdx.x;
+  if (CUT && block_start(blk, nb8) >= lim) return;   // uniform per CTA: nothing kept
   const uint32_t ns = CUT ? super_base[n_views] : 0u;
   const uint32_t* cuts = CUT ? stage_cuts(cut_s, ns, s_cut) : nullptr;
-  const uint32_t first_rank = (uint32_t)(i - lane);
-  if (lane == 0) s_wtot[warp] = CUT ? wsum[blockIdx.x * (kEmitThreads / 32) + warp] : wtot;
-  __syncthreads();
-  unsigned long long wbase = bpre[blockIdx.x];
-  for (int w = 0; w < warp; ++w) wbase += s_wtot[w];
-  uint32_t run = 0;   // CUT: instances the warp wrote in earlier rounds
-  for (uint32_t e0 = 0; e0 < wtot; e0 += 32) {
-    const uint32_t e = e0 + lane;
-    const SuperCell sc = super_cell(si, incl, excl, e);
-    const bool keep = e < wtot && (!CUT || super_kept(sc.sid, first_rank + (uint32_t)sc.owner, ns, cuts));
-    unsigned long long pos = wbase + e;
-    if (CUT) {
-      const unsigned bal = __ballot_sync(0xffffffffu, keep);
-      pos = wbase + run + (uint32_t)__popc(bal & ((1u << lane) - 1u));
-      run += (uint32_t)__popc(bal);
+  const int ipw = block_ipw(blk, nb8);
+  {
+    const int64_t first = block_start(blk, nb8) + warp * ipw;   // the warp's first item (rank)
+    const int64_t i = first + lane;                             // this lane's item, for lane < ipw
+    const SuperItem si = super_item(order, rect, views, n_views, super_base, i, lane < ipw && i < lim);
+    uint32_t incl = si.cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
     }
-    if (keep && pos < (unsigned long long)capacity) {
-      skeys[pos] = (KeyT)sc.sid;
-      svals[pos] = sc.item;
-      const uint32_t rh = sc.edge >> 8;
-      const uint32_t lx0 = sc.tx == 0 ? (sc.edge & 3u) : 0u, lx1 = sc.tx == sc.rw - 1 ? ((sc.edge >> 2) & 3u) : 3u;
-      const uint32_t ly0 = sc.ty == 0 ? ((sc.edge >> 4) & 3u) : 0u, ly1 = sc.ty == rh - 1 ? ((sc.edge >> 6) & 3u) : 3u;
-      saux[pos] = (uint8_t)(lx0 | (lx1 << 2) | (ly0 << 4) | (ly1 << 6));
+    const uint32_t wtot = __shfl_sync(0xffffffffu, incl, 31);
+    const uint32_t excl = incl - si.cnt;
+    const uint32_t first_rank = (uint32_t)first;
+    if (lane == 0) s_wtot[warp] = CUT ? wsum[blk * (kEmitThreads / 32) + warp] : wtot;
+    __syncthreads();
+    unsigned long long wbase = bpre[blk];
+    for (int w = 0; w < warp; ++w) wbase += s_wtot[w];
+    uint32_t run = 0;   // CUT: instances the warp wrote in earlier rounds
+    for (uint32_t e0 = 0; e0 < wtot; e0 += 32) {
+      const uint32_t e = e0 + lane;
+      const SuperCell sc = super_cell(si, incl, excl, e);
+      const bool keep = e < wtot && (!CUT || super_kept(sc.sid, first_rank + (uint32_t)sc.owner, ns, cuts));
+      unsigned long long pos = wbase + e;
+      if (CUT) {
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        pos = wbase + run + (uint32_t)__popc(bal & ((1u << lane) - 1u));
+        run += (uint32_t)__popc(bal);
+      }
+      if (keep && pos < (unsigned long long)capacity) {
+        skeys[pos] = (KeyT)sc.sid;
+        svals[pos] = sc.item;
+        const uint32_t rh = sc.edge >> 8;
+        const uint32_t lx0 = sc.tx == 0 ? (sc.edge & 3u) : 0u;
+        const uint32_t lx1 = sc.tx == sc.rw - 1 ? ((sc.edge >> 2) & 3u) : 3u;
+        const uint32_t ly0 = sc.ty == 0 ? ((sc.edge >> 4) & 3u) : 0u;
+        const uint32_t ly1 = sc.ty == rh - 1 ? ((sc.edge >> 6) & 3u) : 3u;
+        saux[pos] = (uint8_t)(lx0 | (lx1 << 2) | (ly0 << 4) | (ly1 << 6));
+      }
     }
   }
 }
@@ -909,14 +982,15 @@ size_t bin_sort_ws_bytes(const rs_view_batch* b, int64_t capacity) {
 // Returns which buffer set (0 or 1) holds the sorted items and cover bytes.
 template <typename KeyT, bool CUT>
 static int super_instances(const BinWs& w, const uint32_t* order, const uint32_t* n_kept, const rs_projected* proj,
-                           const rs_view_batch* batch, int64_t cap, int64_t nblk, int n_super_max, cudaStream_t s) {
+                           const rs_view_batch* batch, int64_t cap, int64_t nblk, int64_t nb8, int n_super_max,
+                           cudaStream_t s) {
   KeyT* k0 = reinterpret_cast<KeyT*>(w.skeys[0]);
   KeyT* k1 = reinterpret_cast<KeyT*>(w.skeys[1]);
   {
     prof::Scope ps("k_emit", s);
     k_emit<KeyT, CUT><<<(unsigned)nblk, kEmitThreads, 0, s>>>(
         order, n_kept, reinterpret_cast<const ushort4*>(proj->rect), batch->views, batch->n_views, w.super_base,
-        w.cut_s, w.counters + 17, w.bsum, cap, w.wsum, k0, w.svals[0], w.saux[0]);
+        w.cut_s, w.counters + 17, nb8, w.bsum, cap, w.wsum, k0, w.svals[0], w.saux[0]);
   }
   const int cur = tiles::sort_pairs<KeyT>(k0, w.svals[0], k1, w.svals[1], w.counters, cap, bits_for(n_super_max),
                                           w.sweep, s, true,
@@ -930,9 +1004,11 @@ static int super_instances(const BinWs& w, const uint32_t* order, const uint32_t
 
 template <bool CUT>
 static int super_stage(const BinWs& w, const uint32_t* order, const uint32_t* n_kept, const rs_projected* proj,
-                       const rs_view_batch* batch, int64_t cap, int64_t nblk, int n_super_max, cudaStream_t s) {
-  return (n_super_max <= 65536) ? super_instances<uint16_t, CUT>(w, order, n_kept, proj, batch, cap, nblk, n_super_max, s)
-                                : super_instances<uint32_t, CUT>(w, order, n_kept, proj, batch, cap, nblk, n_super_max, s);
+                       const rs_view_batch* batch, int64_t cap, int64_t nblk, int64_t nb8, int n_super_max,
+                       cudaStream_t s) {
+  return (n_super_max <= 65536)
+             ? super_instances<uint16_t, CUT>(w, order, n_kept, proj, batch, cap, nblk, nb8, n_super_max, s)
+             : super_instances<uint32_t, CUT>(w, order, n_kept, proj, batch, cap, nblk, nb8, n_super_max, s);
 }
 
 static rs_status bin_sort_impl(const rs_projected* proj, const rs_view_batch* batch, const rs_bins* bins, void* ws,
@@ -1004,27 +1080,34 @@ static rs_status bin_sort_impl(const rs_projected* proj, const rs_view_batch* ba
       }
     }
     // 2) super instances in depth order, sorted stably on the super-tile id
-    const int64_t nblk = (n + kEmitThreads - 1) / kEmitThreads;
+    // front: the cut's window (at most ceil(n / 32) ranks) in blocks of 64 items
+    const int64_t nb8 = front ? ((n + kCutWindowDiv - 1) / kCutWindowDiv + 63) / 64 : 0;
+    const int64_t nblk = block_count(n, nb8);
     if (cudaMemsetAsync(w.csum, 0, (size_t)((nblk + kCountChunk - 1) / kCountChunk) * 8, s) != cudaSuccess)
       return RS_ERR_CUDA;
     {
       prof::Scope ps("k_count_blocks", s);
       if (front)
         k_count_blocks<true><<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n_kept, rect, batch->views, batch->n_views,
-                                                                     w.super_base, w.cut_s, w.counters + 17, w.bsum,
-                                                                     w.csum, w.wsum);
+                                                                     w.super_base, w.cut_s, w.counters + 17, nb8,
+                                                                     w.bsum, w.csum, w.wsum);
       else
         k_count_blocks<false><<<(unsigned)nblk, kEmitThreads, 0, s>>>(order, n_kept, rect, batch->views,
                                                                       batch->n_views, w.super_base, nullptr, nullptr,
-                                                                      w.bsum, w.csum, nullptr);
+                                                                      0, w.bsum, w.csum, nullptr);
     }
     {
+      const int64_t n_chunks = (nblk + kCountChunk - 1) / kCountChunk;
+      {
+        prof::Scope pc("k_count_chunks", s);
+        k_count_chunks<<<1, 1024, 0, s>>>(w.csum, n_chunks);
+      }
       prof::Scope ps("k_count_top", s);
-      k_count_top<<<(unsigned)((nblk + kCountChunk - 1) / kCountChunk), kCountChunk, 0, s>>>(w.bsum, w.csum, nblk, cap,
-                                                                                          w.counters, status);
+      k_count_top<<<(unsigned)n_chunks, kCountChunk, 0, s>>>(w.bsum, w.csum, nblk, cap, w.counters, status, n_kept,
+                                                             front ? w.counters + 17 : nullptr, nb8);
     }
-    scur = front ? super_stage<true>(w, order, n_kept, proj, batch, cap, nblk, n_super_max, s)
-                 : super_stage<false>(w, order, n_kept, proj, batch, cap, nblk, n_super_max, s);
+    scur = front ? super_stage<true>(w, order, n_kept, proj, batch, cap, nblk, nb8, n_super_max, s)
+                 : super_stage<false>(w, order, n_kept, proj, batch, cap, nblk, nb8, n_super_max, s);
   }
   const uint32_t* svals = w.svals[scur];
   const uint8_t* saux = w.saux[scur];
