@@ -111,35 +111,45 @@ __global__ void __launch_bounds__(TW* TH / PX) k_render(RenderArgs a) {
       // out of the maximum, and all done gives NaN, which compares false
       if (!__any_sync(0xffffffffu, max_p2(p2) >= r.bc.z)) continue;
       float m = 0.f;
+      // An entry outside a pixel's support gets alpha 0: weight 0 and T(1 - 0) = T exactly.
+      // A live pixel keeps T >= 1e-4, so T(1 - a) < 1e-4 holds exactly for the pixels whose
+      // stop rule fires on this entry; one comparison per pixel finds them, and the rare
+      // stopping thread takes their alpha back to 0 and retires them before compositing.
+      float2 a_in[NP], Tn[NP];
       bool stop = false;
-      bool st[PX];
 #pragma unroll
       for (int q = 0; q < NP; ++q) {
         const PairAlpha al = pair_alpha<false>(r, p2[q]);
-        const float2 Tn = __fmul2_rn(T[q], one_minus(al.alpha));
-        const bool ok0 = al.in0 && Tn.x >= kTMin, ok1 = al.in1 && Tn.y >= kTMin;
-        st[2 * q] = al.in0 && !ok0;   // stop before compositing this entry
-        st[2 * q + 1] = al.in1 && !ok1;
-        stop |= st[2 * q] | st[2 * q + 1];
-        // an entry that is not composited gets alpha 0: weight 0 and T(1 - 0) = T exactly, so
-        // one select per pixel replaces the weight and transmittance selects
-        const float2 a_eff = make_float2(ok0 ? al.alpha.x : 0.f, ok1 ? al.alpha.y : 0.f);
-        const float2 w = __fmul2_rn(a_eff, T[q]);
-        T[q] = __fmul2_rn(T[q], one_minus(a_eff));
+        a_in[q] = make_float2(al.in0 ? al.alpha.x : 0.f, al.in1 ? al.alpha.y : 0.f);
+        Tn[q] = __fmul2_rn(T[q], one_minus(a_in[q]));
+        stop = stop || Tn[q].x < kTMin || Tn[q].y < kTMin;
+      }
+      if (stop) {   // rare: retire the stopped pixels, their entry not composited
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+          if (Tn[q].x < kTMin) {
+            a_in[q].x = 0.f;
+            Tn[q].x = T[q].x;
+            nv[q].x = __int_as_float(0x7fc00000);
+          }
+          if (Tn[q].y < kTMin) {
+            a_in[q].y = 0.f;
+            Tn[q].y = T[q].y;
+            nv[q].y = __int_as_float(0x7fc00000);
+          }
+        }
+        my_done = all_done();
+      }
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        const float2 w = __fmul2_rn(a_in[q], T[q]);
+        T[q] = Tn[q];
         cr[q] = __ffma2_rn(w, lo2(r.rg), cr[q]);
         cg[q] = __ffma2_rn(w, hi2(r.rg), cg[q]);
         cb[q] = __ffma2_rn(w, lo2(r.bc), cb[q]);
-        last[2 * q] = ok0 ? base + j + 1 : last[2 * q];
-        last[2 * q + 1] = ok1 ? base + j + 1 : last[2 * q + 1];
+        last[2 * q] = a_in[q].x > 0.f ? base + j + 1 : last[2 * q];
+        last[2 * q + 1] = a_in[q].y > 0.f ? base + j + 1 : last[2 * q + 1];
         if (IMPORTANCE) m = max3f(m, w.x, w.y);
-      }
-      if (stop) {   // rare: retire the stopped pixels
-#pragma unroll
-        for (int q = 0; q < NP; ++q) {
-          if (st[2 * q]) nv[q].x = __int_as_float(0x7fc00000);
-          if (st[2 * q + 1]) nv[q].y = __int_as_float(0x7fc00000);
-        }
-        my_done = all_done();
       }
       if (IMPORTANCE) {
         const uint32_t mm = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
