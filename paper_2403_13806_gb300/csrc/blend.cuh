@@ -19,14 +19,25 @@ namespace rs {
 // conic (a, b, c) times (-log2(e)/2, -log2(e), -log2(e)/2), so that
 // p2 = A dx^2 + B dx dy + C dy^2 = log2(e) * power; cut = log2(1/(255 o)) - 1e-3: below it
 // alpha = o 2^p2 < 1/255 for sure, and only pairs above it take the exact test.
+//
+// The clamp alpha = min(0.99, o 2^p2) is applied as alpha = 0.99 s with the saturated product
+// s = sat(o' 2^p2), o' = o / 0.99 (the same function of o and p2; a saturating multiply runs
+// on the FMA pipe where a minimum would take the ALU pipe).  The record holds o'; the
+// forward pass composites s T with colours pre-scaled by 0.99, so it never forms alpha.
 struct BlendRec {
   float4 xy;    // (x, x, y, y)
   float4 ab;    // (A, A, B, B)
-  float4 co;    // (C, C, o, o)
-  float4 rg;    // (r, r, g, g)
-  float4 bc;    // (b, b, cut, cut)
+  float4 co;    // (C, C, o', o')
+  float4 rg;    // (r, r, g, g), times 0.99 in the forward pass
+  float4 bc;    // (b, b, cut, cut), b times 0.99 in the forward pass
 };
 
+constexpr float kInvAlphaMax = 1.0f / kAlphaMax;
+// alpha >= 1/255 as a test on s = alpha / 0.99
+constexpr float kSMin = (float)(1.0 / (255.0 * 0.99));
+
+// FWD: colours pre-scaled by 0.99 (the forward pass's weight is s T = alpha T / 0.99).
+template <bool FWD>
 __device__ __forceinline__ void stage_record(const float2* xy, const float4* conic_o, const float4* rgb_d,
                                              uint32_t item, BlendRec& r) {
   const float2 p = __ldg(xy + item);
@@ -34,11 +45,15 @@ __device__ __forceinline__ void stage_record(const float2* xy, const float4* con
   const float4 cd = __ldg(rgb_d + item);
   const float A = __fmul_rn(-0.5f * kLog2e, co.x), B = __fmul_rn(-kLog2e, co.y), C = __fmul_rn(-0.5f * kLog2e, co.z);
   const float cut = __fsub_rn(log2f(__fdiv_rn(kAlphaMin, co.w)), 1e-3f);
+  const float os = __fmul_rn(co.w, kInvAlphaMax);
+  const float cr = FWD ? __fmul_rn(kAlphaMax, cd.x) : cd.x;
+  const float cg = FWD ? __fmul_rn(kAlphaMax, cd.y) : cd.y;
+  const float cb = FWD ? __fmul_rn(kAlphaMax, cd.z) : cd.z;
   r.xy = make_float4(p.x, p.x, p.y, p.y);
   r.ab = make_float4(A, A, B, B);
-  r.co = make_float4(C, C, co.w, co.w);
-  r.rg = make_float4(cd.x, cd.x, cd.y, cd.y);
-  r.bc = make_float4(cd.z, cd.z, cut, cut);
+  r.co = make_float4(C, C, os, os);
+  r.rg = make_float4(cr, cr, cg, cg);
+  r.bc = make_float4(cb, cb, cut, cut);
 }
 
 __device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
@@ -95,35 +110,41 @@ __device__ __forceinline__ float2 pair_power(const BlendRec& r, const ColTerms& 
   return __ffma2_rn(dy, __ffma2_rn(lo2(r.co), dy, c.bdx), c.adx2);
 }
 
+// x y rounded and clamped to [0, 1] (a NaN product gives 0), on the FMA pipe.
+__device__ __forceinline__ float mul_sat(float x, float y) {
+  float r;
+  asm("mul.rn.sat.f32 %0, %1, %2;" : "=f"(r) : "f"(x), "f"(y));
+  return r;
+}
+
 // Per-pixel outcome of the blend rule's tests on one record.
 struct PairAlpha {
   float2 ex;      // 2^min(p2, 0)
-  float2 raw;     // o 2^min(p2, 0) (before the 0.99 clamp)
-  float2 alpha;   // min(0.99, raw)
+  float2 s;       // sat(o' 2^p2) = alpha / 0.99; s = 1 exactly where the 0.99 clamp is active
   bool in0, in1;  // p2 <= 0 and alpha >= 1/255
 };
 
 // CLAMP: evaluate 2^min(p2, 0) so that ex stays finite for every pair (the backward multiplies
-// it); the forward only uses alpha, where min(0.99, .) already bounds a large 2^p2, and the
+// it); the forward only uses s, where the saturation already bounds a large 2^p2, and the
 // decision (p2 <= 0 and alpha >= 1/255) is the same either way.
 template <bool CLAMP = true>
 __device__ __forceinline__ PairAlpha pair_alpha(const BlendRec& r, float2 p2) {
   PairAlpha a;
   a.ex = CLAMP ? make_float2(ex2_approx(fminf(p2.x, 0.f)), ex2_approx(fminf(p2.y, 0.f)))
                : make_float2(ex2_approx(p2.x), ex2_approx(p2.y));
-  a.raw = __fmul2_rn(hi2(r.co), a.ex);
-  a.alpha = make_float2(fminf(kAlphaMax, a.raw.x), fminf(kAlphaMax, a.raw.y));
+  a.s = make_float2(mul_sat(r.co.z, a.ex.x), mul_sat(r.co.w, a.ex.y));
   // alpha >= 1/255 implies p2 >= cut (the cut's 1e-3 margin exceeds the rounding of
-  // 2^p2, o 2^p2 and the cut itself), so the exact test needs no cut comparison; the cut
+  // 2^p2, o' 2^p2 and the cut itself), so the exact test needs no cut comparison; the cut
   // only serves the warp-level pre-test of the kernels
-  a.in0 = p2.x <= 0.f && a.alpha.x >= kAlphaMin;
-  a.in1 = p2.y <= 0.f && a.alpha.y >= kAlphaMin;
+  a.in0 = p2.x <= 0.f && a.s.x >= kSMin;
+  a.in1 = p2.y <= 0.f && a.s.y >= kSMin;
   return a;
 }
 
-// 1 - alpha on both lanes (one rounding, as the scalar subtraction).
-__device__ __forceinline__ float2 one_minus(float2 a) {
-  return __ffma2_rn(a, make_float2(-1.f, -1.f), make_float2(1.f, 1.f));
+// 1 - alpha = 1 - 0.99 s on both lanes (one rounding); the forward and backward passes both
+// form it this way, so the backward divides by the forward's factors exactly.
+__device__ __forceinline__ float2 one_minus_alpha(float2 s) {
+  return __ffma2_rn(s, make_float2(-kAlphaMax, -kAlphaMax), make_float2(1.f, 1.f));
 }
 
 }  // namespace rs

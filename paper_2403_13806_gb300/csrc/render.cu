@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(TW* TH / PX) k_render(RenderArgs a) {
       const int slot = tid + k * NT;
       if (slot < nb) {
         const uint32_t item = __ldg(a.vals + b0 + slot);
-        stage_record(a.xy, a.conic_o, a.rgb_d, item, s_rec[slot]);
+        stage_record<true>(a.xy, a.conic_o, a.rgb_d, item, s_rec[slot]);
         if (IMPORTANCE) {
           s_h[slot] = 0u;
           s_gid[slot] = a.subset ? __ldg(a.subset + item) : (uint32_t)((int64_t)item - cam.item_base);
@@ -111,29 +111,29 @@ __global__ void __launch_bounds__(TW* TH / PX) k_render(RenderArgs a) {
       // out of the maximum, and all done gives NaN, which compares false
       if (!__any_sync(0xffffffffu, max_p2(p2) >= r.bc.z)) continue;
       float m = 0.f;
-      // An entry outside a pixel's support gets alpha 0: weight 0 and T(1 - 0) = T exactly.
-      // A live pixel keeps T >= 1e-4, so T(1 - a) < 1e-4 holds exactly for the pixels whose
-      // stop rule fires on this entry; one comparison per pixel finds them, and the rare
-      // stopping thread takes their alpha back to 0 and retires them before compositing.
-      float2 a_in[NP], Tn[NP];
+      // An entry outside a pixel's support gets s = 0: weight 0 and T(1 - 0) = T exactly.
+      // A live pixel keeps T >= 1e-4, so T(1 - alpha) < 1e-4 holds exactly for the pixels
+      // whose stop rule fires on this entry; one comparison per pixel finds them, and the rare
+      // stopping thread takes their s back to 0 and retires them before compositing.
+      float2 s_in[NP], Tn[NP];
       bool stop = false;
 #pragma unroll
       for (int q = 0; q < NP; ++q) {
         const PairAlpha al = pair_alpha<false>(r, p2[q]);
-        a_in[q] = make_float2(al.in0 ? al.alpha.x : 0.f, al.in1 ? al.alpha.y : 0.f);
-        Tn[q] = __fmul2_rn(T[q], one_minus(a_in[q]));
+        s_in[q] = make_float2(al.in0 ? al.s.x : 0.f, al.in1 ? al.s.y : 0.f);
+        Tn[q] = __fmul2_rn(T[q], one_minus_alpha(s_in[q]));
         stop = stop || Tn[q].x < kTMin || Tn[q].y < kTMin;
       }
       if (stop) {   // rare: retire the stopped pixels, their entry not composited
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
           if (Tn[q].x < kTMin) {
-            a_in[q].x = 0.f;
+            s_in[q].x = 0.f;
             Tn[q].x = T[q].x;
             nv[q].x = __int_as_float(0x7fc00000);
           }
           if (Tn[q].y < kTMin) {
-            a_in[q].y = 0.f;
+            s_in[q].y = 0.f;
             Tn[q].y = T[q].y;
             nv[q].y = __int_as_float(0x7fc00000);
           }
@@ -142,18 +142,21 @@ __global__ void __launch_bounds__(TW* TH / PX) k_render(RenderArgs a) {
       }
 #pragma unroll
       for (int q = 0; q < NP; ++q) {
-        const float2 w = __fmul2_rn(a_in[q], T[q]);
+        // weight s T = alpha T / 0.99 against colours pre-scaled by 0.99
+        const float2 w = __fmul2_rn(s_in[q], T[q]);
         T[q] = Tn[q];
         cr[q] = __ffma2_rn(w, lo2(r.rg), cr[q]);
         cg[q] = __ffma2_rn(w, hi2(r.rg), cg[q]);
         cb[q] = __ffma2_rn(w, lo2(r.bc), cb[q]);
-        last[2 * q] = a_in[q].x > 0.f ? base + j + 1 : last[2 * q];
-        last[2 * q + 1] = a_in[q].y > 0.f ? base + j + 1 : last[2 * q + 1];
+        last[2 * q] = s_in[q].x > 0.f ? base + j + 1 : last[2 * q];
+        last[2 * q + 1] = s_in[q].y > 0.f ? base + j + 1 : last[2 * q + 1];
         if (IMPORTANCE) m = max3f(m, w.x, w.y);
       }
       if (IMPORTANCE) {
+        // the largest s T of the warp; alpha T = 0.99 s T (rounding is monotone, so scaling
+        // the maximum equals the maximum of the scaled values)
         const uint32_t mm = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
-        if (lane == 0 && mm) atomicMax(&s_h[j], mm);
+        if (lane == 0 && mm) atomicMax(&s_h[j], __float_as_uint(__fmul_rn(kAlphaMax, __uint_as_float(mm))));
       }
       if (__all_sync(0xffffffffu, my_done)) break;
     }

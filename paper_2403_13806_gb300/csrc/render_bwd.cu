@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(TW* TH / PX, 16) k_render_bwd(BwdBlendArgs a) 
       const int slot = tid + k * NT;
       if (slot < nb) {
         const uint32_t item = __ldg(a.vals + start + lo + slot);
-        stage_record(a.xy, a.conic_o, a.rgb_d, item, s_rec[slot]);
+        stage_record<false>(a.xy, a.conic_o, a.rgb_d, item, s_rec[slot]);
         s_item[slot] = item;
       }
     }
@@ -231,8 +231,9 @@ __global__ void __launch_bounds__(TW* TH / PX, 16) k_render_bwd(BwdBlendArgs a) 
         const PairAlpha al = pair_alpha(r, p2[q]);
         act |= al.in0 || al.in1;
         // a skipped entry gets alpha 0: its weight is 0 and T_j = T exactly (1/(1 - 0) = 1)
-        const float2 a_eff = sel2(al.in0, al.in1, al.alpha);
-        const float2 om = one_minus(a_eff);
+        const float2 s_eff = sel2(al.in0, al.in1, al.s);
+        const float2 om = one_minus_alpha(s_eff);
+        const float2 a_eff = __fmul2_rn(make_float2(kAlphaMax, kAlphaMax), s_eff);
         // 1 / (1 - alpha) with alpha <= 0.99: the hardware reciprocal
         const float2 inv = make_float2(rcp_approx(om.x), rcp_approx(om.y));
         const float2 Tj = __fmul2_rn(T[q], inv);
@@ -240,12 +241,12 @@ __global__ void __launch_bounds__(TW* TH / PX, 16) k_render_bwd(BwdBlendArgs a) 
         const float2 cG = __ffma2_rn(lo2(r.rg), Gr[q], __ffma2_rn(hi2(r.rg), Gg[q], __fmul2_rn(lo2(r.bc), Gb[q])));
         const float2 X = __fmul2_rn(SG[q], inv);
         const float2 dLda = __ffma2_rn(Tj, cG, make_float2(-X.x, -X.y));
-        const float2 dl = sel2(al.in0 && al.raw.x < kAlphaMax, al.in1 && al.raw.y < kAlphaMax, dLda);
+        const float2 dl = sel2(al.in0 && al.s.x < 1.f, al.in1 && al.s.y < 1.f, dLda);
         acc_r = __ffma2_rn(w, Gr[q], acc_r);
         acc_g = __ffma2_rn(w, Gg[q], acc_g);
         acc_b = __ffma2_rn(w, Gb[q], acc_b);
         acc_o = __ffma2_rn(dl, al.ex, acc_o);
-        const float2 qp = __fmul2_rn(dl, al.alpha);   // d alpha / d power = alpha
+        const float2 qp = __fmul2_rn(dl, a_eff);   // d alpha / d power = alpha (dl = 0 off the support)
         const float2 qy = __fmul2_rn(qp, dy[q]);
         acc_q = __fadd2_rn(acc_q, qp);
         acc_qy = __fadd2_rn(acc_qy, qy);
