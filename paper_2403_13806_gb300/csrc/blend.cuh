@@ -60,7 +60,8 @@ __device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x,
 __device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
 
 // 2^x by the hardware approximation (ex2.approx.ftz: relative error below 2^-22 for the
-// arguments used here, x in [-8.1, 0], whose results are normal numbers).
+// arguments whose result decides anything here, x in [-8.1, 0] up to rounding, where the
+// results are normal numbers; far below that the result flushes to 0).
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -118,26 +119,33 @@ __device__ __forceinline__ float mul_sat(float x, float y) {
 }
 
 // Per-pixel outcome of the blend rule's tests on one record.
+//
+// The rule skips pairs with power > 0 or alpha < 1/255.  Sigma' is positive definite (the
+// 2D covariance plus eps I), so power <= 0 holds exactly; a positive FP32 p2 is a rounding
+// artefact of a power near 0 (at the centre, or along the long axis of a needle-thin
+// Gaussian, where the rounding of the three terms exceeds the true value) and is composited
+// at its rounded value, which lies closer to the exact alpha than skipping the pair would.
+// The test reduces to alpha >= 1/255.
 struct PairAlpha {
-  float2 ex;      // 2^min(p2, 0)
+  float2 ex;      // min(2^p2, 1) (CLAMP) or 2^p2
   float2 s;       // sat(o' 2^p2) = alpha / 0.99; s = 1 exactly where the 0.99 clamp is active
-  bool in0, in1;  // p2 <= 0 and alpha >= 1/255
+  bool in0, in1;  // alpha >= 1/255
 };
 
-// CLAMP: evaluate 2^min(p2, 0) so that ex stays finite for every pair (the backward multiplies
-// it); the forward only uses s, where the saturation already bounds a large 2^p2, and the
-// decision (p2 <= 0 and alpha >= 1/255) is the same either way.
+// CLAMP: keep ex finite for every pair, NaN (gated) p2 included (the backward multiplies it;
+// min(NaN, 1) = 1); the forward only uses s, where sat() already maps a large or NaN product
+// to 1 or 0.  Both passes take s from the unclamped 2^p2, so they make the same decisions.
 template <bool CLAMP = true>
 __device__ __forceinline__ PairAlpha pair_alpha(const BlendRec& r, float2 p2) {
   PairAlpha a;
-  a.ex = CLAMP ? make_float2(ex2_approx(fminf(p2.x, 0.f)), ex2_approx(fminf(p2.y, 0.f)))
-               : make_float2(ex2_approx(p2.x), ex2_approx(p2.y));
-  a.s = make_float2(mul_sat(r.co.z, a.ex.x), mul_sat(r.co.w, a.ex.y));
+  const float2 e = make_float2(ex2_approx(p2.x), ex2_approx(p2.y));
+  a.ex = CLAMP ? make_float2(fminf(e.x, 1.f), fminf(e.y, 1.f)) : e;
+  a.s = make_float2(mul_sat(r.co.z, e.x), mul_sat(r.co.w, e.y));
   // alpha >= 1/255 implies p2 >= cut (the cut's 1e-3 margin exceeds the rounding of
   // 2^p2, o' 2^p2 and the cut itself), so the exact test needs no cut comparison; the cut
   // only serves the warp-level pre-test of the kernels
-  a.in0 = p2.x <= 0.f && a.s.x >= kSMin;
-  a.in1 = p2.y <= 0.f && a.s.y >= kSMin;
+  a.in0 = a.s.x >= kSMin;
+  a.in1 = a.s.y >= kSMin;
   return a;
 }
 
