@@ -367,7 +367,7 @@ def run_ours(args):
                         "and backward per view, one prune filter per step"}
 
     # end to end through the public API: host parameters and targets in pinned memory
-    e2e = e2e_run(api, N, torch, scene, vbs, cfg, targets, cap, reps=max(3, min(args.steps, 5)), dev=dev, world=world,
+    e2e = e2e_run(api, N, torch, scene, vbs, cfg, targets, cap, reps=max(3, args.steps), dev=dev, world=world,
                   loss_fn=loss_fn)
 
     # roofline of the dominant kernel
