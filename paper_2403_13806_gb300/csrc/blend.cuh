@@ -149,6 +149,19 @@ __device__ __forceinline__ PairAlpha pair_alpha(const BlendRec& r, float2 p2) {
   return a;
 }
 
+// The test s >= kSMin as an exact factor 1 or 0 on the FMA pipe: sat(s 2^31 + (1 - kSMin 2^31)).
+// kSMin lies in [2^-8, 2^-7), where floats are spaced 2^-31, so kSMin 2^31 is an integer below
+// 2^24 (the constant is exact) and every s < kSMin is at most kSMin - 2^-31 (smaller s are
+// below 2^-8, further still): the fused product-sum is <= 0 exactly when s < kSMin and >= 1
+// otherwise, which rounding preserves.  s is never NaN (it comes from sat()).
+constexpr float kInC = 1.0f - kSMin * 0x1p31f;
+static_assert(kSMin >= 0x1p-8f && kSMin < 0x1p-7f, "spacing of floats near kSMin");
+__device__ __forceinline__ float in_factor(float s) {
+  float r;
+  asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(s), "f"(0x1p31f), "f"(kInC));
+  return r;
+}
+
 // 1 - alpha = 1 - 0.99 s on both lanes (one rounding); the forward and backward passes both
 // form it this way, so the backward divides by the forward's factors exactly.
 __device__ __forceinline__ float2 one_minus_alpha(float2 s) {

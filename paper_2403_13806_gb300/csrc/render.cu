@@ -120,7 +120,8 @@ __global__ void __launch_bounds__(TW* TH / PX) k_render(RenderArgs a) {
 #pragma unroll
       for (int q = 0; q < NP; ++q) {
         const PairAlpha al = pair_alpha<false>(r, p2[q]);
-        s_in[q] = make_float2(al.in0 ? al.s.x : 0.f, al.in1 ? al.s.y : 0.f);
+        // s where alpha >= 1/255, else 0 (the same decision as al.in0, al.in1, taken on the FMA pipe)
+        s_in[q] = __fmul2_rn(al.s, make_float2(in_factor(al.s.x), in_factor(al.s.y)));
         Tn[q] = __fmul2_rn(T[q], one_minus_alpha(s_in[q]));
         stop = stop || Tn[q].x < kTMin || Tn[q].y < kTMin;
       }
