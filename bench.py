@@ -974,11 +974,11 @@ def e2e_run(api, N, torch, scene, vbs, cfg, targets, cap, reps, dev, world=1, lo
 FP32_OPS_PER_PAIR = {"k_render_importance": 16, "k_render": 15, "k_render_bwd": 40}
 EX2_PER_PAIR = 1
 # The FP32 operations the kernels as written execute per pair (counted from their source:
-# forward 20 = offsets 1.5, quadratic form 3.5 (its column terms shared by a thread's four
-# pixels), warp pre-test 0.75, power test 1, exp2 and saturated scale 2, alpha test and
-# select 2, transmittance and stop test 3, weight 1, colour 3, last-entry test and select 2,
+# forward 18 = offsets 1.25, quadratic form 2.75 (its column terms shared by a thread's
+# eight pixels), warp pre-test 0.6, exp2 and saturated scale 2, alpha factor and product 2,
+# transmittance and stop test 3, weight 1, colour 3, last-entry test and select 2,
 # importance max 0.5; backward 43), reported beside the algorithmic figure.
-INSTR_OPS_PER_PAIR = {"k_render_importance": 20, "k_render": 20, "k_render_bwd": 43}
+INSTR_OPS_PER_PAIR = {"k_render_importance": 18, "k_render": 18, "k_render_bwd": 43}
 L2_BYTES = 126 * 2 ** 20     # the working set below which a kernel's bytes stay in L2
 
 # Probe kernels (rs_peak_probe): name, kind, iterations per launch (about 1-3 ms each).

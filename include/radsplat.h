@@ -126,10 +126,10 @@ typedef struct rs_config {
   float near_plane;      /* cull if the FP32 camera depth <= near_plane, default 0.2 */
   float bg[3];           /* background colour composited with T_final, default 0 */
   int32_t batch;         /* Gaussian records staged in shared memory per batch of the blend
-                            kernels: 0 (default: 128 in the forward, 64 in the backward) or
-                            1, 2 or 4 x 64 for 16x16 and 32x8 tiles (x 32 for 8x8); the forward
-                            runs 64 threads per tile (32 for 8x8), the backward one warp per
-                            tile; other values give RS_ERR_UNSUPPORTED */
+                            kernels: 0 (default: 64) or 32, 64 or 128 (1, 2 or 4 per thread);
+                            both blend kernels run one warp per tile (eight pixels of a column
+                            per thread, two for 8x8 tiles); other values give
+                            RS_ERR_UNSUPPORTED */
   int32_t grad_overwrite;  /* rs_render_backward: 0 (default) adds the call's parameter
                             gradients into the caller's arrays (which the caller zeroes);
                             1 writes them over the arrays (zero where the call gives none),

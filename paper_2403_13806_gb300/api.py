@@ -350,8 +350,9 @@ def image_grads(vb: ViewBatch, ws: Workspace):
 
 
 def blend_threads(tile) -> int:
-    """Threads of a blend CTA for a tile shape (four pixels per thread, two for 8x8)."""
-    return 32 if tuple(tile) == (8, 8) else tile[0] * tile[1] // 4
+    """Threads of a blend CTA for a tile shape: one warp per tile (eight pixels per thread,
+    two for 8x8), so rs_config.batch is 1, 2 or 4 x 32 for every shape."""
+    return 32
 
 
 def autotune(g: Gaussians, cams: Sequence[dict], subsets: Optional[Sequence] = None, cfg=None,

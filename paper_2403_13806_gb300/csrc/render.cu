@@ -1,10 +1,10 @@
 // rs_render / rs_importance: per-tile front-to-back compositing, Eq. (render-gs), with the
 // importance max of Eq. (importance-score) fused in.
 //
-// One CTA per (view, tile); each thread owns PX vertically adjacent pixels of one column
-// (PX = 4, or 2 for 8x8 tiles), evaluated as PX/2 pixel pairs with packed two-lane FP32
-// instructions, so every Gaussian record read from shared memory serves PX pixel
-// evaluations.  The tile's sorted list is consumed in batches of NBM records per thread
+// One warp per (view, tile); each thread owns PX vertically adjacent pixels of one column
+// (PX = 8 for 16x16 and 32x8 tiles, 2 for 8x8), evaluated as PX/2 pixel pairs with packed
+// two-lane FP32 instructions, so every Gaussian record read from shared memory serves PX
+// pixel evaluations and each thread carries PX/2 independent chains through a record.  The tile's sorted list is consumed in batches of NBM records per thread
 // (rs_config.batch = NBM x threads with NBM one of 1, 2, 4; the autotuner picks it),
 // staged into shared memory in blend-ready form (conic pre-scaled to the log2 domain); the
 // per-pixel decisions are predicated, not branched.  A warp skips a record that none of
@@ -236,9 +236,9 @@ rs_status render_dispatch(const rs_projected* proj, const rs_bins* bins, const r
   const bool imp = importance != nullptr;
   rs_status st = RS_ERR_UNSUPPORTED;
   if (batch->tile_w == 16 && batch->tile_h == 16)
-    st = launch_render_nb<16, 16, 4>(a, batch->n_tiles, imp, cfg->batch, s);
+    st = launch_render_nb<16, 16, 8>(a, batch->n_tiles, imp, cfg->batch, s);
   else if (batch->tile_w == 32 && batch->tile_h == 8)
-    st = launch_render_nb<32, 8, 4>(a, batch->n_tiles, imp, cfg->batch, s);
+    st = launch_render_nb<32, 8, 8>(a, batch->n_tiles, imp, cfg->batch, s);
   else if (batch->tile_w == 8 && batch->tile_h == 8)
     st = launch_render_nb<8, 8, 2>(a, batch->n_tiles, imp, cfg->batch, s);
   if (st != RS_OK) return st;

@@ -42,16 +42,35 @@ constexpr unsigned long long kBwdClean = 0x52534277734c6e21ull;
 // Before the blend: zero the image-space gradients and flags of the items the previous call
 // on this workspace touched, or of every item if the workspace is not in that call's clean
 // state (first use, another item count, an interrupted call).
+// In the clean state a thread reads the flags of 16 consecutive items as one 16-byte word
+// (the flags start 256-byte aligned) and touches nothing more unless one is set; otherwise
+// one thread per item zeroes everything, coalesced.
 __global__ void k_bwd_prepare(Grad2D g, const unsigned long long* __restrict__ state, int64_t n) {
   const bool clean = *state == (kBwdClean ^ (unsigned long long)n);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    if (!clean || g.touched[i]) {
-      g.ga[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      g.gb[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      g.gc[i] = 0.f;
-      g.touched[i] = 0;
-    }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  auto zero = [&](int64_t i) {
+    g.ga[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    g.gb[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    g.gc[i] = 0.f;
+    g.touched[i] = 0;
+  };
+  if (!clean) {
+    for (int64_t i = t; i < n; i += stride) zero(i);
+    return;
   }
+  const int64_t n16 = n >> 4;
+  uint4* flags = reinterpret_cast<uint4*>(g.touched);
+  for (int64_t b = t; b < n16; b += stride) {
+    const uint4 f = flags[b];
+    if ((f.x | f.y | f.z | f.w) == 0u) continue;
+    const uint32_t w[4] = {f.x, f.y, f.z, f.w};
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+      if ((w[k >> 2] >> (8 * (k & 3))) & 0xffu) zero(16 * b + k);
+  }
+  for (int64_t i = 16 * n16 + t; i < n; i += stride)
+    if (g.touched[i]) zero(i);
 }
 
 struct BwdBlendArgs {
@@ -705,7 +724,8 @@ extern "C" rs_status rs_render_backward(const rs_gaussians* g, const rs_view_bat
   const Grad2D g2{w.ga, w.gb, w.gc, w.touched};
   {
     prof::Scope ps("k_bwd_prepare", s);
-    const int64_t pg = (batch->n_items + 255) / 256;
+    // (the clean path covers 16 items per thread; a grid of a few waves strides over the rest)
+    const int64_t pg = (batch->n_items / 16 + 255) / 256 + 1;
     k_bwd_prepare<<<(unsigned)(pg < 8 * kNumSMs ? pg : 8 * kNumSMs), 256, 0, s>>>(g2, w.state, batch->n_items);
   }
 

@@ -60,8 +60,9 @@ inline bool aligned(const void* p, size_t a) {
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Threads of a blend CTA: four pixels of a column per thread (two for 8x8 tiles).
-inline int blend_threads(int tile_w, int tile_h) { return (tile_w == 8 && tile_h == 8) ? 32 : tile_w * tile_h / 4; }
+// Threads of a blend CTA: one warp per tile (eight pixels of a column per thread, two for
+// 8x8 tiles), in the forward and the backward pass alike.
+inline int blend_threads(int, int) { return 32; }
 
 // rs_config.batch (records staged per blend batch): 0 (default) or 1, 2 or 4 per thread.
 inline bool blend_batch_ok(int tile_w, int tile_h, int batch) {
