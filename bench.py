@@ -1033,9 +1033,9 @@ def probe_peaks(N, torch, dev, reps=5):
 # of the sources the kernel was built from.  A capture stays valid only while those sources
 # are unchanged; otherwise the roofline reports traffic as null.
 NCU_TRAFFIC = {
-    "k_render_bwd": {"bytes_per_view": 25188608, "files": ['render_bwd.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "119fe5a8eba1fb30",
+    "k_render_bwd": {"bytes_per_view": 25188352, "files": ['render_bwd.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "412731d5bbe40a0e",
                 "profile": "k_render_bwd_1M_1view.md"},
-    "k_render_importance": {"bytes_per_view": 4420864, "files": ['render.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "81d78b74c4917e09",
+    "k_render_importance": {"bytes_per_view": 4438016, "files": ['render.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "15c2dc3e6d519687",
                 "profile": "k_render_1M_1view.md"},
     "k_fine_scatter": {"bytes_per_view": 20112128, "files": ['binsort.cu', 'rs_common.cuh'], "sha": "4cffedcde21798e1",
                 "profile": "k_fine_scatter_1M_1view.md"},
