@@ -801,7 +801,10 @@ def plain_loop(api, N, torch, g, vb1, cfg, target, cams, reps, dev, loss_fn):
         api.bin_sort(proj, vb, bins, r.ws_sort, st, front=FRONT)
         img, T, L = api.render(proj, bins, vb, r.cfg, importance=h)
         l, dl = loss_fn(img, tg[i])
-        api.render_backward(g, vb, proj, bins, T, L, dl, grads, r.ws_bwd, r.cfg)
+        # a step's first view writes the gradients and the others add theirs, as in the
+        # batched step
+        api.render_backward(g, vb, proj, bins, T, L, dl, grads, r.ws_bwd,
+                            overwrite_cfg(N, r.cfg) if i == 0 else r.cfg)
         if i == V - 1:
             api.filter(h, 0.01, N.RS_PRUNE_BELOW, ws_f)
 

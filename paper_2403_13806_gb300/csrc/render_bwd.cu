@@ -574,14 +574,38 @@ __global__ void __launch_bounds__(kProjBwdThreads) k_project_bwd_dense(BwdProjAr
     return;
   }
   if (!touched) return;
-  for (int c = 0; c < 3; ++c) {
-    a.out.means[c * N + gid] += pg.m[c];
-    a.out.log_scales[c * N + gid] += pg.ls[c];
-  }
-  for (int c = 0; c < 4; ++c) a.out.quats[c * N + gid] += pg.q[c];
-  a.out.opacity_logit[gid] += pg.lg;
+  // The old values are read a group at a time before the group's writes: the compiler cannot
+  // tell the rows' addresses apart, so a plain += per row would chain every read behind the
+  // previous write (one memory round trip per row instead of one per group).
+  {
+    float o[11];
 #pragma unroll
-  for (int k = 0; k < 3 * NC; ++k) a.out.sh[(int64_t)k * N + gid] += s_gsh[k][threadIdx.x];
+    for (int c = 0; c < 3; ++c) {
+      o[c] = a.out.means[c * N + gid];
+      o[3 + c] = a.out.log_scales[c * N + gid];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) o[6 + c] = a.out.quats[c * N + gid];
+    o[10] = a.out.opacity_logit[gid];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      a.out.means[c * N + gid] = o[c] + pg.m[c];
+      a.out.log_scales[c * N + gid] = o[3 + c] + pg.ls[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) a.out.quats[c * N + gid] = o[6 + c] + pg.q[c];
+    a.out.opacity_logit[gid] = o[10] + pg.lg;
+  }
+#pragma unroll
+  for (int k0 = 0; k0 < 3 * NC; k0 += 8) {
+    float o[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (k0 + j < 3 * NC) o[j] = a.out.sh[(int64_t)(k0 + j) * N + gid];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (k0 + j < 3 * NC) a.out.sh[(int64_t)(k0 + j) * N + gid] = o[j] + s_gsh[k0 + j][threadIdx.x];
+  }
 }
 
 // Visibility-list batches: one thread per item, atomic adds (items of one Gaussian can sit
