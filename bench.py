@@ -1036,7 +1036,7 @@ def probe_peaks(N, torch, dev, reps=5):
 # of the sources the kernel was built from.  A capture stays valid only while those sources
 # are unchanged; otherwise the roofline reports traffic as null.
 NCU_TRAFFIC = {
-    "k_render_bwd": {"bytes_per_view": 25188352, "files": ['render_bwd.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "412731d5bbe40a0e",
+    "k_render_bwd": {"bytes_per_view": 25188352, "files": ['render_bwd.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "a467508de8517e80",
                 "profile": "k_render_bwd_1M_1view.md"},
     "k_render_importance": {"bytes_per_view": 4438016, "files": ['render.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "15c2dc3e6d519687",
                 "profile": "k_render_1M_1view.md"},
