@@ -1038,7 +1038,7 @@ def probe_peaks(N, torch, dev, reps=5):
 NCU_TRAFFIC = {
     "k_render_bwd": {"bytes_per_view": 25188352, "files": ['render_bwd.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "a467508de8517e80",
                 "profile": "k_render_bwd_1M_1view.md"},
-    "k_render_importance": {"bytes_per_view": 4438016, "files": ['render.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "15c2dc3e6d519687",
+    "k_render_importance": {"bytes_per_view": 4438016, "files": ['render.cu', 'blend.cuh', 'rs_common.cuh'], "sha": "178210ccb9e97d95",
                 "profile": "k_render_1M_1view.md"},
     "k_fine_scatter": {"bytes_per_view": 20112128, "files": ['binsort.cu', 'rs_common.cuh'], "sha": "4cffedcde21798e1",
                 "profile": "k_fine_scatter_1M_1view.md"},

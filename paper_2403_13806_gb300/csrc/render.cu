@@ -4,15 +4,18 @@
 // One warp per (view, tile); each thread owns PX vertically adjacent pixels of one column
 // (PX = 8 for 16x16 and 32x8 tiles, 2 for 8x8), evaluated as PX/2 pixel pairs with packed
 // two-lane FP32 instructions, so every Gaussian record read from shared memory serves PX
-// pixel evaluations and each thread carries PX/2 independent chains through a record.  The tile's sorted list is consumed in batches of NBM records per thread
-// (rs_config.batch = NBM x threads with NBM one of 1, 2, 4; the autotuner picks it),
-// staged into shared memory in blend-ready form (conic pre-scaled to the log2 domain); the
-// per-pixel decisions are predicated, not branched.  A warp skips a record that none of
-// its pixels' alpha-support tests accept, leaves a batch once all of its pixels are done,
-// and the CTA stops fetching batches once every pixel is done (__syncthreads_count).
-// Importance: composited alpha*T values are max-reduced across the warp (redux.sync on the
-// float bits, which order like the values for non-negative floats), then across the CTA in
-// shared memory, then one global atomicMax per (tile, Gaussian).
+// pixel evaluations and each thread carries PX/2 independent chains through a record.  The
+// tile's sorted list is consumed in batches of NBM records per thread (rs_config.batch =
+// NBM x threads with NBM one of 1, 2, 4; the autotuner picks it), staged into shared memory
+// in blend-ready form (conic pre-scaled to the log2 domain, opacity divided by 0.99, colours
+// multiplied by 0.99); the per-pixel decisions are predicated or exact 0/1 factors, not
+// branches.  A warp skips a record that none of its pixels' alpha-support tests accept,
+// leaves a batch once all of its pixels are done, and the CTA stops fetching batches once
+// every pixel is done (__syncthreads_count).
+// Importance: the composited weights s T = alpha T / 0.99 are max-reduced across the warp
+// (redux.sync on the float bits, which order like the values for non-negative floats),
+// scaled by 0.99, combined across the CTA in shared memory, then one global atomicMax per
+// (tile, Gaussian).
 #include <math.h>
 
 #include "blend.cuh"
