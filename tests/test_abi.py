@@ -146,3 +146,31 @@ def test_workspace_sizes_grow_with_the_problem(native):
     assert L.rs_workspace_size(native.RS_STAGE_FILTER, ctypes.byref(b), 0) >= 4 * (10_000_000 // 4096)
     assert L.rs_workspace_size(native.RS_STAGE_BACKWARD, ctypes.byref(b), 0) >= 36 * 10_000_000
     assert L.rs_workspace_size(native.RS_STAGE_PROJECT, ctypes.byref(b), 0) == 0
+
+
+def test_staging_batch_values(native):
+    """rs_config.batch: 0, or 1, 2 or 4 records per thread of the one-warp blend CTA (32, 64,
+    128) for every tile shape; other values are rejected before anything is launched.  The
+    batch below has no tiles, so an accepted call returns at once (the host pointers are
+    only checked, never read)."""
+    L = native.lib()
+    mem = np.zeros(4096, np.float32)
+    p = mem.ctypes.data
+    assert p % 16 == 0
+    proj = native.RsProjected(p, p, p, p, p)
+    bins = native.RsBins(None, p, p, 0)
+    for tile in ((16, 16), (32, 8), (8, 8)):
+        b = native.RsViewBatch()
+        b.views = p
+        b.n_views = 1
+        b.n_tiles = 0
+        b.tile_w, b.tile_h = tile
+        for batch, ok in ((0, True), (32, True), (64, True), (128, True), (96, False), (256, False), (16, False),
+                          (-32, False)):
+            cfg = L.rs_config_default()
+            cfg.batch = batch
+            want = native.RS_OK if ok else native.RS_ERR_UNSUPPORTED
+            assert L.rs_render(ctypes.byref(proj), ctypes.byref(bins), ctypes.byref(b), ctypes.byref(cfg),
+                               None, None, None, None, 0, None) == want, (tile, batch)
+            assert L.rs_importance(ctypes.byref(proj), ctypes.byref(bins), ctypes.byref(b), ctypes.byref(cfg),
+                                   p, 1, None) == want, (tile, batch)
